@@ -1,0 +1,407 @@
+"""Benchmark of the bricked ray-cast + sort-last composite path on GB300.
+
+One step = one frame of the hot path: work-list (rendering rectangles, order, bins), the brick
+ray-cast launch and the compositing launch, for view j of a 64-view orbit about y (Fig. 7 of
+the paper sweeps the rotation angle the same way).  Default workload: the HIPASS-shaped cube,
+1720 x 1720 x 1024 float32 (12.1 GB, larger than L2, so no flush is needed between steps),
+256^3 bricks + 1 ghost voxel, 1024^2 perspective frames (60 deg), step 1 voxel, early ray
+termination at 0.99, 256-entry ramp table over [-3, 100].
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ms per 1024² frame & Gsamples/s (FP32 vs FP16 bricks); adjoint ms; p99 latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="hipass", choices=["hipass", "gass", "pr1"])
+    ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
+    ap.add_argument("--cpu-rays", type=int, default=8192)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed plumbing (replicas: every rank renders its own frames; no data-path collective)
+# ---------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        load = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(name: str):
+    """dram bytes per launch from a committed ncu summary, if the kernel source is unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(name)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1008_0135_gb300", "csrc", "vr_raycast.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def make_cube(cfg_name: str, device: str):
+    if cfg_name == "hipass":
+        return synth.hipass_cube(device=device), synth.HIPASS
+    if cfg_name == "gass":
+        return synth.gass_cube(device=device), synth.GASS
+    import torch
+    return torch.from_numpy(synth.pr1_cube(seed=0)).to(device), dict(synth.PR1, n_views=64,
+                                                                       fov_deg=60.0, eye_factor=1.5)
+
+
+def cameras(cfg, n):
+    return [synth.orbit_camera(cfg, j) for j in range(n)]
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def timed_frames(ctx, cid, cams, lut, vr, cfg, steps, warmup, dist, out, clocks=None):
+    import torch
+    ctx.set_transfer_function(lut, *vr)
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    stream = torch.cuda.current_stream()
+    for w in range(warmup):
+        ctx.set_camera_dict(cams[w % len(cams)])
+        ctx.render_frame(cid, out)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        ctx.set_camera_dict(cams[(warmup + k) % len(cams)])
+        ctx.render_frame(cid, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ctx.set_timing(False)
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    return ms, st, clk
+
+
+def roofline(st, steps, peak, src, name):
+    per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
+    ms = st["ms_raycast"] / max(st["timed_frames"], 1)
+    achieved = per_launch / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(name),
+            "peak_source": src, "kernel": name, "algorithmic_bytes_per_launch": int(per_launch),
+            "launch_ms": round(ms, 4)}
+
+
+def adjoint_leg(ctx, device):
+    """Differentiation workload: 256^3 cube, 8 views at 512^2, L2 loss vs a target rendered with
+    a shifted ramp; timed forward (8 frames) and backward (8 adjoint passes)."""
+    import torch
+    cfg = synth.DIFF
+    cube = torch.from_numpy(synth.diff_cube(seed=cfg["seed"])).to(device)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+    lut = synth.ramp_lut()
+    target_lut = synth.shifted_ramp_lut()
+    c = np.array(cfg["shape"], np.float64) / 2
+    cams = []
+    for j in range(cfg["n_views"]):
+        view = synth.orbit_view(45.0 * j, c, 1.5 * 0.5 * math.sqrt(3) * cfg["shape"][0])
+        cams.append(dict(view=view, proj=1, param=math.radians(60.0), W=cfg["W"], H=cfg["H"]))
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    targets = []
+    ctx.set_transfer_function(target_lut, *cfg["vrange"])
+    for cam in cams:
+        ctx.set_camera_dict(cam)
+        targets.append(ctx.render_frame(cid).clone())
+    ctx.set_transfer_function(lut, *cfg["vrange"])
+    glut = torch.zeros((256, 4), device=device)
+    gvox = torch.zeros_like(cube)
+    acc = torch.zeros_like(glut)
+
+    def step():
+        acc.zero_()
+        gvox.zero_()
+        for cam, tgt in zip(cams, targets):
+            ctx.set_camera_dict(cam)
+            img = ctx.render_frame(cid)
+            g = 2.0 * (img - tgt)
+            ctx.render_backward(cid, g.contiguous(), glut, gvox)
+            acc.add_(glut)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.free_cube(cid)
+    return {"workload": "256^3, 8 views x 512^2, L2 loss, grads w.r.t. 256x4 table and voxels",
+            "ms_per_batch_fwd_bwd": round(ms, 3), "ms_per_view_fwd_bwd": round(ms / len(cams), 3)}
+
+
+def cpu_baseline(cube_np, cfg, lut, vr, n_rays):
+    import oracle
+    cam = synth.orbit_camera(cfg, 0)
+    pix = synth.sample_pixels(cfg["seed"], cam["W"], cam["H"], n_rays)
+    t0 = time.perf_counter()
+    _, _, ns = oracle.render(cube_np, lut, vr, cam, step=cfg["step"], tau=cfg["tau"],
+                             brick=cfg["brick"], pix=pix)
+    dt = time.perf_counter() - t0
+    return {"value": round(ns / dt / 1e9, 6), "unit": "Gsamples/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(pix)} seeded pixels of orbit view 0 ({ns} samples, {dt:.1f} s)"}
+
+
+def run_ours(args, dist):
+    import torch
+    import paper_1008_0135_gb300 as P
+    P.build()
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    cube, cfg = make_cube(args.config, device)
+    nz, ny, nx = cube.shape
+    lut = synth.ramp_lut()
+    vr = cfg["vrange"]
+    cams = cameras(cfg, cfg.get("n_views", 64))
+    W, H = cfg["W"], cfg["H"]
+    ctx = P.Context(dev)
+    cid = ctx.load_cube(cube)
+    cube_np = None
+    if dist.rank == 0 and not args.no_extras:
+        cube_np = cube.cpu().numpy()
+    del cube
+    torch.cuda.empty_cache()
+    ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+    out = torch.empty((H, W, 4), dtype=torch.float32, device=device)
+    peak, psrc = peaks()
+    clocks = Clocks(dev)
+    ms, st, clk = timed_frames(ctx, cid, cams, lut, vr, cfg, args.steps, args.warmup, dist, out,
+                               clocks)
+    t_max = dist.max(ms)
+    samples_all = dist.sum(st["samples"])
+    value = samples_all / (t_max * 1e-3) / 1e9
+    rl = roofline(st, args.steps, peak, psrc, "k_raycast<f32,DVR>")
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gsamples/s", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded stand-in for the HIPASS cube; no dataset available)",
+        "config": {"workload": cfg["name"] + f", {W}x{H} perspective 64-view orbit, step "
+                   f"{cfg['step']}, 256^3 bricks + ghost 1, FP32 bricks, ERT 0.99",
+                   "cube_xyz": [nx, ny, nz], "frame": [W, H], "bricks": list(cfg["brick"]),
+                   "l2": "inputs larger than L2 (12.1 GB cube); no flush",
+                   "parallelism": f"replicas x{dist.world}"},
+        "ms_per_frame": round(t_max / args.steps, 4),
+        "samples_per_frame": st["samples"] // max(args.steps, 1),
+        "roofline": rl,
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+    }
+    if not args.no_extras:
+        ctx.set_bricking(cid, cfg["brick"], 1, "f16")
+        ms16, st16, _ = timed_frames(ctx, cid, cams, lut, vr, cfg, args.steps, args.warmup, dist,
+                                     out)
+        t16 = dist.max(ms16)
+        res["fp16_bricks"] = {
+            "value": round(dist.sum(st16["samples"]) / (t16 * 1e-3) / 1e9, 3),
+            "unit": "Gsamples/s", "ms_per_frame": round(t16 / args.steps, 4),
+            "roofline": roofline(st16, args.steps, peak, psrc, "k_raycast<f16,DVR>")}
+        ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+        # end to end through the C ABI with host buffers: table + camera in, frame out
+        host_out = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+        lut_h = torch.from_numpy(lut).pin_memory()
+        ctx.reset_stats()
+        for w in range(args.warmup):
+            ctx.set_camera_dict(cams[w])
+            ctx.render_frame(cid, host_out.numpy())
+        ctx.reset_stats()
+        dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ctx.set_transfer_function(lut_h.numpy(), *vr)
+            ctx.set_camera_dict(cams[(args.warmup + k) % len(cams)])
+            ctx.render_frame(cid, host_out.numpy())
+            _ = float(host_out[H // 2, W // 2, 3])
+        e2e_s = dist.max(time.perf_counter() - t0)
+        ste = ctx.stats()
+        res["e2e"] = {"value": round(dist.sum(ste["samples"]) / e2e_s / 1e9, 3),
+                      "unit": "Gsamples/s", "h2d_bytes_per_step": 64 + lut.nbytes,
+                      "d2h_bytes_per_step": W * H * 16,
+                      "ms_per_frame": round(1e3 * e2e_s / args.steps, 4)}
+        if dist.rank == 0:
+            res["adjoint"] = adjoint_leg(ctx, device)
+            res["cpu_baseline"] = cpu_baseline(cube_np, cfg, lut, vr, args.cpu_rays)
+    ctx.close()
+    if dist.rank == 0:
+        print(json.dumps(res))
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores, a bounded sample per step
+# ---------------------------------------------------------------------------------------------
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    import torch
+    import oracle
+    oracle.build()
+    device = "cuda:0" if torch.cuda.is_available() else "cpu"
+    cube, cfg = make_cube(args.config, device)
+    cube_np = cube.cpu().numpy()
+    del cube
+    lut = synth.ramp_lut()
+    cams = cameras(cfg, cfg.get("n_views", 64))
+    rays = 2048
+    total, t_all = 0, 0.0
+    for k in range(args.warmup + args.steps):
+        cam = cams[k % len(cams)]
+        pix = synth.sample_pixels(cfg["seed"] + k, cam["W"], cam["H"], rays)
+        t0 = time.perf_counter()
+        _, _, ns = oracle.render(cube_np, lut, cfg["vrange"], cam, step=cfg["step"],
+                                 tau=cfg["tau"], brick=cfg["brick"], pix=pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            total += ns
+            t_all += dt
+    value = total / t_all / 1e9
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gsamples/s",
+           "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * t_all / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded stand-in for the HIPASS cube)",
+           "config": {"workload": cfg["name"] + f" {cfg['W']}x{cfg['H']} orbit; per step "
+                      f"{rays} seeded pixels of one view (FP64 CPU oracle)"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "Gsamples/s",
+                            "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"{rays} pixels per step, {args.steps} steps"},
+           "e2e": {"value": round(value, 6), "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+    else:
+        run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    main()

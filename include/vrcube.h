@@ -1,0 +1,214 @@
+/*
+ * vrcube.h -- C ABI of libvrcube.so: bricked direct-volume ray casting of a scalar 3D cube on
+ * one GB300 GPU (sm_103a), with depth-ordered (sort-last) compositing of the per-brick
+ * sub-images into one frame.
+ *
+ * Method: Hassan, Fluke & Barnes, "Interactive Visualization of the Largest Radioastronomy
+ * Cubes" (arXiv:1008.0135).  The calls follow the paper's statement of the rendering problem:
+ * Section 2.3 (load a cube or a sub-cube, optional min/max recomputation, colour map sent by the
+ * viewer, render requests carrying the transformation and projection matrices), Section 2.4
+ * (each part is ray-cast inside its rendering rectangle; ray/box test; early ray termination;
+ * MIP output), Section 2.5 (sub-images composited with the associative "over" operator).
+ *
+ * Conventions shared by every call
+ *   - Return value: VR_OK (0) on success, a negative VR_ERR_* status otherwise.  A failed call
+ *     leaves the context usable; vr_error_string() names the status.
+ *   - Ownership: the caller owns every buffer it passes.  The library copies voxels, tables and
+ *     camera parameters into its own storage before returning and never keeps caller pointers.
+ *   - Geometry: a cube of nx*ny*nz voxels is stored x fastest: index = x + nx*(y + ny*z).
+ *     World units are voxels; voxel (x,y,z) sits at (x+0.5, y+0.5, z+0.5), so the volume box is
+ *     [0,nx] x [0,ny] x [0,nz].  Sampling between voxel centres is trilinear, clamped to the
+ *     edge at the border.
+ *   - Images: width W, height H, row 0 at the top, pixel (col i, row j) at flat index j*W + i.
+ *     DVR output is premultiplied RGBA float32 (4 floats per pixel) over a transparent black
+ *     background; MIP output is one float32 per pixel (the maximum sampled value, vmin where
+ *     the ray has no sample).
+ *   - Streams: rendering calls are ordered on the CUDA stream passed in (NULL = the legacy
+ *     default stream).  Loading and bricking calls are synchronous with respect to the host.
+ *   - Threads: one context must not be used by two host threads at once.
+ *   - Device: every call makes the context's device current on the calling thread.
+ */
+#ifndef VRCUBE_H
+#define VRCUBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define VR_OK 0
+#define VR_ERR_ARG (-1)       /* invalid argument (sizes, ids, null pointers, ranges) */
+#define VR_ERR_OOM (-2)       /* device or pinned host allocation failed */
+#define VR_ERR_CUDA (-3)      /* a CUDA runtime call or kernel launch failed */
+#define VR_ERR_TIMEOUT (-4)   /* a bounded wait (brick copy, admission) ran out */
+#define VR_ERR_STATE (-5)     /* call out of order (no bricking / table / camera set yet) */
+#define VR_ERR_NOT_FOUND (-6) /* unknown cube id */
+#define VR_ERR_UNSUPPORTED (-7)
+
+/* element / storage types */
+#define VR_F32 0
+#define VR_F16 1
+#define VR_BF16 2
+/* buffer locations */
+#define VR_HOST 0
+#define VR_DEVICE 1
+/* projections */
+#define VR_ORTHO 0
+#define VR_PERSP 1
+/* render modes */
+#define VR_DVR 0
+#define VR_MIP 1
+
+typedef struct vr_ctx vr_ctx;
+
+/* Cumulative counters since vr_create or the last vr_reset_stats. */
+typedef struct {
+    int64_t frames;              /* vr_render_frame calls completed */
+    int64_t samples;             /* lattice samples evaluated (DVR: composited samples) */
+    int64_t fragments;           /* brick x pixel sub-image entries written */
+    int64_t bricks_drawn;        /* bricks in the frames' work-lists (not culled) */
+    int64_t bricks_sampled;      /* of those, bricks where at least one ray took a sample */
+    int64_t brick_bytes_sampled; /* stored bytes (voxels incl. ghost) of the sampled bricks */
+    double ms_raycast;           /* device time of the ray-cast kernels (timing enabled) */
+    double ms_composite;         /* device time of the compositing kernels (timing enabled) */
+    double ms_frame;             /* device time from work-list upload to composite end */
+    int64_t timed_frames;        /* frames that carried timing events */
+    int64_t bytes_streamed;      /* host -> device brick bytes copied by the residency cache */
+    int64_t cache_hits;          /* brick lookups served from the HBM cache */
+    int64_t cache_misses;        /* brick lookups that needed a copy */
+} vr_stats;
+
+/* Creates a context on CUDA device `device`.  cache_bytes bounds the HBM brick cache used for
+ * cubes whose bricks are streamed from host memory (0 = no streaming cache).  *out receives
+ * the context; it is released by vr_destroy.  Errors: VR_ERR_ARG (null out, bad device),
+ * VR_ERR_CUDA, VR_ERR_OOM. */
+int vr_create(vr_ctx **out, int device, size_t cache_bytes);
+
+/* Waits for the context's outstanding work, then frees everything it owns.  NULL is a no-op. */
+void vr_destroy(vr_ctx *ctx);
+
+/* Loads a cube (Section 2.3: "the whole cube or a manually specified sub-cube").
+ * voxels: nx*ny*nz elements of `dtype` (VR_F32 only) in host (VR_HOST) or device (VR_DEVICE)
+ *   memory, x fastest.
+ * sub_origin / sub_extent: optional (both NULL or both set) voxel box [origin, origin+extent)
+ *   inside the given array; the loaded cube has the extent's dimensions.
+ * cube_id: receives the new cube's id.  The voxels are copied; the cube has no bricking yet.
+ * Errors: VR_ERR_ARG (null pointers, non-positive sizes, box outside the array, dtype),
+ *   VR_ERR_OOM, VR_ERR_CUDA. */
+int vr_load_cube(vr_ctx *ctx, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz,
+                 int where, const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id);
+
+/* Replaces the voxels of a loaded cube (same dimensions, VR_F32, host or device) and rebuilds
+ * its bricks with the current bricking.  For fitting loops that update the voxels.  The copy
+ * and the rebuild are ordered on `cuda_stream`.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND,
+ * VR_ERR_CUDA. */
+int vr_update_cube(vr_ctx *ctx, int cube_id, const void *voxels, int where, void *cuda_stream);
+
+/* Frees a cube and its bricks.  Errors: VR_ERR_NOT_FOUND. */
+int vr_free_cube(vr_ctx *ctx, int cube_id);
+
+/* Exact minimum and maximum of the cube's voxels (Section 2.3: "ask the server to recalculate
+ * the cube minimum and maximum").  Synchronous.  Errors: VR_ERR_NOT_FOUND, VR_ERR_CUDA. */
+int vr_compute_minmax(vr_ctx *ctx, int cube_id, float *vmin, float *vmax);
+
+/* Splits the cube into a regular grid of bricks of core size bx*by*bz voxels (the last brick
+ * along an axis is the remainder) and stores each with `ghost` voxels copied from its
+ * neighbours on every side (replicated at the cube border), so the trilinear stencil of every
+ * sample a brick owns lies inside that brick (Section 2.2: object-space partitioning; each
+ * part is rendered on its own).  storage: VR_F32, VR_F16 or VR_BF16.  16-bit storage keeps,
+ * per brick, a power-of-two scale 2^e with e chosen from the brick's stored max |v| (FP16:
+ * max|v| 2^-e <= 2^14; BF16: <= 1), the codes being round-to-nearest-even of v 2^-e.
+ * Synchronous.  Errors: VR_ERR_ARG (sizes < 1, ghost != 1, storage), VR_ERR_NOT_FOUND,
+ * VR_ERR_OOM, VR_ERR_CUDA. */
+int vr_set_bricking(vr_ctx *ctx, int cube_id, int bx, int by, int bz, int ghost, int storage);
+
+/* Transfer function (Section 2: value -> colour and opacity; Section 2.3: colour map sent by
+ * the viewer).  rgba: n x 4 float32 non-premultiplied entries, 2 <= n <= 4096, host memory.
+ * A value v maps to u = clamp((v - vmin)/(vmax - vmin), 0, 1), x = u (n-1), and the colour is
+ * linear between entries floor(x) and floor(x)+1.  Requires vmax > vmin.  Errors: VR_ERR_ARG. */
+int vr_set_transfer_function(vr_ctx *ctx, const float *rgba, int n, float vmin, float vmax);
+
+/* Camera (Section 2.3: "transformation and projection matrices").
+ * view: 4x4 row-major world -> eye matrix [R | t] (eye looks down -z, x right, y up).
+ * proj: VR_ORTHO (param = image height in world units) or VR_PERSP (param = vertical field of
+ * view in radians, 0 < param < pi).  width, height: frame size in pixels (1..16384).
+ * The ray of pixel (i, j) goes through the image-plane point of the pixel centre; orthographic
+ * rays start on the plane z_eye = 0, perspective rays at the eye.  Only t >= 0 is sampled.
+ * Errors: VR_ERR_ARG. */
+int vr_set_camera(vr_ctx *ctx, const float view[16], int proj, float param, int width,
+                  int height);
+
+/* Render parameters.  mode: VR_DVR or VR_MIP.  step: lattice spacing along the ray in world
+ * units (samples at t = k*step, k integer, measured from the ray origin; Section 3 uses a step
+ * that samples every voxel a ray crosses at least once).  ert_threshold tau: early ray
+ * termination (Section 2.4) stops a brick's segment of a ray once its accumulated opacity
+ * reaches tau (test: transmittance <= 1 - tau after compositing a sample); tau >= 1 disables
+ * it.  Errors: VR_ERR_ARG (mode, step <= 0, tau <= 0). */
+int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold);
+
+/* Renders one frame of cube `cube_id` with the current table, camera and parameters.
+ * out: W*H*4 floats (DVR) or W*H floats (MIP) in host (VR_HOST) or device (VR_DEVICE) memory.
+ * With VR_DEVICE the call returns once the work is queued on `cuda_stream`; with VR_HOST it
+ * returns after the frame has been copied into `out`.
+ * Steps: per-brick rendering rectangles and culling (host), one ray-cast launch over all
+ * (brick, 16x16 pixel tile) work items writing one premultiplied fragment per brick and pixel,
+ * one compositing launch blending each pixel's fragments front to back (Section 2.5).
+ * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE (no bricking, table or camera),
+ * VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT (streamed bricks did not arrive in time). */
+int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *cuda_stream);
+
+/* Gradient of a scalar image loss L with respect to the transfer-function table and the
+ * voxels, for the current camera, table and parameters (DVR only, VR_F32 bricks).
+ * grad_out: W*H*4 floats dL/d(output RGBA), device memory.
+ * grad_lut: n*4 floats, device memory, overwritten with dL/d(table).
+ * grad_voxels: nx*ny*nz floats, device memory, dL/d(voxel) ADDED to its contents (NULL: skip).
+ * The forward fragments are recomputed; each ray segment is then replayed front to back from
+ * its stored final colour and transmittance (no per-sample state is kept).  The early
+ * termination stops of the forward pass are held fixed.  Ordered on `cuda_stream`.
+ * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_UNSUPPORTED (MIP or 16-bit
+ * bricks), VR_ERR_OOM, VR_ERR_CUDA. */
+int vr_render_backward(vr_ctx *ctx, int cube_id, const float *grad_out, float *grad_lut,
+                       float *grad_voxels, void *cuda_stream);
+
+/* Enables (1) or disables (0) device timing of every frame's phases (CUDA events on the frame's
+ * stream, read by vr_get_stats).  Errors: VR_ERR_ARG. */
+int vr_set_timing(vr_ctx *ctx, int enable);
+
+/* Debug switch: full_rect = 1 launches every brick over the whole frame instead of its
+ * rendering rectangle (Section 2.4 states the rectangle does not change the image; tests use
+ * this to check it).  Errors: VR_ERR_ARG. */
+int vr_set_full_rect(vr_ctx *ctx, int full_rect);
+
+/* Copies the counters (waits for the context's outstanding frames).  Errors: VR_ERR_ARG. */
+int vr_get_stats(vr_ctx *ctx, vr_stats *stats);
+
+/* Zeroes the counters.  Errors: VR_ERR_ARG. */
+int vr_reset_stats(vr_ctx *ctx);
+
+/* Brick grid of a cube: number of bricks per axis and the storage type.  Errors: VR_ERR_ARG,
+ * VR_ERR_NOT_FOUND, VR_ERR_STATE (no bricking). */
+int vr_get_brick_grid(vr_ctx *ctx, int cube_id, int64_t nbricks[3], int *storage);
+
+/* Copies brick `brick` (index cx + nbx*(cy + nby*cz)) as stored: its stored dimensions dims[3]
+ * (core + 2*ghost per axis), its global voxel origin org[3] (index of stored element (0,0,0),
+ * i.e. core origin - ghost), its scale exponent *exp2 (0 for VR_F32), and, when data != NULL,
+ * its elements (dims product x 4 bytes for VR_F32, x 2 bytes for 16-bit codes) into host
+ * memory.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_CUDA. */
+int vr_get_brick(vr_ctx *ctx, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2,
+                 void *data);
+
+/* Name of a status code (static string). */
+const char *vr_error_string(int status);
+
+/* Detail of the last failure on the calling thread (which call or CUDA error), "" if none.
+ * The string stays valid until the thread's next failing call. */
+const char *vr_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRCUBE_H */

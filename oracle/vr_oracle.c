@@ -141,7 +141,7 @@ static int box_krange(const float o[3], const float d[3], const float lo[3], con
         if (en > tin) tin = en;
         if (ex < tout) tout = ex;
     }
-    if (!(tout > tin)) return 0;
+    if (!(tout > tin) || !(tout < INFINITY)) return 0;   /* zero direction: no samples */
     *k0 = kceil(tin, step);
     *k1 = kceil(tout, step);
     return *k1 > *k0;

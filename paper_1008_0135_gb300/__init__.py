@@ -1,0 +1,210 @@
+"""Python binding of libvrcube.so: bricked volume ray casting + sort-last compositing on GB300.
+
+Argument marshalling only: every step of the rendering path runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams; numpy arrays are accepted for host data.
+There is no CPU fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import (VR_BF16, VR_DEVICE, VR_DVR, VR_F16, VR_F32, VR_HOST, VR_MIP, VR_ORTHO,
+                   VR_PERSP)
+
+__all__ = ["Context", "VrError", "build", "STORAGE", "VR_DVR", "VR_MIP", "VR_ORTHO", "VR_PERSP",
+           "VR_F32", "VR_F16", "VR_BF16", "VR_HOST", "VR_DEVICE"]
+
+STORAGE = {"f32": VR_F32, "f16": VR_F16, "bf16": VR_BF16}
+MODES = {"dvr": VR_DVR, "mip": VR_MIP}
+
+
+def build(force: bool = False) -> str:
+    from .build_ext import build as _b
+    return _b(force=force)
+
+
+class VrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = _abi.lib()
+        msg = L.vr_error_string(status).decode()
+        detail = L.vr_last_error_message().decode()
+        super().__init__(f"{where}: {msg}" + (f" [{detail}]" if detail else ""))
+        self.status = status
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise VrError(rc, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_handle(stream) -> int:
+    """CUDA stream handle: a torch.cuda.Stream, a raw handle, or torch's current stream."""
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _buffer(x):
+    """(pointer, location) of a contiguous float32 numpy array or torch tensor."""
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        loc = VR_DEVICE if x.is_cuda else VR_HOST
+        return x.data_ptr(), loc
+    a = np.asarray(x)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, VR_HOST
+
+
+class Context:
+    """One library context on one CUDA device (vr_create / vr_destroy)."""
+
+    def __init__(self, device: int = 0, cache_bytes: int = 0):
+        self._L = _abi.lib()
+        h = C.c_void_p()
+        _check(self._L.vr_create(C.byref(h), int(device), int(cache_bytes)), "vr_create")
+        self._h = h
+        self.device = device
+        self.cam = None
+        self.mode = VR_DVR
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.vr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------------------------- cubes
+    def load_cube(self, voxels, sub_origin=None, sub_extent=None) -> int:
+        """voxels: float32 [z][y][x] numpy array (host) or CUDA tensor (device)."""
+        if _is_torch(voxels):
+            import torch
+            if voxels.dtype != torch.float32:
+                raise ValueError("voxels must be float32")
+        else:
+            voxels = np.ascontiguousarray(voxels, dtype=np.float32)
+        nz, ny, nx = voxels.shape
+        ptr, loc = _buffer(voxels)
+        so = (C.c_int64 * 3)(*sub_origin) if sub_origin is not None else None
+        se = (C.c_int64 * 3)(*sub_extent) if sub_extent is not None else None
+        cid = C.c_int()
+        _check(self._L.vr_load_cube(self._h, ptr, VR_F32, nx, ny, nz, loc, so, se, C.byref(cid)),
+               "vr_load_cube")
+        return cid.value
+
+    def update_cube(self, cube_id: int, voxels, stream=None):
+        ptr, loc = _buffer(voxels)
+        sh = _stream_handle(stream) if loc == VR_DEVICE else 0
+        _check(self._L.vr_update_cube(self._h, cube_id, ptr, loc, sh), "vr_update_cube")
+
+    def free_cube(self, cube_id: int):
+        _check(self._L.vr_free_cube(self._h, cube_id), "vr_free_cube")
+
+    def compute_minmax(self, cube_id: int):
+        lo, hi = C.c_float(), C.c_float()
+        _check(self._L.vr_compute_minmax(self._h, cube_id, C.byref(lo), C.byref(hi)),
+               "vr_compute_minmax")
+        return lo.value, hi.value
+
+    def set_bricking(self, cube_id: int, brick, ghost: int = 1, storage: str = "f32"):
+        bx, by, bz = brick
+        _check(self._L.vr_set_bricking(self._h, cube_id, bx, by, bz, ghost, STORAGE[storage]),
+               "vr_set_bricking")
+
+    def brick_grid(self, cube_id: int):
+        nb = (C.c_int64 * 3)()
+        st = C.c_int()
+        _check(self._L.vr_get_brick_grid(self._h, cube_id, nb, C.byref(st)), "vr_get_brick_grid")
+        return tuple(nb), st.value
+
+    def get_brick(self, cube_id: int, brick: int, with_data: bool = True):
+        dims, org, e = (C.c_int * 3)(), (C.c_int * 3)(), C.c_int()
+        _check(self._L.vr_get_brick(self._h, cube_id, brick, dims, org, C.byref(e), None),
+               "vr_get_brick")
+        data = None
+        if with_data:
+            _, st = self.brick_grid(cube_id)
+            dt = np.float32 if st == VR_F32 else np.uint16
+            data = np.zeros((dims[2], dims[1], dims[0]), dt)
+            _check(self._L.vr_get_brick(self._h, cube_id, brick, dims, org, C.byref(e),
+                                        data.ctypes.data), "vr_get_brick")
+        return tuple(dims), tuple(org), e.value, data
+
+    # ---------------------------------------------------------------------------- rendering
+    def set_transfer_function(self, rgba, vmin: float, vmax: float):
+        lut = np.ascontiguousarray(
+            rgba.detach().cpu().numpy() if _is_torch(rgba) else rgba, dtype=np.float32)
+        _check(self._L.vr_set_transfer_function(self._h, lut.ctypes.data, lut.shape[0],
+                                                float(vmin), float(vmax)),
+               "vr_set_transfer_function")
+
+    def set_camera(self, view, proj: int, param: float, width: int, height: int):
+        v = np.ascontiguousarray(view, dtype=np.float32).reshape(16)
+        _check(self._L.vr_set_camera(self._h, v.ctypes.data, int(proj), float(param), int(width),
+                                     int(height)), "vr_set_camera")
+        self.cam = (int(width), int(height))
+
+    def set_camera_dict(self, cam: dict):
+        self.set_camera(cam["view"], cam["proj"], cam["param"], cam["W"], cam["H"])
+
+    def set_render_params(self, mode: str = "dvr", step: float = 0.5, tau: float = 0.99):
+        self.mode = MODES[mode]
+        _check(self._L.vr_set_render_params(self._h, self.mode, float(step), float(tau)),
+               "vr_set_render_params")
+
+    def set_timing(self, enable: bool):
+        _check(self._L.vr_set_timing(self._h, int(bool(enable))), "vr_set_timing")
+
+    def set_full_rect(self, enable: bool):
+        _check(self._L.vr_set_full_rect(self._h, int(bool(enable))), "vr_set_full_rect")
+
+    def render_frame(self, cube_id: int, out=None, stream=None):
+        """Renders into ``out`` (CUDA tensor or numpy array; allocated as a CUDA tensor when None).
+        DVR: (H, W, 4) premultiplied RGBA; MIP: (H, W)."""
+        if self.cam is None:
+            raise VrError(_abi.VR_ERR_STATE, "render_frame: set a camera first")
+        W, H = self.cam
+        if out is None:
+            import torch
+            shape = (H, W, 4) if self.mode == VR_DVR else (H, W)
+            out = torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}")
+        ptr, loc = _buffer(out)
+        sh = _stream_handle(stream) if (loc == VR_DEVICE or stream is not None) else 0
+        _check(self._L.vr_render_frame(self._h, cube_id, ptr, loc, sh), "vr_render_frame")
+        return out
+
+    def render_backward(self, cube_id: int, grad_out, grad_lut, grad_voxels=None, stream=None):
+        gv = grad_voxels.data_ptr() if grad_voxels is not None else None
+        _check(self._L.vr_render_backward(self._h, cube_id, grad_out.data_ptr(),
+                                          grad_lut.data_ptr(), gv, _stream_handle(stream)),
+               "vr_render_backward")
+
+    def stats(self) -> dict:
+        s = _abi.VrStats()
+        _check(self._L.vr_get_stats(self._h, C.byref(s)), "vr_get_stats")
+        return {k: getattr(s, k) for k, _ in _abi.VrStats._fields_}
+
+    def reset_stats(self):
+        _check(self._L.vr_reset_stats(self._h), "vr_reset_stats")

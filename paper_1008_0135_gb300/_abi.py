@@ -1,0 +1,67 @@
+"""ctypes declarations of libvrcube.so (include/vrcube.h).  Marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvrcube.so")
+
+VR_OK, VR_ERR_ARG, VR_ERR_OOM, VR_ERR_CUDA = 0, -1, -2, -3
+VR_ERR_TIMEOUT, VR_ERR_STATE, VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED = -4, -5, -6, -7
+VR_F32, VR_F16, VR_BF16 = 0, 1, 2
+VR_HOST, VR_DEVICE = 0, 1
+VR_ORTHO, VR_PERSP = 0, 1
+VR_DVR, VR_MIP = 0, 1
+
+
+class VrStats(C.Structure):
+    _fields_ = [
+        ("frames", C.c_int64), ("samples", C.c_int64), ("fragments", C.c_int64),
+        ("bricks_drawn", C.c_int64), ("bricks_sampled", C.c_int64),
+        ("brick_bytes_sampled", C.c_int64), ("ms_raycast", C.c_double),
+        ("ms_composite", C.c_double), ("ms_frame", C.c_double), ("timed_frames", C.c_int64),
+        ("bytes_streamed", C.c_int64), ("cache_hits", C.c_int64), ("cache_misses", C.c_int64),
+    ]
+
+
+# name -> (restype, argtypes); every entry point declared in include/vrcube.h
+P, I, I64, F, VP = C.POINTER, C.c_int, C.c_int64, C.c_float, C.c_void_p
+SIGNATURES = {
+    "vr_create": (I, [P(VP), I, C.c_size_t]),
+    "vr_destroy": (None, [VP]),
+    "vr_load_cube": (I, [VP, VP, I, I64, I64, I64, I, P(I64), P(I64), P(I)]),
+    "vr_update_cube": (I, [VP, I, VP, I, VP]),
+    "vr_free_cube": (I, [VP, I]),
+    "vr_compute_minmax": (I, [VP, I, P(F), P(F)]),
+    "vr_set_bricking": (I, [VP, I, I, I, I, I, I]),
+    "vr_set_transfer_function": (I, [VP, VP, I, F, F]),
+    "vr_set_camera": (I, [VP, VP, I, F, I, I]),
+    "vr_set_render_params": (I, [VP, I, F, F]),
+    "vr_render_frame": (I, [VP, I, VP, I, VP]),
+    "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),
+    "vr_set_timing": (I, [VP, I]),
+    "vr_set_full_rect": (I, [VP, I]),
+    "vr_get_stats": (I, [VP, P(VrStats)]),
+    "vr_reset_stats": (I, [VP]),
+    "vr_get_brick_grid": (I, [VP, I, P(I64), P(I)]),
+    "vr_get_brick": (I, [VP, I, I64, P(I), P(I), P(I), VP]),
+    "vr_error_string": (C.c_char_p, [I]),
+    "vr_last_error_message": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libvrcube.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1008_0135_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib

@@ -1,0 +1,849 @@
+// vr_api.cu -- the C ABI of libvrcube.so (include/vrcube.h): context, cubes, bricking, and the
+// per-frame host work-list (rendering rectangles, culling, front-to-back order, screen bins).
+//
+// Section 2.3 gives the call sequence (load, min/max, colour map, render requests with the
+// view matrices); Section 2.4 the rendering rectangle of each part (here: the screen bounding
+// box of each brick's projected corners); Section 2.5 the depth-ordered compositing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vr_internal.cuh"
+#include "../../include/vrcube.h"
+
+using namespace vr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+}
+int arg_fail(const char *what) {
+    g_last_error = what;
+    return VR_ERR_ARG;
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Cube {
+    int64_t n[3] = {0, 0, 0};
+    float *d_src = nullptr;           // FP32 source voxels, x fastest
+    bool bricked = false;
+    int B[3] = {0, 0, 0};
+    int ghost = 1;
+    int storage = VR_F32;
+    int64_t nb[3] = {0, 0, 0};
+    std::vector<DrawBrick> tmpl;      // one record per brick (geometry, pool offsets, exponent)
+    DrawBrick *d_tmpl = nullptr;      // device copy used by the build kernels
+    void *d_pool = nullptr;
+    size_t pool_bytes = 0;
+    unsigned int *d_bs = nullptr;     // per-brick max |v| bits, then exponents (2 per brick)
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;                   // elements
+};
+
+}  // namespace
+
+struct vr_ctx {
+    int device = 0;
+    cudaStream_t load_stream = nullptr;
+    std::map<int, Cube *> cubes;
+    int next_id = 1;
+    // transfer function (copied into every frame's upload)
+    std::vector<float4> lut;
+    float vmin = 0.0f, vmax = 1.0f;
+    bool tf_set = false;
+    // camera
+    Cam cam{};
+    bool cam_set = false;
+    // render parameters
+    int mode = VR_DVR;
+    float step = 0.5f;
+    float tau = 0.99f;
+    bool full_rect = false;
+    bool timing = false;
+    // frame scratch (reused; guarded by events)
+    char *h_stage = nullptr;
+    size_t h_cap = 0;
+    DevBuf<char> d_stage;
+    DevBuf<char> d_frags;             // bytes
+    DevBuf<float4> d_gfrag;
+    DevBuf<float> d_gpart;
+    DevBuf<float> d_out;
+    cudaEvent_t upload_done = nullptr, frame_done = nullptr;
+    bool frame_pending = false;
+    Counters *d_ctr = nullptr;
+    unsigned int *d_mm = nullptr;     // min/max scratch (2 ordered-bit words)
+    // statistics
+    int64_t frames = 0, fragments = 0, bricks_drawn = 0, timed_frames = 0;
+    double ms_raycast = 0, ms_composite = 0, ms_frame = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::vector<cudaEvent_t>> ev_pending;
+    size_t cache_bytes = 0;
+};
+
+namespace {
+
+int set_dev(vr_ctx *c) {
+    CK(cudaSetDevice(c->device));
+    return VR_OK;
+}
+
+Cube *find_cube(vr_ctx *c, int id) {
+    auto it = c->cubes.find(id);
+    return it == c->cubes.end() ? nullptr : it->second;
+}
+
+template <typename T>
+int ensure(DevBuf<T> &b, size_t n, vr_ctx *c) {
+    if (b.cap >= n && b.p) return VR_OK;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    size_t want = std::max(n, b.cap * 3 / 2);
+    if (b.p) CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+    CK(cudaMalloc(&b.p, std::max<size_t>(want, 1) * sizeof(T)));
+    b.cap = want;
+    return VR_OK;
+}
+
+int ensure_host(vr_ctx *c, size_t bytes) {
+    if (c->h_cap >= bytes && c->h_stage) return VR_OK;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    if (c->h_stage) CK(cudaFreeHost(c->h_stage));
+    c->h_stage = nullptr;
+    size_t want = std::max(bytes, c->h_cap * 3 / 2);
+    CK(cudaMallocHost(&c->h_stage, want));
+    c->h_cap = want;
+    return VR_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// per-frame work-list
+// ---------------------------------------------------------------------------------------------
+struct WorkList {
+    std::vector<DrawBrick> db;
+    std::vector<TileItem> items;
+    std::vector<int> tile_start, tile_list;
+    long long frag_px = 0;
+    // offsets inside the staged upload
+    size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, bytes = 0;
+};
+
+// World position of the perspective eye in the renderer's FP32 arithmetic (R^T (0 - t)); every
+// perspective ray starts exactly there.
+void eye_f32(const Cam &c, float o[3]) {
+    volatile float y0 = 0.0f - c.t[0], y1 = 0.0f - c.t[1], y2 = 0.0f - c.t[2];
+    for (int k = 0; k < 3; ++k) {
+        volatile float a = c.R[k] * y0;
+        volatile float b = c.R[3 + k] * y1;
+        volatile float s = a + b;
+        volatile float d = c.R[6 + k] * y2;
+        volatile float r = s + d;
+        o[k] = r;
+    }
+}
+
+void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
+    const Cam &cam = c->cam;
+    const int W = cam.W, H = cam.H;
+    const double R[9] = {cam.R[0], cam.R[1], cam.R[2], cam.R[3], cam.R[4], cam.R[5], cam.R[6], cam.R[7], cam.R[8]};
+    const double t[3] = {cam.t[0], cam.t[1], cam.t[2]};
+    // ordering reference: the perspective eye's cell, or the orthographic direction
+    int ecell[3] = {0, 0, 0};
+    int dsign[3] = {1, 1, 1};
+    if (cam.proj == VR_PERSP) {
+        float e[3];
+        eye_f32(cam, e);
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] < 0.0f) ecell[a] = -1;
+            else if (e[a] >= (float)cb->n[a]) ecell[a] = (int)cb->nb[a];
+            else ecell[a] = std::min((int)(e[a] / (float)cb->B[a]), (int)cb->nb[a] - 1);
+            // e >= lo of that cell holds: a cell index is floor(e / B) for exact integers lo
+            while (ecell[a] > 0 && ecell[a] < cb->nb[a] && (float)((int64_t)ecell[a] * cb->B[a]) > e[a]) --ecell[a];
+            while (ecell[a] + 1 < cb->nb[a] && (float)((int64_t)(ecell[a] + 1) * cb->B[a]) <= e[a]) ++ecell[a];
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) dsign[a] = (-cam.R[6 + a] >= 0.0f) ? 1 : -1;   // d = -R row 2
+    }
+    std::vector<std::pair<long long, int>> order;
+    std::vector<DrawBrick> cand;
+    cand.reserve(cb->tmpl.size());
+    for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) {
+        const DrawBrick &b = cb->tmpl[bi];
+        int x0 = 0, y0 = 0, x1 = W, y1 = H;
+        bool cull = false;
+        if (!c->full_rect) {
+            double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300;
+            int behind = 0, front = 0;
+            for (int k = 0; k < 8; ++k) {
+                double p[3] = {(k & 1) ? b.hi[0] : b.lo[0], (k & 2) ? b.hi[1] : b.lo[1], (k & 4) ? b.hi[2] : b.lo[2]};
+                double e[3];
+                for (int r = 0; r < 3; ++r) e[r] = R[3 * r] * p[0] + R[3 * r + 1] * p[1] + R[3 * r + 2] * p[2] + t[r];
+                double sx, sy;
+                if (cam.proj == VR_PERSP) {
+                    if (e[2] > -1e-6) { ++behind; continue; }
+                    ++front;
+                    sx = e[0] / (-e[2]) / cam.th_w;
+                    sy = e[1] / (-e[2]) / cam.th;
+                } else {
+                    if (e[2] > 0.0) ++behind; else ++front;
+                    sx = e[0] / cam.half_w;
+                    sy = e[1] / cam.half_h;
+                }
+                double px = (sx + 1.0) * 0.5 * W, py = (1.0 - sy) * 0.5 * H;
+                mnx = std::min(mnx, px); mxx = std::max(mxx, px);
+                mny = std::min(mny, py); mxy = std::max(mxy, py);
+            }
+            if (front == 0) {
+                cull = true;                       // entirely behind the eye / image plane
+            } else if (cam.proj == VR_PERSP && behind > 0) {
+                x0 = 0; y0 = 0; x1 = W; y1 = H;     // straddles the eye plane: whole frame
+            } else {
+                x0 = (int)std::max(0.0, std::floor(mnx) - 1.0);
+                y0 = (int)std::max(0.0, std::floor(mny) - 1.0);
+                x1 = (int)std::min((double)W, std::ceil(mxx) + 1.0);
+                y1 = (int)std::min((double)H, std::ceil(mxy) + 1.0);
+                if (x1 <= x0 || y1 <= y0) cull = true;
+            }
+        }
+        if (cull) continue;
+        DrawBrick d = b;
+        d.rect[0] = x0; d.rect[1] = y0; d.rect[2] = x1 - x0; d.rect[3] = y1 - y0;
+        d.sampled = 0;
+        int cidx[3] = {(int)(b.brick % cb->nb[0]), (int)((b.brick / cb->nb[0]) % cb->nb[1]),
+                       (int)(b.brick / (cb->nb[0] * cb->nb[1]))};
+        long long key = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (cam.proj == VR_PERSP) key += std::abs(cidx[a] - ecell[a]);
+            else key += dsign[a] > 0 ? cidx[a] : (cb->nb[a] - 1 - cidx[a]);
+        }
+        order.push_back({key, (int)cand.size()});
+        cand.push_back(d);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<long long, int> &a, const std::pair<long long, int> &b) { return a.first < b.first; });
+    wl.db.clear();
+    wl.items.clear();
+    wl.db.reserve(order.size());
+    long long frag = 0;
+    for (auto &o : order) {
+        DrawBrick d = cand[o.second];
+        d.frag_off = frag;
+        frag += (long long)d.rect[2] * d.rect[3];
+        int tw = (d.rect[2] + kTile - 1) / kTile, th = (d.rect[3] + kTile - 1) / kTile;
+        int di = (int)wl.db.size();
+        for (int ty = 0; ty < th; ++ty)
+            for (int tx = 0; tx < tw; ++tx) wl.items.push_back(TileItem{di, tx, ty});
+        wl.db.push_back(d);
+    }
+    wl.frag_px = frag;
+    // screen-tile bins in front-to-back order
+    const int ntx = (W + kTile - 1) / kTile, nty = (H + kTile - 1) / kTile;
+    wl.tile_start.assign((size_t)ntx * nty + 1, 0);
+    for (auto &d : wl.db) {
+        int tx0 = d.rect[0] / kTile, tx1 = (d.rect[0] + d.rect[2] - 1) / kTile;
+        int ty0 = d.rect[1] / kTile, ty1 = (d.rect[1] + d.rect[3] - 1) / kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) wl.tile_start[(size_t)ty * ntx + tx + 1]++;
+    }
+    for (size_t i = 1; i < wl.tile_start.size(); ++i) wl.tile_start[i] += wl.tile_start[i - 1];
+    wl.tile_list.assign(wl.tile_start.back(), 0);
+    std::vector<int> fill(wl.tile_start.begin(), wl.tile_start.end() - 1);
+    for (size_t di = 0; di < wl.db.size(); ++di) {
+        const DrawBrick &d = wl.db[di];
+        int tx0 = d.rect[0] / kTile, tx1 = (d.rect[0] + d.rect[2] - 1) / kTile;
+        int ty0 = d.rect[1] / kTile, ty1 = (d.rect[1] + d.rect[3] - 1) / kTile;
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) wl.tile_list[fill[(size_t)ty * ntx + tx]++] = (int)di;
+    }
+    // layout of the staged upload
+    size_t off = 0;
+    wl.off_lut = off; off = align_up(off + sizeof(float4) * c->lut.size(), 256);
+    wl.off_db = off; off = align_up(off + sizeof(DrawBrick) * wl.db.size(), 256);
+    wl.off_items = off; off = align_up(off + sizeof(TileItem) * wl.items.size(), 256);
+    wl.off_ts = off; off = align_up(off + sizeof(int) * wl.tile_start.size(), 256);
+    wl.off_tl = off; off = align_up(off + sizeof(int) * wl.tile_list.size(), 256);
+    wl.bytes = off;
+}
+
+FrameConsts make_consts(vr_ctx *c, Cube *cb) {
+    FrameConsts fc{};
+    fc.cam = c->cam;
+    fc.step = c->step;
+    volatile float one_minus = 1.0f - std::min(c->tau, 1.0f);
+    fc.thr = one_minus;
+    fc.vmin = c->vmin;
+    fc.inv_range = (float)(1.0 / ((double)c->vmax - (double)c->vmin));
+    fc.lutmax = (float)(c->lut.size() - 1);
+    fc.nlut = (int)c->lut.size();
+    fc.mode = c->mode;
+    fc.storage = cb->storage;
+    fc.nx = (int)cb->n[0]; fc.ny = (int)cb->n[1]; fc.nz = (int)cb->n[2];
+    return fc;
+}
+
+int timing_events(vr_ctx *c, cudaEvent_t ev[4]) {
+    for (int i = 0; i < 4; ++i) {
+        if (c->ev_pool.empty()) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            c->ev_pool.push_back(e);
+        }
+        ev[i] = c->ev_pool.back();
+        c->ev_pool.pop_back();
+    }
+    return VR_OK;
+}
+
+int collect_timing(vr_ctx *c) {
+    for (auto &ev : c->ev_pending) {
+        CK(cudaEventSynchronize(ev[3]));
+        float a = 0, b = 0, f = 0;
+        CK(cudaEventElapsedTime(&a, ev[1], ev[2]));
+        CK(cudaEventElapsedTime(&b, ev[2], ev[3]));
+        CK(cudaEventElapsedTime(&f, ev[0], ev[3]));
+        c->ms_raycast += a;
+        c->ms_composite += b;
+        c->ms_frame += f;
+        c->timed_frames++;
+        for (auto e : ev) c->ev_pool.push_back(e);
+    }
+    c->ev_pending.clear();
+    return VR_OK;
+}
+
+// Stages the work-list (table, bricks, items, bins) and uploads it on `s`.
+int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t ev0) {
+    build_worklist(c, cb, wl);
+    // the previous frame must be done with the pinned staging and the device scratch
+    if (c->frame_pending) {
+        CK(cudaEventSynchronize(c->upload_done));
+        CK(cudaStreamWaitEvent(s, c->frame_done, 0));
+    }
+    int rc;
+    if ((rc = ensure_host(c, wl.bytes)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_stage, wl.bytes, c)) != VR_OK) return rc;
+    char *h = c->h_stage;
+    std::memcpy(h + wl.off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
+    if (!wl.db.empty()) std::memcpy(h + wl.off_db, wl.db.data(), sizeof(DrawBrick) * wl.db.size());
+    if (!wl.items.empty()) std::memcpy(h + wl.off_items, wl.items.data(), sizeof(TileItem) * wl.items.size());
+    std::memcpy(h + wl.off_ts, wl.tile_start.data(), sizeof(int) * wl.tile_start.size());
+    if (!wl.tile_list.empty()) std::memcpy(h + wl.off_tl, wl.tile_list.data(), sizeof(int) * wl.tile_list.size());
+    if (ev0) CK(cudaEventRecord(ev0, s));
+    CK(cudaMemcpyAsync(c->d_stage.p, h, wl.bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->upload_done, s));
+    return VR_OK;
+}
+
+int check_ready(vr_ctx *c, Cube *cb) {
+    if (!cb->bricked) { g_last_error = "cube has no bricking"; return VR_ERR_STATE; }
+    if (!c->tf_set) { g_last_error = "no transfer function"; return VR_ERR_STATE; }
+    if (!c->cam_set) { g_last_error = "no camera"; return VR_ERR_STATE; }
+    // every lattice index k = t/step reached inside the cube must fit comfortably in an int:
+    // t <= |camera - cube centre| + half diagonal
+    const Cam &m = c->cam;
+    double eye[3], cen[3], dist2 = 0.0, diag2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        eye[k] = -((double)m.R[k] * m.t[0] + (double)m.R[3 + k] * m.t[1] + (double)m.R[6 + k] * m.t[2]);
+        cen[k] = 0.5 * (double)cb->n[k];
+        dist2 += (eye[k] - cen[k]) * (eye[k] - cen[k]);
+        diag2 += (double)cb->n[k] * cb->n[k];
+    }
+    const double tmax = std::sqrt(dist2) + std::sqrt(diag2);
+    if (tmax / (double)c->step > (double)(1 << 28) || std::sqrt(diag2) / c->step > (double)(1 << 24))
+        return arg_fail("step too small for this camera and cube (lattice index would overflow)");
+    return VR_OK;
+}
+
+int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
+    const int nbr = (int)cb->tmpl.size();
+    if (cb->storage != VR_F32) CK(cudaMemsetAsync(cb->d_bs, 0, sizeof(unsigned int) * nbr, s));
+    if (cb->storage != VR_F32)
+        CK(launch_brick_maxabs(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs, s));
+    int *d_exps = reinterpret_cast<int *>(cb->d_bs + nbr);
+    CK(launch_brick_build(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs,
+                          cb->storage, cb->d_pool, d_exps, s));
+    if (cb->storage != VR_F32) {
+        std::vector<int> e(nbr);
+        CK(cudaMemcpyAsync(e.data(), d_exps, sizeof(int) * nbr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < nbr; ++i) cb->tmpl[i].exp2 = e[i];
+    } else {
+        CK(cudaStreamSynchronize(s));
+    }
+    return VR_OK;
+}
+
+void free_cube(Cube *cb) {
+    if (cb->d_src) cudaFree(cb->d_src);
+    if (cb->d_pool) cudaFree(cb->d_pool);
+    if (cb->d_tmpl) cudaFree(cb->d_tmpl);
+    if (cb->d_bs) cudaFree(cb->d_bs);
+    delete cb;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI (the only symbols the library exports; everything else is built with hidden visibility)
+// =============================================================================================
+#pragma GCC visibility push(default)
+extern "C" {
+
+const char *vr_error_string(int status) {
+    switch (status) {
+        case VR_OK: return "VR_OK";
+        case VR_ERR_ARG: return "VR_ERR_ARG: invalid argument";
+        case VR_ERR_OOM: return "VR_ERR_OOM: out of memory";
+        case VR_ERR_CUDA: return "VR_ERR_CUDA: CUDA runtime error";
+        case VR_ERR_TIMEOUT: return "VR_ERR_TIMEOUT: bounded wait expired";
+        case VR_ERR_STATE: return "VR_ERR_STATE: call out of order";
+        case VR_ERR_NOT_FOUND: return "VR_ERR_NOT_FOUND: unknown cube id";
+        case VR_ERR_UNSUPPORTED: return "VR_ERR_UNSUPPORTED: unsupported combination";
+        default: return "unknown status";
+    }
+}
+
+const char *vr_last_error_message(void) { return g_last_error.c_str(); }
+
+int vr_create(vr_ctx **out, int device, size_t cache_bytes) {
+    if (!out) return arg_fail("null out");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return arg_fail("bad device");
+    vr_ctx *c = new (std::nothrow) vr_ctx();
+    if (!c) return VR_ERR_OOM;
+    c->device = device;
+    c->cache_bytes = cache_bytes;
+    int rc = VR_OK;
+    do {
+        if ((e = cudaSetDevice(device)) != cudaSuccess) { rc = cuda_fail(e, "cudaSetDevice"); break; }
+        if ((e = cudaStreamCreateWithFlags(&c->load_stream, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_fail(e, "stream"); break; }
+        if ((e = cudaEventCreateWithFlags(&c->upload_done, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = cudaEventCreateWithFlags(&c->frame_done, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+        if ((e = cudaMalloc(&c->d_ctr, sizeof(Counters))) != cudaSuccess) { rc = cuda_fail(e, "counters"); break; }
+        if ((e = cudaMemset(c->d_ctr, 0, sizeof(Counters))) != cudaSuccess) { rc = cuda_fail(e, "counters"); break; }
+        if ((e = cudaMalloc(&c->d_mm, sizeof(unsigned int) * 2)) != cudaSuccess) { rc = cuda_fail(e, "minmax"); break; }
+    } while (0);
+    if (rc != VR_OK) { vr_destroy(c); return rc; }
+    *out = c;
+    return VR_OK;
+}
+
+void vr_destroy(vr_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->cubes) free_cube(kv.second);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->d_stage.p) cudaFree(c->d_stage.p);
+    if (c->d_frags.p) cudaFree(c->d_frags.p);
+    if (c->d_gfrag.p) cudaFree(c->d_gfrag.p);
+    if (c->d_gpart.p) cudaFree(c->d_gpart.p);
+    if (c->d_out.p) cudaFree(c->d_out.p);
+    if (c->d_ctr) cudaFree(c->d_ctr);
+    if (c->d_mm) cudaFree(c->d_mm);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &v : c->ev_pending) for (auto e : v) cudaEventDestroy(e);
+    if (c->upload_done) cudaEventDestroy(c->upload_done);
+    if (c->frame_done) cudaEventDestroy(c->frame_done);
+    if (c->load_stream) cudaStreamDestroy(c->load_stream);
+    delete c;
+}
+
+int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz, int where,
+                 const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id) {
+    if (!c || !voxels || !cube_id) return arg_fail("null argument");
+    if (dtype != VR_F32) return arg_fail("dtype must be VR_F32");
+    if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return arg_fail("non-positive size");
+    if ((sub_origin == nullptr) != (sub_extent == nullptr)) return arg_fail("sub-cube needs origin and extent");
+    int64_t org[3] = {0, 0, 0}, ext[3] = {nx, ny, nz}, full[3] = {nx, ny, nz};
+    if (sub_origin) {
+        for (int a = 0; a < 3; ++a) {
+            org[a] = sub_origin[a];
+            ext[a] = sub_extent[a];
+            if (org[a] < 0 || ext[a] <= 0 || org[a] + ext[a] > full[a]) return arg_fail("sub-cube outside the array");
+        }
+    }
+    if (ext[0] > (1 << 30) || ext[1] > (1 << 30) || ext[2] > (1 << 30)) return arg_fail("size too large");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    Cube *cb = new (std::nothrow) Cube();
+    if (!cb) return VR_ERR_OOM;
+    for (int a = 0; a < 3; ++a) cb->n[a] = ext[a];
+    const size_t bytes = sizeof(float) * (size_t)ext[0] * ext[1] * ext[2];
+    cudaError_t e = cudaMalloc(&cb->d_src, bytes);
+    if (e != cudaSuccess) { delete cb; return cuda_fail(e, "cudaMalloc(cube)"); }
+    cudaMemcpyKind kind = where == VR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // 3D copy of the box: rows of ext[0] floats
+    cudaMemcpy3DParms p{};
+    p.srcPtr = make_cudaPitchedPtr(const_cast<void *>(voxels), sizeof(float) * nx, nx, ny);
+    p.srcPos = make_cudaPos(sizeof(float) * org[0], org[1], org[2]);
+    p.dstPtr = make_cudaPitchedPtr(cb->d_src, sizeof(float) * ext[0], ext[0], ext[1]);
+    p.extent = make_cudaExtent(sizeof(float) * ext[0], ext[1], ext[2]);
+    p.kind = kind;
+    e = cudaMemcpy3DAsync(&p, c->load_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->load_stream);
+    if (e != cudaSuccess) { free_cube(cb); return cuda_fail(e, "cudaMemcpy3D(cube)"); }
+    int id = c->next_id++;
+    c->cubes[id] = cb;
+    *cube_id = id;
+    return VR_OK;
+}
+
+int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *stream) {
+    if (!c || !voxels) return arg_fail("null argument");
+    if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = set_dev(c);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = sizeof(float) * (size_t)cb->n[0] * cb->n[1] * cb->n[2];
+    if (c->frame_pending) CK(cudaStreamWaitEvent(s, c->frame_done, 0));
+    CK(cudaMemcpyAsync(cb->d_src, voxels, bytes, where == VR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    if (cb->bricked) return build_bricks(c, cb, s);
+    CK(cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
+int vr_free_cube(vr_ctx *c, int cube_id) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    set_dev(c);
+    if (c->frame_pending) cudaEventSynchronize(c->frame_done);
+    free_cube(cb);
+    c->cubes.erase(cube_id);
+    return VR_OK;
+}
+
+int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
+    if (!c || !vmin || !vmax) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = set_dev(c);
+    if (rc) return rc;
+    unsigned int init[2] = {0xffffffffu, 0u}, res[2];
+    CK(cudaMemcpyAsync(c->d_mm, init, sizeof(init), cudaMemcpyHostToDevice, c->load_stream));
+    CK(launch_minmax(cb->d_src, (long long)cb->n[0] * cb->n[1] * cb->n[2], c->d_mm, c->load_stream));
+    CK(cudaMemcpyAsync(res, c->d_mm, sizeof(res), cudaMemcpyDeviceToHost, c->load_stream));
+    CK(cudaStreamSynchronize(c->load_stream));
+    auto dec = [](unsigned int e) {
+        unsigned int b = (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e;
+        float f;
+        std::memcpy(&f, &b, 4);
+        return f;
+    };
+    *vmin = dec(res[0]);
+    *vmax = dec(res[1]);
+    return VR_OK;
+}
+
+int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, int storage) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (bx < 1 || by < 1 || bz < 1) return arg_fail("brick size < 1");
+    if (ghost != 1) return arg_fail("ghost must be 1");
+    if (storage != VR_F32 && storage != VR_F16 && storage != VR_BF16) return arg_fail("bad storage");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    const int B[3] = {bx, by, bz};
+    int64_t nb[3];
+    for (int a = 0; a < 3; ++a) nb[a] = (cb->n[a] + B[a] - 1) / B[a];
+    const int64_t nbr = nb[0] * nb[1] * nb[2];
+    if (nbr > (1 << 24)) return arg_fail("too many bricks");
+    for (int a = 0; a < 3; ++a)
+        if ((int64_t)std::min<int64_t>(B[a], cb->n[a]) + 2 * ghost > 65536) return arg_fail("brick too large");
+    const size_t esz = storage == VR_F32 ? 4 : 2;
+    std::vector<DrawBrick> t((size_t)nbr);
+    size_t off = 0;  // elements
+    for (int64_t bi = 0; bi < nbr; ++bi) {
+        int64_t ci[3] = {bi % nb[0], (bi / nb[0]) % nb[1], bi / (nb[0] * nb[1])};
+        DrawBrick &d = t[bi];
+        std::memset(&d, 0, sizeof(d));
+        for (int a = 0; a < 3; ++a) {
+            int64_t lo = ci[a] * B[a], hi = std::min<int64_t>(lo + B[a], cb->n[a]);
+            d.lo[a] = (float)lo;
+            d.hi[a] = (float)hi;
+            d.org[a] = (int)(lo - ghost);
+            d.org_c[a] = (float)d.org[a] + 0.5f;
+            d.dim[a] = (int)(hi - lo + 2 * ghost);
+        }
+        d.brick = (int)bi;
+        d.data_off = (long long)off;
+        const size_t elems = (size_t)d.dim[0] * d.dim[1] * d.dim[2];
+        d.bytes = (long long)(elems * esz);
+        off = align_up(off + elems, 64);
+    }
+    if (cb->d_pool) { cudaFree(cb->d_pool); cb->d_pool = nullptr; }
+    if (cb->d_tmpl) { cudaFree(cb->d_tmpl); cb->d_tmpl = nullptr; }
+    cb->bricked = false;
+    CK(cudaMalloc(&cb->d_pool, std::max<size_t>(off * esz, 16)));
+    cb->pool_bytes = off * esz;
+    CK(cudaMalloc(&cb->d_tmpl, sizeof(DrawBrick) * nbr));
+    CK(cudaMemcpy(cb->d_tmpl, t.data(), sizeof(DrawBrick) * nbr, cudaMemcpyHostToDevice));
+    if (cb->d_bs) { cudaFree(cb->d_bs); cb->d_bs = nullptr; }
+    CK(cudaMalloc(&cb->d_bs, sizeof(unsigned int) * 2 * nbr));
+    cb->tmpl = std::move(t);
+    for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
+    cb->ghost = ghost;
+    cb->storage = storage;
+    if ((rc = build_bricks(c, cb, c->load_stream)) != VR_OK) return rc;
+    cb->bricked = true;
+    return VR_OK;
+}
+
+int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
+    if (!c || !rgba) return arg_fail("null argument");
+    if (n < 2 || n > kMaxLut) return arg_fail("table size must be 2..4096");
+    if (!(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax)) return arg_fail("need vmax > vmin");
+    for (int i = 0; i < 4 * n; ++i)
+        if (!std::isfinite(rgba[i])) return arg_fail("non-finite table entry");
+    c->lut.resize(n);
+    std::memcpy(c->lut.data(), rgba, sizeof(float) * 4 * n);
+    c->vmin = vmin;
+    c->vmax = vmax;
+    c->tf_set = true;
+    return VR_OK;
+}
+
+int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int width, int height) {
+    if (!c || !view) return arg_fail("null argument");
+    if (proj != VR_ORTHO && proj != VR_PERSP) return arg_fail("bad projection");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384) return arg_fail("bad frame size");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(view[i])) return arg_fail("non-finite view matrix");
+    if (!(param > 0.0f) || !std::isfinite(param)) return arg_fail("bad projection parameter");
+    if (proj == VR_PERSP && !(param < 3.14159f)) return arg_fail("fov must be < pi");
+    // the rotation part must be (close to) orthonormal: rays need a unit direction
+    double det = (double)view[0] * ((double)view[5] * view[10] - (double)view[6] * view[9]) -
+                 (double)view[1] * ((double)view[4] * view[10] - (double)view[6] * view[8]) +
+                 (double)view[2] * ((double)view[4] * view[9] - (double)view[5] * view[8]);
+    if (!(det > 0.5 && det < 2.0)) return arg_fail("view rotation is not a rotation");
+    Cam &cam = c->cam;
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) cam.R[3 * r + k] = view[4 * r + k];
+        cam.t[r] = view[4 * r + 3];
+    }
+    cam.proj = proj;
+    cam.W = width;
+    cam.H = height;
+    volatile float aspect = (float)width / (float)height;
+    volatile float hh = param * 0.5f;
+    volatile float hw = hh * aspect;
+    cam.half_h = hh;
+    cam.half_w = hw;
+    volatile float th = (float)std::tan((double)param * 0.5);
+    volatile float thw = th * aspect;
+    cam.th = th;
+    cam.th_w = thw;
+    c->cam_set = true;
+    return VR_OK;
+}
+
+int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
+    if (!c) return arg_fail("null ctx");
+    if (mode != VR_DVR && mode != VR_MIP) return arg_fail("bad mode");
+    if (!(step > 0.0f) || !std::isfinite(step)) return arg_fail("step must be > 0");
+    if (!(tau > 0.0f) || std::isnan(tau)) return arg_fail("tau must be > 0");
+    c->mode = mode;
+    c->step = step;
+    c->tau = tau;
+    return VR_OK;
+}
+
+int vr_set_timing(vr_ctx *c, int enable) {
+    if (!c) return arg_fail("null ctx");
+    c->timing = enable != 0;
+    return VR_OK;
+}
+
+int vr_set_full_rect(vr_ctx *c, int full) {
+    if (!c) return arg_fail("null ctx");
+    c->full_rect = full != 0;
+    return VR_OK;
+}
+
+int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
+    if (!c || !out) return arg_fail("null argument");
+    if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const FrameConsts fc = make_consts(c, cb);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
+    WorkList wl;
+    if ((rc = stage_frame(c, cb, wl, s, ev[0])) != VR_OK) return rc;
+    const size_t fbytes = (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
+    if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
+    const size_t opix = (size_t)fc.cam.W * fc.cam.H;
+    const size_t ofl = opix * (c->mode == VR_DVR ? 4 : 1);
+    float *dst = out;
+    const bool direct = out_where == VR_DEVICE && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    if (!direct) {
+        if ((rc = ensure(c->d_out, ofl, c)) != VR_OK) return rc;
+        dst = c->d_out.p;
+    }
+    char *d = c->d_stage.p;
+    const float4 *d_lut = reinterpret_cast<const float4 *>(d + wl.off_lut);
+    const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(d + wl.off_db);
+    const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
+    const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
+    const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
+    if (ev[1]) CK(cudaEventRecord(ev[1], s));
+    CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
+    if (ev[2]) CK(cudaEventRecord(ev[2], s));
+    CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
+    if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    if (!direct) {
+        CK(cudaMemcpyAsync(out, dst, ofl * sizeof(float),
+                           out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaEventRecord(c->frame_done, s));
+    c->frame_pending = true;
+    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    c->frames++;
+    c->fragments += wl.frag_px;
+    c->bricks_drawn += (int64_t)wl.db.size();
+    if (out_where == VR_HOST) CK(cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
+int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,
+                       void *stream) {
+    if (!c || !grad_out || !grad_lut) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if (c->mode != VR_DVR || cb->storage != VR_F32) {
+        g_last_error = "backward needs DVR mode and FP32 bricks";
+        return VR_ERR_UNSUPPORTED;
+    }
+    if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const FrameConsts fc = make_consts(c, cb);
+    WorkList wl;
+    if ((rc = stage_frame(c, cb, wl, s, nullptr)) != VR_OK) return rc;
+    const size_t nfr = (size_t)std::max<long long>(wl.frag_px, 1);
+    if ((rc = ensure(c->d_frags, nfr * sizeof(float4), c)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_gfrag, nfr, c)) != VR_OK) return rc;
+    const int nitems = (int)wl.items.size();
+    if ((rc = ensure(c->d_gpart, (size_t)std::max(nitems, 1) * 4 * fc.nlut, c)) != VR_OK) return rc;
+    char *d = c->d_stage.p;
+    const float4 *d_lut = reinterpret_cast<const float4 *>(d + wl.off_lut);
+    const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(d + wl.off_db);
+    const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
+    const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
+    const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
+    CK(launch_raycast(fc, d_lut, d_db, d_items, nitems, cb->d_pool, c->d_frags.p, c->d_ctr, s));
+    CK(launch_composite_backward(fc, d_db, d_ts, d_tl, reinterpret_cast<const float4 *>(c->d_frags.p),
+                                 reinterpret_cast<const float4 *>(grad_out), c->d_gfrag.p, s));
+    if (nitems > 0) {
+        CK(launch_adjoint(fc, d_lut, d_db, d_items, nitems, static_cast<const float *>(cb->d_pool),
+                          reinterpret_cast<const float4 *>(c->d_frags.p), c->d_gfrag.p, c->d_gpart.p,
+                          grad_voxels, s));
+        CK(launch_lut_grad_reduce(c->d_gpart.p, nitems, fc.nlut, grad_lut, s));
+    } else {
+        CK(cudaMemsetAsync(grad_lut, 0, sizeof(float) * 4 * fc.nlut, s));
+    }
+    CK(cudaEventRecord(c->frame_done, s));
+    c->frame_pending = true;
+    return VR_OK;
+}
+
+int vr_get_stats(vr_ctx *c, vr_stats *st) {
+    if (!c || !st) return arg_fail("null argument");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    if ((rc = collect_timing(c)) != VR_OK) return rc;
+    Counters h{};
+    CK(cudaMemcpy(&h, c->d_ctr, sizeof(h), cudaMemcpyDeviceToHost));
+    std::memset(st, 0, sizeof(*st));
+    st->frames = c->frames;
+    st->samples = (int64_t)h.samples;
+    st->fragments = c->fragments;
+    st->bricks_drawn = c->bricks_drawn;
+    st->bricks_sampled = (int64_t)h.bricks_sampled;
+    st->brick_bytes_sampled = (int64_t)h.brick_bytes_sampled;
+    st->ms_raycast = c->ms_raycast;
+    st->ms_composite = c->ms_composite;
+    st->ms_frame = c->ms_frame;
+    st->timed_frames = c->timed_frames;
+    return VR_OK;
+}
+
+int vr_reset_stats(vr_ctx *c) {
+    if (!c) return arg_fail("null ctx");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    if ((rc = collect_timing(c)) != VR_OK) return rc;
+    CK(cudaMemset(c->d_ctr, 0, sizeof(Counters)));
+    c->frames = c->fragments = c->bricks_drawn = c->timed_frames = 0;
+    c->ms_raycast = c->ms_composite = c->ms_frame = 0;
+    return VR_OK;
+}
+
+int vr_get_brick_grid(vr_ctx *c, int cube_id, int64_t nbricks[3], int *storage) {
+    if (!c || !nbricks || !storage) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (!cb->bricked) return VR_ERR_STATE;
+    for (int a = 0; a < 3; ++a) nbricks[a] = cb->nb[a];
+    *storage = cb->storage;
+    return VR_OK;
+}
+
+int vr_get_brick(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2, void *data) {
+    if (!c || !dims || !org || !exp2) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (!cb->bricked) return VR_ERR_STATE;
+    if (brick < 0 || brick >= (int64_t)cb->tmpl.size()) return arg_fail("brick index out of range");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    const DrawBrick &b = cb->tmpl[brick];
+    for (int a = 0; a < 3; ++a) { dims[a] = b.dim[a]; org[a] = b.org[a]; }
+    *exp2 = b.exp2;
+    if (data) {
+        const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+        CK(cudaMemcpy(data, static_cast<char *>(cb->d_pool) + b.data_off * esz, (size_t)b.bytes, cudaMemcpyDeviceToHost));
+    }
+    return VR_OK;
+}
+
+}  // extern "C"
+#pragma GCC visibility pop

@@ -1,0 +1,89 @@
+// vr_internal.cuh -- types and launchers shared by the translation units of libvrcube.so.
+// Nothing here is part of the public ABI (include/vrcube.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace vr {
+
+constexpr int kTile = 16;          // ray-cast work item: 16x16 pixels of one brick's rectangle
+constexpr int kMaxLut = 4096;      // transfer-function entries (float4 each) held in shared memory
+
+// Camera constants in the FP32 decision arithmetic (computed once per frame on the host).
+struct Cam {
+    float R[9];                    // rows of the view rotation (world -> eye)
+    float t[3];                    // view translation
+    float half_w, half_h;          // orthographic half extents of the image plane
+    float th_w, th;                // perspective: tan(fov/2) * aspect, tan(fov/2)
+    int proj, W, H;
+};
+
+struct FrameConsts {
+    Cam cam;
+    float step;                    // lattice spacing along the ray
+    float thr;                     // early-termination transmittance threshold 1 - tau (>= 0)
+    float vmin, inv_range;         // table mapping u = (v - vmin) * inv_range
+    float lutmax;                  // n - 1
+    int nlut;
+    int mode;                      // 0 DVR, 1 MIP
+    int storage;                   // 0 f32, 1 f16, 2 bf16
+    int nx, ny, nz;                // cube size
+};
+
+// One brick of the current frame's work-list (front-to-back order).
+struct DrawBrick {
+    float lo[3], hi[3];            // core box [lo, hi) in world units
+    float org_c[3];                // stored origin + 0.5: local stored coordinate = p - org_c
+    int org[3];                    // global voxel index of stored element (0,0,0)
+    int dim[3];                    // stored dimensions (core + 2 ghost)
+    int exp2;                      // power-of-two scale exponent (0 for f32)
+    int rect[4];                   // x0, y0, w, h of the rendering rectangle (pixels)
+    int brick;                     // brick index in the cube's grid
+    int sampled;                   // set by the ray-cast kernel when a ray sampled this brick
+    long long data_off;            // element offset of the stored brick in the pool
+    long long frag_off;            // fragment offset (pixels) of the brick's sub-image
+    long long bytes;               // stored bytes of the brick
+};
+
+struct TileItem {                  // one ray-cast work item
+    int db;                        // DrawBrick index
+    int tx, ty;                    // 16x16 tile inside the brick's rectangle
+};
+
+struct Counters {                  // device-side cumulative counters
+    unsigned long long samples;
+    unsigned long long brick_bytes_sampled;
+    unsigned long long bricks_sampled;
+    unsigned long long pad;
+};
+
+// ---------------------------------------------------------------------------------------------
+// launchers (return cudaError_t of the launch)
+// ---------------------------------------------------------------------------------------------
+cudaError_t launch_minmax(const float *v, long long n, unsigned int *enc_minmax,
+                          cudaStream_t s);
+cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
+                                int nbricks, unsigned int *maxbits, cudaStream_t s);
+cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
+                               int nbricks, const unsigned int *maxbits, int storage, void *pool,
+                               int *exps, cudaStream_t s);
+cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
+                           const TileItem *items, int nitems, const void *pool, void *frags,
+                           Counters *ctr, cudaStream_t s);
+cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,
+                             const int *tile_list, const void *frags, float *out, cudaStream_t s);
+cudaError_t launch_composite_backward(const FrameConsts &fc, const DrawBrick *db,
+                                      const int *tile_start, const int *tile_list,
+                                      const float4 *frags, const float4 *gout, float4 *gfrag,
+                                      cudaStream_t s);
+cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
+                           const TileItem *items, int nitems, const float *pool,
+                           const float4 *frags, const float4 *gfrag, float *glut_partial,
+                           float *gvox, cudaStream_t s);
+cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, float *glut,
+                                   cudaStream_t s);
+
+}  // namespace vr

@@ -1,0 +1,531 @@
+// vr_raycast.cu -- brick ray casting (DVR and MIP) and sort-last compositing.
+//
+// Section 2.4: every ray inside a part's rendering rectangle is tested against the part's box;
+// rays that hit are sampled between entry and exit, colours accumulated front to back, with
+// early ray termination; MIP keeps the maximum sampled value.  Section 2.5: the parts'
+// sub-images are blended with the associative "over" operator.
+//
+// Sample positions lie on the global lattice t = k*step of each ray, so which samples exist
+// does not depend on the bricking.  A brick owns the lattice indices k with
+// ceil(t_in/step) <= k < ceil(t_out/step), t_in/t_out from its core box's slab planes.  Those
+// decisions use IEEE binary32 operations in one fixed order (the __f*_rn intrinsics are never
+// contracted), identical for every brick, so neighbouring bricks split each ray's samples
+// exactly, with no sample lost or counted twice.
+#include <math.h>
+#include "vr_internal.cuh"
+
+namespace vr {
+namespace {
+
+// ----------------------------------------------------------------------------------------------
+// FP32 decision arithmetic: ray generation and slab clipping
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ray_for_pixel(const Cam &c, int i, int j, float o[3], float d[3]) {
+    float sx = __fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn((float)i, 0.5f), (float)c.W), 2.0f), 1.0f);
+    float sy = __fsub_rn(1.0f, __fmul_rn(__fdiv_rn(__fadd_rn((float)j, 0.5f), (float)c.H), 2.0f));
+    float e0, e1, e2, de0, de1, de2;
+    if (c.proj == 0) {
+        e0 = __fmul_rn(sx, c.half_w);
+        e1 = __fmul_rn(sy, c.half_h);
+        e2 = 0.0f;
+        de0 = 0.0f; de1 = 0.0f; de2 = -1.0f;
+    } else {
+        e0 = e1 = e2 = 0.0f;
+        float x = __fmul_rn(sx, c.th_w), y = __fmul_rn(sy, c.th), z = -1.0f;
+        float n2 = __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+        float len = __fsqrt_rn(n2);
+        de0 = __fdiv_rn(x, len); de1 = __fdiv_rn(y, len); de2 = __fdiv_rn(z, len);
+    }
+    float y0 = __fsub_rn(e0, c.t[0]), y1 = __fsub_rn(e1, c.t[1]), y2 = __fsub_rn(e2, c.t[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {   // world = R^T (eye - t)
+        o[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], y0), __fmul_rn(c.R[3 + k], y1)),
+                         __fmul_rn(c.R[6 + k], y2));
+        d[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], de0), __fmul_rn(c.R[3 + k], de1)),
+                         __fmul_rn(c.R[6 + k], de2));
+    }
+}
+
+// Lattice range [k0, k1) of the samples inside the half-open box [lo, hi), t >= 0.
+__device__ __forceinline__ bool box_krange(const float o[3], const float d[3], const float lo[3],
+                                           const float hi[3], float step, int &k0, int &k1) {
+    float tin = 0.0f, tout = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0f) {
+            if (!(lo[a] <= o[a] && o[a] < hi[a])) return false;
+        } else {
+            float t0 = __fdiv_rn(__fsub_rn(lo[a], o[a]), d[a]);
+            float t1 = __fdiv_rn(__fsub_rn(hi[a], o[a]), d[a]);
+            float en = t0 < t1 ? t0 : t1, ex = t0 < t1 ? t1 : t0;
+            if (en > tin) tin = en;
+            if (ex < tout) tout = ex;
+        }
+    }
+    if (!(tout > tin) || !(tout < INFINITY)) return false;   // no direction: no samples
+    k0 = (int)ceilf(__fdiv_rn(tin, step));
+    k1 = (int)ceilf(__fdiv_rn(tout, step));
+    return k1 > k0;
+}
+
+// Local stored coordinate of sample k along one axis, x = o + (k*step)*d - c, evaluated with
+// error-free transformations (two-sum, fma residuals) and rounded once, so the anchor is
+// accurate to half an ulp of a brick-local coordinate even when t is thousands of voxels.
+__device__ __forceinline__ float anchor(float o, float d, float c, int k, float step) {
+    float kf = (float)k;
+    float th = __fmul_rn(kf, step);
+    float tl = __fmaf_rn(kf, step, -th);          // k*step = th + tl exactly
+    float ph = __fmul_rn(th, d);
+    float pl = __fmaf_rn(th, d, -ph);             // th*d = ph + pl exactly
+    float s = __fsub_rn(o, c);                    // two-sum of o and -c
+    float bb = __fsub_rn(s, o);
+    float sl = __fadd_rn(__fsub_rn(o, __fsub_rn(s, bb)), __fsub_rn(-c, bb));
+    float r = __fadd_rn(s, ph);                   // two-sum of s and ph
+    float rb = __fsub_rn(r, s);
+    float rl = __fadd_rn(__fsub_rn(s, __fsub_rn(r, rb)), __fsub_rn(ph, rb));
+    float lo = __fadd_rn(__fadd_rn(rl, sl), __fadd_rn(pl, __fmul_rn(tl, d)));
+    return __fadd_rn(r, lo);
+}
+
+template <int S>
+__device__ __forceinline__ float ldv(const void *p, int i);
+template <>
+__device__ __forceinline__ float ldv<0>(const void *p, int i) { return __ldg(static_cast<const float *>(p) + i); }
+template <>
+__device__ __forceinline__ float ldv<1>(const void *p, int i) {
+    return __half2float(__ldg(static_cast<const __half *>(p) + i));
+}
+template <>
+__device__ __forceinline__ float ldv<2>(const void *p, int i) {
+    return __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(p) + i));
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float f) {
+    return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a)));
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// One DVR sample: trilinear value at local stored coordinate (x, y, z), table lookup.  Every
+// operation is an explicit intrinsic (no contraction), so the forward kernel and the adjoint's
+// replay of a ray produce bit-identical values.
+struct DvrSample {
+    int i0;                 // stored index of the lower stencil corner
+    float fx, fy, fz;       // trilinear fractions
+    float u;                // unclamped table coordinate (v - vmin) / (vmax - vmin)
+    int li;                 // table interval
+    float lf;               // fraction inside the interval
+    float4 L0, L1;          // the interval's two entries
+    float r, g, b, a;       // interpolated colour and opacity
+};
+
+template <int S>
+__device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int mx, int my, int mz,
+                                           float scale, float x, float y, float z, float vmin,
+                                           float inv_range, float lutmax, int lmax,
+                                           const float4 *s_lut, DvrSample &o) {
+    const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+    o.fx = __fsub_rn(x, flx); o.fy = __fsub_rn(y, fly); o.fz = __fsub_rn(z, flz);
+    const int ix = clampi((int)flx, 0, mx), iy = clampi((int)fly, 0, my), iz = clampi((int)flz, 0, mz);
+    const int i0 = ix + dx * iy + dxy * iz;
+    o.i0 = i0;
+    const float v000 = ldv<S>(src, i0), v100 = ldv<S>(src, i0 + 1);
+    const float v010 = ldv<S>(src, i0 + dx), v110 = ldv<S>(src, i0 + dx + 1);
+    const float v001 = ldv<S>(src, i0 + dxy), v101 = ldv<S>(src, i0 + dxy + 1);
+    const float v011 = ldv<S>(src, i0 + dxy + dx), v111 = ldv<S>(src, i0 + dxy + dx + 1);
+    const float a00 = __fmaf_rn(o.fx, __fsub_rn(v100, v000), v000);
+    const float a10 = __fmaf_rn(o.fx, __fsub_rn(v110, v010), v010);
+    const float a01 = __fmaf_rn(o.fx, __fsub_rn(v101, v001), v001);
+    const float a11 = __fmaf_rn(o.fx, __fsub_rn(v111, v011), v011);
+    const float b0 = __fmaf_rn(o.fy, __fsub_rn(a10, a00), a00);
+    const float b1 = __fmaf_rn(o.fy, __fsub_rn(a11, a01), a01);
+    float v = __fmaf_rn(o.fz, __fsub_rn(b1, b0), b0);
+    if (S != 0) v = __fmul_rn(v, scale);
+    o.u = __fmul_rn(__fsub_rn(v, vmin), inv_range);
+    const float uc = fminf(fmaxf(o.u, 0.0f), 1.0f);
+    const float xl = __fmul_rn(uc, lutmax);
+    o.li = min((int)xl, lmax);
+    o.lf = __fsub_rn(xl, (float)o.li);
+    o.L0 = s_lut[o.li];
+    o.L1 = s_lut[o.li + 1];
+    o.r = __fmaf_rn(o.lf, __fsub_rn(o.L1.x, o.L0.x), o.L0.x);
+    o.g = __fmaf_rn(o.lf, __fsub_rn(o.L1.y, o.L0.y), o.L0.y);
+    o.b = __fmaf_rn(o.lf, __fsub_rn(o.L1.z, o.L0.z), o.L0.z);
+    o.a = __fmaf_rn(o.lf, __fsub_rn(o.L1.w, o.L0.w), o.L0.w);
+}
+
+// Front-to-back "over" of one sample into (c, T): c += T a rgb, T *= 1 - a.
+__device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, float &c2, float &T) {
+    const float w = __fmul_rn(T, s.a);
+    c0 = __fmaf_rn(w, s.r, c0);
+    c1 = __fmaf_rn(w, s.g, c1);
+    c2 = __fmaf_rn(w, s.b, c2);
+    T = __fmul_rn(T, __fsub_rn(1.0f, s.a));
+}
+
+// ----------------------------------------------------------------------------------------------
+// ray cast: one CTA = 16x16 pixels of one brick's rendering rectangle; warp = 8x4 pixels
+// ----------------------------------------------------------------------------------------------
+template <int S, int MODE>
+__global__ void __launch_bounds__(256)
+k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
+          const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
+          Counters *__restrict__ ctr) {
+    extern __shared__ float4 s_lut[];
+    if (MODE == 0) {
+        for (int i = threadIdx.x; i < fc.nlut; i += blockDim.x) s_lut[i] = lut[i];
+        __syncthreads();
+    }
+    const TileItem it = items[blockIdx.x];
+    const DrawBrick &b = dbs[it.db];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rx = it.tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int ry = it.ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    const int rw = b.rect[2];
+    int nsamp = 0;
+    if (rx < rw && ry < b.rect[3]) {
+        float o[3], d[3];
+        ray_for_pixel(fc.cam, b.rect[0] + rx, b.rect[1] + ry, o, d);
+        int k0 = 0, k1 = 0;
+        const bool hit = box_krange(o, d, b.lo, b.hi, fc.step, k0, k1);
+        const long long fi = b.frag_off + (long long)ry * rw + rx;
+        const void *src = static_cast<const char *>(pool) +
+                          b.data_off * (S == 0 ? 4 : 2);
+        const int dx = b.dim[0], dxy = b.dim[0] * b.dim[1];
+        const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
+        const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
+        if (MODE == 0) {
+            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+            if (hit) {
+                const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
+                const float qy = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
+                const float qz = anchor(o[2], d[2], b.org_c[2], k0, fc.step);
+                const int n = k1 - k0;
+                const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax;
+                const int lmax = fc.nlut - 2;
+                const float thr = fc.thr;
+                int j = 0;
+                for (; j < n; ++j) {
+                    const float tj = __fmul_rn((float)j, fc.step);
+                    DvrSample sm;
+                    dvr_sample<S>(src, dx, dxy, mx, my, mz, scale, __fmaf_rn(tj, d[0], qx),
+                                  __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), vmin, inv_range,
+                                  lutmax, lmax, s_lut, sm);
+                    over(sm, c0, c1, c2, T);
+                    if (T <= thr) { ++j; break; }
+                }
+                nsamp = j;
+            }
+            static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
+        } else {
+            float m = -INFINITY;
+            if (hit) {
+                for (int k = k0; k < k1; ++k) {
+                    const float t = __fmul_rn((float)k, fc.step);
+                    const float px = __fadd_rn(o[0], __fmul_rn(t, d[0]));
+                    const float py = __fadd_rn(o[1], __fmul_rn(t, d[1]));
+                    const float pz = __fadd_rn(o[2], __fmul_rn(t, d[2]));
+                    const float x = __fsub_rn(px, 0.5f), y = __fsub_rn(py, 0.5f), z = __fsub_rn(pz, 0.5f);
+                    const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+                    const float fx = __fsub_rn(x, flx), fy = __fsub_rn(y, fly), fz = __fsub_rn(z, flz);
+                    const int ix = clampi((int)flx - b.org[0], 0, mx);
+                    const int iy = clampi((int)fly - b.org[1], 0, my);
+                    const int iz = clampi((int)flz - b.org[2], 0, mz);
+                    const int i0 = ix + dx * iy + dxy * iz;
+                    const float c00 = lerp_rn(ldv<S>(src, i0), ldv<S>(src, i0 + 1), fx);
+                    const float c10 = lerp_rn(ldv<S>(src, i0 + dx), ldv<S>(src, i0 + dx + 1), fx);
+                    const float c01 = lerp_rn(ldv<S>(src, i0 + dxy), ldv<S>(src, i0 + dxy + 1), fx);
+                    const float c11 = lerp_rn(ldv<S>(src, i0 + dxy + dx), ldv<S>(src, i0 + dxy + dx + 1), fx);
+                    float v = lerp_rn(lerp_rn(c00, c10, fy), lerp_rn(c01, c11, fy), fz);
+                    if (S != 0) v = __fmul_rn(v, scale);
+                    m = v > m ? v : m;
+                }
+                nsamp = k1 - k0;
+            }
+            static_cast<float *>(frags)[fi] = m;
+        }
+    }
+    const unsigned int tot = __reduce_add_sync(0xffffffffu, (unsigned int)nsamp);
+    if (lane == 0 && tot > 0) {
+        atomicAdd(&ctr->samples, (unsigned long long)tot);
+        if (atomicExch(&dbs[it.db].sampled, 1) == 0) {
+            atomicAdd(&ctr->bricks_sampled, 1ull);
+            atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)b.bytes);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
+// compositing: one CTA = one 16x16 screen tile; each pixel blends the fragments of the bricks
+// binned to its tile, in the work-list's front-to-back order (Section 2.5)
+// ----------------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_composite(const FrameConsts fc, const DrawBrick *__restrict__ dbs, const int *__restrict__ tile_start,
+            const int *__restrict__ tile_list, const void *__restrict__ frags, float *__restrict__ out) {
+    const int px = blockIdx.x * kTile + (threadIdx.x & 15);
+    const int py = blockIdx.y * kTile + (threadIdx.x >> 4);
+    if (px >= fc.cam.W || py >= fc.cam.H) return;
+    const int t = blockIdx.y * gridDim.x + blockIdx.x;
+    const int s0 = tile_start[t], s1 = tile_start[t + 1];
+    const long long pix = (long long)py * fc.cam.W + px;
+    if (MODE == 0) {
+        float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+        for (int e = s0; e < s1; ++e) {
+            const DrawBrick &b = dbs[tile_list[e]];
+            const int rx = px - b.rect[0], ry = py - b.rect[1];
+            if ((unsigned)rx < (unsigned)b.rect[2] && (unsigned)ry < (unsigned)b.rect[3]) {
+                const float4 f = static_cast<const float4 *>(frags)[b.frag_off + (long long)ry * b.rect[2] + rx];
+                c0 = __fmaf_rn(T, f.x, c0);
+                c1 = __fmaf_rn(T, f.y, c1);
+                c2 = __fmaf_rn(T, f.z, c2);
+                T = __fmul_rn(T, f.w);         // fragment .w holds the segment's transmittance
+            }
+        }
+        reinterpret_cast<float4 *>(out)[pix] = make_float4(c0, c1, c2, 1.0f - T);
+    } else {
+        float m = -INFINITY;
+        for (int e = s0; e < s1; ++e) {
+            const DrawBrick &b = dbs[tile_list[e]];
+            const int rx = px - b.rect[0], ry = py - b.rect[1];
+            if ((unsigned)rx < (unsigned)b.rect[2] && (unsigned)ry < (unsigned)b.rect[3]) {
+                const float f = static_cast<const float *>(frags)[b.frag_off + (long long)ry * b.rect[2] + rx];
+                m = f > m ? f : m;
+            }
+        }
+        out[pix] = (m == -INFINITY) ? fc.vmin : m;
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
+// backward pass
+// ----------------------------------------------------------------------------------------------
+// Composite backward: per pixel, fragments b = 1..B in front-to-back order with premultiplied
+// colour C_b and transmittance T_b; C = sum_b P_b C_b, P_b = prod_{b'<b} T_b', output alpha
+// A = 1 - prod_b T_b.  Then dL/dC_b = P_b gC and
+// dL/dT_b = P_b (gC . Crest_b) - gA P_b Trest_b, with Crest_b / Trest_b the composite of the
+// fragments behind b.  Pass 1 (front to back) parks P_b in gfrag.w; pass 2 (back to front)
+// accumulates Crest/Trest and writes (dL/dC_b, dL/dT_b).
+__global__ void __launch_bounds__(256)
+k_composite_backward(const FrameConsts fc, const DrawBrick *__restrict__ dbs,
+                     const int *__restrict__ tile_start, const int *__restrict__ tile_list,
+                     const float4 *__restrict__ frags, const float4 *__restrict__ gout,
+                     float4 *__restrict__ gfrag) {
+    const int px = blockIdx.x * kTile + (threadIdx.x & 15);
+    const int py = blockIdx.y * kTile + (threadIdx.x >> 4);
+    if (px >= fc.cam.W || py >= fc.cam.H) return;
+    const int t = blockIdx.y * gridDim.x + blockIdx.x;
+    const int s0 = tile_start[t], s1 = tile_start[t + 1];
+    const float4 g = gout[(long long)py * fc.cam.W + px];
+    float P = 1.0f;
+    for (int e = s0; e < s1; ++e) {
+        const DrawBrick &b = dbs[tile_list[e]];
+        const int rx = px - b.rect[0], ry = py - b.rect[1];
+        if ((unsigned)rx < (unsigned)b.rect[2] && (unsigned)ry < (unsigned)b.rect[3]) {
+            const long long fi = b.frag_off + (long long)ry * b.rect[2] + rx;
+            gfrag[fi].w = P;
+            P = __fmul_rn(P, frags[fi].w);
+        }
+    }
+    float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f, Tr = 1.0f;   // composite of the fragments behind
+    for (int e = s1 - 1; e >= s0; --e) {
+        const DrawBrick &b = dbs[tile_list[e]];
+        const int rx = px - b.rect[0], ry = py - b.rect[1];
+        if ((unsigned)rx < (unsigned)b.rect[2] && (unsigned)ry < (unsigned)b.rect[3]) {
+            const long long fi = b.frag_off + (long long)ry * b.rect[2] + rx;
+            const float Pb = gfrag[fi].w;
+            const float4 f = frags[fi];
+            const float gT = Pb * (g.x * r0 + g.y * r1 + g.z * r2 - g.w * Tr);
+            gfrag[fi] = make_float4(Pb * g.x, Pb * g.y, Pb * g.z, gT);
+            r0 = fmaf(f.w, r0, f.x);
+            r1 = fmaf(f.w, r1, f.y);
+            r2 = fmaf(f.w, r2, f.z);
+            Tr *= f.w;
+        }
+    }
+}
+
+// Adjoint ray cast (FP32 bricks).  Each (brick, pixel) segment is replayed front to back with
+// the forward's arithmetic; from the stored segment colour C_b and transmittance T_b the
+// gradient of every sample follows without per-sample storage:
+//   dL/dc_j = gC T_{j-1} a_j
+//   dL/da_j = T_{j-1} [ gC.c_j - (gC.(C_b - C_{<=j}) + gT T_b) / T_j ]   (T_j = T_{j-1}(1-a_j))
+//   last composited sample: dL/da_j = T_{j-1} [ gC.c_j - gT ]
+// Table gradients accumulate per CTA in shared memory and are written as one partial per CTA;
+// voxel gradients scatter to the cube's voxels (ghost copies map back to their source voxel).
+__global__ void __launch_bounds__(256)
+k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick *__restrict__ dbs,
+          const TileItem *__restrict__ items, const float *__restrict__ pool,
+          const float4 *__restrict__ frags, const float4 *__restrict__ gfrag,
+          float *__restrict__ glut_partial, float *__restrict__ gvox) {
+    extern __shared__ float4 s_lut[];
+    float *s_g = reinterpret_cast<float *>(s_lut + fc.nlut);
+    for (int i = threadIdx.x; i < fc.nlut; i += blockDim.x) s_lut[i] = lut[i];
+    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) s_g[i] = 0.0f;
+    __syncthreads();
+    const TileItem it = items[blockIdx.x];
+    const DrawBrick &b = dbs[it.db];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rx = it.tx * kTile + (warp & 1) * 8 + (lane & 7);
+    const int ry = it.ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    if (rx < b.rect[2] && ry < b.rect[3]) {
+        const long long fi = b.frag_off + (long long)ry * b.rect[2] + rx;
+        const float4 gf = gfrag[fi];
+        float o[3], d[3];
+        ray_for_pixel(fc.cam, b.rect[0] + rx, b.rect[1] + ry, o, d);
+        int k0 = 0, k1 = 0;
+        if ((gf.x != 0.0f || gf.y != 0.0f || gf.z != 0.0f || gf.w != 0.0f) &&
+            box_krange(o, d, b.lo, b.hi, fc.step, k0, k1)) {
+            const float4 fr = frags[fi];
+            const float *src = pool + b.data_off;
+            const int dx = b.dim[0], dy = b.dim[1], dxy = b.dim[0] * b.dim[1];
+            const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
+            const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
+            const float qy = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
+            const float qz = anchor(o[2], d[2], b.org_c[2], k0, fc.step);
+            const int n = k1 - k0;
+            const float dxdv = __fmul_rn(fc.lutmax, fc.inv_range);
+            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+            for (int j = 0; j < n; ++j) {
+                const float tj = __fmul_rn((float)j, fc.step);
+                DvrSample sm;
+                dvr_sample<0>(src, dx, dxy, mx, my, mz, 1.0f, __fmaf_rn(tj, d[0], qx),
+                              __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), fc.vmin,
+                              fc.inv_range, fc.lutmax, fc.nlut - 2, s_lut, sm);
+                const float Tb = T;
+                over(sm, c0, c1, c2, T);
+                const bool last = (T <= fc.thr) || (j == n - 1);
+                const float gcdot = gf.x * sm.r + gf.y * sm.g + gf.z * sm.b;
+                float ga;
+                if (last) {
+                    ga = Tb * (gcdot - gf.w);
+                } else {
+                    const float sdot = gf.x * (fr.x - c0) + gf.y * (fr.y - c1) + gf.z * (fr.z - c2);
+                    ga = Tb * (gcdot - (sdot + gf.w * fr.w) / T);
+                }
+                const float wa = Tb * sm.a;
+                const float gr = gf.x * wa, gg = gf.y * wa, gb = gf.z * wa;
+                float *g0 = s_g + 4 * sm.li;
+                const float w1 = sm.lf, w0 = 1.0f - sm.lf;
+                atomicAdd(g0 + 0, w0 * gr); atomicAdd(g0 + 4, w1 * gr);
+                atomicAdd(g0 + 1, w0 * gg); atomicAdd(g0 + 5, w1 * gg);
+                atomicAdd(g0 + 2, w0 * gb); atomicAdd(g0 + 6, w1 * gb);
+                atomicAdd(g0 + 3, w0 * ga); atomicAdd(g0 + 7, w1 * ga);
+                if (gvox != nullptr && sm.u > 0.0f && sm.u < 1.0f) {
+                    const float gx = gr * (sm.L1.x - sm.L0.x) + gg * (sm.L1.y - sm.L0.y) +
+                                     gb * (sm.L1.z - sm.L0.z) + ga * (sm.L1.w - sm.L0.w);
+                    const float gv = gx * dxdv;
+                    if (gv != 0.0f) {
+                        const int iz = sm.i0 / dxy, rem = sm.i0 - iz * dxy;
+                        const int iy = rem / dx, ix = rem - iy * dx;
+                        const int gx0 = clampi(b.org[0] + ix, 0, fc.nx - 1), gx1 = clampi(b.org[0] + ix + 1, 0, fc.nx - 1);
+                        const int gy0 = clampi(b.org[1] + iy, 0, fc.ny - 1), gy1 = clampi(b.org[1] + iy + 1, 0, fc.ny - 1);
+                        const int gz0 = clampi(b.org[2] + iz, 0, fc.nz - 1), gz1 = clampi(b.org[2] + iz + 1, 0, fc.nz - 1);
+                        const long long sy = fc.nx, sz = (long long)fc.nx * fc.ny;
+                        const float ux = sm.fx, uy = sm.fy, uz = sm.fz;
+                        const float vx = 1.0f - ux, vy = 1.0f - uy, vz = 1.0f - uz;
+                        atomicAdd(gvox + gz0 * sz + gy0 * sy + gx0, gv * vx * vy * vz);
+                        atomicAdd(gvox + gz0 * sz + gy0 * sy + gx1, gv * ux * vy * vz);
+                        atomicAdd(gvox + gz0 * sz + gy1 * sy + gx0, gv * vx * uy * vz);
+                        atomicAdd(gvox + gz0 * sz + gy1 * sy + gx1, gv * ux * uy * vz);
+                        atomicAdd(gvox + gz1 * sz + gy0 * sy + gx0, gv * vx * vy * uz);
+                        atomicAdd(gvox + gz1 * sz + gy0 * sy + gx1, gv * ux * vy * uz);
+                        atomicAdd(gvox + gz1 * sz + gy1 * sy + gx0, gv * vx * uy * uz);
+                        atomicAdd(gvox + gz1 * sz + gy1 * sy + gx1, gv * ux * uy * uz);
+                    }
+                }
+                if (T <= fc.thr) break;
+            }
+            (void)dy;
+        }
+    }
+    __syncthreads();
+    float *dst = glut_partial + (long long)blockIdx.x * 4 * fc.nlut;
+    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) dst[i] = s_g[i];
+}
+
+// Final reduction of the per-CTA table-gradient partials, accumulated in FP64.
+__global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts, int n,
+                                  float *__restrict__ glut) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int p = 0; p < nparts; ++p) acc += (double)partial[(long long)p * n + i];
+    glut[i] = (float)acc;
+}
+
+template <int S, int MODE>
+cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
+                      int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
+    static bool attr = false;
+    const size_t smem = MODE == 0 ? sizeof(float4) * (size_t)fc.nlut : 0;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float4) * kMaxLut));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_raycast<S, MODE><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
+                           const TileItem *items, int nitems, const void *pool, void *frags,
+                           Counters *ctr, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (fc.mode == 0) {
+        if (fc.storage == 0) return launch_rc<0, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+        if (fc.storage == 1) return launch_rc<1, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+        return launch_rc<2, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    }
+    if (fc.storage == 0) return launch_rc<0, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.storage == 1) return launch_rc<1, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    return launch_rc<2, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+}
+
+cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,
+                             const int *tile_list, const void *frags, float *out, cudaStream_t s) {
+    dim3 grid((fc.cam.W + kTile - 1) / kTile, (fc.cam.H + kTile - 1) / kTile);
+    if (fc.mode == 0)
+        k_composite<0><<<grid, 256, 0, s>>>(fc, db, tile_start, tile_list, frags, out);
+    else
+        k_composite<1><<<grid, 256, 0, s>>>(fc, db, tile_start, tile_list, frags, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_backward(const FrameConsts &fc, const DrawBrick *db,
+                                      const int *tile_start, const int *tile_list,
+                                      const float4 *frags, const float4 *gout, float4 *gfrag,
+                                      cudaStream_t s) {
+    dim3 grid((fc.cam.W + kTile - 1) / kTile, (fc.cam.H + kTile - 1) / kTile);
+    k_composite_backward<<<grid, 256, 0, s>>>(fc, db, tile_start, tile_list, frags, gout, gfrag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
+                           const TileItem *items, int nitems, const float *pool,
+                           const float4 *frags, const float4 *gfrag, float *glut_partial,
+                           float *gvox, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(32 * kMaxLut));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const size_t smem = 32 * (size_t)fc.nlut;     // table (16 B) + gradient accumulators (16 B)
+    k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, float *glut,
+                                   cudaStream_t s) {
+    const int n = 4 * nlut;
+    k_lut_grad_reduce<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, glut);
+    return cudaGetLastError();
+}
+
+}  // namespace vr

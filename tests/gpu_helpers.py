@@ -1,0 +1,38 @@
+"""Helpers shared by the GPU parity tests: render through the C ABI and compare with the oracle."""
+import numpy as np
+import pytest
+
+ATOL_F32 = 1e-4          # per RGBA channel, FP32 bricks vs the FP64 oracle
+BOUND_16 = 2e-3          # per RGBA channel, FP16/BF16 bricks vs the FP64 oracle on FP32 voxels
+
+
+def gpu_ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1008_0135_gb300 as P
+    P.build()
+    return P.Context(0)
+
+
+def render(ctx, cube_id, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, full_rect=False):
+    ctx.set_transfer_function(lut, vrange[0], vrange[1])
+    ctx.set_camera_dict(cam)
+    ctx.set_render_params(mode, step, tau)
+    ctx.set_full_rect(full_rect)
+    out = ctx.render_frame(cube_id)
+    a = out.cpu().numpy()
+    return a.reshape(-1, 4) if mode == "dvr" else a.reshape(-1)
+
+
+def compare_dvr(gpu, ref, flags, tau, atol=ATOL_F32):
+    """Non-fragile pixels within atol; pixels whose early-termination decision lies within
+    rounding of the threshold may take either stop, both valid: bounded by 1 - tau."""
+    fragile = (flags & 1).astype(bool)
+    err = np.abs(gpu.astype(np.float64) - ref)
+    firm = err[~fragile]
+    assert firm.size == 0 or firm.max() <= atol, f"max err {firm.max():.3e} > {atol}"
+    if fragile.any():
+        assert err[fragile].max() <= (1.0 - min(tau, 1.0)) + atol
+        assert fragile.mean() < 0.02
+    return float(firm.max()) if firm.size else 0.0

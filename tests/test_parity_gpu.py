@@ -1,0 +1,279 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import ATOL_F32, BOUND_16, compare_dvr, gpu_ctx, render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gpu_ctx()
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pr1(ctx):
+    cube = synth.pr1_cube(seed=0)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (32, 32, 32), 1, "f32")
+    return cube, cid
+
+
+# ---------------------------------------------------------------------------------------------
+# PR1 (64^3, 256^2, 2x2x2 bricks of 32^3 + ghost 1)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("alpha", [0.1, 0.9])
+def test_pr1_dvr_matches_oracle(ctx, orc, pr1, alpha):
+    cube, cid = pr1
+    cam = synth.pr1_camera()
+    lut = synth.ramp_lut(alpha=alpha)
+    g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    ref, flags, ns = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(32, 32, 32))
+    compare_dvr(g, ref, flags, 0.99)
+    assert not np.any(flags & 4)
+
+
+def test_pr1_dvr_ert_off_matches_unbricked_oracle(ctx, orc, pr1):
+    cube, cid = pr1
+    cam = synth.pr1_camera()
+    lut = synth.ramp_lut(alpha=0.5)
+    g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=1.0)
+    ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=1.0)
+    compare_dvr(g, ref, flags, 1.0)
+
+
+def test_pr1_sample_count_matches_oracle(ctx, orc, pr1):
+    cube, cid = pr1
+    cam = synth.pr1_camera()
+    lut = synth.ramp_lut()
+    ctx.reset_stats()
+    render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)
+    st = ctx.stats()
+    _, _, ns = orc.render(cube, lut, (-3, 20), cam, mode="mip", step=0.5)
+    assert st["samples"] == ns          # integer work: every lattice sample exactly once
+
+
+def test_pr1_mip_bit_exact(ctx, orc, pr1):
+    cube, cid = pr1
+    cam = synth.pr1_camera()
+    g = render(ctx, cid, synth.ramp_lut(), (-3, 20), cam, mode="mip", step=0.5)
+    ref32, _, _ = orc.render(cube, synth.ramp_lut(), (-3, 20), cam, mode="mip32", step=0.5,
+                             brick=(32, 32, 32))
+    assert np.array_equal(g.view(np.uint32), ref32.astype(np.float32).view(np.uint32))
+    ref64, _, _ = orc.render(cube, synth.ramp_lut(), (-3, 20), cam, mode="mip", step=0.5)
+    assert np.abs(g - ref64).max() < 1e-4 * max(1.0, np.abs(ref64).max())
+
+
+def test_mip_axis_aligned_is_column_max(ctx):
+    cube = synth.pr1_cube(seed=4, n=32)[:20].copy()
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (8, 16, 6), 1, "f32")
+    cam = synth.axis_ortho_camera((32, 32, 20))
+    g = render(ctx, cid, synth.ramp_lut(), (-3, 20), cam, mode="mip", step=0.5)
+    expect = cube.max(axis=0)[::-1, ::-1].ravel()
+    assert np.array_equal(g, expect)
+    ctx.free_cube(cid)
+
+
+def test_bricked_equals_unbricked(ctx, pr1):
+    cube, _ = pr1
+    lut = synth.ramp_lut(alpha=0.4)
+    cam = synth.pr1_camera()
+    one = ctx.load_cube(cube)
+    ctx.set_bricking(one, (64, 64, 64), 1, "f32")
+    many = ctx.load_cube(cube)
+    ctx.set_bricking(many, (16, 8, 32), 1, "f32")
+    a = render(ctx, one, lut, (-3, 20), cam, step=0.5, tau=1.0)
+    b = render(ctx, many, lut, (-3, 20), cam, step=0.5, tau=1.0)
+    assert np.abs(a - b).max() <= 1e-5
+    ma = render(ctx, one, lut, (-3, 20), cam, mode="mip", step=0.5)
+    mb = render(ctx, many, lut, (-3, 20), cam, mode="mip", step=0.5)
+    assert np.array_equal(ma, mb)
+    ctx.free_cube(one)
+    ctx.free_cube(many)
+
+
+@pytest.mark.parametrize("mode", ["dvr", "mip"])
+def test_rendering_rectangle_does_not_change_image(ctx, pr1, mode):
+    _, cid = pr1
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        cam = synth.random_camera(rng, (64, 64, 64), 200, 120)
+        a = render(ctx, cid, synth.ramp_lut(alpha=0.3), (-3, 20), cam, mode=mode, step=0.5)
+        b = render(ctx, cid, synth.ramp_lut(alpha=0.3), (-3, 20), cam, mode=mode, step=0.5,
+                   full_rect=True)
+        assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------------------------
+# random geometry, tiny cubes, ragged bricks
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(10))
+def test_random_tiny_cubes(ctx, orc, seed):
+    rng = np.random.default_rng(200 + seed)
+    shape = tuple(int(x) for x in rng.integers(2, 10, 3))
+    nx, ny, nz = shape
+    cube = rng.uniform(-1, 3, (nz, ny, nx)).astype(np.float32)
+    lut = synth.random_lut(seed, n=int(rng.integers(2, 64)), alpha_max=0.7)
+    W, H = int(rng.integers(1, 40)), int(rng.integers(1, 40))
+    cam = synth.random_camera(rng, shape, W, H)
+    step = float(rng.choice([0.5, 0.25, 0.3, 1.0, 0.7]))
+    tau = float(rng.choice([1.0, 0.9, 0.6, 0.99]))
+    brick = tuple(int(x) for x in rng.integers(1, 5, 3))
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, brick, 1, "f32")
+    g = render(ctx, cid, lut, (-1, 3), cam, step=step, tau=tau)
+    ref, flags, _ = orc.render(cube, lut, (-1, 3), cam, step=step, tau=tau, brick=brick)
+    compare_dvr(g, ref, flags, tau)
+    m = render(ctx, cid, lut, (-1, 3), cam, mode="mip", step=step)
+    m32, _, _ = orc.render(cube, lut, (-1, 3), cam, mode="mip32", step=step, brick=brick)
+    assert np.array_equal(m, m32.astype(np.float32))
+    ctx.free_cube(cid)
+
+
+def test_eye_inside_volume(ctx, orc, pr1):
+    cube, cid = pr1
+    lut = synth.ramp_lut(alpha=0.3)
+    for k, (eye, tgt) in enumerate([((30.0, 33.0, 31.0), (60.0, 10.0, 40.0)),
+                                    ((32.0, 32.0, 32.0), (0.0, 64.0, 0.0)),
+                                    ((1.0, 63.5, 17.0), (64.0, 0.0, 64.0))]):
+        cam = dict(view=synth.look_at(eye, tgt), proj=1, param=math.radians(80.0), W=96, H=64)
+        g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+        ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(32, 32, 32))
+        compare_dvr(g, ref, flags, 0.99)
+
+
+def test_ragged_bricks(ctx, orc):
+    cube = synth.pr1_cube(seed=6, n=64)[:61, :50, :].copy()        # 64 x 50 x 61
+    lut = synth.ramp_lut(alpha=0.5)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (24, 20, 28), 1, "f32")
+    nb, _ = ctx.brick_grid(cid)
+    assert nb == (3, 3, 3)
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        cam = synth.random_camera(rng, (64, 50, 61), 70, 90)
+        g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.95)
+        ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.95, brick=(24, 20, 28))
+        compare_dvr(g, ref, flags, 0.95)
+    ctx.free_cube(cid)
+
+
+def test_empty_and_degenerate_frames(ctx, pr1):
+    _, cid = pr1
+    lut = synth.ramp_lut()
+    away = dict(view=synth.look_at((-10.0, -10.0, -10.0), (-20.0, -30.0, -40.0)), proj=1,
+                param=0.5, W=33, H=17)
+    g = render(ctx, cid, lut, (-3, 20), away, step=0.5)
+    assert np.all(g == 0)
+    m = render(ctx, cid, lut, (-3, 20), away, mode="mip", step=0.5)
+    assert np.all(m == np.float32(-3))
+    one = dict(view=synth.look_at((32.0, 32.0, -50.0), (32.0, 32.0, 32.0)), proj=0, param=1.0,
+               W=1, H=1)
+    g1 = render(ctx, cid, lut, (-3, 20), one, step=0.5)
+    assert g1.shape == (1, 4) and g1[0, 3] > 0
+    big_step = render(ctx, cid, lut, (-3, 20), synth.pr1_camera(W=40, H=30), step=500.0)
+    assert big_step.shape == (1200, 4)
+
+
+# ---------------------------------------------------------------------------------------------
+# cube operations
+# ---------------------------------------------------------------------------------------------
+def test_minmax_exact_and_subcube(ctx, orc):
+    cube = synth.pr1_cube(seed=7, n=40)
+    cid = ctx.load_cube(cube)
+    assert ctx.compute_minmax(cid) == orc.minmax(cube)
+    sid = ctx.load_cube(cube, sub_origin=(3, 5, 7), sub_extent=(20, 11, 30))
+    sub = cube[7:37, 5:16, 3:23]
+    assert ctx.compute_minmax(sid) == orc.minmax(sub)
+    ctx.set_bricking(sid, (8, 8, 8), 1, "f32")
+    dims, org, e, data = ctx.get_brick(sid, 0)
+    assert dims == (10, 10, 10) and org == (-1, -1, -1) and e == 0
+    idx = np.clip(np.arange(-1, 9), 0, None)
+    assert np.array_equal(data, sub[np.ix_(idx, idx, idx)])
+    ctx.free_cube(cid)
+    ctx.free_cube(sid)
+
+
+def test_update_cube_rebuilds_bricks(ctx, orc):
+    import torch
+    cube = synth.pr1_cube(seed=1, n=32)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (16, 16, 16), 1, "f32")
+    cube2 = (cube * 0.5 + 1.0).astype(np.float32)
+    ctx.update_cube(cid, torch.from_numpy(cube2).cuda())
+    cam = synth.pr1_camera(n=32, W=64, H=64)
+    lut = synth.ramp_lut(alpha=0.4)
+    g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    ref, flags, _ = orc.render(cube2, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(16, 16, 16))
+    compare_dvr(g, ref, flags, 0.99)
+    ctx.free_cube(cid)
+
+
+def test_error_statuses(ctx):
+    import paper_1008_0135_gb300 as P
+    with pytest.raises(P.VrError) as e:
+        ctx.set_bricking(12345, (8, 8, 8))
+    assert e.value.status == -6
+    cube = synth.pr1_cube(seed=2, n=16)
+    cid = ctx.load_cube(cube)
+    with pytest.raises(P.VrError) as e:
+        ctx.set_camera_dict(synth.pr1_camera(n=16, W=8, H=8))
+        ctx.render_frame(cid)
+    assert e.value.status == -5            # no bricking yet
+    with pytest.raises(P.VrError) as e:
+        ctx.set_bricking(cid, (0, 8, 8))
+    assert e.value.status == -1
+    with pytest.raises(P.VrError):
+        ctx.set_transfer_function(synth.ramp_lut(), 5.0, 5.0)
+    with pytest.raises(P.VrError):
+        ctx.load_cube(cube, sub_origin=(0, 0, 0), sub_extent=(17, 1, 1))
+    ctx.free_cube(cid)
+
+
+# ---------------------------------------------------------------------------------------------
+# 16-bit bricks
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_16bit_bricks(ctx, orc, storage):
+    cube = synth.pr1_cube(seed=0)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (32, 32, 32), 1, storage)
+    exps = orc.brick_exponents(cube, (32, 32, 32), 1, storage)
+    # stored codes, bit for bit (integer work), ghost included
+    for b in (0, 5, 7):
+        dims, org, e, data = ctx.get_brick(cid, b)
+        cz, cy, cx = b // 4, (b // 2) % 2, b % 2
+        assert e == exps[cz, cy, cx]
+        iz = np.clip(np.arange(org[2], org[2] + dims[2]), 0, 63)
+        iy = np.clip(np.arange(org[1], org[1] + dims[1]), 0, 63)
+        ix = np.clip(np.arange(org[0], org[0] + dims[0]), 0, 63)
+        region = cube[np.ix_(iz, iy, ix)]
+        scaled = np.ldexp(region, -e).astype(np.float32)
+        want = (orc.round_fp16(scaled) if storage == "f16" else orc.round_bf16(scaled))
+        if storage == "f16":
+            bits = want.astype(np.float16).view(np.uint16)
+        else:
+            bits = (want.view(np.uint32) >> 16).astype(np.uint16)
+        assert np.array_equal(data.ravel(), bits)
+    cam = synth.pr1_camera()
+    lut = synth.ramp_lut(alpha=0.5)
+    g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    # against the oracle reading the same rounded bricks: the kernel's own error
+    refq, flq, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(32, 32, 32),
+                              quant=storage)
+    compare_dvr(g, refq, flq, 0.99)
+    # against the FP32 cube: the stated bound for 16-bit storage
+    ref, fl, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(32, 32, 32))
+    compare_dvr(g, ref, fl, 0.99, atol=BOUND_16)
+    m = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)
+    m32, _, _ = orc.render(cube, lut, (-3, 20), cam, mode="mip32", step=0.5, brick=(32, 32, 32),
+                           quant=storage)
+    assert np.array_equal(m, m32.astype(np.float32))
+    ctx.free_cube(cid)
