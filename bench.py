@@ -34,12 +34,12 @@ METRIC = "ms per 1024² frame & Gsamples/s (FP32 vs FP16 bricks); adjoint ms; p9
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=64)
+    ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="hipass", choices=["hipass", "gass", "pr1"])
+    ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "gass", "pr1"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
-    ap.add_argument("--cpu-rays", type=int, default=8192)
+    ap.add_argument("--cpu-rays", type=int, default=1 << 20)
     return ap.parse_args()
 
 
@@ -91,7 +91,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -147,6 +147,10 @@ def kernel_traffic(name: str):
 def make_cube(cfg_name: str, device: str):
     if cfg_name == "hipass":
         return synth.hipass_cube(device=device), synth.HIPASS
+    if cfg_name == "hipass_small":
+        c = synth.HIPASS_SMALL
+        return synth.hipass_cube(seed=c["seed"], shape_xyz=c["shape"], n_sources=c["n_sources"],
+                                 device=device), c
     if cfg_name == "gass":
         return synth.gass_cube(device=device), synth.GASS
     import torch
@@ -263,7 +267,7 @@ def cpu_baseline(cube_np, cfg, lut, vr, n_rays):
     dt = time.perf_counter() - t0
     return {"value": round(ns / dt / 1e9, 6), "unit": "Gsamples/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"{len(pix)} seeded pixels of orbit view 0 ({ns} samples, {dt:.1f} s)"}
+            "sample": f"{len(pix)} seeded pixels of orbit view 0 ({ns} samples, {dt:.2f} s wall)"}
 
 
 def run_ours(args, dist):

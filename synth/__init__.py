@@ -29,7 +29,7 @@ __all__ = [
     "ramp_lut", "shifted_ramp_lut", "constant_lut", "random_lut",
     "look_at", "orbit_view", "pr1_camera", "axis_ortho_camera", "random_camera",
     "sample_pixels", "poisson_arrivals",
-    "PR1", "HIPASS", "GASS", "DIFF",
+    "PR1", "HIPASS", "HIPASS_SMALL", "GASS", "DIFF", "orbit_camera",
 ]
 
 # ----------------------------------------------------------------------------------------------
@@ -40,6 +40,9 @@ PR1 = dict(name="PR1 64^3", shape=(64, 64, 64), seed=0, W=256, H=256, step=0.5, 
 HIPASS = dict(name="HIPASS-scale 1720x1720x1024", shape=(1720, 1720, 1024), seed=1, W=1024,
               H=1024, step=1.0, tau=0.99, vrange=(-3.0, 100.0), brick=(256, 256, 256), ghost=1,
               n_views=64, fov_deg=60.0, eye_factor=1.5)
+# the HIPASS recipe at 768x768x512 (1.2 GB, still above L2): the case hardware counters are
+# captured on (a full-size capture would replay a 12 GB working set dozens of times)
+HIPASS_SMALL = dict(HIPASS, name="HIPASS-recipe 768x768x512", shape=(768, 768, 512), n_sources=1000)
 GASS = dict(name="GASS-scale 2048x2048x1600", shape=(2048, 2048, 1600), seed=2, W=1024,
             H=1024, step=0.5, tau=0.99, vrange=(-2.0, 8.0), brick=(256, 256, 256), ghost=1,
             n_views=64, fov_deg=60.0, eye_factor=1.5)

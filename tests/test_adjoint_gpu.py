@@ -1,0 +1,110 @@
+"""Adjoint ray casting on the GPU against the FP64 oracle gradient and finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import gpu_ctx, render
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gpu_ctx()
+    yield c
+    c.close()
+
+
+def _setup(ctx, seed, n=24, brick=(8, 8, 8), W=48, H=40):
+    rng = np.random.default_rng(seed)
+    cube = synth.pr1_cube(seed=seed, n=n, amp=(1.0, 4.0))
+    lut = synth.random_lut(seed, n=32, alpha_max=0.4)
+    cam = synth.random_camera(rng, (n, n, n), W, H)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, brick, 1, "f32")
+    return rng, cube, lut, cam, cid
+
+
+def _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau):
+    import torch
+    render(ctx, cid, lut, vr, cam, step=step, tau=tau)
+    g = torch.from_numpy(gout.astype(np.float32).reshape(cam["H"], cam["W"], 4)).cuda()
+    glut = torch.zeros((lut.shape[0], 4), device="cuda")
+    gvox = torch.zeros(cube.shape, device="cuda")
+    ctx.render_backward(cid, g.contiguous(), glut, gvox)
+    return glut.cpu().numpy().astype(np.float64), gvox.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("seed,tau", [(0, 0.95), (1, 1.0), (2, 0.9)])
+def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau):
+    rng, cube, lut, cam, cid = _setup(ctx, seed)
+    vr = (-3.0, 8.0)
+    step = 0.5
+    gout = rng.standard_normal((cam["W"] * cam["H"], 4))
+    _, flags, _ = orc.render(cube, lut, vr, cam, step=step, tau=tau, brick=(8, 8, 8))
+    gout[(flags & 1).astype(bool)] = 0.0        # stops at the threshold: either side is valid
+    gl, gv = _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau)
+    rl, rv = orc.render_grad(cube, lut, vr, cam, gout.astype(np.float32).astype(np.float64),
+                             step=step, tau=tau, brick=(8, 8, 8))
+    assert np.abs(rl).max() > 0 and np.abs(rv).max() > 0
+    assert np.abs(gl - rl).max() <= 2e-4 * np.abs(rl).max(), np.abs(gl - rl).max()
+    assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max(), np.abs(gv - rv).max()
+    ctx.free_cube(cid)
+
+
+def test_adjoint_matches_gpu_finite_differences(ctx):
+    """Central differences of the GPU forward itself (no early termination, so no stop moves)."""
+    import torch
+    rng, cube, lut, cam, cid = _setup(ctx, 7, n=16, brick=(8, 8, 8), W=24, H=24)
+    vr = (-3.0, 8.0)
+    gout = rng.standard_normal((cam["W"] * cam["H"], 4))
+    gl, _ = _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, 0.5, 1.0)
+
+    def loss(l):
+        img = render(ctx, cid, l, vr, cam, step=0.5, tau=1.0).astype(np.float64)
+        return float((img * gout).sum())
+
+    checked = 0
+    for i in rng.choice(lut.shape[0], 10, replace=False):
+        ch = int(rng.integers(0, 4))
+        h = 1e-2
+        lp, lm = lut.copy(), lut.copy()
+        lp[i, ch] += h
+        lm[i, ch] -= h
+        fd = (loss(lp) - loss(lm)) / (float(lp[i, ch]) - float(lm[i, ch]))
+        if abs(gl[i, ch]) < 1e-3:
+            continue
+        assert abs(fd - gl[i, ch]) <= 2e-2 * abs(gl[i, ch]) + 1e-3, (i, ch, fd, gl[i, ch])
+        checked += 1
+    assert checked >= 4
+    ctx.free_cube(cid)
+
+
+def test_autograd_function_sums_views(ctx, orc):
+    import torch
+    from paper_1008_0135_gb300.autograd import render_views
+    n = 20
+    cube = synth.pr1_cube(seed=11, n=n, amp=(1.0, 4.0))
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (10, 10, 10), 1, "f32")
+    lut = torch.from_numpy(synth.random_lut(4, n=16, alpha_max=0.3)).cuda().requires_grad_(True)
+    vox = torch.from_numpy(cube).cuda().requires_grad_(True)
+    c = np.array([n / 2] * 3)
+    cams = [dict(view=synth.orbit_view(a, c, 40.0), proj=1, param=math.radians(50), W=32, H=32)
+            for a in (0.0, 100.0)]
+    imgs = render_views(ctx, cid, lut, cams, (-3.0, 8.0), voxels=vox, step=0.5, tau=1.0)
+    w = torch.from_numpy(np.random.default_rng(0).standard_normal(imgs.shape).astype(np.float32)).cuda()
+    (imgs * w).sum().backward()
+    wl = w.cpu().numpy().reshape(2, -1, 4).astype(np.float64)
+    rl = np.zeros((16, 4))
+    rv = np.zeros(cube.shape)
+    for k, cam in enumerate(cams):
+        a, b = orc.render_grad(cube, lut.detach().cpu().numpy(), (-3.0, 8.0), cam, wl[k],
+                               step=0.5, tau=1.0, brick=(10, 10, 10))
+        rl += a
+        rv += b
+    assert np.abs(lut.grad.cpu().numpy() - rl).max() <= 2e-4 * np.abs(rl).max()
+    assert np.abs(vox.grad.cpu().numpy() - rv).max() <= 2e-4 * np.abs(rv).max()
+    ctx.free_cube(cid)
