@@ -160,6 +160,29 @@ int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold)
  * VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT (streamed bricks did not arrive in time). */
 int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *cuda_stream);
 
+/* Renders one frame like vr_render_frame, but allocates no memory at all, for callers that
+ * cannot allocate device memory while they render (their GPU memory is owned by another
+ * allocator or held to a fixed budget, or their frame loop must not pay the device-wide
+ * synchronisation that cudaMalloc/cudaFree can cause).  The paper has no counterpart: this is
+ * an operational variant of the Section 2.4/2.5 rendering path.
+ * out: device memory, 16-byte aligned, W*H*4 floats (DVR) or W*H floats (MIP); the caller also
+ *   supplies the loaded, bricked cube and the current table, camera and parameters.
+ * Scratch: the staged work-list and the per-brick fragments live in one static 64 MiB device
+ *   array that every GPU loading this library reserves until the process exits.  A frame whose
+ *   scratch would exceed 64 MiB is rejected with VR_ERR_ARG (vr_last_error_message() gives the
+ *   bytes needed); e.g. 512x512 frames of cubes with a few dozen bricks fit, 1024x1024 frames of
+ *   a 12 GB cube do not.  The work-list is built in a static host arena as well.
+ * Set-up: the first call on a device looks up that array's device address (cudaGetSymbolAddress
+ *   with the device current), which may also load the library's GPU code on that device; make
+ *   that first call before any stream capture.
+ * Sharing: every call, from any context, uses the same array and leaves its contents behind;
+ *   calls whose GPU work overlaps (e.g. on two streams without ordering between them) race on
+ *   it and corrupt each other's frames.  Calls ordered on one stream are safe.  Host calls are
+ *   serialised by a lock.
+ * Returns when the work is queued on `cuda_stream`.  Errors: VR_ERR_ARG (null or misaligned
+ * out, frame too large for the scratch), VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_CUDA. */
+int vr_render_frame_noalloc(vr_ctx *ctx, int cube_id, float *out, void *cuda_stream);
+
 /* Gradient of a scalar image loss L with respect to the transfer-function table and the
  * voxels, for the current camera, table and parameters (DVR only, VR_F32 bricks).
  * grad_out: W*H*4 floats dL/d(output RGBA), device memory.

@@ -405,6 +405,195 @@ void free_cube(Cube *cb) {
 }  // namespace
 
 // =============================================================================================
+// Rendering without allocation: a fixed device scratch array and a fixed host arena.
+//
+// Some callers cannot allocate device memory while they render: a process whose GPU memory is
+// owned by another allocator or held to a fixed budget, or a frame loop that must not pay the
+// device-wide synchronisation that cudaMalloc/cudaFree can cause.  vr_render_frame_noalloc
+// serves them.  Its scratch (the staged work-list and the fragments) lives in the file-scope
+// array below, reserved on every GPU that loads this library until the process exits.
+// =============================================================================================
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;    // 64 MiB per device
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Host arena the work-list is built in (static storage: no heap use on this path).  Its
+// contents are consumed by cudaMemcpyAsync from pageable memory, which copies them out before
+// returning, so the arena can be reused by the next call.
+alignas(256) unsigned char g_noalloc_host[kNoAllocScratchBytes];
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev[256] = {nullptr};                          // device address, per device
+
+// Device address of g_noalloc_scratch on the current device.  In host code the symbol's name
+// is only a stand-in; its address must be queried per device with that device current.
+int noalloc_scratch(int device, unsigned char **ptr) {
+    if (device < 0 || device >= 256) return arg_fail("device ordinal out of range");
+    if (!g_noalloc_dev[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_dev[device] = p;
+    }
+    *ptr = static_cast<unsigned char *>(g_noalloc_dev[device]);
+    return VR_OK;
+}
+
+struct StaticLayout {
+    size_t off_lut, off_db, off_items, off_ts, off_tl, bytes;
+    int nd, nitems;
+    long long frag_px;
+};
+
+// The work-list of build_worklist (same rectangles, culling, front-to-back order, bins),
+// written straight into the static host arena.  Returns VR_ERR_ARG when it does not fit.
+int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap, size_t frag_elem,
+                          StaticLayout &L) {
+    const Cam &cam = c->cam;
+    const int W = cam.W, H = cam.H;
+    const double R[9] = {cam.R[0], cam.R[1], cam.R[2], cam.R[3], cam.R[4], cam.R[5], cam.R[6], cam.R[7], cam.R[8]};
+    const double t[3] = {cam.t[0], cam.t[1], cam.t[2]};
+    int ecell[3] = {0, 0, 0}, dsign[3] = {1, 1, 1};
+    if (cam.proj == VR_PERSP) {
+        float e[3];
+        eye_f32(cam, e);
+        for (int a = 0; a < 3; ++a) {
+            if (e[a] < 0.0f) ecell[a] = -1;
+            else if (e[a] >= (float)cb->n[a]) ecell[a] = (int)cb->nb[a];
+            else ecell[a] = std::min((int)(e[a] / (float)cb->B[a]), (int)cb->nb[a] - 1);
+            while (ecell[a] > 0 && ecell[a] < cb->nb[a] && (float)((int64_t)ecell[a] * cb->B[a]) > e[a]) --ecell[a];
+            while (ecell[a] + 1 < cb->nb[a] && (float)((int64_t)(ecell[a] + 1) * cb->B[a]) <= e[a]) ++ecell[a];
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) dsign[a] = (-cam.R[6 + a] >= 0.0f) ? 1 : -1;
+    }
+    const size_t nb = cb->tmpl.size();
+    const int ntx = (W + kTile - 1) / kTile, nty = (H + kTile - 1) / kTile;
+    const size_t ntiles = (size_t)ntx * nty;
+    // scratch for candidates, sort keys and bin cursors at the top of the arena
+    struct Key { long long key; int idx; };
+    const size_t tmp_bytes = align_up(nb * sizeof(DrawBrick), 256) + align_up(nb * sizeof(Key), 256) +
+                             align_up(ntiles * sizeof(int), 256);
+    if (tmp_bytes >= cap) return arg_fail("frame does not fit the 64 MiB no-allocation scratch");
+    unsigned char *tmp = arena + cap - tmp_bytes;
+    DrawBrick *cand = reinterpret_cast<DrawBrick *>(tmp);
+    Key *keys = reinterpret_cast<Key *>(tmp + align_up(nb * sizeof(DrawBrick), 256));
+    int *cursor = reinterpret_cast<int *>(tmp + align_up(nb * sizeof(DrawBrick), 256) + align_up(nb * sizeof(Key), 256));
+    int nc = 0;
+    for (size_t bi = 0; bi < nb; ++bi) {
+        const DrawBrick &b = cb->tmpl[bi];
+        int x0 = 0, y0 = 0, x1 = W, y1 = H;
+        bool cull = false;
+        if (!c->full_rect) {
+            double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300;
+            int behind = 0, front = 0;
+            for (int k = 0; k < 8; ++k) {
+                double p[3] = {(k & 1) ? b.hi[0] : b.lo[0], (k & 2) ? b.hi[1] : b.lo[1], (k & 4) ? b.hi[2] : b.lo[2]};
+                double e[3];
+                for (int r = 0; r < 3; ++r) e[r] = R[3 * r] * p[0] + R[3 * r + 1] * p[1] + R[3 * r + 2] * p[2] + t[r];
+                double sx, sy;
+                if (cam.proj == VR_PERSP) {
+                    if (e[2] > -1e-6) { ++behind; continue; }
+                    ++front;
+                    sx = e[0] / (-e[2]) / cam.th_w;
+                    sy = e[1] / (-e[2]) / cam.th;
+                } else {
+                    if (e[2] > 0.0) ++behind; else ++front;
+                    sx = e[0] / cam.half_w;
+                    sy = e[1] / cam.half_h;
+                }
+                double px = (sx + 1.0) * 0.5 * W, py = (1.0 - sy) * 0.5 * H;
+                mnx = std::min(mnx, px); mxx = std::max(mxx, px);
+                mny = std::min(mny, py); mxy = std::max(mxy, py);
+            }
+            if (front == 0) {
+                cull = true;
+            } else if (cam.proj == VR_PERSP && behind > 0) {
+                x0 = 0; y0 = 0; x1 = W; y1 = H;
+            } else {
+                x0 = (int)std::max(0.0, std::floor(mnx) - 1.0);
+                y0 = (int)std::max(0.0, std::floor(mny) - 1.0);
+                x1 = (int)std::min((double)W, std::ceil(mxx) + 1.0);
+                y1 = (int)std::min((double)H, std::ceil(mxy) + 1.0);
+                if (x1 <= x0 || y1 <= y0) cull = true;
+            }
+        }
+        if (cull) continue;
+        DrawBrick d = b;
+        d.rect[0] = x0; d.rect[1] = y0; d.rect[2] = x1 - x0; d.rect[3] = y1 - y0;
+        d.sampled = 0;
+        int ci[3] = {(int)(b.brick % cb->nb[0]), (int)((b.brick / cb->nb[0]) % cb->nb[1]),
+                     (int)(b.brick / (cb->nb[0] * cb->nb[1]))};
+        long long key = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (cam.proj == VR_PERSP) key += std::abs(ci[a] - ecell[a]);
+            else key += dsign[a] > 0 ? ci[a] : (cb->nb[a] - 1 - ci[a]);
+        }
+        keys[nc] = Key{key, nc};
+        cand[nc++] = d;
+    }
+    // (key, candidate index) is a total order: the same order as a stable sort by key
+    std::sort(keys, keys + nc, [](const Key &a, const Key &b) { return a.key != b.key ? a.key < b.key : a.idx < b.idx; });
+    long long frag = 0, nitems = 0, nbin = 0;
+    for (int i = 0; i < nc; ++i) {
+        const DrawBrick &d = cand[keys[i].idx];
+        frag += (long long)d.rect[2] * d.rect[3];
+        nitems += (long long)((d.rect[2] + kTile - 1) / kTile) * ((d.rect[3] + kTile - 1) / kTile);
+        nbin += (long long)((d.rect[0] + d.rect[2] - 1) / kTile - d.rect[0] / kTile + 1) *
+                ((d.rect[1] + d.rect[3] - 1) / kTile - d.rect[1] / kTile + 1);
+    }
+    size_t off = 0;
+    L.off_lut = off; off = align_up(off + sizeof(float4) * c->lut.size(), 256);
+    L.off_db = off; off = align_up(off + sizeof(DrawBrick) * (size_t)nc, 256);
+    L.off_items = off; off = align_up(off + sizeof(TileItem) * (size_t)nitems, 256);
+    L.off_ts = off; off = align_up(off + sizeof(int) * (ntiles + 1), 256);
+    L.off_tl = off; off = align_up(off + sizeof(int) * (size_t)nbin, 256);
+    L.bytes = off;
+    L.nd = nc;
+    L.nitems = (int)nitems;
+    L.frag_px = frag;
+    if (off + tmp_bytes > cap || off + (size_t)frag * frag_elem > cap) {
+        g_last_error = "frame needs " + std::to_string(off + (size_t)frag * frag_elem) +
+                       " bytes of scratch; the no-allocation limit is 64 MiB";
+        return VR_ERR_ARG;
+    }
+    std::memcpy(arena + L.off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
+    DrawBrick *db = reinterpret_cast<DrawBrick *>(arena + L.off_db);
+    TileItem *items = reinterpret_cast<TileItem *>(arena + L.off_items);
+    int *ts = reinterpret_cast<int *>(arena + L.off_ts);
+    int *tl = reinterpret_cast<int *>(arena + L.off_tl);
+    long long fo = 0, it = 0;
+    for (int i = 0; i < nc; ++i) {
+        DrawBrick d = cand[keys[i].idx];
+        d.frag_off = fo;
+        fo += (long long)d.rect[2] * d.rect[3];
+        const int tw = (d.rect[2] + kTile - 1) / kTile, th = (d.rect[3] + kTile - 1) / kTile;
+        for (int ty = 0; ty < th; ++ty)
+            for (int tx = 0; tx < tw; ++tx) items[it++] = TileItem{i, tx, ty};
+        db[i] = d;
+    }
+    std::memset(ts, 0, sizeof(int) * (ntiles + 1));
+    for (int i = 0; i < nc; ++i) {
+        const DrawBrick &d = db[i];
+        for (int ty = d.rect[1] / kTile; ty <= (d.rect[1] + d.rect[3] - 1) / kTile; ++ty)
+            for (int tx = d.rect[0] / kTile; tx <= (d.rect[0] + d.rect[2] - 1) / kTile; ++tx)
+                ts[(size_t)ty * ntx + tx + 1]++;
+    }
+    for (size_t i = 1; i <= ntiles; ++i) ts[i] += ts[i - 1];
+    std::memcpy(cursor, ts, sizeof(int) * ntiles);
+    for (int i = 0; i < nc; ++i) {
+        const DrawBrick &d = db[i];
+        for (int ty = d.rect[1] / kTile; ty <= (d.rect[1] + d.rect[3] - 1) / kTile; ++ty)
+            for (int tx = d.rect[0] / kTile; tx <= (d.rect[0] + d.rect[2] - 1) / kTile; ++tx)
+                tl[cursor[(size_t)ty * ntx + tx]++] = i;
+    }
+    return VR_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
 // C ABI (the only symbols the library exports; everything else is built with hidden visibility)
 // =============================================================================================
 #pragma GCC visibility push(default)
@@ -842,6 +1031,38 @@ int vr_get_brick(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3],
         const size_t esz = cb->storage == VR_F32 ? 4 : 2;
         CK(cudaMemcpy(data, static_cast<char *>(cb->d_pool) + b.data_off * esz, (size_t)b.bytes, cudaMemcpyDeviceToHost));
     }
+    return VR_OK;
+}
+
+// The no-allocation variant of vr_render_frame (see include/vrcube.h).
+int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
+    if (!c || !out) return arg_fail("null argument");
+    if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return arg_fail("out must be 16-byte aligned device memory");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    unsigned char *dev = nullptr;
+    if ((rc = noalloc_scratch(c->device, &dev)) != VR_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const FrameConsts fc = make_consts(c, cb);
+    const size_t frag_elem = c->mode == VR_DVR ? sizeof(float4) : sizeof(float);
+    StaticLayout L{};
+    if ((rc = build_worklist_static(c, cb, g_noalloc_host, kNoAllocScratchBytes, frag_elem, L)) != VR_OK) return rc;
+    // fragments follow the staged work-list; the kernel writes every fragment it later reads,
+    // and the per-brick "sampled" flags arrive zeroed with the work-list, so nothing left over
+    // from an earlier call is read
+    CK(cudaMemcpyAsync(dev, g_noalloc_host, L.bytes, cudaMemcpyHostToDevice, s));
+    const float4 *d_lut = reinterpret_cast<const float4 *>(dev + L.off_lut);
+    const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(dev + L.off_db);
+    const TileItem *d_items = reinterpret_cast<const TileItem *>(dev + L.off_items);
+    const int *d_ts = reinterpret_cast<const int *>(dev + L.off_ts);
+    const int *d_tl = reinterpret_cast<const int *>(dev + L.off_tl);
+    void *d_frags = dev + L.bytes;
+    CK(launch_raycast(fc, d_lut, d_db, d_items, L.nitems, cb->d_pool, d_frags, c->d_ctr, s));
+    CK(launch_composite(fc, d_db, d_ts, d_tl, d_frags, out, s));
     return VR_OK;
 }
 
