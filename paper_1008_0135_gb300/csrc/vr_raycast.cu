@@ -119,29 +119,33 @@ struct DvrSample {
     float r, g, b, a;       // interpolated colour and opacity
 };
 
-template <int S>
-__device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int mx, int my, int mz,
-                                           float scale, float x, float y, float z, float vmin,
-                                           float inv_range, float lutmax, int lmax,
-                                           const float4 *s_lut, DvrSample &o) {
+// Cell of a sample: lower stencil corner (local stored index, clamped so the 2x2x2 stencil stays
+// inside the stored brick) and the trilinear fractions.
+struct Cell {
+    int ix, iy, iz;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ void cell_of(float x, float y, float z, int mx, int my, int mz, Cell &c) {
     const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
-    o.fx = __fsub_rn(x, flx); o.fy = __fsub_rn(y, fly); o.fz = __fsub_rn(z, flz);
-    const int ix = clampi((int)flx, 0, mx), iy = clampi((int)fly, 0, my), iz = clampi((int)flz, 0, mz);
-    const int i0 = ix + dx * iy + dxy * iz;
-    o.i0 = i0;
-    const float v000 = ldv<S>(src, i0), v100 = ldv<S>(src, i0 + 1);
-    const float v010 = ldv<S>(src, i0 + dx), v110 = ldv<S>(src, i0 + dx + 1);
-    const float v001 = ldv<S>(src, i0 + dxy), v101 = ldv<S>(src, i0 + dxy + 1);
-    const float v011 = ldv<S>(src, i0 + dxy + dx), v111 = ldv<S>(src, i0 + dxy + dx + 1);
-    const float a00 = __fmaf_rn(o.fx, __fsub_rn(v100, v000), v000);
-    const float a10 = __fmaf_rn(o.fx, __fsub_rn(v110, v010), v010);
-    const float a01 = __fmaf_rn(o.fx, __fsub_rn(v101, v001), v001);
-    const float a11 = __fmaf_rn(o.fx, __fsub_rn(v111, v011), v011);
-    const float b0 = __fmaf_rn(o.fy, __fsub_rn(a10, a00), a00);
-    const float b1 = __fmaf_rn(o.fy, __fsub_rn(a11, a01), a01);
-    float v = __fmaf_rn(o.fz, __fsub_rn(b1, b0), b0);
-    if (S != 0) v = __fmul_rn(v, scale);
-    o.u = __fmul_rn(__fsub_rn(v, vmin), inv_range);
+    c.fx = __fsub_rn(x, flx); c.fy = __fsub_rn(y, fly); c.fz = __fsub_rn(z, flz);
+    c.ix = clampi((int)flx, 0, mx); c.iy = clampi((int)fly, 0, my); c.iz = clampi((int)flz, 0, mz);
+}
+
+// Trilinear value from the 8 corners v[x + 2y + 4z], then the table lookup.
+__device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool scaled, float scale,
+                                          float vmin, float inv_range, float lutmax, int lmax,
+                                          const float4 *s_lut, DvrSample &o) {
+    o.fx = c.fx; o.fy = c.fy; o.fz = c.fz;
+    const float a00 = __fmaf_rn(c.fx, __fsub_rn(v[1], v[0]), v[0]);
+    const float a10 = __fmaf_rn(c.fx, __fsub_rn(v[3], v[2]), v[2]);
+    const float a01 = __fmaf_rn(c.fx, __fsub_rn(v[5], v[4]), v[4]);
+    const float a11 = __fmaf_rn(c.fx, __fsub_rn(v[7], v[6]), v[6]);
+    const float b0 = __fmaf_rn(c.fy, __fsub_rn(a10, a00), a00);
+    const float b1 = __fmaf_rn(c.fy, __fsub_rn(a11, a01), a01);
+    float val = __fmaf_rn(c.fz, __fsub_rn(b1, b0), b0);
+    if (scaled) val = __fmul_rn(val, scale);
+    o.u = __fmul_rn(__fsub_rn(val, vmin), inv_range);
     const float uc = fminf(fmaxf(o.u, 0.0f), 1.0f);
     const float xl = __fmul_rn(uc, lutmax);
     o.li = min((int)xl, lmax);
@@ -152,6 +156,73 @@ __device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int
     o.g = __fmaf_rn(o.lf, __fsub_rn(o.L1.y, o.L0.y), o.L0.y);
     o.b = __fmaf_rn(o.lf, __fsub_rn(o.L1.z, o.L0.z), o.L0.z);
     o.a = __fmaf_rn(o.lf, __fsub_rn(o.L1.w, o.L0.w), o.L0.w);
+}
+
+template <int S>
+__device__ __forceinline__ void fetch8(const void *src, int i0, int dx, int dxy, float v[8]) {
+    v[0] = ldv<S>(src, i0);            v[1] = ldv<S>(src, i0 + 1);
+    v[2] = ldv<S>(src, i0 + dx);       v[3] = ldv<S>(src, i0 + dx + 1);
+    v[4] = ldv<S>(src, i0 + dxy);      v[5] = ldv<S>(src, i0 + dxy + 1);
+    v[6] = ldv<S>(src, i0 + dxy + dx); v[7] = ldv<S>(src, i0 + dxy + dx + 1);
+}
+
+template <int S>
+__device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int mx, int my, int mz,
+                                           float scale, float x, float y, float z, float vmin,
+                                           float inv_range, float lutmax, int lmax,
+                                           const float4 *s_lut, DvrSample &o) {
+    Cell c;
+    cell_of(x, y, z, mx, my, mz, c);
+    o.i0 = c.ix + dx * c.iy + dxy * c.iz;
+    float v[8];
+    fetch8<S>(src, o.i0, dx, dxy, v);
+    interp_tf(v, c, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, o);
+}
+
+// Stencil cache of one ray: the 8 corner values of the previous sample's cell.  Moving to an
+// adjacent cell (each index changes by at most 1) keeps the corners the two cells share and
+// gathers only the others; any larger jump reloads all 8.  `need` bit c marks corner c as
+// still to be gathered; shifting the values shifts their bits too.
+template <int S>
+__device__ __forceinline__ void fetch8_cached(const void *src, int dx, int dxy, const Cell &c,
+                                              int &px, int &py, int &pz, float v[8]) {
+    const int ddx = c.ix - px, ddy = c.iy - py, ddz = c.iz - pz;
+    unsigned need = 0u;
+    if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1 || ddz < -1 || ddz > 1) {
+        need = 0xffu;
+    } else {
+        if (ddx == 1) {
+            v[0] = v[1]; v[2] = v[3]; v[4] = v[5]; v[6] = v[7];
+            need = ((need >> 1) & 0x55u) | 0xaau;
+        } else if (ddx == -1) {
+            v[1] = v[0]; v[3] = v[2]; v[5] = v[4]; v[7] = v[6];
+            need = ((need << 1) & 0xaau) | 0x55u;
+        }
+        if (ddy == 1) {
+            v[0] = v[2]; v[1] = v[3]; v[4] = v[6]; v[5] = v[7];
+            need = ((need >> 2) & 0x33u) | 0xccu;
+        } else if (ddy == -1) {
+            v[2] = v[0]; v[3] = v[1]; v[6] = v[4]; v[7] = v[5];
+            need = ((need << 2) & 0xccu) | 0x33u;
+        }
+        if (ddz == 1) {
+            v[0] = v[4]; v[1] = v[5]; v[2] = v[6]; v[3] = v[7];
+            need = ((need >> 4) & 0x0fu) | 0xf0u;
+        } else if (ddz == -1) {
+            v[4] = v[0]; v[5] = v[1]; v[6] = v[2]; v[7] = v[3];
+            need = ((need << 4) & 0xf0u) | 0x0fu;
+        }
+    }
+    px = c.ix; py = c.iy; pz = c.iz;
+    const int i0 = c.ix + dx * c.iy + dxy * c.iz;
+    if (need & 0x01u) v[0] = ldv<S>(src, i0);
+    if (need & 0x02u) v[1] = ldv<S>(src, i0 + 1);
+    if (need & 0x04u) v[2] = ldv<S>(src, i0 + dx);
+    if (need & 0x08u) v[3] = ldv<S>(src, i0 + dx + 1);
+    if (need & 0x10u) v[4] = ldv<S>(src, i0 + dxy);
+    if (need & 0x20u) v[5] = ldv<S>(src, i0 + dxy + 1);
+    if (need & 0x40u) v[6] = ldv<S>(src, i0 + dxy + dx);
+    if (need & 0x80u) v[7] = ldv<S>(src, i0 + dxy + dx + 1);
 }
 
 // Front-to-back "over" of one sample into (c, T): c += T a rgb, T *= 1 - a.
@@ -205,12 +276,16 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                 const int lmax = fc.nlut - 2;
                 const float thr = fc.thr;
                 int j = 0;
+                int px = -4, py = -4, pz = -4;        // no cell cached yet
+                float v[8];
                 for (; j < n; ++j) {
                     const float tj = __fmul_rn((float)j, fc.step);
+                    Cell cl;
+                    cell_of(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
+                            mx, my, mz, cl);
+                    fetch8_cached<S>(src, dx, dxy, cl, px, py, pz, v);
                     DvrSample sm;
-                    dvr_sample<S>(src, dx, dxy, mx, my, mz, scale, __fmaf_rn(tj, d[0], qx),
-                                  __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), vmin, inv_range,
-                                  lutmax, lmax, s_lut, sm);
+                    interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
                     over(sm, c0, c1, c2, T);
                     if (T <= thr) { ++j; break; }
                 }

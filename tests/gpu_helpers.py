@@ -25,14 +25,16 @@ def render(ctx, cube_id, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, full_
     return a.reshape(-1, 4) if mode == "dvr" else a.reshape(-1)
 
 
-def compare_dvr(gpu, ref, flags, tau, atol=ATOL_F32):
+def compare_dvr(gpu, ref, flags, tau, atol=ATOL_F32, max_fragile=0.10):
     """Non-fragile pixels within atol; pixels whose early-termination decision lies within
-    rounding of the threshold may take either stop, both valid: bounded by 1 - tau."""
+    rounding of the threshold may take either stop, both valid: bounded by 1 - tau.  Their share
+    depends on how slowly segments cross the threshold (small steps, faint media), so it is only
+    bounded loosely."""
     fragile = (flags & 1).astype(bool)
     err = np.abs(gpu.astype(np.float64) - ref)
     firm = err[~fragile]
     assert firm.size == 0 or firm.max() <= atol, f"max err {firm.max():.3e} > {atol}"
     if fragile.any():
         assert err[fragile].max() <= (1.0 - min(tau, 1.0)) + atol
-        assert fragile.mean() < 0.02
+        assert fragile.mean() < max_fragile
     return float(firm.max()) if firm.size else 0.0
