@@ -46,7 +46,8 @@ extern "C" {
 #define VR_ERR_TIMEOUT (-4)   /* a bounded wait (brick copy, admission) ran out */
 #define VR_ERR_STATE (-5)     /* call out of order (no bricking / table / camera set yet) */
 #define VR_ERR_NOT_FOUND (-6) /* unknown cube id */
-#define VR_ERR_UNSUPPORTED (-7)
+#define VR_ERR_UNSUPPORTED (-7) /* valid call, combination not offered (e.g. MIP backward) */
+#define VR_ERR_IO (-8)          /* a brick source failed (host-side generator or reader) */
 
 /* element / storage types */
 #define VR_F32 0
@@ -101,6 +102,33 @@ void vr_destroy(vr_ctx *ctx);
 int vr_load_cube(vr_ctx *ctx, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz,
                  int where, const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id);
 
+/* Creates a streamed cube whose voxels are generated on demand, brick by brick, on host
+ * threads: the stand-in for cubes larger than HBM (Section 1.2: HIPASS 12 GB, GASS 25 GB,
+ * ASKAP-size cubes of terabytes).  Voxel (x,y,z) = hash noise + Gaussian sources, defined by:
+ *   SplitMix64 (state += 0x9E3779B97F4A7C15; two xor-shift-multiply rounds; final xor-shift);
+ *   noise: counter c = (z*ny + y)*ceil(nx/2) + floor(x/2), h = SplitMix64 of c ^ (seed *
+ *   0xD1B54A32D192ED03), u1 = ((h>>40) + 0.5) 2^-24, u2 = ((h>>16) & 0xFFFFFF) 2^-24,
+ *   r = sqrt(-2 ln u1), even x: r cos(2 pi u2), odd x: r sin(2 pi u2) (Box-Muller);
+ *   sources: 4 per 256^3 cell q = (qz*ncy + qy)*ncx + qx from the SplitMix64 stream seeded
+ *   with seed ^ (q * 0x9E3779B97F4A7C15) ^ 0x632BE59BD9B4E019, six uniforms (top 53 bits)
+ *   each: centre (q + u) 256, sigma_xy = 1 + 3u, sigma_z = sigma_xy (2 + 3u), amplitude
+ *   exp(ln 3 + (ln 100 - ln 3) u); a source adds amp exp(-r^2/2) inside |dx|,|dy| <= 4 sigma_xy,
+ *   |dz| <= 4 sigma_z, d measured from the voxel centre;
+ *   voxel = (float)(noise + sources in increasing (cell, k) order), computed in double.
+ * The cube must be bricked (vr_set_bricking) before rendering.  Frames stream the bricks they
+ * need through the context's HBM brick cache (cache_bytes of vr_create, LRU, pinned staging,
+ * copies on a side stream); frames needing more bricks than the cache holds are ray-cast in
+ * chunks.  Not offered for streamed cubes: min/max, update, backward, no-allocation frames.
+ * Errors: VR_ERR_ARG (null, sizes < 1 or > 2^30). */
+int vr_load_cube_procedural(vr_ctx *ctx, uint64_t seed, int64_t nx, int64_t ny, int64_t nz,
+                            int *cube_id);
+
+/* Test hook: host-side fault injection into the brick streaming path (nothing is injected on
+ * the GPU).  kind 0: off; 1: the brick source throws on the after-th brick it produces
+ * (the frame fails with VR_ERR_IO); 2: pinned staging allocation fails (VR_ERR_OOM);
+ * 3: waits for staging buffers report expiry (VR_ERR_TIMEOUT).  Errors: VR_ERR_ARG. */
+int vr_set_fault_injection(vr_ctx *ctx, int kind, int64_t after);
+
 /* Replaces the voxels of a loaded cube (same dimensions, VR_F32, host or device) and rebuilds
  * its bricks with the current bricking.  For fitting loops that update the voxels.  The copy
  * and the rebuild are ordered on `cuda_stream`.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND,
@@ -124,6 +152,15 @@ int vr_compute_minmax(vr_ctx *ctx, int cube_id, float *vmin, float *vmax);
  * Synchronous.  Errors: VR_ERR_ARG (sizes < 1, ghost != 1, storage), VR_ERR_NOT_FOUND,
  * VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_bricking(vr_ctx *ctx, int cube_id, int bx, int by, int bz, int ghost, int storage);
+
+/* Brick layouts kept for a cube: bit a of `mask` keeps a copy of every brick whose axis a
+ * (0 x, 1 y, 2 z) is the contiguous one in memory; bit 0 is always kept.  Each frame reads the
+ * copy whose contiguous axis is most aligned with an image axis and runs its warps along that
+ * image axis, so the 32 rays of a warp gather neighbouring addresses (each extra layout costs
+ * one more copy of the pool in HBM).  A bricked cube is rebuilt.  Streamed cubes keep the
+ * x-contiguous copy only.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED,
+ * VR_ERR_OOM, VR_ERR_CUDA. */
+int vr_set_brick_layouts(vr_ctx *ctx, int cube_id, int mask);
 
 /* Transfer function (Section 2: value -> colour and opacity; Section 2.3: colour map sent by
  * the viewer).  rgba: n x 4 float32 non-premultiplied entries, 2 <= n <= 4096, host memory.
@@ -222,6 +259,57 @@ int vr_get_brick_grid(vr_ctx *ctx, int cube_id, int64_t nbricks[3], int *storage
  * memory.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_CUDA. */
 int vr_get_brick(vr_ctx *ctx, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2,
                  void *data);
+
+/* ----------------------------------------------------------------------------------------- */
+/* Serving: an interactive request loop with continuous batching                             */
+/* ----------------------------------------------------------------------------------------- */
+typedef struct {
+    int cube_id;
+    float view[16];              /* as vr_set_camera */
+    int proj;
+    float param;
+    int width, height;
+    int mode;                    /* as vr_set_render_params */
+    float step, ert_threshold;
+    const float *lut;            /* n x 4 host table, read when the request is admitted */
+    int nlut;
+    float vmin, vmax;
+    double arrival_ms;           /* arrival time, ms after the loop starts (non-decreasing) */
+    float *out;                  /* caller's frame buffer (device or pinned host memory) */
+    int out_where;               /* VR_DEVICE or VR_HOST */
+} vr_request;
+
+typedef struct {
+    int status;                  /* VR_OK or this request's error */
+    double admit_ms, done_ms;    /* ms after the loop starts */
+    double latency_ms;           /* completion - arrival */
+} vr_request_result;
+
+typedef struct {
+    int max_inflight;            /* frame slots (streams with their own scratch), 1..64 */
+} vr_serve_config;
+
+typedef struct {
+    int64_t completed, failed;
+    double wall_ms;              /* loop start to last completion */
+    double p50_ms, p99_ms, max_ms;  /* latency percentiles of the completed requests */
+    double frames_per_s;
+    int max_concurrent;          /* most frames in flight at once */
+} vr_serve_summary;
+
+/* Serves `n` requests that arrive at their arrival times (the paper's server answering render
+ * requests, Section 2.3, with many viewers): requests that have arrived are admitted, in
+ * arrival order, as soon as a frame slot is free and -- for streamed cubes -- the brick cache
+ * holds enough slots that no frame in flight needs for the bricks the request still lacks (a
+ * request needing more than the whole cache runs alone, in chunks).  Admitted frames run
+ * concurrently, one CUDA stream per slot; each result equals what vr_render_frame gives for
+ * the same request.  Blocks until every request has completed or failed.  res[i] receives
+ * request i's status and times; sum (nullable) the latency percentiles and throughput.
+ * Host outputs should be pinned (a pageable copy serialises the loop).  Errors: VR_ERR_ARG
+ * (null, max_inflight, unordered arrivals, request without table or output),
+ * VR_ERR_NOT_FOUND (cube), VR_ERR_STATE (some request failed: see res[i].status). */
+int vr_serve(vr_ctx *ctx, const vr_request *reqs, int n, const vr_serve_config *cfg,
+             vr_request_result *res, vr_serve_summary *sum);
 
 /* Name of a status code (static string). */
 const char *vr_error_string(int status);

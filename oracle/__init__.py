@@ -36,6 +36,7 @@ class Args(C.Structure):
         ("W", C.c_int32), ("H", C.c_int32), ("mode", C.c_int32), ("step", C.c_float),
         ("tau", C.c_float), ("bx", C.c_int64), ("by", C.c_int64), ("bz", C.c_int64),
         ("quant", C.c_int32), ("ghost", C.c_int32), ("nthreads", C.c_int32),
+        ("procedural", C.c_int32), ("proc_seed", C.c_uint64),
     ]
 
 
@@ -62,6 +63,12 @@ def lib():
                                           C.c_int64, C.c_int64, C.c_int64, C.c_int, C.c_int,
                                           C.c_void_p]
         L.orc_minmax.argtypes = [C.c_void_p, C.c_int64, P(C.c_float), P(C.c_float)]
+        L.orc_proc_voxel.argtypes = [C.c_uint64] + [C.c_int64] * 6
+        L.orc_proc_voxel.restype = C.c_float
+        L.orc_proc_noise.argtypes = [C.c_uint64] + [C.c_int64] * 5
+        L.orc_proc_noise.restype = C.c_double
+        L.orc_proc_region.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -70,13 +77,26 @@ MODES = {"dvr": 0, "mip": 1, "mip32": 2}
 QUANT = {"f32": 0, "f16": 1, "bf16": 2}
 
 
+class Procedural:
+    """The procedural cube of a seed and a size (voxels evaluated on demand)."""
+
+    def __init__(self, seed: int, shape_xyz):
+        self.seed = int(seed)
+        self.shape_xyz = tuple(int(v) for v in shape_xyz)
+
+
 def _args(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, quant="f32",
           ghost=1, nthreads=0):
-    cube = np.ascontiguousarray(cube, dtype=np.float32)
     lut = np.ascontiguousarray(lut, dtype=np.float32)
-    nz, ny, nx = cube.shape
     a = Args()
-    a.vox = cube.ctypes.data
+    if isinstance(cube, Procedural):
+        nx, ny, nz = cube.shape_xyz
+        a.vox = None
+        a.procedural, a.proc_seed = 1, cube.seed
+    else:
+        cube = np.ascontiguousarray(cube, dtype=np.float32)
+        nz, ny, nx = cube.shape
+        a.vox = cube.ctypes.data
     a.nx, a.ny, a.nz = nx, ny, nz
     a.lut = lut.ctypes.data
     a.nlut = lut.shape[0]
@@ -118,6 +138,26 @@ def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, q
         raise ValueError(f"orc_render failed ({rc})")
     del keep
     return (out if stride == 4 else out[:, 0]), flags, int(ns.value)
+
+
+def proc_region(seed, shape_xyz, lo, dim):
+    """Voxels [z][y][x] of the procedural cube in the box [lo, lo+dim) (coordinates clamped)."""
+    lo = np.ascontiguousarray(lo, dtype=np.int64)
+    dim = np.ascontiguousarray(dim, dtype=np.int64)
+    out = np.zeros((int(dim[2]), int(dim[1]), int(dim[0])), np.float32)
+    nx, ny, nz = shape_xyz
+    lib().orc_proc_region(int(seed), nx, ny, nz, lo.ctypes.data, dim.ctypes.data, out.ctypes.data)
+    return out
+
+
+def proc_noise(seed, shape_xyz, x, y, z) -> float:
+    nx, ny, nz = shape_xyz
+    return float(lib().orc_proc_noise(int(seed), nx, ny, int(x), int(y), int(z)))
+
+
+def proc_voxel(seed, shape_xyz, x, y, z) -> float:
+    nx, ny, nz = shape_xyz
+    return float(lib().orc_proc_voxel(int(seed), nx, ny, nz, int(x), int(y), int(z)))
 
 
 def render_grad(cube, lut, vrange, cam, gout, step=0.5, tau=0.99, brick=None, pix=None,

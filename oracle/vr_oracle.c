@@ -54,6 +54,8 @@ typedef struct {
     int32_t quant;                  /* 0 FP32 voxels, 1 FP16 bricks, 2 BF16 bricks */
     int32_t ghost;                  /* ghost width of the stored brick region */
     int32_t nthreads;
+    int32_t procedural;             /* 1: voxels come from the procedural cube (vox unused) */
+    uint64_t proc_seed;
 } orc_args;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -278,6 +280,126 @@ static int64_t owner_cell(const rayinfo *r, int ax, int64_t k) {
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Procedural cube (the out-of-core stand-in for cubes larger than HBM).  An input generator,   */
+/* not part of the method: defined here from its published parts, independently of the        */
+/* renderer's own copy.                                                                         */
+/*   SplitMix64 (Steele, Lea & Flood 2014): state += 0x9E3779B97F4A7C15, then the two          */
+/*   xor-shift-multiply rounds and a final xor-shift.                                           */
+/*   noise(x,y,z): c = (z*ny + y)*ceil(nx/2) + floor(x/2); h = SplitMix64 of the state         */
+/*   c ^ (seed * 0xD1B54A32D192ED03); u1 = (h>>40 + 1/2) 2^-24, u2 = ((h>>16) & 0xFFFFFF) 2^-24; */
+/*   Box-Muller: r = sqrt(-2 ln u1), even x -> r cos(2 pi u2), odd x -> r sin(2 pi u2).        */
+/*   sources: 4 per 256^3 cell q = (qz*ncy + qy)*ncx + qx, drawn from the SplitMix64 stream   */
+/*   seeded with seed ^ (q * 0x9E3779B97F4A7C15) ^ 0x632BE59BD9B4E019, six uniforms each       */
+/*   (top 53 bits): centre (q + u) 256, sigma_xy = 1 + 3u, sigma_z = sigma_xy (2 + 3u),        */
+/*   amplitude exp(ln 3 + (ln 100 - ln 3) u); a source adds amp exp(-r^2/2) to voxels with    */
+/*   |dx|,|dy| <= 4 sigma_xy and |dz| <= 4 sigma_z (d from the voxel centre).                  */
+/*   voxel = (float)(noise + the sources in increasing (q, k) order).                          */
+/* ------------------------------------------------------------------------------------------ */
+static uint64_t sm64_next(uint64_t *state) {
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+#define PROC_CELL 256
+#define PROC_K 4
+typedef struct { double cx, cy, cz, sxy, sz, amp; } psrc;
+
+static void proc_cell_sources(uint64_t seed, int64_t qx, int64_t qy, int64_t qz, int64_t ncx,
+                              int64_t ncy, psrc out[PROC_K]) {
+    uint64_t q = (uint64_t)((qz * ncy + qy) * ncx + qx);
+    uint64_t st = seed ^ (q * 0x9E3779B97F4A7C15ULL) ^ 0x632BE59BD9B4E019ULL;
+    for (int k = 0; k < PROC_K; ++k) {
+        double u[6];
+        for (int i = 0; i < 6; ++i) u[i] = (double)(sm64_next(&st) >> 11) * 0x1.0p-53;
+        out[k].cx = ((double)qx + u[0]) * PROC_CELL;
+        out[k].cy = ((double)qy + u[1]) * PROC_CELL;
+        out[k].cz = ((double)qz + u[2]) * PROC_CELL;
+        out[k].sxy = 1.0 + 3.0 * u[3];
+        out[k].sz = out[k].sxy * (2.0 + 3.0 * u[4]);
+        out[k].amp = exp(log(3.0) + (log(100.0) - log(3.0)) * u[5]);
+    }
+}
+
+static double proc_noise(uint64_t seed, int64_t nx, int64_t ny, int64_t x, int64_t y, int64_t z) {
+    uint64_t c = (uint64_t)((z * ny + y) * ((nx + 1) / 2) + (x >> 1));
+    uint64_t st = c ^ (seed * 0xD1B54A32D192ED03ULL);
+    uint64_t h = sm64_next(&st);
+    double u1 = ((double)(h >> 40) + 0.5) * 0x1.0p-24;   /* in (0, 1): r > 0, never -0 */
+    double u2 = (double)((h >> 16) & 0xFFFFFFULL) * 0x1.0p-24;
+    double r = sqrt(-2.0 * log(u1));
+    double th = 6.283185307179586 * u2;
+    return (x & 1) ? r * sin(th) : r * cos(th);
+}
+
+static double proc_source_term(const psrc *s, int64_t x, int64_t y, int64_t z) {
+    double dx = ((double)x + 0.5) - s->cx, dy = ((double)y + 0.5) - s->cy, dz = ((double)z + 0.5) - s->cz;
+    if (!(fabs(dx) <= 4.0 * s->sxy && fabs(dy) <= 4.0 * s->sxy && fabs(dz) <= 4.0 * s->sz)) return 0.0;
+    return s->amp * exp(-0.5 * (dx * dx / (s->sxy * s->sxy) + dy * dy / (s->sxy * s->sxy) +
+                                dz * dz / (s->sz * s->sz)));
+}
+
+/* One voxel of the procedural cube (the sources of the 27 cells around the voxel's cell, in
+ * increasing cell order; farther cells cannot reach it: 4 sigma <= 80 < 256). */
+float orc_proc_voxel(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int64_t x, int64_t y,
+                     int64_t z) {
+    /* per-thread copy of the last neighbourhood's sources (cells in increasing order) */
+    static __thread uint64_t c_seed;
+    static __thread int64_t c_key[6] = {-1, -1, -1, -1, -1, -1};
+    static __thread psrc c_src[27 * PROC_K];
+    static __thread int c_n;
+    int64_t ncx = (nx + PROC_CELL - 1) / PROC_CELL, ncy = (ny + PROC_CELL - 1) / PROC_CELL,
+            ncz = (nz + PROC_CELL - 1) / PROC_CELL;
+    int64_t qx = x / PROC_CELL, qy = y / PROC_CELL, qz = z / PROC_CELL;
+    if (c_seed != seed || c_key[0] != qx || c_key[1] != qy || c_key[2] != qz || c_key[3] != nx ||
+        c_key[4] != ny || c_key[5] != nz) {
+        c_n = 0;
+        for (int64_t cz = qz - 1; cz <= qz + 1; ++cz)
+            for (int64_t cy = qy - 1; cy <= qy + 1; ++cy)
+                for (int64_t cx = qx - 1; cx <= qx + 1; ++cx) {
+                    if (cx < 0 || cy < 0 || cz < 0 || cx >= ncx || cy >= ncy || cz >= ncz) continue;
+                    proc_cell_sources(seed, cx, cy, cz, ncx, ncy, &c_src[c_n]);
+                    c_n += PROC_K;
+                }
+        c_seed = seed;
+        c_key[0] = qx; c_key[1] = qy; c_key[2] = qz; c_key[3] = nx; c_key[4] = ny; c_key[5] = nz;
+    }
+    double v = proc_noise(seed, nx, ny, x, y, z);
+    for (int i = 0; i < c_n; ++i) v += proc_source_term(&c_src[i], x, y, z);
+    return (float)v;
+}
+
+double orc_proc_noise(uint64_t seed, int64_t nx, int64_t ny, int64_t x, int64_t y, int64_t z) {
+    return proc_noise(seed, nx, ny, x, y, z);
+}
+
+/* The voxels of the box [lo, lo + dim) with coordinates clamped to the cube, x fastest. */
+void orc_proc_region(uint64_t seed, int64_t nx, int64_t ny, int64_t nz, const int64_t lo[3],
+                     const int64_t dim[3], float *out) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t r = 0; r < dim[1] * dim[2]; ++r) {
+        int64_t y = lo[1] + r % dim[1], z = lo[2] + r / dim[1];
+        y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+        z = z < 0 ? 0 : (z >= nz ? nz - 1 : z);
+        for (int64_t i = 0; i < dim[0]; ++i) {
+            int64_t x = lo[0] + i;
+            x = x < 0 ? 0 : (x >= nx ? nx - 1 : x);
+            out[r * dim[0] + i] = orc_proc_voxel(seed, nx, ny, nz, x, y, z);
+        }
+    }
+}
+
+/* Voxel value at flat index idx of the cube described by a (array or procedural). */
+static float vox_at(const orc_args *a, int64_t idx) {
+    if (!a->procedural) return a->vox[idx];
+    int64_t x = idx % a->nx, y = (idx / a->nx) % a->ny, z = idx / (a->nx * a->ny);
+    return orc_proc_voxel(a->proc_seed, a->nx, a->ny, a->nz, x, y, z);
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Field evaluation                                                                           */
 /* ------------------------------------------------------------------------------------------ */
 typedef struct {
@@ -290,7 +412,7 @@ static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : 
 
 /* voxel value as seen from a brick (dequantised with the brick's exponent when quantised) */
 static double voxel_val(const orc_args *a, int64_t idx, int e) {
-    float v = a->vox[idx];
+    float v = vox_at(a, idx);
     if (a->quant == 0) return (double)v;
     return ldexp((double)quant_code(v, e, a->quant), e);
 }
@@ -342,7 +464,7 @@ static float sample32(const orc_args *a, const float o[3], const float d[3], int
     for (int cc = 0; cc < 8; ++cc) {
         int64_t idx = ((cc & 1) ? i1[0] : i0[0]) +
                       n[0] * (((cc & 2) ? i1[1] : i0[1]) + n[1] * ((cc & 4) ? i1[2] : i0[2]));
-        float v = a->vox[idx];
+        float v = vox_at(a, idx);
         c[cc] = a->quant ? quant_code(v, e, a->quant) : v;
     }
     float c00 = lerp32(c[0], c[1], f[0]), c10 = lerp32(c[2], c[3], f[0]);
@@ -459,7 +581,7 @@ static int64_t bufsize(const orc_args *a) {
 }
 
 static int32_t *make_exps(const orc_args *a) {
-    if (a->quant == 0) return NULL;
+    if (a->quant == 0 || a->procedural) return NULL;
     int64_t bx = a->bx > 0 ? a->bx : a->nx, by = a->by > 0 ? a->by : a->ny,
             bz = a->bz > 0 ? a->bz : a->nz;
     int64_t nb = ((a->nx + bx - 1) / bx) * ((a->ny + by - 1) / by) * ((a->nz + bz - 1) / bz);
@@ -475,6 +597,7 @@ static int32_t *make_exps(const orc_args *a) {
 int orc_render(const orc_args *a, const int64_t *pix, int64_t npix, double *out, uint8_t *flags,
                int64_t *nsamples) {
     if (a->nlut < 2 || a->W <= 0 || a->H <= 0 || !(a->step > 0.0f)) return -1;
+    if (a->procedural && a->quant) return -2;
     cam32 c;
     cam_setup(&c, a);
     int32_t *exps = make_exps(a);

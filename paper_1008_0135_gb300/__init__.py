@@ -114,6 +114,18 @@ class Context:
                "vr_load_cube")
         return cid.value
 
+    def load_cube_procedural(self, seed: int, shape_xyz) -> int:
+        """Streamed procedural cube (bricks generated on host threads, cached in HBM)."""
+        nx, ny, nz = shape_xyz
+        cid = C.c_int()
+        _check(self._L.vr_load_cube_procedural(self._h, int(seed), nx, ny, nz, C.byref(cid)),
+               "vr_load_cube_procedural")
+        return cid.value
+
+    def set_fault_injection(self, kind: int, after: int = 0):
+        _check(self._L.vr_set_fault_injection(self._h, int(kind), int(after)),
+               "vr_set_fault_injection")
+
     def update_cube(self, cube_id: int, voxels, stream=None):
         ptr, loc = _buffer(voxels)
         sh = _stream_handle(stream) if loc == VR_DEVICE else 0
@@ -132,6 +144,10 @@ class Context:
         bx, by, bz = brick
         _check(self._L.vr_set_bricking(self._h, cube_id, bx, by, bz, ghost, STORAGE[storage]),
                "vr_set_bricking")
+
+    def set_brick_layouts(self, cube_id: int, mask: int):
+        """Keep x- (1), y- (2), z-contiguous (4) copies of the bricks (bit 0 always kept)."""
+        _check(self._L.vr_set_brick_layouts(self._h, cube_id, int(mask)), "vr_set_brick_layouts")
 
     def brick_grid(self, cube_id: int):
         nb = (C.c_int64 * 3)()
@@ -200,6 +216,40 @@ class Context:
         _check(self._L.vr_render_backward(self._h, cube_id, grad_out.data_ptr(),
                                           grad_lut.data_ptr(), gv, _stream_handle(stream)),
                "vr_render_backward")
+
+    def serve(self, requests, max_inflight: int = 4):
+        """Runs the continuous-batching request loop (vr_serve).  ``requests``: dicts with cube,
+        cam (view/proj/param/W/H), mode, step, tau, lut (n x 4), vrange, arrival_ms and out (a
+        CUDA tensor or pinned host tensor), in arrival order.  Returns (results, summary)."""
+        n = len(requests)
+        arr = (_abi.VrRequest * max(n, 1))()
+        keep = []
+        for i, r in enumerate(requests):
+            q = arr[i]
+            q.cube_id = int(r["cube"])
+            view = np.ascontiguousarray(r["cam"]["view"], dtype=np.float32).reshape(16)
+            for j in range(16):
+                q.view[j] = float(view[j])
+            q.proj, q.param = int(r["cam"]["proj"]), float(r["cam"]["param"])
+            q.width, q.height = int(r["cam"]["W"]), int(r["cam"]["H"])
+            q.mode = MODES[r.get("mode", "dvr")]
+            q.step, q.ert_threshold = float(r.get("step", 0.5)), float(r.get("tau", 0.99))
+            lut = np.ascontiguousarray(r["lut"], dtype=np.float32)
+            keep.append(lut)
+            q.lut, q.nlut = lut.ctypes.data, lut.shape[0]
+            q.vmin, q.vmax = float(r["vrange"][0]), float(r["vrange"][1])
+            q.arrival_ms = float(r.get("arrival_ms", 0.0))
+            ptr, loc = _buffer(r["out"])
+            q.out, q.out_where = ptr, loc
+        cfg = _abi.VrServeConfig(int(max_inflight))
+        res = (_abi.VrRequestResult * max(n, 1))()
+        summ = _abi.VrServeSummary()
+        rc = self._L.vr_serve(self._h, arr, n, C.byref(cfg), res, C.byref(summ))
+        if rc not in (0, _abi.VR_ERR_STATE):
+            raise VrError(rc, "vr_serve")
+        results = [{k: getattr(res[i], k) for k, _ in _abi.VrRequestResult._fields_} for i in range(n)]
+        summary = {k: getattr(summ, k) for k, _ in _abi.VrServeSummary._fields_}
+        return results, summary
 
     def stats(self) -> dict:
         s = _abi.VrStats()

@@ -8,6 +8,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libvrcube.s
 
 VR_OK, VR_ERR_ARG, VR_ERR_OOM, VR_ERR_CUDA = 0, -1, -2, -3
 VR_ERR_TIMEOUT, VR_ERR_STATE, VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED = -4, -5, -6, -7
+VR_ERR_IO = -8
 VR_F32, VR_F16, VR_BF16 = 0, 1, 2
 VR_HOST, VR_DEVICE = 0, 1
 VR_ORTHO, VR_PERSP = 0, 1
@@ -24,16 +25,44 @@ class VrStats(C.Structure):
     ]
 
 
+class VrRequest(C.Structure):
+    _fields_ = [
+        ("cube_id", C.c_int), ("view", C.c_float * 16), ("proj", C.c_int), ("param", C.c_float),
+        ("width", C.c_int), ("height", C.c_int), ("mode", C.c_int), ("step", C.c_float),
+        ("ert_threshold", C.c_float), ("lut", C.c_void_p), ("nlut", C.c_int),
+        ("vmin", C.c_float), ("vmax", C.c_float), ("arrival_ms", C.c_double),
+        ("out", C.c_void_p), ("out_where", C.c_int),
+    ]
+
+
+class VrRequestResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("admit_ms", C.c_double), ("done_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class VrServeConfig(C.Structure):
+    _fields_ = [("max_inflight", C.c_int)]
+
+
+class VrServeSummary(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("wall_ms", C.c_double),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("frames_per_s", C.c_double), ("max_concurrent", C.c_int)]
+
+
 # name -> (restype, argtypes); every entry point declared in include/vrcube.h
 P, I, I64, F, VP = C.POINTER, C.c_int, C.c_int64, C.c_float, C.c_void_p
 SIGNATURES = {
     "vr_create": (I, [P(VP), I, C.c_size_t]),
     "vr_destroy": (None, [VP]),
     "vr_load_cube": (I, [VP, VP, I, I64, I64, I64, I, P(I64), P(I64), P(I)]),
+    "vr_load_cube_procedural": (I, [VP, C.c_uint64, I64, I64, I64, P(I)]),
+    "vr_set_fault_injection": (I, [VP, I, I64]),
     "vr_update_cube": (I, [VP, I, VP, I, VP]),
     "vr_free_cube": (I, [VP, I]),
     "vr_compute_minmax": (I, [VP, I, P(F), P(F)]),
     "vr_set_bricking": (I, [VP, I, I, I, I, I, I]),
+    "vr_set_brick_layouts": (I, [VP, I, I]),
     "vr_set_transfer_function": (I, [VP, VP, I, F, F]),
     "vr_set_camera": (I, [VP, VP, I, F, I, I]),
     "vr_set_render_params": (I, [VP, I, F, F]),
@@ -46,6 +75,8 @@ SIGNATURES = {
     "vr_reset_stats": (I, [VP]),
     "vr_get_brick_grid": (I, [VP, I, P(I64), P(I)]),
     "vr_get_brick": (I, [VP, I, I64, P(I), P(I), P(I), VP]),
+    "vr_serve": (I, [VP, P(VrRequest), I, P(VrServeConfig), P(VrRequestResult),
+                     P(VrServeSummary)]),
     "vr_error_string": (C.c_char_p, [I]),
     "vr_last_error_message": (C.c_char_p, []),
 }

@@ -14,116 +14,52 @@
 #include <string>
 #include <vector>
 
-#include "vr_internal.cuh"
-#include "../../include/vrcube.h"
+#include "vr_host.h"
 
 using namespace vr;
+using namespace vrh;
 
-namespace {
-
-thread_local std::string g_last_error;
-
-int cuda_fail(cudaError_t e, const char *where) {
-    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
-    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
-}
-int arg_fail(const char *what) {
-    g_last_error = what;
-    return VR_ERR_ARG;
-}
-
-#define CK(call)                                         \
-    do {                                                 \
-        cudaError_t e_ = (call);                         \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
-    } while (0)
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-struct Cube {
-    int64_t n[3] = {0, 0, 0};
-    float *d_src = nullptr;           // FP32 source voxels, x fastest
-    bool bricked = false;
-    int B[3] = {0, 0, 0};
-    int ghost = 1;
-    int storage = VR_F32;
-    int64_t nb[3] = {0, 0, 0};
-    std::vector<DrawBrick> tmpl;      // one record per brick (geometry, pool offsets, exponent)
-    DrawBrick *d_tmpl = nullptr;      // device copy used by the build kernels
-    void *d_pool = nullptr;
-    size_t pool_bytes = 0;
-    unsigned int *d_bs = nullptr;     // per-brick max |v| bits, then exponents (2 per brick)
-};
-
-template <typename T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t cap = 0;                   // elements
-};
-
-}  // namespace
-
-struct vr_ctx {
-    int device = 0;
-    cudaStream_t load_stream = nullptr;
-    std::map<int, Cube *> cubes;
-    int next_id = 1;
-    // transfer function (copied into every frame's upload)
-    std::vector<float4> lut;
-    float vmin = 0.0f, vmax = 1.0f;
-    bool tf_set = false;
-    // camera
-    Cam cam{};
-    bool cam_set = false;
-    // render parameters
-    int mode = VR_DVR;
-    float step = 0.5f;
-    float tau = 0.99f;
-    bool full_rect = false;
-    bool timing = false;
-    // frame scratch (reused; guarded by events)
-    char *h_stage = nullptr;
-    size_t h_cap = 0;
-    DevBuf<char> d_stage;
-    DevBuf<char> d_frags;             // bytes
-    DevBuf<float4> d_gfrag;
-    DevBuf<float> d_gpart;
-    DevBuf<float> d_out;
-    cudaEvent_t upload_done = nullptr, frame_done = nullptr;
-    bool frame_pending = false;
-    Counters *d_ctr = nullptr;
-    unsigned int *d_mm = nullptr;     // min/max scratch (2 ordered-bit words)
-    // statistics
-    int64_t frames = 0, fragments = 0, bricks_drawn = 0, timed_frames = 0;
-    double ms_raycast = 0, ms_composite = 0, ms_frame = 0;
-    std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::vector<cudaEvent_t>> ev_pending;
-    size_t cache_bytes = 0;
-};
-
-namespace {
+namespace vrh {
 
 int set_dev(vr_ctx *c) {
     CK(cudaSetDevice(c->device));
     return VR_OK;
 }
 
+void layout_strides(const int dim[3], int layout, int str[3]) {
+    // the contiguous axis first, then the other two in x, y, z order
+    int ord[3];
+    ord[0] = layout;
+    for (int a = 0, k = 1; a < 3; ++a)
+        if (a != layout) ord[k++] = a;
+    int s = 1;
+    for (int k = 0; k < 3; ++k) {
+        str[ord[k]] = s;
+        s *= dim[ord[k]];
+    }
+}
+
+FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
+    FrameLayout f{0, 0, kRcLong, kRcShort};
+    float best = -1.0f;
+    for (int i = 0; i < 2; ++i)              // image axis: camera right (row 0), up (row 1)
+        for (int a = 0; a < 3; ++a) {
+            if (!(cb->layouts & (1 << a))) continue;
+            const float sc = std::fabs(c->cam.R[3 * i + a]);
+            if (sc > best + 1e-6f) {
+                best = sc;
+                f.layout = a;
+                f.lanes_y = i;
+            }
+        }
+    f.tw = f.lanes_y ? kRcShort : kRcLong;
+    f.th = f.lanes_y ? kRcLong : kRcShort;
+    return f;
+}
+
 Cube *find_cube(vr_ctx *c, int id) {
     auto it = c->cubes.find(id);
     return it == c->cubes.end() ? nullptr : it->second;
-}
-
-template <typename T>
-int ensure(DevBuf<T> &b, size_t n, vr_ctx *c) {
-    if (b.cap >= n && b.p) return VR_OK;
-    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
-    size_t want = std::max(n, b.cap * 3 / 2);
-    if (b.p) CK(cudaFree(b.p));
-    b.p = nullptr;
-    b.cap = 0;
-    CK(cudaMalloc(&b.p, std::max<size_t>(want, 1) * sizeof(T)));
-    b.cap = want;
-    return VR_OK;
 }
 
 int ensure_host(vr_ctx *c, size_t bytes) {
@@ -140,14 +76,6 @@ int ensure_host(vr_ctx *c, size_t bytes) {
 // ---------------------------------------------------------------------------------------------
 // per-frame work-list
 // ---------------------------------------------------------------------------------------------
-struct WorkList {
-    std::vector<DrawBrick> db;
-    std::vector<TileItem> items;
-    std::vector<int> tile_start, tile_list;
-    long long frag_px = 0;
-    // offsets inside the staged upload
-    size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, bytes = 0;
-};
 
 // World position of the perspective eye in the renderer's FP32 arithmetic (R^T (0 - t)); every
 // perspective ray starts exactly there.
@@ -245,12 +173,15 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     wl.db.clear();
     wl.items.clear();
     wl.db.reserve(order.size());
+    const FrameLayout fl = frame_layout(c, cb);
     long long frag = 0;
     for (auto &o : order) {
         DrawBrick d = cand[o.second];
         d.frag_off = frag;
         frag += (long long)d.rect[2] * d.rect[3];
-        int tw = (d.rect[2] + kTile - 1) / kTile, th = (d.rect[3] + kTile - 1) / kTile;
+        if (!cb->loff.empty()) d.data_off = cb->loff[3 * (size_t)d.brick + fl.layout];
+        layout_strides(d.dim, fl.layout, d.str);
+        int tw = (d.rect[2] + fl.tw - 1) / fl.tw, th = (d.rect[3] + fl.th - 1) / fl.th;
         int di = (int)wl.db.size();
         for (int ty = 0; ty < th; ++ty)
             for (int tx = 0; tx < tw; ++tx) wl.items.push_back(TileItem{di, tx, ty});
@@ -299,6 +230,7 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     fc.mode = c->mode;
     fc.storage = cb->storage;
     fc.nx = (int)cb->n[0]; fc.ny = (int)cb->n[1]; fc.nz = (int)cb->n[2];
+    fc.lanes_y = frame_layout(c, cb).lanes_y;
     return fc;
 }
 
@@ -381,15 +313,24 @@ int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
     if (cb->storage != VR_F32)
         CK(launch_brick_maxabs(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs, s));
     int *d_exps = reinterpret_cast<int *>(cb->d_bs + nbr);
-    CK(launch_brick_build(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs,
-                          cb->storage, cb->d_pool, d_exps, s));
+    // one build per kept layout: the records carry that layout's offsets and strides
+    std::vector<DrawBrick> rec(cb->tmpl);
+    for (int a = 0; a < 3; ++a) {
+        if (!(cb->layouts & (1 << a))) continue;
+        for (int i = 0; i < nbr; ++i) {
+            rec[i].data_off = cb->loff[3 * (size_t)i + a];
+            layout_strides(rec[i].dim, a, rec[i].str);
+        }
+        CK(cudaMemcpyAsync(cb->d_tmpl, rec.data(), sizeof(DrawBrick) * nbr, cudaMemcpyHostToDevice, s));
+        CK(launch_brick_build(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs,
+                              cb->storage, cb->d_pool, d_exps, s));
+        CK(cudaStreamSynchronize(s));      // rec is rewritten for the next layout
+    }
     if (cb->storage != VR_F32) {
         std::vector<int> e(nbr);
         CK(cudaMemcpyAsync(e.data(), d_exps, sizeof(int) * nbr, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (int i = 0; i < nbr; ++i) cb->tmpl[i].exp2 = e[i];
-    } else {
-        CK(cudaStreamSynchronize(s));
     }
     return VR_OK;
 }
@@ -535,11 +476,12 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
     }
     // (key, candidate index) is a total order: the same order as a stable sort by key
     std::sort(keys, keys + nc, [](const Key &a, const Key &b) { return a.key != b.key ? a.key < b.key : a.idx < b.idx; });
+    const FrameLayout fl = frame_layout(c, cb);
     long long frag = 0, nitems = 0, nbin = 0;
     for (int i = 0; i < nc; ++i) {
         const DrawBrick &d = cand[keys[i].idx];
         frag += (long long)d.rect[2] * d.rect[3];
-        nitems += (long long)((d.rect[2] + kTile - 1) / kTile) * ((d.rect[3] + kTile - 1) / kTile);
+        nitems += (long long)((d.rect[2] + fl.tw - 1) / fl.tw) * ((d.rect[3] + fl.th - 1) / fl.th);
         nbin += (long long)((d.rect[0] + d.rect[2] - 1) / kTile - d.rect[0] / kTile + 1) *
                 ((d.rect[1] + d.rect[3] - 1) / kTile - d.rect[1] / kTile + 1);
     }
@@ -568,7 +510,9 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
         DrawBrick d = cand[keys[i].idx];
         d.frag_off = fo;
         fo += (long long)d.rect[2] * d.rect[3];
-        const int tw = (d.rect[2] + kTile - 1) / kTile, th = (d.rect[3] + kTile - 1) / kTile;
+        if (!cb->loff.empty()) d.data_off = cb->loff[3 * (size_t)d.brick + fl.layout];
+        layout_strides(d.dim, fl.layout, d.str);
+        const int tw = (d.rect[2] + fl.tw - 1) / fl.tw, th = (d.rect[3] + fl.th - 1) / fl.th;
         for (int ty = 0; ty < th; ++ty)
             for (int tx = 0; tx < tw; ++tx) items[it++] = TileItem{i, tx, ty};
         db[i] = d;
@@ -609,6 +553,7 @@ const char *vr_error_string(int status) {
         case VR_ERR_STATE: return "VR_ERR_STATE: call out of order";
         case VR_ERR_NOT_FOUND: return "VR_ERR_NOT_FOUND: unknown cube id";
         case VR_ERR_UNSUPPORTED: return "VR_ERR_UNSUPPORTED: unsupported combination";
+        case VR_ERR_IO: return "VR_ERR_IO: a brick source failed";
         default: return "unknown status";
     }
 }
@@ -645,6 +590,7 @@ void vr_destroy(vr_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
+    cache_destroy(c);
     for (auto &kv : c->cubes) free_cube(kv.second);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->d_stage.p) cudaFree(c->d_stage.p);
@@ -698,8 +644,32 @@ int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t n
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->load_stream);
     if (e != cudaSuccess) { free_cube(cb); return cuda_fail(e, "cudaMemcpy3D(cube)"); }
     int id = c->next_id++;
+    cb->id = id;
     c->cubes[id] = cb;
     *cube_id = id;
+    return VR_OK;
+}
+
+int vr_load_cube_procedural(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int *cube_id) {
+    if (!c || !cube_id) return arg_fail("null argument");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return arg_fail("non-positive size");
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return arg_fail("size too large");
+    Cube *cb = new (std::nothrow) Cube();
+    if (!cb) return VR_ERR_OOM;
+    cb->n[0] = nx; cb->n[1] = ny; cb->n[2] = nz;
+    cb->streamed = true;
+    cb->proc_seed = seed;
+    int id = c->next_id++;
+    cb->id = id;
+    c->cubes[id] = cb;
+    *cube_id = id;
+    return VR_OK;
+}
+
+int vr_set_fault_injection(vr_ctx *c, int kind, int64_t after) {
+    if (!c || kind < 0 || kind > 3) return arg_fail("bad fault injection");
+    c->fault_kind = kind;
+    c->fault_after = after;
     return VR_OK;
 }
 
@@ -708,6 +678,7 @@ int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *
     if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
+    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed cubes have no resident voxels");
     int rc = set_dev(c);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -725,6 +696,7 @@ int vr_free_cube(vr_ctx *c, int cube_id) {
     if (!cb) return VR_ERR_NOT_FOUND;
     set_dev(c);
     if (c->frame_pending) cudaEventSynchronize(c->frame_done);
+    cache_forget_cube(c, cube_id);
     free_cube(cb);
     c->cubes.erase(cube_id);
     return VR_OK;
@@ -734,6 +706,7 @@ int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
     if (!c || !vmin || !vmax) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
+    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "min/max of a streamed cube would generate all of it");
     int rc = set_dev(c);
     if (rc) return rc;
     unsigned int init[2] = {0xffffffffu, 0u}, res[2];
@@ -785,14 +758,40 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
             d.dim[a] = (int)(hi - lo + 2 * ghost);
         }
         d.brick = (int)bi;
-        d.data_off = (long long)off;
         const size_t elems = (size_t)d.dim[0] * d.dim[1] * d.dim[2];
         d.bytes = (long long)(elems * esz);
-        off = align_up(off + elems, 64);
+        layout_strides(d.dim, 0, d.str);
     }
+    // the pool: one copy of every brick per kept layout (x-contiguous first)
+    const int layouts = cb->streamed ? 1 : cb->layouts;
+    std::vector<long long> loff((size_t)nbr * 3, -1);
+    for (int a = 0; a < 3; ++a) {
+        if (!(layouts & (1 << a))) continue;
+        for (int64_t bi = 0; bi < nbr; ++bi) {
+            loff[3 * bi + a] = (long long)off;
+            off = align_up(off + (size_t)t[bi].dim[0] * t[bi].dim[1] * t[bi].dim[2], 64);
+        }
+    }
+    for (int64_t bi = 0; bi < nbr; ++bi) t[bi].data_off = loff[3 * bi];
     if (cb->d_pool) { cudaFree(cb->d_pool); cb->d_pool = nullptr; }
     if (cb->d_tmpl) { cudaFree(cb->d_tmpl); cb->d_tmpl = nullptr; }
     cb->bricked = false;
+    if (cb->streamed) {                // bricks are produced on demand into the cache
+        cache_forget_cube(c, cube_id);
+        const size_t slot = cache_slot_bytes(c);
+        if (slot) {
+            size_t mx = 0;
+            for (auto &b : t) mx = std::max(mx, (size_t)b.bytes);
+            if (mx > slot) return fail(VR_ERR_UNSUPPORTED, "bricks larger than the cache's slots");
+        }
+        cb->tmpl = std::move(t);
+        cb->loff.clear();
+        for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
+        cb->ghost = ghost;
+        cb->storage = storage;
+        cb->bricked = true;
+        return VR_OK;
+    }
     CK(cudaMalloc(&cb->d_pool, std::max<size_t>(off * esz, 16)));
     cb->pool_bytes = off * esz;
     CK(cudaMalloc(&cb->d_tmpl, sizeof(DrawBrick) * nbr));
@@ -800,12 +799,25 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     if (cb->d_bs) { cudaFree(cb->d_bs); cb->d_bs = nullptr; }
     CK(cudaMalloc(&cb->d_bs, sizeof(unsigned int) * 2 * nbr));
     cb->tmpl = std::move(t);
+    cb->loff = std::move(loff);
     for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
     cb->ghost = ghost;
     cb->storage = storage;
     if ((rc = build_bricks(c, cb, c->load_stream)) != VR_OK) return rc;
     cb->bricked = true;
     return VR_OK;
+}
+
+int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (mask < 1 || mask > 7 || !(mask & 1)) return arg_fail("layout mask must be 1..7 and keep bit 0 (x contiguous)");
+    if (cb->streamed && mask != 1) return fail(VR_ERR_UNSUPPORTED, "streamed bricks are stored x-contiguous only");
+    if (cb->layouts == mask) return VR_OK;
+    cb->layouts = mask;
+    if (!cb->bricked || cb->streamed) return VR_OK;
+    return vr_set_bricking(c, cube_id, cb->B[0], cb->B[1], cb->B[2], cb->ghost, cb->storage);
 }
 
 int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
@@ -879,15 +891,14 @@ int vr_set_full_rect(vr_ctx *c, int full) {
     return VR_OK;
 }
 
-int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
-    if (!c || !out) return arg_fail("null argument");
-    if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
-    Cube *cb = find_cube(c, cube_id);
-    if (!cb) return VR_ERR_NOT_FOUND;
-    int rc = check_ready(c, cb);
-    if (rc) return rc;
-    if ((rc = set_dev(c)) != VR_OK) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+namespace vrh {
+
+// One frame of cube `cb` with the context's current table, camera and parameters.
+__attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
+    int rc;
+    if (cb->streamed) return render_streamed(c, cb, out, out_where, s);
     const FrameConsts fc = make_consts(c, cb);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
@@ -924,8 +935,23 @@ int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *str
     c->frames++;
     c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)wl.db.size();
-    if (out_where == VR_HOST) CK(cudaStreamSynchronize(s));
+    if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
     return VR_OK;
+}
+
+}  // namespace vrh
+
+extern "C" {
+
+int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
+    if (!c || !out) return arg_fail("null argument");
+    if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    return render_frame_impl(c, cb, out, out_where, static_cast<cudaStream_t>(stream));
 }
 
 int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,
@@ -935,8 +961,8 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     if (!cb) return VR_ERR_NOT_FOUND;
     int rc = check_ready(c, cb);
     if (rc) return rc;
-    if (c->mode != VR_DVR || cb->storage != VR_F32) {
-        g_last_error = "backward needs DVR mode and FP32 bricks";
+    if (c->mode != VR_DVR || cb->storage != VR_F32 || cb->streamed) {
+        g_last_error = "backward needs DVR mode and resident FP32 bricks";
         return VR_ERR_UNSUPPORTED;
     }
     if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
@@ -991,6 +1017,7 @@ int vr_get_stats(vr_ctx *c, vr_stats *st) {
     st->ms_composite = c->ms_composite;
     st->ms_frame = c->ms_frame;
     st->timed_frames = c->timed_frames;
+    cache_stats(c, st);
     return VR_OK;
 }
 
@@ -1003,6 +1030,7 @@ int vr_reset_stats(vr_ctx *c) {
     CK(cudaMemset(c->d_ctr, 0, sizeof(Counters)));
     c->frames = c->fragments = c->bricks_drawn = c->timed_frames = 0;
     c->ms_raycast = c->ms_composite = c->ms_frame = 0;
+    cache_reset_stats(c);
     return VR_OK;
 }
 
@@ -1027,6 +1055,7 @@ int vr_get_brick(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3],
     const DrawBrick &b = cb->tmpl[brick];
     for (int a = 0; a < 3; ++a) { dims[a] = b.dim[a]; org[a] = b.org[a]; }
     *exp2 = b.exp2;
+    if (cb->streamed) return data ? streamed_brick(cb, brick, data, exp2) : streamed_exp(cb, brick, exp2);
     if (data) {
         const size_t esz = cb->storage == VR_F32 ? 4 : 2;
         CK(cudaMemcpy(data, static_cast<char *>(cb->d_pool) + b.data_off * esz, (size_t)b.bytes, cudaMemcpyDeviceToHost));
@@ -1040,6 +1069,7 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return arg_fail("out must be 16-byte aligned device memory");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
+    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed cubes need the brick cache");
     int rc = check_ready(c, cb);
     if (rc) return rc;
     if ((rc = set_dev(c)) != VR_OK) return rc;

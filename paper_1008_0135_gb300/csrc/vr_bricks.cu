@@ -75,15 +75,17 @@ __global__ void k_brick_build(const float *__restrict__ cube, int nx, int ny, in
         int ly = r % dy, lz = r / dy;
         int gy = clampi(b.org[1] + ly, 0, ny - 1), gz = clampi(b.org[2] + lz, 0, nz - 1);
         const float *src = cube + ((long long)gz * ny + gy) * nx;
-        long long dst = b.data_off + (long long)r * dx;
+        // the brick's layout decides the strides (x need not be the contiguous axis)
+        const long long dst = b.data_off + (long long)ly * b.str[1] + (long long)lz * b.str[2];
         for (int lx = threadIdx.x; lx < dx; lx += blockDim.x) {
             float v = __ldg(src + clampi(b.org[0] + lx, 0, nx - 1));
+            const long long o = dst + (long long)lx * b.str[0];
             if (S == 0) {
-                static_cast<float *>(pool)[dst + lx] = v;
+                static_cast<float *>(pool)[o] = v;
             } else if (S == 1) {
-                static_cast<__half *>(pool)[dst + lx] = __float2half_rn(ldexpf(v, -e));
+                static_cast<__half *>(pool)[o] = __float2half_rn(ldexpf(v, -e));
             } else {
-                static_cast<__nv_bfloat16 *>(pool)[dst + lx] = __float2bfloat16_rn(ldexpf(v, -e));
+                static_cast<__nv_bfloat16 *>(pool)[o] = __float2bfloat16_rn(ldexpf(v, -e));
             }
         }
     }

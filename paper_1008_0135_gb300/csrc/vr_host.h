@@ -1,0 +1,182 @@
+// vr_host.h -- host-side state of libvrcube.so shared by its translation units (context, cubes,
+// per-frame work-lists, error reporting).  Not part of the public ABI (include/vrcube.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "vr_internal.cuh"
+#include "../../include/vrcube.h"
+
+namespace vrh {
+
+using namespace vr;
+
+// Detail of the last failure on this thread (vr_last_error_message).
+inline thread_local std::string g_last_error;
+
+inline int cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? VR_ERR_OOM : VR_ERR_CUDA;
+}
+inline int arg_fail(const char *what) {
+    g_last_error = what;
+    return VR_ERR_ARG;
+}
+inline int fail(int status, const std::string &what) {
+    g_last_error = what;
+    return status;
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return vrh::cuda_fail(e_, #call); \
+    } while (0)
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct BrickCache;   // HBM brick cache of streamed cubes (vr_residency.cu)
+
+struct Cube {
+    int64_t n[3] = {0, 0, 0};
+    float *d_src = nullptr;           // FP32 source voxels, x fastest (resident cubes)
+    bool bricked = false;
+    int B[3] = {0, 0, 0};
+    int ghost = 1;
+    int storage = VR_F32;
+    int64_t nb[3] = {0, 0, 0};
+    std::vector<DrawBrick> tmpl;      // one record per brick (geometry, pool offsets, exponent)
+    DrawBrick *d_tmpl = nullptr;      // device copy used by the build kernels
+    void *d_pool = nullptr;
+    size_t pool_bytes = 0;
+    unsigned int *d_bs = nullptr;     // per-brick max |v| bits, then exponents (2 per brick)
+    // brick layouts kept in the pool: bit a = a copy whose axis a is contiguous (x always kept)
+    int layouts = 1;
+    std::vector<long long> loff;      // element offset of brick b in layout a: loff[3 b + a]
+    // streamed cubes: bricks are produced on the host and cached in HBM on demand
+    bool streamed = false;
+    uint64_t proc_seed = 0;           // procedural cube: generator seed
+    int id = 0;
+};
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;                   // elements
+};
+
+struct WorkList {
+    std::vector<DrawBrick> db;
+    std::vector<TileItem> items;
+    std::vector<int> tile_start, tile_list;
+    long long frag_px = 0;
+    // offsets inside the staged upload
+    size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, bytes = 0;
+};
+
+}  // namespace vrh
+
+struct vr_ctx {
+    int device = 0;
+    cudaStream_t load_stream = nullptr;
+    std::map<int, vrh::Cube *> cubes;
+    int next_id = 1;
+    // transfer function (copied into every frame's upload)
+    std::vector<float4> lut;
+    float vmin = 0.0f, vmax = 1.0f;
+    bool tf_set = false;
+    // camera
+    vr::Cam cam{};
+    bool cam_set = false;
+    // render parameters
+    int mode = VR_DVR;
+    float step = 0.5f;
+    float tau = 0.99f;
+    bool full_rect = false;
+    bool timing = false;
+    // frame scratch (reused; guarded by events)
+    char *h_stage = nullptr;
+    size_t h_cap = 0;
+    vrh::DevBuf<char> d_stage;
+    vrh::DevBuf<char> d_frags;        // bytes
+    vrh::DevBuf<float4> d_gfrag;
+    vrh::DevBuf<float> d_gpart;
+    vrh::DevBuf<float> d_out;
+    cudaEvent_t upload_done = nullptr, frame_done = nullptr;
+    bool frame_pending = false;
+    vr::Counters *d_ctr = nullptr;
+    unsigned int *d_mm = nullptr;     // min/max scratch (2 ordered-bit words)
+    // statistics
+    int64_t frames = 0, fragments = 0, bricks_drawn = 0, timed_frames = 0;
+    double ms_raycast = 0, ms_composite = 0, ms_frame = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::vector<cudaEvent_t>> ev_pending;
+    // streamed cubes
+    size_t cache_bytes = 0;
+    vrh::BrickCache *cache = nullptr;
+    bool async_host_out = false;      // serving slots: no host sync after a VR_HOST copy
+    int fault_kind = 0;               // host-side fault injection (tests)
+    int64_t fault_after = -1;
+};
+
+namespace vrh {
+
+// Per-frame choice of brick layout and warp orientation: the stored layout whose contiguous
+// world axis is most aligned with an image axis, and warps running along that image axis, so
+// the 32 rays of a warp gather from neighbouring addresses.
+struct FrameLayout {
+    int layout;                       // contiguous world axis of the chosen copy (0 x, 1 y, 2 z)
+    int lanes_y;                      // warps along image y (1) or image x (0)
+    int tw, th;                       // ray-cast tile size in pixels
+};
+FrameLayout frame_layout(const vr_ctx *c, const Cube *cb);
+void layout_strides(const int dim[3], int layout, int str[3]);
+
+int set_dev(vr_ctx *c);
+Cube *find_cube(vr_ctx *c, int id);
+int ensure_host(vr_ctx *c, size_t bytes);
+void eye_f32(const Cam &c, float o[3]);
+void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl);
+FrameConsts make_consts(vr_ctx *c, Cube *cb);
+int timing_events(vr_ctx *c, cudaEvent_t ev[4]);
+int collect_timing(vr_ctx *c);
+int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t ev0);
+int check_ready(vr_ctx *c, Cube *cb);
+int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s);
+int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s);
+void free_cube(Cube *cb);
+
+template <typename T>
+int ensure(DevBuf<T> &b, size_t n, vr_ctx *c) {
+    if (b.cap >= n && b.p) return VR_OK;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    size_t want = n > b.cap * 3 / 2 ? n : b.cap * 3 / 2;
+    if (b.p) CK(cudaFree(b.p));
+    b.p = nullptr;
+    b.cap = 0;
+    CK(cudaMalloc(&b.p, (want > 0 ? want : 1) * sizeof(T)));
+    b.cap = want;
+    return VR_OK;
+}
+
+// residency (vr_residency.cu)
+int cache_create(vr_ctx *c);
+void cache_destroy(vr_ctx *c);
+int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s);
+void cache_stats(vr_ctx *c, vr_stats *st);
+void cache_reset_stats(vr_ctx *c);
+void cache_forget_cube(vr_ctx *c, int cube_id);
+int streamed_brick(Cube *cb, int64_t brick, void *data, int *exp2);
+size_t cache_slot_bytes(vr_ctx *c);   // 0 until the cache has been sized
+// admission accounting of the serving loop: bricks of a work-list not yet resident and the
+// cache slots no in-flight frame holds (VR_ERR_TIMEOUT while another frame is making bricks
+// resident), and holding / releasing a frame's bricks (false if busy and !wait)
+int cache_missing(vr_ctx *c, Cube *cb, const WorkList &wl, int64_t *missing, int64_t *free_slots);
+bool cache_hold(vr_ctx *c, Cube *cb, const std::vector<int64_t> &bricks, int delta, bool wait);
+int streamed_exp(Cube *cb, int64_t brick, int *exp2);
+
+}  // namespace vrh

@@ -9,7 +9,9 @@
 
 namespace vr {
 
-constexpr int kTile = 16;          // ray-cast work item: 16x16 pixels of one brick's rectangle
+constexpr int kTile = 16;          // compositing: 16x16 screen tiles
+constexpr int kRcLong = 32;        // ray-cast work item: 32x8 (or 8x32) pixels of a rectangle,
+constexpr int kRcShort = 8;        // one warp per 32-pixel row (or column)
 constexpr int kMaxLut = 4096;      // transfer-function entries (float4 each) held in shared memory
 
 // Camera constants in the FP32 decision arithmetic (computed once per frame on the host).
@@ -31,6 +33,8 @@ struct FrameConsts {
     int mode;                      // 0 DVR, 1 MIP
     int storage;                   // 0 f32, 1 f16, 2 bf16
     int nx, ny, nz;                // cube size
+    int lanes_y;                   // 0: a warp's 32 lanes run along image x (tiles 32x8);
+                                   // 1: along image y (tiles 8x32)
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -39,6 +43,7 @@ struct DrawBrick {
     float org_c[3];                // stored origin + 0.5: local stored coordinate = p - org_c
     int org[3];                    // global voxel index of stored element (0,0,0)
     int dim[3];                    // stored dimensions (core + 2 ghost)
+    int str[3];                    // element strides of x, y, z in the stored array (layout)
     int exp2;                      // power-of-two scale exponent (0 for f32)
     int rect[4];                   // x0, y0, w, h of the rendering rectangle (pixels)
     int brick;                     // brick index in the cube's grid

@@ -110,7 +110,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // operation is an explicit intrinsic (no contraction), so the forward kernel and the adjoint's
 // replay of a ray produce bit-identical values.
 struct DvrSample {
-    int i0;                 // stored index of the lower stencil corner
+    int ix, iy, iz;         // lower stencil corner (stored indices)
     float fx, fy, fz;       // trilinear fractions
     float u;                // unclamped table coordinate (v - vmin) / (vmax - vmin)
     int li;                 // table interval
@@ -158,24 +158,29 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
     o.a = __fmaf_rn(o.lf, __fsub_rn(o.L1.w, o.L0.w), o.L0.w);
 }
 
+// Strides of x, y, z in the stored brick (its layout: any axis may be the contiguous one).
+struct Strides {
+    int x, y, z;
+};
+
 template <int S>
-__device__ __forceinline__ void fetch8(const void *src, int i0, int dx, int dxy, float v[8]) {
-    v[0] = ldv<S>(src, i0);            v[1] = ldv<S>(src, i0 + 1);
-    v[2] = ldv<S>(src, i0 + dx);       v[3] = ldv<S>(src, i0 + dx + 1);
-    v[4] = ldv<S>(src, i0 + dxy);      v[5] = ldv<S>(src, i0 + dxy + 1);
-    v[6] = ldv<S>(src, i0 + dxy + dx); v[7] = ldv<S>(src, i0 + dxy + dx + 1);
+__device__ __forceinline__ void fetch8(const void *src, int i0, const Strides &t, float v[8]) {
+    v[0] = ldv<S>(src, i0);             v[1] = ldv<S>(src, i0 + t.x);
+    v[2] = ldv<S>(src, i0 + t.y);       v[3] = ldv<S>(src, i0 + t.y + t.x);
+    v[4] = ldv<S>(src, i0 + t.z);       v[5] = ldv<S>(src, i0 + t.z + t.x);
+    v[6] = ldv<S>(src, i0 + t.z + t.y); v[7] = ldv<S>(src, i0 + t.z + t.y + t.x);
 }
 
 template <int S>
-__device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int mx, int my, int mz,
+__device__ __forceinline__ void dvr_sample(const void *src, const Strides &t, int mx, int my, int mz,
                                            float scale, float x, float y, float z, float vmin,
                                            float inv_range, float lutmax, int lmax,
                                            const float4 *s_lut, DvrSample &o) {
     Cell c;
     cell_of(x, y, z, mx, my, mz, c);
-    o.i0 = c.ix + dx * c.iy + dxy * c.iz;
+    o.ix = c.ix; o.iy = c.iy; o.iz = c.iz;
     float v[8];
-    fetch8<S>(src, o.i0, dx, dxy, v);
+    fetch8<S>(src, c.ix * t.x + c.iy * t.y + c.iz * t.z, t, v);
     interp_tf(v, c, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, o);
 }
 
@@ -184,7 +189,7 @@ __device__ __forceinline__ void dvr_sample(const void *src, int dx, int dxy, int
 // gathers only the others; any larger jump reloads all 8.  `need` bit c marks corner c as
 // still to be gathered; shifting the values shifts their bits too.
 template <int S>
-__device__ __forceinline__ void fetch8_cached(const void *src, int dx, int dxy, const Cell &c,
+__device__ __forceinline__ void fetch8_cached(const void *src, const Strides &t, const Cell &c,
                                               int &px, int &py, int &pz, float v[8]) {
     const int ddx = c.ix - px, ddy = c.iy - py, ddz = c.iz - pz;
     unsigned need = 0u;
@@ -214,15 +219,15 @@ __device__ __forceinline__ void fetch8_cached(const void *src, int dx, int dxy, 
         }
     }
     px = c.ix; py = c.iy; pz = c.iz;
-    const int i0 = c.ix + dx * c.iy + dxy * c.iz;
+    const int i0 = c.ix * t.x + c.iy * t.y + c.iz * t.z;
     if (need & 0x01u) v[0] = ldv<S>(src, i0);
-    if (need & 0x02u) v[1] = ldv<S>(src, i0 + 1);
-    if (need & 0x04u) v[2] = ldv<S>(src, i0 + dx);
-    if (need & 0x08u) v[3] = ldv<S>(src, i0 + dx + 1);
-    if (need & 0x10u) v[4] = ldv<S>(src, i0 + dxy);
-    if (need & 0x20u) v[5] = ldv<S>(src, i0 + dxy + 1);
-    if (need & 0x40u) v[6] = ldv<S>(src, i0 + dxy + dx);
-    if (need & 0x80u) v[7] = ldv<S>(src, i0 + dxy + dx + 1);
+    if (need & 0x02u) v[1] = ldv<S>(src, i0 + t.x);
+    if (need & 0x04u) v[2] = ldv<S>(src, i0 + t.y);
+    if (need & 0x08u) v[3] = ldv<S>(src, i0 + t.y + t.x);
+    if (need & 0x10u) v[4] = ldv<S>(src, i0 + t.z);
+    if (need & 0x20u) v[5] = ldv<S>(src, i0 + t.z + t.x);
+    if (need & 0x40u) v[6] = ldv<S>(src, i0 + t.z + t.y);
+    if (need & 0x80u) v[7] = ldv<S>(src, i0 + t.z + t.y + t.x);
 }
 
 // Front-to-back "over" of one sample into (c, T): c += T a rgb, T *= 1 - a.
@@ -250,8 +255,9 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
     const TileItem it = items[blockIdx.x];
     const DrawBrick &b = dbs[it.db];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rx = it.tx * kTile + (warp & 1) * 8 + (lane & 7);
-    const int ry = it.ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
+    const int rx = fc.lanes_y ? it.tx * kRcShort + warp : it.tx * kRcLong + lane;
+    const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + warp;
     const int rw = b.rect[2];
     int nsamp = 0;
     if (rx < rw && ry < b.rect[3]) {
@@ -262,7 +268,7 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
         const long long fi = b.frag_off + (long long)ry * rw + rx;
         const void *src = static_cast<const char *>(pool) +
                           b.data_off * (S == 0 ? 4 : 2);
-        const int dx = b.dim[0], dxy = b.dim[0] * b.dim[1];
+        const Strides st{b.str[0], b.str[1], b.str[2]};
         const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
         const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
         if (MODE == 0) {
@@ -283,7 +289,7 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     Cell cl;
                     cell_of(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
                             mx, my, mz, cl);
-                    fetch8_cached<S>(src, dx, dxy, cl, px, py, pz, v);
+                    fetch8_cached<S>(src, st, cl, px, py, pz, v);
                     DvrSample sm;
                     interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
                     over(sm, c0, c1, c2, T);
@@ -306,11 +312,11 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     const int ix = clampi((int)flx - b.org[0], 0, mx);
                     const int iy = clampi((int)fly - b.org[1], 0, my);
                     const int iz = clampi((int)flz - b.org[2], 0, mz);
-                    const int i0 = ix + dx * iy + dxy * iz;
-                    const float c00 = lerp_rn(ldv<S>(src, i0), ldv<S>(src, i0 + 1), fx);
-                    const float c10 = lerp_rn(ldv<S>(src, i0 + dx), ldv<S>(src, i0 + dx + 1), fx);
-                    const float c01 = lerp_rn(ldv<S>(src, i0 + dxy), ldv<S>(src, i0 + dxy + 1), fx);
-                    const float c11 = lerp_rn(ldv<S>(src, i0 + dxy + dx), ldv<S>(src, i0 + dxy + dx + 1), fx);
+                    const int i0 = ix * st.x + iy * st.y + iz * st.z;
+                    const float c00 = lerp_rn(ldv<S>(src, i0), ldv<S>(src, i0 + st.x), fx);
+                    const float c10 = lerp_rn(ldv<S>(src, i0 + st.y), ldv<S>(src, i0 + st.y + st.x), fx);
+                    const float c01 = lerp_rn(ldv<S>(src, i0 + st.z), ldv<S>(src, i0 + st.z + st.x), fx);
+                    const float c11 = lerp_rn(ldv<S>(src, i0 + st.z + st.y), ldv<S>(src, i0 + st.z + st.y + st.x), fx);
                     float v = lerp_rn(lerp_rn(c00, c10, fy), lerp_rn(c01, c11, fy), fz);
                     if (S != 0) v = __fmul_rn(v, scale);
                     m = v > m ? v : m;
@@ -441,8 +447,9 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
     const TileItem it = items[blockIdx.x];
     const DrawBrick &b = dbs[it.db];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rx = it.tx * kTile + (warp & 1) * 8 + (lane & 7);
-    const int ry = it.ty * kTile + (warp >> 1) * 4 + (lane >> 3);
+    // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
+    const int rx = fc.lanes_y ? it.tx * kRcShort + warp : it.tx * kRcLong + lane;
+    const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + warp;
     if (rx < b.rect[2] && ry < b.rect[3]) {
         const long long fi = b.frag_off + (long long)ry * b.rect[2] + rx;
         const float4 gf = gfrag[fi];
@@ -453,7 +460,7 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
             box_krange(o, d, b.lo, b.hi, fc.step, k0, k1)) {
             const float4 fr = frags[fi];
             const float *src = pool + b.data_off;
-            const int dx = b.dim[0], dy = b.dim[1], dxy = b.dim[0] * b.dim[1];
+            const Strides st{b.str[0], b.str[1], b.str[2]};
             const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
             const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
             const float qy = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
@@ -464,7 +471,7 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
             for (int j = 0; j < n; ++j) {
                 const float tj = __fmul_rn((float)j, fc.step);
                 DvrSample sm;
-                dvr_sample<0>(src, dx, dxy, mx, my, mz, 1.0f, __fmaf_rn(tj, d[0], qx),
+                dvr_sample<0>(src, st, mx, my, mz, 1.0f, __fmaf_rn(tj, d[0], qx),
                               __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), fc.vmin,
                               fc.inv_range, fc.lutmax, fc.nlut - 2, s_lut, sm);
                 const float Tb = T;
@@ -491,8 +498,7 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                                      gb * (sm.L1.z - sm.L0.z) + ga * (sm.L1.w - sm.L0.w);
                     const float gv = gx * dxdv;
                     if (gv != 0.0f) {
-                        const int iz = sm.i0 / dxy, rem = sm.i0 - iz * dxy;
-                        const int iy = rem / dx, ix = rem - iy * dx;
+                        const int ix = sm.ix, iy = sm.iy, iz = sm.iz;
                         const int gx0 = clampi(b.org[0] + ix, 0, fc.nx - 1), gx1 = clampi(b.org[0] + ix + 1, 0, fc.nx - 1);
                         const int gy0 = clampi(b.org[1] + iy, 0, fc.ny - 1), gy1 = clampi(b.org[1] + iy + 1, 0, fc.ny - 1);
                         const int gz0 = clampi(b.org[2] + iz, 0, fc.nz - 1), gz1 = clampi(b.org[2] + iz + 1, 0, fc.nz - 1);
@@ -511,7 +517,6 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                 }
                 if (T <= fc.thr) break;
             }
-            (void)dy;
         }
     }
     __syncthreads();

@@ -37,9 +37,11 @@ def _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau):
     return glut.cpu().numpy().astype(np.float64), gvox.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("seed,tau", [(0, 0.95), (1, 1.0), (2, 0.9)])
-def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau):
+@pytest.mark.parametrize("seed,tau,layouts", [(0, 0.95, 1), (1, 1.0, 1), (2, 0.9, 7)])
+def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau, layouts):
     rng, cube, lut, cam, cid = _setup(ctx, seed)
+    if layouts != 1:
+        ctx.set_brick_layouts(cid, layouts)
     vr = (-3.0, 8.0)
     step = 0.5
     gout = rng.standard_normal((cam["W"] * cam["H"], 4))

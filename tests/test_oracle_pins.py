@@ -386,3 +386,32 @@ def test_gradient_matches_finite_differences(orc):
         if abs(fd - gvox[z, y, x]) <= 1e-5 + 1e-4 * abs(fd):
             checked += 1
     assert checked >= 20
+
+
+# ---------------------------------------------------------------------------------------------
+# procedural cube (input generator of the out-of-core tests)
+# ---------------------------------------------------------------------------------------------
+SEED = 4
+
+
+def test_procedural_noise_is_standard_normal(orc):
+    """Box-Muller of SplitMix64 hashes gives independent standard normals."""
+    stats = pytest.importorskip("scipy.stats")
+    vals = np.array([orc.proc_noise(SEED, (4096, 4096, 4800), x, 17, 33) for x in range(20000)])
+    assert abs(vals.mean()) < 0.03 and abs(vals.std() - 1.0) < 0.02
+    assert stats.kstest(vals, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(vals[0::2], vals[1::2])[0, 1]) < 0.03   # Box-Muller pairs independent
+
+
+def test_procedural_sources_add_gaussian_bumps(orc):
+    """Away from its noise, a voxel holds the sum of the sources' Gaussian terms: the brightest
+    voxel of a region exceeds what N(0,1) noise reaches there, and the field minus its noise is
+    non-negative (sources only add)."""
+    shape = (700, 600, 520)
+    lo, dim = (0, 0, 0), (64, 64, 64)
+    v = orc.proc_region(SEED, shape, lo, (700, 600, 4))
+    z, y, x = np.unravel_index(np.argmax(v), v.shape)
+    noise = orc.proc_noise(SEED, shape, x, y, z)
+    assert v[z, y, x] - noise > 2.5                 # amplitudes are at least 3
+    for (xx, yy, zz) in [(5, 7, 1), (300, 200, 2), (699, 599, 3)]:
+        assert v[zz, yy, xx] - orc.proc_noise(SEED, shape, xx, yy, zz) >= -1e-6

@@ -277,3 +277,37 @@ def test_16bit_bricks(ctx, orc, storage):
                            quant=storage)
     assert np.array_equal(m, m32.astype(np.float32))
     ctx.free_cube(cid)
+
+
+# ---------------------------------------------------------------------------------------------
+# brick layouts: the gathered addresses change, the arithmetic does not
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_brick_layouts_give_identical_images(ctx, orc, storage):
+    cube = synth.pr1_cube(seed=2)
+    lut = synth.ramp_lut(alpha=0.5)
+    one = ctx.load_cube(cube)
+    ctx.set_bricking(one, (24, 32, 20), 1, storage)
+    many = ctx.load_cube(cube)
+    ctx.set_brick_layouts(many, 7)
+    ctx.set_bricking(many, (24, 32, 20), 1, storage)
+    rng = np.random.default_rng(21)
+    cams = [synth.pr1_camera(W=100, H=90), synth.random_camera(rng, (64, 64, 64), 90, 110),
+            dict(view=synth.look_at((32.0, 150.0, 30.0), (32.0, 32.0, 32.0), up=(1.0, 0.0, 0.0)),
+                 proj=1, param=0.9, W=64, H=80),       # up along x: warps along image y = world x
+            dict(view=synth.look_at((150.0, 30.0, 32.0), (32.0, 32.0, 32.0), up=(0.0, 0.0, 1.0)),
+                 proj=0, param=100.0, W=72, H=64)]     # up along z
+    for cam in cams:
+        for mode in ("dvr", "mip"):
+            a = render(ctx, one, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            b = render(ctx, many, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            assert np.array_equal(a, b)
+        if storage == "f32":
+            ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99,
+                                       brick=(24, 32, 20))
+            compare_dvr(render(ctx, many, lut, (-3, 20), cam, step=0.5, tau=0.99), ref, flags, 0.99)
+    dims, org, e, data = ctx.get_brick(many, 3)
+    dims1, org1, e1, data1 = ctx.get_brick(one, 3)
+    assert np.array_equal(data, data1)                  # get_brick returns the x-contiguous copy
+    ctx.free_cube(one)
+    ctx.free_cube(many)

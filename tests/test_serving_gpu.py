@@ -1,0 +1,105 @@
+"""Continuous-batching serving loop: requests for several cubes at different resolutions arrive
+over time, overlap on the device, and each result equals the frame rendered alone."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def world():
+    import paper_1008_0135_gb300 as P
+    c = gpu_ctx()
+    c.close()
+    ctx = P.Context(0, cache_bytes=24 * 130 ** 3 * 4)
+    a = ctx.load_cube(synth.pr1_cube(seed=0))
+    ctx.set_bricking(a, (32, 32, 32), 1, "f32")
+    b = ctx.load_cube(synth.pr1_cube(seed=3, n=96))
+    ctx.set_bricking(b, (32, 48, 40), 1, "f16")
+    v = ctx.load_cube_procedural(4, (300, 270, 260))
+    ctx.set_bricking(v, (128, 128, 128), 1, "f32")
+    yield ctx, {"pr1": (a, (64, 64, 64)), "b96": (b, (96, 96, 96)), "proc": (v, (300, 270, 260))}
+    ctx.close()
+
+
+def _requests(cubes, n, rate_hz, seed, device):
+    import torch
+    rng = np.random.default_rng(seed)
+    arrivals = synth.poisson_arrivals(seed, rate_hz, n) * 1e3
+    luts = [synth.ramp_lut(alpha=0.3), synth.random_lut(7, n=64, alpha_max=0.2)]
+    names = list(cubes)
+    reqs = []
+    for i in range(n):
+        name = names[int(rng.integers(0, len(names)))]
+        cid, shape = cubes[name]
+        W, H = [(128, 128), (96, 80), (160, 120)][int(rng.integers(0, 3))]
+        cam = synth.random_camera(rng, shape, W, H)
+        mode = "mip" if rng.uniform() < 0.25 else "dvr"
+        out = torch.full((H, W, 4) if mode == "dvr" else (H, W), float("nan"), device=device)
+        reqs.append(dict(cube=cid, cam=cam, mode=mode, step=0.5, tau=0.99,
+                         lut=luts[int(rng.integers(0, 2))], vrange=(-3.0, 20.0),
+                         arrival_ms=float(arrivals[i]), out=out))
+    return reqs
+
+
+def _alone(ctx, r):
+    ctx.set_transfer_function(r["lut"], *r["vrange"])
+    ctx.set_camera_dict(r["cam"])
+    ctx.set_render_params(r["mode"], r["step"], r["tau"])
+    return ctx.render_frame(r["cube"])
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(world):
+    import torch
+    ctx, cubes = world
+    reqs = _requests(cubes, 40, 400.0, 11, "cuda")
+    results, summary = ctx.serve(reqs, max_inflight=6)
+    torch.cuda.synchronize()
+    assert all(r["status"] == 0 for r in results), results
+    assert summary["completed"] == 40 and summary["failed"] == 0
+    assert summary["p99_ms"] >= summary["p50_ms"] > 0
+    for r, res in zip(reqs, results):
+        assert res["admit_ms"] >= r["arrival_ms"] - 1e-6
+        assert res["latency_ms"] > 0
+        alone = _alone(ctx, r)
+        assert torch.equal(r["out"], alone)
+
+
+def test_burst_overlaps_on_the_device(world):
+    import torch
+    ctx, cubes = world
+    reqs = _requests({"pr1": cubes["pr1"], "b96": cubes["b96"]}, 24, 1e9, 12, "cuda")
+    for r in reqs:
+        r["arrival_ms"] = 0.0
+    results, summary = ctx.serve(reqs, max_inflight=8)
+    torch.cuda.synchronize()
+    assert summary["failed"] == 0
+    assert summary["max_concurrent"] >= 4
+    for r in reqs:
+        assert torch.equal(r["out"], _alone(ctx, r))
+
+
+def test_pinned_host_outputs_and_errors(world):
+    import torch
+    ctx, cubes = world
+    reqs = _requests({"pr1": cubes["pr1"]}, 6, 1000.0, 13, "cuda")
+    for r in reqs:
+        r["out"] = torch.zeros(r["out"].shape, pin_memory=True)
+    bad = dict(reqs[0])
+    bad["cam"] = dict(bad["cam"], W=0)                 # an invalid request fails alone
+    bad["out"] = torch.zeros(4, pin_memory=True)
+    reqs.insert(3, bad)
+    for i in range(1, len(reqs)):
+        reqs[i]["arrival_ms"] = max(reqs[i]["arrival_ms"], reqs[i - 1]["arrival_ms"])
+    results, summary = ctx.serve(reqs, max_inflight=3)
+    assert results[3]["status"] == -1 and summary["failed"] == 1
+    for i, (r, res) in enumerate(zip(reqs, results)):
+        if i == 3:
+            continue
+        assert res["status"] == 0
+        assert torch.equal(r["out"].cuda(), _alone(ctx, r))
