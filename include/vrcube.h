@@ -131,8 +131,8 @@ int vr_set_fault_injection(vr_ctx *ctx, int kind, int64_t after);
 
 /* Replaces the voxels of a loaded cube (same dimensions, VR_F32, host or device) and rebuilds
  * its bricks with the current bricking.  For fitting loops that update the voxels.  The copy
- * and the rebuild are ordered on `cuda_stream`.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND,
- * VR_ERR_CUDA. */
+ * and the rebuild are ordered on `cuda_stream` and the call returns once they are done.
+ * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_CUDA. */
 int vr_update_cube(vr_ctx *ctx, int cube_id, const void *voxels, int where, void *cuda_stream);
 
 /* Frees a cube and its bricks.  Errors: VR_ERR_NOT_FOUND. */
@@ -238,8 +238,10 @@ int vr_render_backward(vr_ctx *ctx, int cube_id, const float *grad_out, float *g
 int vr_set_timing(vr_ctx *ctx, int enable);
 
 /* Debug switch: full_rect = 1 launches every brick over the whole frame instead of its
- * rendering rectangle (Section 2.4 states the rectangle does not change the image; tests use
- * this to check it).  Errors: VR_ERR_ARG. */
+ * rendering rectangle, and keeps bricks that empty-space skipping would drop (a DVR brick whose
+ * stored value range maps only to table entries of zero opacity adds exactly nothing).
+ * Section 2.4 states such optimisation steps do not change the image; tests use this switch to
+ * check it.  Errors: VR_ERR_ARG. */
 int vr_set_full_rect(vr_ctx *ctx, int full_rect);
 
 /* Copies the counters (waits for the context's outstanding frames).  Errors: VR_ERR_ARG. */

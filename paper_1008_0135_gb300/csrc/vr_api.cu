@@ -40,7 +40,7 @@ void layout_strides(const int dim[3], int layout, int str[3]) {
 }
 
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
-    FrameLayout f{0, 0, kRcLong, kRcShort};
+    FrameLayout f{0, 0, kRcLong, kRcShort, 0.0f};
     float best = -1.0f;
     for (int i = 0; i < 2; ++i)              // image axis: camera right (row 0), up (row 1)
         for (int a = 0; a < 3; ++a) {
@@ -54,7 +54,35 @@ FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
         }
     f.tw = f.lanes_y ? kRcShort : kRcLong;
     f.th = f.lanes_y ? kRcLong : kRcShort;
+    f.align = best;
     return f;
+}
+
+void alpha_prefix(const vr_ctx *c, std::vector<int> &pre) {
+    pre.assign(c->lut.size() + 1, 0);
+    for (size_t i = 0; i < c->lut.size(); ++i) pre[i + 1] = pre[i] + (c->lut[i].w != 0.0f ? 1 : 0);
+}
+
+// A DVR sample's opacity interpolates table entries floor(x) and floor(x)+1 at
+// x = clamp((v - vmin)/(vmax - vmin), 0, 1) (n - 1), and a trilinear value lies within its
+// stencil's range, so a brick whose stored values map only to entries of zero opacity adds
+// exactly nothing (every sample has a = 0: colour += T*0, T *= 1).  The range is widened for
+// the FP32 rounding of the mapping and, for 16-bit bricks, for the rounding of the codes.
+bool skip_brick(const vr_ctx *c, const Cube *cb, size_t b, const int *pre) {
+    if (c->mode != VR_DVR || c->full_rect || b >= cb->vlo.size()) return false;
+    const double lo = cb->vlo[b], hi = cb->vhi[b];
+    if (!(lo <= hi)) return false;
+    const double mag = std::max({1.0, std::fabs(lo), std::fabs(hi)});
+    const double widen = mag * (cb->storage == VR_F32 ? 1e-5 : 1.0 / 64.0);
+    const double n1 = (double)c->lut.size() - 1.0;
+    auto x_of = [&](double v) {
+        const double u = (v - (double)c->vmin) / ((double)c->vmax - (double)c->vmin);
+        return std::min(std::max(u, 0.0), 1.0) * n1;
+    };
+    const double xl = x_of(lo - widen) - 1e-3, xh = x_of(hi + widen) + 1e-3;
+    const long i0 = std::max(0L, (long)std::floor(xl));
+    const long i1 = std::min((long)n1, (long)std::floor(xh) + 1);
+    return pre[i1 + 1] - pre[i0] == 0;
 }
 
 Cube *find_cube(vr_ctx *c, int id) {
@@ -116,8 +144,11 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     std::vector<std::pair<long long, int>> order;
     std::vector<DrawBrick> cand;
     cand.reserve(cb->tmpl.size());
+    std::vector<int> apre;
+    alpha_prefix(c, apre);
     for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) {
         const DrawBrick &b = cb->tmpl[bi];
+        if (skip_brick(c, cb, bi, apre.data())) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
         bool cull = false;
         if (!c->full_rect) {
@@ -230,7 +261,11 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     fc.mode = c->mode;
     fc.storage = cb->storage;
     fc.nx = (int)cb->n[0]; fc.ny = (int)cb->n[1]; fc.nz = (int)cb->n[2];
-    fc.lanes_y = frame_layout(c, cb).lanes_y;
+    const FrameLayout fl = frame_layout(c, cb);
+    fc.lanes_y = fl.lanes_y;
+    // with a warp's rays along the contiguous axis its gathers are nearly coalesced and the
+    // stencil cache's bookkeeping costs more than it saves; with a poor alignment it pays
+    fc.stencil_cache = fl.align < 0.9f ? 1 : 0;
     return fc;
 }
 
@@ -309,9 +344,29 @@ int check_ready(vr_ctx *c, Cube *cb) {
 
 int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
     const int nbr = (int)cb->tmpl.size();
-    if (cb->storage != VR_F32) CK(cudaMemsetAsync(cb->d_bs, 0, sizeof(unsigned int) * nbr, s));
-    if (cb->storage != VR_F32)
-        CK(launch_brick_maxabs(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs, s));
+    unsigned int *d_range = cb->d_bs + 2 * (size_t)nbr;
+    // max |v| (16-bit scales) and the value range (empty-space skipping) of every brick
+    CK(cudaMemsetAsync(cb->d_bs, 0, sizeof(unsigned int) * nbr, s));
+    {
+        std::vector<unsigned int> init(2 * (size_t)nbr);
+        for (int i = 0; i < nbr; ++i) { init[2 * i] = 0xffffffffu; init[2 * i + 1] = 0u; }
+        CK(cudaMemcpyAsync(d_range, init.data(), sizeof(unsigned int) * 2 * nbr, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(cb->d_tmpl, cb->tmpl.data(), sizeof(DrawBrick) * nbr, cudaMemcpyHostToDevice, s));
+        CK(launch_brick_maxabs(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs,
+                               d_range, s));
+        std::vector<unsigned int> r(2 * (size_t)nbr);
+        CK(cudaMemcpyAsync(r.data(), d_range, sizeof(unsigned int) * 2 * nbr, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        auto dec = [](unsigned int e) {
+            unsigned int b = (e & 0x80000000u) ? (e & 0x7fffffffu) : ~e;
+            float f;
+            std::memcpy(&f, &b, 4);
+            return f;
+        };
+        cb->vlo.resize(nbr);
+        cb->vhi.resize(nbr);
+        for (int i = 0; i < nbr; ++i) { cb->vlo[i] = dec(r[2 * i]); cb->vhi[i] = dec(r[2 * i + 1]); }
+    }
     int *d_exps = reinterpret_cast<int *>(cb->d_bs + nbr);
     // one build per kept layout: the records carry that layout's offsets and strides
     std::vector<DrawBrick> rec(cb->tmpl);
@@ -422,8 +477,13 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
     Key *keys = reinterpret_cast<Key *>(tmp + align_up(nb * sizeof(DrawBrick), 256));
     int *cursor = reinterpret_cast<int *>(tmp + align_up(nb * sizeof(DrawBrick), 256) + align_up(nb * sizeof(Key), 256));
     int nc = 0;
+    // the table has at most 4096 entries: its zero-opacity prefix fits on the stack
+    int apre_buf[kMaxLut + 1];
+    apre_buf[0] = 0;
+    for (size_t i = 0; i < c->lut.size(); ++i) apre_buf[i + 1] = apre_buf[i] + (c->lut[i].w != 0.0f ? 1 : 0);
     for (size_t bi = 0; bi < nb; ++bi) {
         const DrawBrick &b = cb->tmpl[bi];
+        if (skip_brick(c, cb, bi, apre_buf)) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
         bool cull = false;
         if (!c->full_rect) {
@@ -797,7 +857,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     CK(cudaMalloc(&cb->d_tmpl, sizeof(DrawBrick) * nbr));
     CK(cudaMemcpy(cb->d_tmpl, t.data(), sizeof(DrawBrick) * nbr, cudaMemcpyHostToDevice));
     if (cb->d_bs) { cudaFree(cb->d_bs); cb->d_bs = nullptr; }
-    CK(cudaMalloc(&cb->d_bs, sizeof(unsigned int) * 2 * nbr));
+    CK(cudaMalloc(&cb->d_bs, sizeof(unsigned int) * 4 * nbr));
     cb->tmpl = std::move(t);
     cb->loff = std::move(loff);
     for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }

@@ -34,22 +34,37 @@ __global__ void k_minmax(const float *__restrict__ v, long long n, unsigned int 
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// max |v| over each brick's stored region (core + ghost, clamped to the cube).
+// max |v|, min and max over each brick's stored region (core + ghost, clamped to the cube):
+// maxbits[b] (float bits), and range[2b], range[2b+1] (order-preserving encodings).
 __global__ void k_brick_maxabs(const float *__restrict__ cube, int nx, int ny, int nz,
-                               const DrawBrick *__restrict__ bricks, unsigned int *maxbits) {
+                               const DrawBrick *__restrict__ bricks, unsigned int *maxbits,
+                               unsigned int *range) {
     const DrawBrick &b = bricks[blockIdx.y];
     int x0 = max(b.org[0], 0), x1 = min(b.org[0] + b.dim[0], nx);
     int y0 = max(b.org[1], 0), y1 = min(b.org[1] + b.dim[1], ny);
     int z0 = max(b.org[2], 0), z1 = min(b.org[2] + b.dim[2], nz);
     int rows = (y1 - y0) * (z1 - z0);
-    float m = 0.0f;
+    float m = 0.0f, lo = INFINITY, hi = -INFINITY;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         int y = y0 + r % (y1 - y0), z = z0 + r / (y1 - y0);
         const float *row = cube + ((long long)z * ny + y) * nx;
-        for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) m = fmaxf(m, fabsf(__ldg(row + x)));
+        for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+            const float v = __ldg(row + x);
+            m = fmaxf(m, fabsf(v));
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(maxbits + blockIdx.y, __float_as_uint(m));
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(maxbits + blockIdx.y, __float_as_uint(m));
+        atomicMin(range + 2 * blockIdx.y, f2ord(lo));
+        atomicMax(range + 2 * blockIdx.y + 1, f2ord(hi));
+    }
 }
 
 // ceil(log2 m) from the exact frexp decomposition; FP16 keeps 14 bits of headroom below 2^15.
@@ -101,10 +116,11 @@ cudaError_t launch_minmax(const float *v, long long n, unsigned int *enc, cudaSt
 }
 
 cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
-                                int nbricks, unsigned int *maxbits, cudaStream_t s) {
+                                int nbricks, unsigned int *maxbits, unsigned int *range,
+                                cudaStream_t s) {
     if (nbricks <= 0) return cudaSuccess;
     dim3 grid(64, nbricks);
-    k_brick_maxabs<<<grid, 256, 0, s>>>(cube, nx, ny, nz, bricks, maxbits);
+    k_brick_maxabs<<<grid, 256, 0, s>>>(cube, nx, ny, nz, bricks, maxbits, range);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,8 @@ struct Cube {
     DrawBrick *d_tmpl = nullptr;      // device copy used by the build kernels
     void *d_pool = nullptr;
     size_t pool_bytes = 0;
-    unsigned int *d_bs = nullptr;     // per-brick max |v| bits, then exponents (2 per brick)
+    unsigned int *d_bs = nullptr;     // per brick: max |v| bits, exponent, min, max (4 words)
+    std::vector<float> vlo, vhi;      // per-brick value range of the stored region
     // brick layouts kept in the pool: bit a = a copy whose axis a is contiguous (x always kept)
     int layouts = 1;
     std::vector<long long> loff;      // element offset of brick b in layout a: loff[3 b + a]
@@ -132,8 +133,13 @@ struct FrameLayout {
     int layout;                       // contiguous world axis of the chosen copy (0 x, 1 y, 2 z)
     int lanes_y;                      // warps along image y (1) or image x (0)
     int tw, th;                       // ray-cast tile size in pixels
+    float align;                      // |cos| between that image axis and the contiguous axis
 };
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb);
+// Empty-space skipping: prefix counts of table entries with non-zero opacity, and whether a
+// brick's value range reaches only zero-opacity entries (its fragment would be a no-op).
+void alpha_prefix(const vr_ctx *c, std::vector<int> &pre);
+bool skip_brick(const vr_ctx *c, const Cube *cb, size_t b, const int *pre);
 void layout_strides(const int dim[3], int layout, int str[3]);
 
 int set_dev(vr_ctx *c);

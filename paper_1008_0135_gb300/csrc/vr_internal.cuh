@@ -35,6 +35,7 @@ struct FrameConsts {
     int nx, ny, nz;                // cube size
     int lanes_y;                   // 0: a warp's 32 lanes run along image x (tiles 32x8);
                                    // 1: along image y (tiles 8x32)
+    int stencil_cache;             // 1: rays reuse shared stencil corners (poorly aligned layout)
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -71,7 +72,8 @@ struct Counters {                  // device-side cumulative counters
 cudaError_t launch_minmax(const float *v, long long n, unsigned int *enc_minmax,
                           cudaStream_t s);
 cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
-                                int nbricks, unsigned int *maxbits, cudaStream_t s);
+                                int nbricks, unsigned int *maxbits, unsigned int *range,
+                                cudaStream_t s);
 cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                int nbricks, const unsigned int *maxbits, int storage, void *pool,
                                int *exps, cudaStream_t s);

@@ -242,7 +242,10 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 // ----------------------------------------------------------------------------------------------
 // ray cast: one CTA = 16x16 pixels of one brick's rendering rectangle; warp = 8x4 pixels
 // ----------------------------------------------------------------------------------------------
-template <int S, int MODE>
+// CACHE: a ray keeps the stencil corners its next cell shares with the last one (fewer
+// gathers, more instructions; pays off when a warp's gathers scatter over many cache lines);
+// otherwise all eight corners are gathered for every sample.
+template <int S, int MODE, bool CACHE>
 __global__ void __launch_bounds__(256)
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
@@ -289,7 +292,10 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     Cell cl;
                     cell_of(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
                             mx, my, mz, cl);
-                    fetch8_cached<S>(src, st, cl, px, py, pz, v);
+                    if (CACHE)
+                        fetch8_cached<S>(src, st, cl, px, py, pz, v);
+                    else
+                        fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
                     DvrSample sm;
                     interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
                     over(sm, c0, c1, c2, T);
@@ -534,19 +540,27 @@ __global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts,
     glut[i] = (float)acc;
 }
 
-template <int S, int MODE>
+template <int S, int MODE, bool CACHE>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = MODE == 0 ? sizeof(float4) * (size_t)fc.nlut : 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(sizeof(float4) * kMaxLut));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_raycast<S, MODE><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
+    k_raycast<S, MODE, CACHE><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
     return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
+                        int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
+    if (fc.mode != 0) return launch_rc<S, 1, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.stencil_cache) return launch_rc<S, 0, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    return launch_rc<S, 0, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
 }
 
 }  // namespace
@@ -555,14 +569,9 @@ cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawB
                            const TileItem *items, int nitems, const void *pool, void *frags,
                            Counters *ctr, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    if (fc.mode == 0) {
-        if (fc.storage == 0) return launch_rc<0, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-        if (fc.storage == 1) return launch_rc<1, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-        return launch_rc<2, 0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    }
-    if (fc.storage == 0) return launch_rc<0, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    if (fc.storage == 1) return launch_rc<1, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    return launch_rc<2, 1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.storage == 0) return launch_rc_s<0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.storage == 1) return launch_rc_s<1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    return launch_rc_s<2>(fc, lut, db, items, nitems, pool, frags, ctr, s);
 }
 
 cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,

@@ -311,3 +311,32 @@ def test_brick_layouts_give_identical_images(ctx, orc, storage):
     assert np.array_equal(data, data1)                  # get_brick returns the x-contiguous copy
     ctx.free_cube(one)
     ctx.free_cube(many)
+
+
+# ---------------------------------------------------------------------------------------------
+# empty-space skipping (a noise-suppressing table: zero opacity below a threshold)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_empty_space_skipping_is_exact(ctx, orc, storage):
+    cube = synth.pr1_cube(seed=0)
+    lut = synth.ramp_lut(alpha=0.6)
+    x = np.linspace(-3, 20, 256)
+    lut[x < 4.0, 3] = 0.0                     # bricks of pure N(0,1) noise become invisible
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (16, 16, 16), 1, storage)
+    cam = synth.pr1_camera()
+    ctx.reset_stats()
+    a = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    skipped = ctx.stats()["bricks_drawn"]
+    ctx.reset_stats()
+    b = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99, full_rect=True)
+    full = ctx.stats()["bricks_drawn"]
+    assert full == 64 and skipped < full          # some bricks were dropped ...
+    assert np.array_equal(a, b)                   # ... without changing a single bit
+    if storage == "f32":
+        ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(16, 16, 16))
+        compare_dvr(a, ref, flags, 0.99)
+    m1 = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)
+    m2 = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5, full_rect=True)
+    assert np.array_equal(m1, m2)                 # MIP never skips
+    ctx.free_cube(cid)
