@@ -14,6 +14,21 @@
 #include <math.h>
 #include "vr_internal.cuh"
 
+// Tuning knobs of the ray-cast kernel (build-time): unroll factor of the sample loop, and the
+// blocks per SM the register allocation must allow (0: no constraint).
+#ifndef VR_SAMPLE_UNROLL
+#define VR_SAMPLE_UNROLL 2
+#endif
+#ifndef VR_RAYCAST_MIN_BLOCKS
+#define VR_RAYCAST_MIN_BLOCKS 0
+#endif
+constexpr int kSampleUnroll = VR_SAMPLE_UNROLL;
+#if VR_RAYCAST_MIN_BLOCKS > 0
+#define VR_RAYCAST_BOUNDS __launch_bounds__(256, VR_RAYCAST_MIN_BLOCKS)
+#else
+#define VR_RAYCAST_BOUNDS __launch_bounds__(256)
+#endif
+
 namespace vr {
 namespace {
 
@@ -115,7 +130,7 @@ struct DvrSample {
     float u;                // unclamped table coordinate (v - vmin) / (vmax - vmin)
     int li;                 // table interval
     float lf;               // fraction inside the interval
-    float4 L0, L1;          // the interval's two entries
+    float4 L0, D;           // the interval's first entry and the difference to the next
     float r, g, b, a;       // interpolated colour and opacity
 };
 
@@ -126,10 +141,15 @@ struct Cell {
     float fx, fy, fz;
 };
 
+template <bool CLAMP = true>
 __device__ __forceinline__ void cell_of(float x, float y, float z, int mx, int my, int mz, Cell &c) {
     const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
     c.fx = __fsub_rn(x, flx); c.fy = __fsub_rn(y, fly); c.fz = __fsub_rn(z, flz);
-    c.ix = clampi((int)flx, 0, mx); c.iy = clampi((int)fly, 0, my); c.iz = clampi((int)flz, 0, mz);
+    if (CLAMP) {
+        c.ix = clampi((int)flx, 0, mx); c.iy = clampi((int)fly, 0, my); c.iz = clampi((int)flz, 0, mz);
+    } else {                          // caller has shown every index of the segment is in range
+        c.ix = (int)flx; c.iy = (int)fly; c.iz = (int)flz;
+    }
 }
 
 // Trilinear value from the 8 corners v[x + 2y + 4z], then the table lookup.
@@ -150,12 +170,24 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
     const float xl = __fmul_rn(uc, lutmax);
     o.li = min((int)xl, lmax);
     o.lf = __fsub_rn(xl, (float)o.li);
-    o.L0 = s_lut[o.li];
-    o.L1 = s_lut[o.li + 1];
-    o.r = __fmaf_rn(o.lf, __fsub_rn(o.L1.x, o.L0.x), o.L0.x);
-    o.g = __fmaf_rn(o.lf, __fsub_rn(o.L1.y, o.L0.y), o.L0.y);
-    o.b = __fmaf_rn(o.lf, __fsub_rn(o.L1.z, o.L0.z), o.L0.z);
-    o.a = __fmaf_rn(o.lf, __fsub_rn(o.L1.w, o.L0.w), o.L0.w);
+    o.L0 = s_lut[2 * o.li];
+    o.D = s_lut[2 * o.li + 1];
+    o.r = __fmaf_rn(o.lf, o.D.x, o.L0.x);
+    o.g = __fmaf_rn(o.lf, o.D.y, o.L0.y);
+    o.b = __fmaf_rn(o.lf, o.D.z, o.L0.z);
+    o.a = __fmaf_rn(o.lf, o.D.w, o.L0.w);
+}
+
+// The table in shared memory as (entry i, entry i+1 - entry i) pairs: the differences are the
+// same IEEE subtractions a lookup would do, made once per block instead of once per sample.
+__device__ __forceinline__ void load_table(const float4 *__restrict__ lut, int n, float4 *s) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 a = lut[i];
+        const float4 b = i + 1 < n ? lut[i + 1] : a;
+        s[2 * i] = a;
+        s[2 * i + 1] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z),
+                                   __fsub_rn(b.w, a.w));
+    }
 }
 
 // Strides of x, y, z in the stored brick (its layout: any axis may be the contiguous one).
@@ -242,17 +274,47 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 // ----------------------------------------------------------------------------------------------
 // ray cast: one CTA = 16x16 pixels of one brick's rendering rectangle; warp = 8x4 pixels
 // ----------------------------------------------------------------------------------------------
+// One brick segment of a ray: n lattice samples from the anchor q, composited front to back
+// until the segment's transmittance reaches the threshold.  Returns the samples composited.
+template <int S, bool CACHE, bool CLAMP>
+__device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, int mx, int my, int mz,
+                                           float scale, float qx, float qy, float qz, const float d[3],
+                                           int n, const FrameConsts &fc, const float4 *s_lut,
+                                           float &c0, float &c1, float &c2, float &T) {
+    const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
+    const int lmax = fc.nlut - 2;
+    int px = -4, py = -4, pz = -4;        // no cell cached yet
+    float v[8];
+    int j = 0;
+#pragma unroll kSampleUnroll
+    for (; j < n; ++j) {
+        const float tj = __fmul_rn((float)j, fc.step);
+        Cell cl;
+        cell_of<CLAMP>(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
+                       mx, my, mz, cl);
+        if (CACHE)
+            fetch8_cached<S>(src, st, cl, px, py, pz, v);
+        else
+            fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
+        DvrSample sm;
+        interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
+        over(sm, c0, c1, c2, T);
+        if (T <= thr) return j + 1;
+    }
+    return j;
+}
+
 // CACHE: a ray keeps the stencil corners its next cell shares with the last one (fewer
 // gathers, more instructions; pays off when a warp's gathers scatter over many cache lines);
 // otherwise all eight corners are gathered for every sample.
 template <int S, int MODE, bool CACHE>
-__global__ void __launch_bounds__(256)
+__global__ void VR_RAYCAST_BOUNDS
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
           Counters *__restrict__ ctr) {
     extern __shared__ float4 s_lut[];
     if (MODE == 0) {
-        for (int i = threadIdx.x; i < fc.nlut; i += blockDim.x) s_lut[i] = lut[i];
+        load_table(lut, fc.nlut, s_lut);
         __syncthreads();
     }
     const TileItem it = items[blockIdx.x];
@@ -281,26 +343,21 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                 const float qy = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
                 const float qz = anchor(o[2], d[2], b.org_c[2], k0, fc.step);
                 const int n = k1 - k0;
-                const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax;
-                const int lmax = fc.nlut - 2;
-                const float thr = fc.thr;
-                int j = 0;
-                int px = -4, py = -4, pz = -4;        // no cell cached yet
-                float v[8];
-                for (; j < n; ++j) {
-                    const float tj = __fmul_rn((float)j, fc.step);
-                    Cell cl;
-                    cell_of(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
-                            mx, my, mz, cl);
-                    if (CACHE)
-                        fetch8_cached<S>(src, st, cl, px, py, pz, v);
-                    else
-                        fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
-                    DvrSample sm;
-                    interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
-                    over(sm, c0, c1, c2, T);
-                    if (T <= thr) { ++j; break; }
-                }
+                // sample positions are monotone along the ray: when the segment's first and last
+                // cells are inside the stored brick, every cell in between is too
+                Cell e0, e1;
+                const float tl = __fmul_rn((float)(n - 1), fc.step);
+                cell_of<false>(qx, qy, qz, mx, my, mz, e0);
+                cell_of<false>(__fmaf_rn(tl, d[0], qx), __fmaf_rn(tl, d[1], qy), __fmaf_rn(tl, d[2], qz),
+                               mx, my, mz, e1);
+                const bool inside = min(e0.ix, e1.ix) >= 0 && max(e0.ix, e1.ix) <= mx &&
+                                    min(e0.iy, e1.iy) >= 0 && max(e0.iy, e1.iy) <= my &&
+                                    min(e0.iz, e1.iz) >= 0 && max(e0.iz, e1.iz) <= mz;
+                const int j = inside
+                    ? dvr_segment<S, CACHE, false>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                                                   c0, c1, c2, T)
+                    : dvr_segment<S, CACHE, true>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                                                  c0, c1, c2, T);
                 nsamp = j;
             }
             static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
@@ -446,8 +503,8 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
           const float4 *__restrict__ frags, const float4 *__restrict__ gfrag,
           float *__restrict__ glut_partial, float *__restrict__ gvox) {
     extern __shared__ float4 s_lut[];
-    float *s_g = reinterpret_cast<float *>(s_lut + fc.nlut);
-    for (int i = threadIdx.x; i < fc.nlut; i += blockDim.x) s_lut[i] = lut[i];
+    float *s_g = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);
+    load_table(lut, fc.nlut, s_lut);
     for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) s_g[i] = 0.0f;
     __syncthreads();
     const TileItem it = items[blockIdx.x];
@@ -500,8 +557,7 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                 atomicAdd(g0 + 2, w0 * gb); atomicAdd(g0 + 6, w1 * gb);
                 atomicAdd(g0 + 3, w0 * ga); atomicAdd(g0 + 7, w1 * ga);
                 if (gvox != nullptr && sm.u > 0.0f && sm.u < 1.0f) {
-                    const float gx = gr * (sm.L1.x - sm.L0.x) + gg * (sm.L1.y - sm.L0.y) +
-                                     gb * (sm.L1.z - sm.L0.z) + ga * (sm.L1.w - sm.L0.w);
+                    const float gx = gr * sm.D.x + gg * sm.D.y + gb * sm.D.z + ga * sm.D.w;
                     const float gv = gx * dxdv;
                     if (gv != 0.0f) {
                         const int ix = sm.ix, iy = sm.iy, iz = sm.iz;
@@ -544,10 +600,10 @@ template <int S, int MODE, bool CACHE>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = MODE == 0 ? sizeof(float4) * (size_t)fc.nlut : 0;
+    const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(float4) * kMaxLut));
+                                             (int)(2 * sizeof(float4) * kMaxLut));
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -601,11 +657,11 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(32 * kMaxLut));
+                                             (int)(48 * kMaxLut));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t smem = 32 * (size_t)fc.nlut;     // table (16 B) + gradient accumulators (16 B)
+    const size_t smem = 48 * (size_t)fc.nlut;     // table pairs (32 B) + gradient accumulators (16 B)
     k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
     return cudaGetLastError();
 }
