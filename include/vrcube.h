@@ -233,6 +233,20 @@ int vr_render_frame_noalloc(vr_ctx *ctx, int cube_id, float *out, void *cuda_str
 int vr_render_backward(vr_ctx *ctx, int cube_id, const float *grad_out, float *grad_lut,
                        float *grad_voxels, void *cuda_stream);
 
+/* Spectral channels (Section 2.3: "enabling/disabling spectral channel(s), which are handled in
+ * the same manner" as a colour-map change).  mask[z] = 0 switches channel z of the rendered
+ * cube off: its voxels take the value vmin of the transfer function (the bottom of the table
+ * range) in place of their data, for DVR, MIP and the gradient (which they then do not
+ * receive).  n must equal the cube's nz at render time; mask NULL or n = 0 switches every
+ * channel on.  The mask is copied.  Errors: VR_ERR_ARG. */
+int vr_set_channel_mask(vr_ctx *ctx, const unsigned char *mask, int64_t n);
+
+/* Render window (Section 2.3: the whole cube or a sub-cube): every ray is clipped to the voxel
+ * box [lo, hi) (world coordinates, intersected with the cube) with the same slab decisions as
+ * the bricks; voxels outside still feed the trilinear stencils at the window's faces.
+ * lo = hi = NULL removes the window.  Errors: VR_ERR_ARG (hi <= lo on an axis). */
+int vr_set_window(vr_ctx *ctx, const int64_t lo[3], const int64_t hi[3]);
+
 /* Enables (1) or disables (0) device timing of every frame's phases (CUDA events on the frame's
  * stream, read by vr_get_stats).  Errors: VR_ERR_ARG. */
 int vr_set_timing(vr_ctx *ctx, int enable);

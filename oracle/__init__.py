@@ -37,6 +37,7 @@ class Args(C.Structure):
         ("tau", C.c_float), ("bx", C.c_int64), ("by", C.c_int64), ("bz", C.c_int64),
         ("quant", C.c_int32), ("ghost", C.c_int32), ("nthreads", C.c_int32),
         ("procedural", C.c_int32), ("proc_seed", C.c_uint64),
+        ("channels", C.c_void_p), ("win_lo", C.c_int64 * 3), ("win_hi", C.c_int64 * 3),
     ]
 
 
@@ -86,7 +87,7 @@ class Procedural:
 
 
 def _args(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, quant="f32",
-          ghost=1, nthreads=0):
+          ghost=1, nthreads=0, channels=None, window=None):
     lut = np.ascontiguousarray(lut, dtype=np.float32)
     a = Args()
     if isinstance(cube, Procedural):
@@ -112,7 +113,14 @@ def _args(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, qu
     a.quant = QUANT[quant]
     a.ghost = int(ghost)
     a.nthreads = int(nthreads)
-    return a, (cube, lut)  # keep the arrays alive
+    ch = None
+    if channels is not None:
+        ch = np.ascontiguousarray(channels, dtype=np.uint8)
+        a.channels = ch.ctypes.data
+    if window is not None:
+        for i in range(3):
+            a.win_lo[i], a.win_hi[i] = int(window[0][i]), int(window[1][i])
+    return a, (cube, lut, ch)  # keep the arrays alive
 
 
 def _pix(pix):
@@ -123,10 +131,12 @@ def _pix(pix):
 
 
 def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, quant="f32",
-           pix=None, ghost=1, nthreads=0):
+           pix=None, ghost=1, nthreads=0, channels=None, window=None):
     """Returns (out, flags, nsamples).  out: (npix, 4) premultiplied RGBA for DVR, (npix,) for
-    MIP; float64.  pix: flat pixel indices (row*W + col) or None for the whole frame."""
-    a, keep = _args(cube, lut, vrange, cam, mode, step, tau, brick, quant, ghost, nthreads)
+    MIP; float64.  pix: flat pixel indices (row*W + col) or None for the whole frame.
+    channels: per-z 0/1 enable mask; window: ((x0,y0,z0), (x1,y1,z1)) voxel box."""
+    a, keep = _args(cube, lut, vrange, cam, mode, step, tau, brick, quant, ghost, nthreads,
+                    channels, window)
     pixa, pp = _pix(pix)
     npix = cam["W"] * cam["H"] if pix is None else len(pixa)
     stride = 4 if mode == "dvr" else 1
@@ -161,9 +171,10 @@ def proc_voxel(seed, shape_xyz, x, y, z) -> float:
 
 
 def render_grad(cube, lut, vrange, cam, gout, step=0.5, tau=0.99, brick=None, pix=None,
-                want_vox=True):
+                want_vox=True, channels=None, window=None):
     """Gradient of sum(gout * out) w.r.t. (lut, cube) in FP64; DVR only."""
-    a, keep = _args(cube, lut, vrange, cam, "dvr", step, tau, brick, "f32")
+    a, keep = _args(cube, lut, vrange, cam, "dvr", step, tau, brick, "f32", channels=channels,
+                    window=window)
     pixa, pp = _pix(pix)
     npix = cam["W"] * cam["H"] if pix is None else len(pixa)
     g = np.ascontiguousarray(gout, dtype=np.float64).reshape(npix, 4)

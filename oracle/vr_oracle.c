@@ -56,6 +56,8 @@ typedef struct {
     int32_t nthreads;
     int32_t procedural;             /* 1: voxels come from the procedural cube (vox unused) */
     uint64_t proc_seed;
+    const uint8_t *channels;        /* per spectral channel z: 0 = disabled (NULL: all enabled) */
+    int64_t win_lo[3], win_hi[3];   /* render window [lo, hi) in voxels (hi <= lo: whole cube) */
 } orc_args;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -232,14 +234,26 @@ typedef struct {
     int inside0[3];                 /* d == 0: index of the cell holding o, else -1 */
 } rayinfo;
 
+/* Window of the render along axis ax: [wlo, whi) clipped to the cube (the whole axis if no
+ * window is set).  Section 2.3: the user views the whole cube or a sub-cube. */
+static void window_axis(const orc_args *a, int ax, int64_t n, int64_t *wlo, int64_t *whi) {
+    int has = a->win_hi[0] > a->win_lo[0] && a->win_hi[1] > a->win_lo[1] && a->win_hi[2] > a->win_lo[2];
+    *wlo = has ? (a->win_lo[ax] > 0 ? a->win_lo[ax] : 0) : 0;
+    *whi = has ? (a->win_hi[ax] < n ? a->win_hi[ax] : n) : n;
+}
+
 static int ray_setup(const orc_args *a, const cam32 *c, int64_t pix, rayinfo *r,
                      int64_t *buf) {
     int64_t i = pix % a->W, j = pix / a->W;
     ray32(c, i, j, r->o, r->d);
     int64_t n[3] = {a->nx, a->ny, a->nz};
     int64_t bb[3] = {a->bx, a->by, a->bz};
-    float lo[3] = {0, 0, 0}, hi[3] = {(float)n[0], (float)n[1], (float)n[2]};
-    if (!box_krange(r->o, r->d, lo, hi, a->step, &r->k0, &r->k1)) { r->k0 = r->k1 = 0; }
+    int64_t wl[3], wh[3];
+    for (int ax = 0; ax < 3; ++ax) window_axis(a, ax, n[ax], &wl[ax], &wh[ax]);
+    float lo[3] = {(float)wl[0], (float)wl[1], (float)wl[2]};
+    float hi[3] = {(float)wh[0], (float)wh[1], (float)wh[2]};
+    if (!(wh[0] > wl[0] && wh[1] > wl[1] && wh[2] > wl[2])) { r->k0 = r->k1 = 0; }
+    else if (!box_krange(r->o, r->d, lo, hi, a->step, &r->k0, &r->k1)) { r->k0 = r->k1 = 0; }
     int64_t off = 0;
     for (int ax = 0; ax < 3; ++ax) {
         r->b[ax] = bb[ax] > 0 ? bb[ax] : n[ax];
@@ -248,11 +262,14 @@ static int ray_setup(const orc_args *a, const cam32 *c, int64_t pix, rayinfo *r,
         r->kx[ax] = buf + off; off += r->nb[ax];
         r->inside0[ax] = -1;
         for (int64_t cc = 0; cc < r->nb[ax]; ++cc) {
-            float plo = (float)(cc * r->b[ax]);
-            int64_t h = (cc + 1) * r->b[ax];
-            float phi = (float)(h < n[ax] ? h : n[ax]);
+            /* the cell's planes, clipped to the window (shared planes stay identical) */
+            int64_t l = cc * r->b[ax], h = (cc + 1) * r->b[ax];
+            if (h > n[ax]) h = n[ax];
+            if (l < wl[ax]) l = wl[ax];
+            if (h > wh[ax]) h = wh[ax];
+            float plo = (float)l, phi = (float)h;
             float en, ex;
-            if (!slab32(r->o[ax], r->d[ax], plo, phi, &en, &ex)) {
+            if (h <= l || !slab32(r->o[ax], r->d[ax], plo, phi, &en, &ex)) {
                 r->ke[ax][cc] = 1; r->kx[ax][cc] = 0;  /* empty */
                 continue;
             }
@@ -410,8 +427,15 @@ typedef struct {
 
 static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+/* A disabled spectral channel (Section 2.3: channels switched off like a colour-map change)
+ * holds vmin, the bottom of the table range, in place of its data. */
+static int channel_off(const orc_args *a, int64_t idx) {
+    return a->channels && !a->channels[idx / (a->nx * a->ny)];
+}
+
 /* voxel value as seen from a brick (dequantised with the brick's exponent when quantised) */
 static double voxel_val(const orc_args *a, int64_t idx, int e) {
+    if (channel_off(a, idx)) return (double)a->vmin;
     float v = vox_at(a, idx);
     if (a->quant == 0) return (double)v;
     return ldexp((double)quant_code(v, e, a->quant), e);
@@ -466,6 +490,7 @@ static float sample32(const orc_args *a, const float o[3], const float d[3], int
                       n[0] * (((cc & 2) ? i1[1] : i0[1]) + n[1] * ((cc & 4) ? i1[2] : i0[2]));
         float v = vox_at(a, idx);
         c[cc] = a->quant ? quant_code(v, e, a->quant) : v;
+        if (channel_off(a, idx)) c[cc] = a->quant ? ldexpf(a->vmin, -e) : a->vmin;
     }
     float c00 = lerp32(c[0], c[1], f[0]), c10 = lerp32(c[2], c[3], f[0]);
     float c01 = lerp32(c[4], c[5], f[0]), c11 = lerp32(c[6], c[7], f[0]);
@@ -669,7 +694,8 @@ int orc_render_grad(const orc_args *a, const int64_t *pix, int64_t npix, const d
             }
             if (gvox) {
                 double gv = dvdx * s->tf.dxdv;
-                for (int cc = 0; cc < 8; ++cc) gvox[s->tri.idx[cc]] += s->tri.w[cc] * gv;
+                for (int cc = 0; cc < 8; ++cc)
+                    if (!channel_off(a, s->tri.idx[cc])) gvox[s->tri.idx[cc]] += s->tri.w[cc] * gv;
             }
         }
     }

@@ -190,6 +190,22 @@ class Context:
         _check(self._L.vr_set_render_params(self._h, self.mode, float(step), float(tau)),
                "vr_set_render_params")
 
+    def set_channel_mask(self, mask=None):
+        """0/1 per spectral channel (cube z); None switches every channel on."""
+        if mask is None:
+            _check(self._L.vr_set_channel_mask(self._h, None, 0), "vr_set_channel_mask")
+            return
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        _check(self._L.vr_set_channel_mask(self._h, m.ctypes.data, m.size), "vr_set_channel_mask")
+
+    def set_window(self, lo=None, hi=None):
+        """Clip rendering to the voxel box [lo, hi) (x, y, z); None removes the window."""
+        if lo is None:
+            _check(self._L.vr_set_window(self._h, None, None), "vr_set_window")
+            return
+        _check(self._L.vr_set_window(self._h, (C.c_int64 * 3)(*lo), (C.c_int64 * 3)(*hi)),
+               "vr_set_window")
+
     def set_timing(self, enable: bool):
         _check(self._L.vr_set_timing(self._h, int(bool(enable))), "vr_set_timing")
 

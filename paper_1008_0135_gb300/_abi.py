@@ -69,6 +69,8 @@ SIGNATURES = {
     "vr_render_frame": (I, [VP, I, VP, I, VP]),
     "vr_render_frame_noalloc": (I, [VP, I, VP, VP]),
     "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),
+    "vr_set_channel_mask": (I, [VP, VP, I64]),
+    "vr_set_window": (I, [VP, P(I64), P(I64)]),
     "vr_set_timing": (I, [VP, I]),
     "vr_set_full_rect": (I, [VP, I]),
     "vr_get_stats": (I, [VP, P(VrStats)]),

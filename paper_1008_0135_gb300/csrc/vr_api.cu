@@ -68,9 +68,26 @@ void alpha_prefix(const vr_ctx *c, std::vector<int> &pre) {
 // stencil's range, so a brick whose stored values map only to entries of zero opacity adds
 // exactly nothing (every sample has a = 0: colour += T*0, T *= 1).  The range is widened for
 // the FP32 rounding of the mapping and, for 16-bit bricks, for the rounding of the codes.
+bool window_clip(const vr_ctx *c, const Cube *cb, const DrawBrick &b, float lo[3], float hi[3]) {
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = b.lo[a];
+        hi[a] = b.hi[a];
+        if (c->has_window) {
+            lo[a] = std::max(lo[a], (float)std::max<int64_t>(c->win_lo[a], 0));
+            hi[a] = std::min(hi[a], (float)std::min<int64_t>(c->win_hi[a], cb->n[a]));
+        }
+        if (!(hi[a] > lo[a])) return false;
+    }
+    return true;
+}
+
 bool skip_brick(const vr_ctx *c, const Cube *cb, size_t b, const int *pre) {
     if (c->mode != VR_DVR || c->full_rect || b >= cb->vlo.size()) return false;
-    const double lo = cb->vlo[b], hi = cb->vhi[b];
+    double lo = cb->vlo[b], hi = cb->vhi[b];
+    if (!c->chmask.empty()) {                // disabled channels hold vmin
+        lo = std::min(lo, (double)c->vmin);
+        hi = std::max(hi, (double)c->vmin);
+    }
     if (!(lo <= hi)) return false;
     const double mag = std::max({1.0, std::fabs(lo), std::fabs(hi)});
     const double widen = mag * (cb->storage == VR_F32 ? 1e-5 : 1.0 / 64.0);
@@ -147,7 +164,8 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     std::vector<int> apre;
     alpha_prefix(c, apre);
     for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) {
-        const DrawBrick &b = cb->tmpl[bi];
+        DrawBrick b = cb->tmpl[bi];
+        if (!window_clip(c, cb, b, b.lo, b.hi)) continue;
         if (skip_brick(c, cb, bi, apre.data())) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
         bool cull = false;
@@ -245,6 +263,7 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     wl.off_items = off; off = align_up(off + sizeof(TileItem) * wl.items.size(), 256);
     wl.off_ts = off; off = align_up(off + sizeof(int) * wl.tile_start.size(), 256);
     wl.off_tl = off; off = align_up(off + sizeof(int) * wl.tile_list.size(), 256);
+    wl.off_mask = off; off = align_up(off + c->chmask.size(), 256);
     wl.bytes = off;
 }
 
@@ -316,6 +335,7 @@ int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t e
     if (!wl.items.empty()) std::memcpy(h + wl.off_items, wl.items.data(), sizeof(TileItem) * wl.items.size());
     std::memcpy(h + wl.off_ts, wl.tile_start.data(), sizeof(int) * wl.tile_start.size());
     if (!wl.tile_list.empty()) std::memcpy(h + wl.off_tl, wl.tile_list.data(), sizeof(int) * wl.tile_list.size());
+    if (!c->chmask.empty()) std::memcpy(h + wl.off_mask, c->chmask.data(), c->chmask.size());
     if (ev0) CK(cudaEventRecord(ev0, s));
     CK(cudaMemcpyAsync(c->d_stage.p, h, wl.bytes, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->upload_done, s));
@@ -324,6 +344,8 @@ int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t e
 
 int check_ready(vr_ctx *c, Cube *cb) {
     if (!cb->bricked) { g_last_error = "cube has no bricking"; return VR_ERR_STATE; }
+    if (!c->chmask.empty() && (int64_t)c->chmask.size() != cb->n[2])
+        return arg_fail("the channel mask must have one entry per z of the cube");
     if (!c->tf_set) { g_last_error = "no transfer function"; return VR_ERR_STATE; }
     if (!c->cam_set) { g_last_error = "no camera"; return VR_ERR_STATE; }
     // every lattice index k = t/step reached inside the cube must fit comfortably in an int:
@@ -437,7 +459,7 @@ int noalloc_scratch(int device, unsigned char **ptr) {
 }
 
 struct StaticLayout {
-    size_t off_lut, off_db, off_items, off_ts, off_tl, bytes;
+    size_t off_lut, off_db, off_items, off_ts, off_tl, off_mask, bytes;
     int nd, nitems;
     long long frag_px;
 };
@@ -482,7 +504,8 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
     apre_buf[0] = 0;
     for (size_t i = 0; i < c->lut.size(); ++i) apre_buf[i + 1] = apre_buf[i] + (c->lut[i].w != 0.0f ? 1 : 0);
     for (size_t bi = 0; bi < nb; ++bi) {
-        const DrawBrick &b = cb->tmpl[bi];
+        DrawBrick b = cb->tmpl[bi];
+        if (!window_clip(c, cb, b, b.lo, b.hi)) continue;
         if (skip_brick(c, cb, bi, apre_buf)) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
         bool cull = false;
@@ -551,6 +574,7 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
     L.off_items = off; off = align_up(off + sizeof(TileItem) * (size_t)nitems, 256);
     L.off_ts = off; off = align_up(off + sizeof(int) * (ntiles + 1), 256);
     L.off_tl = off; off = align_up(off + sizeof(int) * (size_t)nbin, 256);
+    L.off_mask = off; off = align_up(off + c->chmask.size(), 256);
     L.bytes = off;
     L.nd = nc;
     L.nitems = (int)nitems;
@@ -561,6 +585,7 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
         return VR_ERR_ARG;
     }
     std::memcpy(arena + L.off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
+    if (!c->chmask.empty()) std::memcpy(arena + L.off_mask, c->chmask.data(), c->chmask.size());
     DrawBrick *db = reinterpret_cast<DrawBrick *>(arena + L.off_db);
     TileItem *items = reinterpret_cast<TileItem *>(arena + L.off_items);
     int *ts = reinterpret_cast<int *>(arena + L.off_ts);
@@ -939,6 +964,31 @@ int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
     return VR_OK;
 }
 
+int vr_set_channel_mask(vr_ctx *c, const unsigned char *mask, int64_t n) {
+    if (!c) return arg_fail("null ctx");
+    if (!mask || n == 0) {
+        c->chmask.clear();
+        return VR_OK;
+    }
+    if (n < 0 || n > (1 << 30)) return arg_fail("bad channel count");
+    c->chmask.assign(mask, mask + n);
+    for (auto &m : c->chmask) m = m ? 1 : 0;
+    return VR_OK;
+}
+
+int vr_set_window(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]) {
+    if (!c) return arg_fail("null ctx");
+    if (!lo || !hi) {
+        c->has_window = false;
+        return VR_OK;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!(hi[a] > lo[a])) return arg_fail("window must have hi > lo on every axis");
+    for (int a = 0; a < 3; ++a) { c->win_lo[a] = lo[a]; c->win_hi[a] = hi[a]; }
+    c->has_window = true;
+    return VR_OK;
+}
+
 int vr_set_timing(vr_ctx *c, int enable) {
     if (!c) return arg_fail("null ctx");
     c->timing = enable != 0;
@@ -959,11 +1009,12 @@ namespace vrh {
 __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
     if (cb->streamed) return render_streamed(c, cb, out, out_where, s);
-    const FrameConsts fc = make_consts(c, cb);
+    FrameConsts fc = make_consts(c, cb);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     WorkList wl;
     if ((rc = stage_frame(c, cb, wl, s, ev[0])) != VR_OK) return rc;
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
     const size_t fbytes = (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
     if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
     const size_t opix = (size_t)fc.cam.W * fc.cam.H;
@@ -1028,9 +1079,10 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
     if ((rc = set_dev(c)) != VR_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const FrameConsts fc = make_consts(c, cb);
+    FrameConsts fc = make_consts(c, cb);
     WorkList wl;
     if ((rc = stage_frame(c, cb, wl, s, nullptr)) != VR_OK) return rc;
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
     const size_t nfr = (size_t)std::max<long long>(wl.frag_px, 1);
     if ((rc = ensure(c->d_frags, nfr * sizeof(float4), c)) != VR_OK) return rc;
     if ((rc = ensure(c->d_gfrag, nfr, c)) != VR_OK) return rc;
@@ -1137,7 +1189,7 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     unsigned char *dev = nullptr;
     if ((rc = noalloc_scratch(c->device, &dev)) != VR_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const FrameConsts fc = make_consts(c, cb);
+    FrameConsts fc = make_consts(c, cb);
     const size_t frag_elem = c->mode == VR_DVR ? sizeof(float4) : sizeof(float);
     StaticLayout L{};
     if ((rc = build_worklist_static(c, cb, g_noalloc_host, kNoAllocScratchBytes, frag_elem, L)) != VR_OK) return rc;
@@ -1151,6 +1203,7 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     const int *d_ts = reinterpret_cast<const int *>(dev + L.off_ts);
     const int *d_tl = reinterpret_cast<const int *>(dev + L.off_tl);
     void *d_frags = dev + L.bytes;
+    if (!c->chmask.empty()) fc.chmask = dev + L.off_mask;
     CK(launch_raycast(fc, d_lut, d_db, d_items, L.nitems, cb->d_pool, d_frags, c->d_ctr, s));
     CK(launch_composite(fc, d_db, d_ts, d_tl, d_frags, out, s));
     return VR_OK;

@@ -76,7 +76,7 @@ struct WorkList {
     std::vector<int> tile_start, tile_list;
     long long frag_px = 0;
     // offsets inside the staged upload
-    size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, bytes = 0;
+    size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, off_mask = 0, bytes = 0;
 };
 
 }  // namespace vrh
@@ -99,6 +99,10 @@ struct vr_ctx {
     float tau = 0.99f;
     bool full_rect = false;
     bool timing = false;
+    // Section 2.3 viewer controls: spectral channels switched off, sub-cube window
+    std::vector<unsigned char> chmask;   // per cube z; empty = every channel on
+    bool has_window = false;
+    int64_t win_lo[3] = {0, 0, 0}, win_hi[3] = {0, 0, 0};
     // frame scratch (reused; guarded by events)
     char *h_stage = nullptr;
     size_t h_cap = 0;
@@ -152,6 +156,8 @@ int timing_events(vr_ctx *c, cudaEvent_t ev[4]);
 int collect_timing(vr_ctx *c);
 int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t ev0);
 int check_ready(vr_ctx *c, Cube *cb);
+// Core box of brick b clipped to the render window; false when nothing of it is left.
+bool window_clip(const vr_ctx *c, const Cube *cb, const DrawBrick &b, float lo[3], float hi[3]);
 int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s);
 int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s);
 void free_cube(Cube *cb);

@@ -36,6 +36,7 @@ struct FrameConsts {
     int lanes_y;                   // 0: a warp's 32 lanes run along image x (tiles 32x8);
                                    // 1: along image y (tiles 8x32)
     int stencil_cache;             // 1: rays reuse shared stencil corners (poorly aligned layout)
+    const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
 };
 
 // One brick of the current frame's work-list (front-to-back order).

@@ -180,6 +180,7 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
 
 // The table in shared memory as (entry i, entry i+1 - entry i) pairs: the differences are the
 // same IEEE subtractions a lookup would do, made once per block instead of once per sample.
+// (Pairs beat two separate arrays: one address for both loads.)
 __device__ __forceinline__ void load_table(const float4 *__restrict__ lut, int n, float4 *s) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 a = lut[i];
@@ -203,16 +204,28 @@ __device__ __forceinline__ void fetch8(const void *src, int i0, const Strides &t
     v[6] = ldv<S>(src, i0 + t.z + t.y); v[7] = ldv<S>(src, i0 + t.z + t.y + t.x);
 }
 
+// Disabled spectral channels hold vmin (the bottom of the table range) in place of their data:
+// the stencil's two z-planes are global channels org_z + iz and + 1 (clamped at the cube
+// border, like the ghost copies).  `vcode` is vmin in the brick's stored units.
+__device__ __forceinline__ void mask_channels(float v[8], int iz, int org_z, int nz,
+                                              const unsigned char *chmask, float vcode) {
+    const int z0 = clampi(org_z + iz, 0, nz - 1), z1 = clampi(org_z + iz + 1, 0, nz - 1);
+    if (!chmask[z0]) { v[0] = vcode; v[1] = vcode; v[2] = vcode; v[3] = vcode; }
+    if (!chmask[z1]) { v[4] = vcode; v[5] = vcode; v[6] = vcode; v[7] = vcode; }
+}
+
 template <int S>
 __device__ __forceinline__ void dvr_sample(const void *src, const Strides &t, int mx, int my, int mz,
                                            float scale, float x, float y, float z, float vmin,
                                            float inv_range, float lutmax, int lmax,
-                                           const float4 *s_lut, DvrSample &o) {
+                                           const float4 *s_lut, const unsigned char *chmask,
+                                           int org_z, int nz, float vcode, DvrSample &o) {
     Cell c;
     cell_of(x, y, z, mx, my, mz, c);
     o.ix = c.ix; o.iy = c.iy; o.iz = c.iz;
     float v[8];
     fetch8<S>(src, c.ix * t.x + c.iy * t.y + c.iz * t.z, t, v);
+    if (chmask) mask_channels(v, c.iz, org_z, nz, chmask, vcode);
     interp_tf(v, c, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, o);
 }
 
@@ -280,8 +293,10 @@ template <int S, bool CACHE, bool CLAMP>
 __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, int mx, int my, int mz,
                                            float scale, float qx, float qy, float qz, const float d[3],
                                            int n, const FrameConsts &fc, const float4 *s_lut,
+                                           int org_z, float vcode,
                                            float &c0, float &c1, float &c2, float &T) {
     const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
+    const unsigned char *chmask = fc.chmask;
     const int lmax = fc.nlut - 2;
     int px = -4, py = -4, pz = -4;        // no cell cached yet
     float v[8];
@@ -296,6 +311,7 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, i
             fetch8_cached<S>(src, st, cl, px, py, pz, v);
         else
             fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
+        if (chmask) mask_channels(v, cl.iz, org_z, fc.nz, chmask, vcode);
         DvrSample sm;
         interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
         over(sm, c0, c1, c2, T);
@@ -353,11 +369,12 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                 const bool inside = min(e0.ix, e1.ix) >= 0 && max(e0.ix, e1.ix) <= mx &&
                                     min(e0.iy, e1.iy) >= 0 && max(e0.iy, e1.iy) <= my &&
                                     min(e0.iz, e1.iz) >= 0 && max(e0.iz, e1.iz) <= mz;
+                const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
                 const int j = inside
                     ? dvr_segment<S, CACHE, false>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                   c0, c1, c2, T)
+                                                   b.org[2], vcode, c0, c1, c2, T)
                     : dvr_segment<S, CACHE, true>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                  c0, c1, c2, T);
+                                                  b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
             static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
@@ -376,13 +393,18 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     const int iy = clampi((int)fly - b.org[1], 0, my);
                     const int iz = clampi((int)flz - b.org[2], 0, mz);
                     const int i0 = ix * st.x + iy * st.y + iz * st.z;
-                    const float c00 = lerp_rn(ldv<S>(src, i0), ldv<S>(src, i0 + st.x), fx);
-                    const float c10 = lerp_rn(ldv<S>(src, i0 + st.y), ldv<S>(src, i0 + st.y + st.x), fx);
-                    const float c01 = lerp_rn(ldv<S>(src, i0 + st.z), ldv<S>(src, i0 + st.z + st.x), fx);
-                    const float c11 = lerp_rn(ldv<S>(src, i0 + st.z + st.y), ldv<S>(src, i0 + st.z + st.y + st.x), fx);
-                    float v = lerp_rn(lerp_rn(c00, c10, fy), lerp_rn(c01, c11, fy), fz);
-                    if (S != 0) v = __fmul_rn(v, scale);
-                    m = v > m ? v : m;
+                    float v[8];
+                    fetch8<S>(src, i0, st, v);
+                    if (fc.chmask)
+                        mask_channels(v, iz, b.org[2], fc.nz, fc.chmask,
+                                      S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2));
+                    const float c00 = lerp_rn(v[0], v[1], fx);
+                    const float c10 = lerp_rn(v[2], v[3], fx);
+                    const float c01 = lerp_rn(v[4], v[5], fx);
+                    const float c11 = lerp_rn(v[6], v[7], fx);
+                    float val = lerp_rn(lerp_rn(c00, c10, fy), lerp_rn(c01, c11, fy), fz);
+                    if (S != 0) val = __fmul_rn(val, scale);
+                    m = val > m ? val : m;
                 }
                 nsamp = k1 - k0;
             }
@@ -536,7 +558,8 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                 DvrSample sm;
                 dvr_sample<0>(src, st, mx, my, mz, 1.0f, __fmaf_rn(tj, d[0], qx),
                               __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), fc.vmin,
-                              fc.inv_range, fc.lutmax, fc.nlut - 2, s_lut, sm);
+                              fc.inv_range, fc.lutmax, fc.nlut - 2, s_lut, fc.chmask, b.org[2],
+                              fc.nz, fc.vmin, sm);
                 const float Tb = T;
                 over(sm, c0, c1, c2, T);
                 const bool last = (T <= fc.thr) || (j == n - 1);
@@ -565,8 +588,11 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                         const int gy0 = clampi(b.org[1] + iy, 0, fc.ny - 1), gy1 = clampi(b.org[1] + iy + 1, 0, fc.ny - 1);
                         const int gz0 = clampi(b.org[2] + iz, 0, fc.nz - 1), gz1 = clampi(b.org[2] + iz + 1, 0, fc.nz - 1);
                         const long long sy = fc.nx, sz = (long long)fc.nx * fc.ny;
-                        const float ux = sm.fx, uy = sm.fy, uz = sm.fz;
-                        const float vx = 1.0f - ux, vy = 1.0f - uy, vz = 1.0f - uz;
+                        const float ux = sm.fx, uy = sm.fy;
+                        const float vx = 1.0f - ux, vy = 1.0f - uy;
+                        // a disabled channel's voxels do not reach the image: no gradient
+                        const float uz = (fc.chmask && !fc.chmask[gz1]) ? 0.0f : sm.fz;
+                        const float vz = (fc.chmask && !fc.chmask[gz0]) ? 0.0f : 1.0f - sm.fz;
                         atomicAdd(gvox + gz0 * sz + gy0 * sy + gx0, gv * vx * vy * vz);
                         atomicAdd(gvox + gz0 * sz + gy0 * sy + gx1, gv * ux * vy * vz);
                         atomicAdd(gvox + gz0 * sz + gy1 * sy + gx0, gv * vx * uy * vz);

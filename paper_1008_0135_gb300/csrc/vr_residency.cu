@@ -551,7 +551,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     size_t max_bytes = 0;
     for (auto &b : cb->tmpl) max_bytes = std::max(max_bytes, (size_t)b.bytes);
     if ((rc = cache_size(c, max_bytes)) != VR_OK) return rc;
-    const FrameConsts fc = make_consts(c, cb);
+    FrameConsts fc = make_consts(c, cb);
     WorkList wl;
     build_worklist(c, cb, wl);
     const size_t nd = wl.db.size();
@@ -567,6 +567,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     wl.off_db = off; off = align_up(off + sizeof(DrawBrick) * nd, 256);
     wl.off_ts = off; off = align_up(off + sizeof(int) * wl.tile_start.size(), 256);
     wl.off_tl = off; off = align_up(off + sizeof(int) * wl.tile_list.size(), 256);
+    wl.off_mask = off; off = align_up(off + c->chmask.size(), 256);
     std::vector<size_t> off_cdb(nchunks), off_cit(nchunks);
     for (size_t ch = 0; ch < nchunks; ++ch) {
         const size_t d0 = ch * per, d1 = std::min(nd, d0 + per);
@@ -593,10 +594,12 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     std::memcpy(h + wl.off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
     std::memcpy(h + wl.off_ts, wl.tile_start.data(), sizeof(int) * wl.tile_start.size());
     if (!wl.tile_list.empty()) std::memcpy(h + wl.off_tl, wl.tile_list.data(), sizeof(int) * wl.tile_list.size());
-    // the shared part (table, bins) first; brick records once every chunk is resident
+    if (!c->chmask.empty()) std::memcpy(h + wl.off_mask, c->chmask.data(), c->chmask.size());
+    // the shared part (table, bins, mask) first; brick records once every chunk is resident
     CK(cudaMemcpyAsync(d, h, wl.off_db, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(d + wl.off_ts, h + wl.off_ts, wl.off_tl - wl.off_ts + sizeof(int) * wl.tile_list.size(),
+    CK(cudaMemcpyAsync(d + wl.off_ts, h + wl.off_ts, wl.off_mask - wl.off_ts + c->chmask.size(),
                        cudaMemcpyHostToDevice, s));
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(d + wl.off_mask);
     for (size_t ch = 0; ch < nchunks; ++ch) {
         const size_t d0 = ch * per, d1 = std::min(nd, d0 + per);
         const int64_t chunk_id = ++k->chunk_counter;

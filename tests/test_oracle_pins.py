@@ -415,3 +415,65 @@ def test_procedural_sources_add_gaussian_bumps(orc):
     assert v[z, y, x] - noise > 2.5                 # amplitudes are at least 3
     for (xx, yy, zz) in [(5, 7, 1), (300, 200, 2), (699, 599, 3)]:
         assert v[zz, yy, xx] - orc.proc_noise(SEED, shape, xx, yy, zz) >= -1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# spectral-channel masks and render windows (Section 2.3)
+# ---------------------------------------------------------------------------------------------
+def test_channel_mask_equals_cube_with_vmin_slices(orc):
+    """A disabled channel holds vmin: the same as editing those z-slices of the cube."""
+    rng = np.random.default_rng(31)
+    cube = synth.pr1_cube(seed=31, n=24)
+    mask = (rng.uniform(size=24) > 0.4).astype(np.uint8)
+    edited = cube.copy()
+    edited[mask == 0] = np.float32(-3.0)
+    lut = synth.random_lut(2, n=40, alpha_max=0.4)
+    for proj in (0, 1):
+        cam = synth.random_camera(rng, (24, 24, 24), 30, 26, proj=proj)
+        for mode in ("dvr", "mip", "mip32"):
+            a, _, _ = orc.render(cube, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.95,
+                                 brick=(8, 8, 8), channels=mask)
+            b, _, _ = orc.render(edited, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.95,
+                                 brick=(8, 8, 8))
+            assert np.array_equal(a, b)
+    ones = np.ones(24, np.uint8)
+    a, _, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, channels=ones)
+    b, _, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5)
+    assert np.array_equal(a, b)
+    # gradient: disabled channels receive none
+    gout = rng.standard_normal((30 * 26, 4))
+    _, gv = orc.render_grad(cube, lut, (-3, 20), cam, gout, step=0.5, tau=1.0, channels=mask)
+    assert np.all(gv[mask == 0] == 0) and np.abs(gv[mask == 1]).max() > 0
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_window_clips_the_lattice(orc, seed):
+    """Samples are the lattice points inside the window box (checked in FP64 away from its
+    faces); the field is still the whole cube's (no clamping at the window)."""
+    rng = np.random.default_rng(40 + seed)
+    shape = (9, 8, 7)
+    nx, ny, nz = shape
+    cube = rng.uniform(-1, 3, (nz, ny, nx)).astype(np.float32)
+    lut = synth.random_lut(seed, n=20, alpha_max=0.5)
+    win = ((1, 2, 1), (7, 6, 5))
+    cam = synth.random_camera(rng, shape, 11, 9)
+    out, _, _ = orc.render(cube, lut, (-1, 3), cam, step=0.5, tau=1.0, window=win)
+    o, d, _ = orc.rays(cam, shape, step=0.5)
+    checked = 0
+    for p in range(11 * 9):
+        tt = _slab64(o[p].astype(np.float64) - np.array(win[0]), d[p].astype(np.float64),
+                     np.subtract(win[1], win[0]))
+        if tt is None:
+            k0 = k1 = 0
+        else:
+            t0, t1 = tt
+            if min(abs(t0 / 0.5 - round(t0 / 0.5)), abs(t1 / 0.5 - round(t1 / 0.5))) < 1e-3:
+                continue
+            k0, k1 = math.ceil(t0 / 0.5), math.ceil(t1 / 0.5)
+        ref = _brute(cube, lut, (-1, 3), o[p], d[p], k0, k1, 0.5, 1.0)
+        assert np.allclose(out[p], ref, atol=1e-12)
+        checked += 1
+    assert checked > 60
+    whole, _, _ = orc.render(cube, lut, (-1, 3), cam, step=0.5, window=((0, 0, 0), shape))
+    plain, _, _ = orc.render(cube, lut, (-1, 3), cam, step=0.5)
+    assert np.array_equal(whole, plain)

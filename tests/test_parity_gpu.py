@@ -340,3 +340,68 @@ def test_empty_space_skipping_is_exact(ctx, orc, storage):
     m2 = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5, full_rect=True)
     assert np.array_equal(m1, m2)                 # MIP never skips
     ctx.free_cube(cid)
+
+
+# ---------------------------------------------------------------------------------------------
+# spectral-channel masks and render windows (Section 2.3)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_channel_mask_and_window(ctx, orc, storage):
+    rng = np.random.default_rng(77)
+    cube = synth.pr1_cube(seed=8)
+    mask = (rng.uniform(size=64) > 0.3).astype(np.uint8)
+    win = ((5, 9, 3), (57, 50, 61))
+    lut = synth.ramp_lut(alpha=0.4)
+    lut[:20, 3] = 0.05                        # vmin itself visible: masked slices show
+    cid = ctx.load_cube(cube)
+    ctx.set_brick_layouts(cid, 7)
+    ctx.set_bricking(cid, (16, 32, 24), 1, storage)
+    q = "f32" if storage == "f32" else storage
+    try:
+        for k, (m, w) in enumerate([(mask, None), (None, win), (mask, win)]):
+            ctx.set_channel_mask(m)
+            if w is None:
+                ctx.set_window()
+            else:
+                ctx.set_window(*w)
+            cam = synth.random_camera(rng, (64, 64, 64), 90, 70)
+            g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+            ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99,
+                                       brick=(16, 32, 24), quant=q, channels=m, window=w)
+            compare_dvr(g, ref, flags, 0.99)
+            gm = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)
+            rm, _, _ = orc.render(cube, lut, (-3, 20), cam, mode="mip32", step=0.5,
+                                  brick=(16, 32, 24), quant=q, channels=m, window=w)
+            assert np.array_equal(gm, rm.astype(np.float32))
+    finally:
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+        ctx.free_cube(cid)
+
+
+def test_channel_mask_gradient(ctx, orc):
+    import torch
+    rng = np.random.default_rng(78)
+    n = 20
+    cube = synth.pr1_cube(seed=9, n=n, amp=(1.0, 4.0))
+    mask = (rng.uniform(size=n) > 0.4).astype(np.uint8)
+    lut = synth.random_lut(5, n=32, alpha_max=0.4)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (8, 8, 8), 1, "f32")
+    cam = synth.random_camera(rng, (n, n, n), 40, 32, proj=1)
+    ctx.set_channel_mask(mask)
+    try:
+        render(ctx, cid, lut, (-3, 8), cam, step=0.5, tau=1.0)
+        gout = rng.standard_normal((40 * 32, 4)).astype(np.float32)
+        glut = torch.zeros((32, 4), device="cuda")
+        gvox = torch.zeros(cube.shape, device="cuda")
+        ctx.render_backward(cid, torch.from_numpy(gout.reshape(32, 40, 4)).cuda(), glut, gvox)
+        rl, rv = orc.render_grad(cube, lut, (-3, 8), cam, gout.astype(np.float64), step=0.5,
+                                 tau=1.0, brick=(8, 8, 8), channels=mask)
+        gv = gvox.cpu().numpy()
+        assert np.all(gv[mask == 0] == 0)
+        assert np.abs(glut.cpu().numpy() - rl).max() <= 2e-4 * np.abs(rl).max()
+        assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max()
+    finally:
+        ctx.set_channel_mask(None)
+        ctx.free_cube(cid)
