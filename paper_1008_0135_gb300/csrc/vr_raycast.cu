@@ -285,18 +285,20 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 }
 
 // ----------------------------------------------------------------------------------------------
-// ray cast: one CTA = 16x16 pixels of one brick's rendering rectangle; warp = 8x4 pixels
+// ray cast: one CTA = 32x8 (or 8x32) pixels of one brick's rendering rectangle; warp = 32 pixels
+// along the image axis that the brick layout follows
 // ----------------------------------------------------------------------------------------------
 // One brick segment of a ray: n lattice samples from the anchor q, composited front to back
 // until the segment's transmittance reaches the threshold.  Returns the samples composited.
-template <int S, bool CACHE, bool CLAMP>
+// MASK: a spectral-channel mask is set (its own instantiation, so unmasked frames carry none of
+// its registers or branches).
+template <int S, bool CACHE, bool CLAMP, bool MASK>
 __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, int mx, int my, int mz,
                                            float scale, float qx, float qy, float qz, const float d[3],
                                            int n, const FrameConsts &fc, const float4 *s_lut,
                                            int org_z, float vcode,
                                            float &c0, float &c1, float &c2, float &T) {
     const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
-    const unsigned char *chmask = fc.chmask;
     const int lmax = fc.nlut - 2;
     int px = -4, py = -4, pz = -4;        // no cell cached yet
     float v[8];
@@ -311,7 +313,7 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, i
             fetch8_cached<S>(src, st, cl, px, py, pz, v);
         else
             fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
-        if (chmask) mask_channels(v, cl.iz, org_z, fc.nz, chmask, vcode);
+        if (MASK) mask_channels(v, cl.iz, org_z, fc.nz, fc.chmask, vcode);
         DvrSample sm;
         interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
         over(sm, c0, c1, c2, T);
@@ -323,7 +325,7 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, i
 // CACHE: a ray keeps the stencil corners its next cell shares with the last one (fewer
 // gathers, more instructions; pays off when a warp's gathers scatter over many cache lines);
 // otherwise all eight corners are gathered for every sample.
-template <int S, int MODE, bool CACHE>
+template <int S, int MODE, bool CACHE, bool MASK>
 __global__ void VR_RAYCAST_BOUNDS
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
@@ -371,9 +373,9 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                                     min(e0.iz, e1.iz) >= 0 && max(e0.iz, e1.iz) <= mz;
                 const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
                 const int j = inside
-                    ? dvr_segment<S, CACHE, false>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                    ? dvr_segment<S, CACHE, false, MASK>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
                                                    b.org[2], vcode, c0, c1, c2, T)
-                    : dvr_segment<S, CACHE, true>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                    : dvr_segment<S, CACHE, true, MASK>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
                                                   b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
@@ -395,7 +397,7 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     const int i0 = ix * st.x + iy * st.y + iz * st.z;
                     float v[8];
                     fetch8<S>(src, i0, st, v);
-                    if (fc.chmask)
+                    if (MASK)
                         mask_channels(v, iz, b.org[2], fc.nz, fc.chmask,
                                       S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2));
                     const float c00 = lerp_rn(v[0], v[1], fx);
@@ -622,27 +624,31 @@ __global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts,
     glut[i] = (float)acc;
 }
 
-template <int S, int MODE, bool CACHE>
+template <int S, int MODE, bool CACHE, bool MASK>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, CACHE, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(2 * sizeof(float4) * kMaxLut));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_raycast<S, MODE, CACHE><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
+    k_raycast<S, MODE, CACHE, MASK><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
     return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                         int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
-    if (fc.mode != 0) return launch_rc<S, 1, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    if (fc.stencil_cache) return launch_rc<S, 0, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    return launch_rc<S, 0, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.chmask) {     // masked frames: the uncached stencil (same values, fewer instantiations)
+        if (fc.mode != 0) return launch_rc<S, 1, false, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+        return launch_rc<S, 0, false, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    }
+    if (fc.mode != 0) return launch_rc<S, 1, false, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.stencil_cache) return launch_rc<S, 0, true, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    return launch_rc<S, 0, false, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
 }
 
 }  // namespace
