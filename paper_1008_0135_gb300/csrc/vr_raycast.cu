@@ -152,6 +152,12 @@ __device__ __forceinline__ void cell_of(float x, float y, float z, int mx, int m
     }
 }
 
+// Shared-memory slots (float4) of table entry i and of its difference to entry i + 1, n entries:
+// all entries, then all differences.  16-byte strides put any 8 consecutive entries in 8
+// different bank groups (interleaved pairs repeat every 4 entries: measurably more conflicts).
+__device__ __forceinline__ int tab_entry(int i, int) { return i; }
+__device__ __forceinline__ int tab_diff(int i, int n) { return n + i; }
+
 // Trilinear value from the 8 corners v[x + 2y + 4z], then the table lookup.
 __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool scaled, float scale,
                                           float vmin, float inv_range, float lutmax, int lmax,
@@ -170,23 +176,22 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
     const float xl = __fmul_rn(uc, lutmax);
     o.li = min((int)xl, lmax);
     o.lf = __fsub_rn(xl, (float)o.li);
-    o.L0 = s_lut[2 * o.li];
-    o.D = s_lut[2 * o.li + 1];
+    o.L0 = s_lut[tab_entry(o.li, lmax + 2)];
+    o.D = s_lut[tab_diff(o.li, lmax + 2)];
     o.r = __fmaf_rn(o.lf, o.D.x, o.L0.x);
     o.g = __fmaf_rn(o.lf, o.D.y, o.L0.y);
     o.b = __fmaf_rn(o.lf, o.D.z, o.L0.z);
     o.a = __fmaf_rn(o.lf, o.D.w, o.L0.w);
 }
 
-// The table in shared memory as (entry i, entry i+1 - entry i) pairs: the differences are the
-// same IEEE subtractions a lookup would do, made once per block instead of once per sample.
-// (Pairs beat two separate arrays: one address for both loads.)
+// The table in shared memory with its differences entry i+1 - entry i: the same IEEE
+// subtractions a lookup would do, made once per block instead of once per sample.
 __device__ __forceinline__ void load_table(const float4 *__restrict__ lut, int n, float4 *s) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 a = lut[i];
         const float4 b = i + 1 < n ? lut[i + 1] : a;
-        s[2 * i] = a;
-        s[2 * i + 1] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z),
+        s[tab_entry(i, n)] = a;
+        s[tab_diff(i, n)] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z),
                                    __fsub_rn(b.w, a.w));
     }
 }
@@ -693,7 +698,7 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t smem = 48 * (size_t)fc.nlut;     // table pairs (32 B) + gradient accumulators (16 B)
+    const size_t smem = 48 * (size_t)fc.nlut;     // table + differences (32 B) + gradient accumulators (16 B)
     k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
     return cudaGetLastError();
 }
