@@ -134,7 +134,11 @@ def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, q
            pix=None, ghost=1, nthreads=0, channels=None, window=None):
     """Returns (out, flags, nsamples).  out: (npix, 4) premultiplied RGBA for DVR, (npix,) for
     MIP; float64.  pix: flat pixel indices (row*W + col) or None for the whole frame.
-    channels: per-z 0/1 enable mask; window: ((x0,y0,z0), (x1,y1,z1)) voxel box."""
+    channels: per-z 0/1 enable mask; window: ((x0,y0,z0), (x1,y1,z1)) voxel box.
+    flags per pixel: bit 0 early-termination decision within 2e-4 (relative) of the threshold,
+    bit 1 no samples, bit 2 broken sample partition (never expected), bit 3 a composited DVR
+    sample's table coordinate within 1e-4 of a table entry (the image's derivative with respect
+    to that sample's value jumps there)."""
     a, keep = _args(cube, lut, vrange, cam, mode, step, tau, brick, quant, ghost, nthreads,
                     channels, window)
     pixa, pp = _pix(pix)

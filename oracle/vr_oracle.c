@@ -525,7 +525,13 @@ typedef struct {
     tri64 tri; tf64 tf; double Tb;  /* transmittance before this sample */
 } smp;
 
-enum { FLAG_ERT_FRAGILE = 1, FLAG_NO_SAMPLES = 2, FLAG_PARTITION_ERROR = 4 };
+enum { FLAG_ERT_FRAGILE = 1, FLAG_NO_SAMPLES = 2, FLAG_PARTITION_ERROR = 4, FLAG_TABLE_KINK = 8 };
+
+/* Half-width, in table-coordinate units, of the band around a table entry inside which the
+ * interval a sample falls in may differ between this FP64 trilinear value and a binary32 one
+ * (whose error is ~1e-6 of the value range here): the image is continuous there, its
+ * derivative with respect to the value is not. */
+#define TABLE_KINK_BAND 1e-4
 
 /* Traces one pixel.  If keep != NULL, the composited samples are stored there (capacity cap). */
 static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, int64_t pix,
@@ -588,6 +594,11 @@ static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, i
         Tseg *= (1.0 - al);
         ++*ns;
         if (keep && *nkeep < cap) keep[(*nkeep)++] = s;
+        {
+            double xr = (s.tri.v - (double)a->vmin) / ((double)a->vmax - (double)a->vmin) * (double)(a->nlut - 1);
+            if (xr > -0.5 && xr < (double)a->nlut - 0.5 && fabs(xr - nearbyint(xr)) < TABLE_KINK_BAND)
+                *flag |= FLAG_TABLE_KINK;
+        }
         if (thr > 0.0 && fabs(Tseg - thr) <= fragile_band) *flag |= FLAG_ERT_FRAGILE;
         if (Tseg <= thr) stopped = 1;
     }
@@ -618,7 +629,8 @@ static int32_t *make_exps(const orc_args *a) {
 /* Renders the listed pixels (pix = row*W + col; NULL = every pixel in order).
  * out: npix x 4 (DVR: premultiplied r, g, b, alpha) or npix x 1 (MIP).
  * flags: per pixel, bit0 = ERT decision within 2e-4 (relative) of the threshold,
- * bit1 = no samples, bit2 = broken sample partition (never expected). */
+ * bit1 = no samples, bit2 = broken sample partition (never expected), bit3 = a composited DVR
+ * sample's table coordinate within TABLE_KINK_BAND of an entry (its gradient is ambiguous). */
 int orc_render(const orc_args *a, const int64_t *pix, int64_t npix, double *out, uint8_t *flags,
                int64_t *nsamples) {
     if (a->nlut < 2 || a->W <= 0 || a->H <= 0 || !(a->step > 0.0f)) return -1;

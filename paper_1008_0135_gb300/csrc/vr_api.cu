@@ -40,10 +40,14 @@ void layout_strides(const int dim[3], int layout, int str[3]) {
 }
 
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
-    FrameLayout f{0, 0, kRcLong, kRcShort, 0.0f};
+    FrameLayout f{0, 0, kRcLong, kRcShort, 0.0f, 0};
     float best = -1.0f;
+    const bool atlas = !cb->streamed && !cb->atlas_tex.empty();
+    // with atlases, the image axis is fixed first: the one with the smaller z component
+    const int only = atlas ? (std::fabs(c->cam.R[5]) < std::fabs(c->cam.R[2]) ? 1 : 0) : -1;
     for (int i = 0; i < 2; ++i)              // image axis: camera right (row 0), up (row 1)
         for (int a = 0; a < 3; ++a) {
+            if (only >= 0 && i != only) continue;
             if (!(cb->layouts & (1 << a))) continue;
             const float sc = std::fabs(c->cam.R[3 * i + a]);
             if (sc > best + 1e-6f) {
@@ -55,6 +59,7 @@ FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
     f.tw = f.lanes_y ? kRcShort : kRcLong;
     f.th = f.lanes_y ? kRcLong : kRcShort;
     f.align = best;
+    f.atlas = atlas ? 1 : 0;
     return f;
 }
 
@@ -282,9 +287,10 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     fc.nx = (int)cb->n[0]; fc.ny = (int)cb->n[1]; fc.nz = (int)cb->n[2];
     const FrameLayout fl = frame_layout(c, cb);
     fc.lanes_y = fl.lanes_y;
-    // with a warp's rays along the contiguous axis its gathers are nearly coalesced and the
-    // stencil cache's bookkeeping costs more than it saves; with a poor alignment it pays
-    fc.stencil_cache = fl.align < 0.9f ? 1 : 0;
+    // atlases: two gathers per sample.  Linear copies: with a warp's rays along the contiguous
+    // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
+    // it saves; with a poor alignment it pays
+    fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
     return fc;
 }
 
@@ -364,6 +370,96 @@ int check_ready(vr_ctx *c, Cube *cb) {
     return VR_OK;
 }
 
+// Releases a cube's slice atlases.  Frames in flight may still gather from them: the device is
+// drained first (atlases change only with the bricking or the voxels).
+void free_atlases(Cube *cb) {
+    if (cb->atlas_arr.empty() && cb->atlas_tex.empty()) return;
+    cudaDeviceSynchronize();
+    for (auto t : cb->atlas_tex)
+        if (t) cudaDestroyTextureObject(t);
+    for (auto a : cb->atlas_arr)
+        if (a) cudaFreeArray(a);
+    cb->atlas_tex.clear();
+    cb->atlas_arr.clear();
+    cb->atlas_bytes = 0;
+    for (auto &d : cb->tmpl) { d.atlas = 0; d.alog = 0; }
+}
+
+// Slice atlas of every brick (layout bit 3) from its x-contiguous copy in the pool: slice z
+// of a brick of dx x dy x dz stored elements becomes tile (z mod 2^alog, z div 2^alog) of a 2D
+// array of 2^alog dx x ceil(dz / 2^alog) dy texels, with 2^alog the smallest power of two whose
+// square is >= dz.  FP32 bricks keep their values, 16-bit bricks their codes (as 16-bit
+// unsigned texels).  The array must fit the device's limit for 2D gathers.
+int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
+    free_atlases(cb);
+    const int nbr = (int)cb->tmpl.size();
+    const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+    int gw = 0, gh = 0;
+    CK(cudaDeviceGetAttribute(&gw, cudaDevAttrMaxTexture2DGatherWidth, c->device));
+    CK(cudaDeviceGetAttribute(&gh, cudaDevAttrMaxTexture2DGatherHeight, c->device));
+    std::vector<int> lg(nbr);
+    size_t most = 16;
+    for (int i = 0; i < nbr; ++i) {
+        const int *dm = cb->tmpl[i].dim;
+        int l = 0;
+        while ((1ll << (2 * l)) < dm[2]) ++l;
+        const long long w = (long long)dm[0] << l, h = (long long)((dm[2] + (1 << l) - 1) >> l) * dm[1];
+        if (w > gw || h > gh) return fail(VR_ERR_UNSUPPORTED, "bricks too large for a slice atlas (2D gather limit)");
+        lg[i] = l;
+        most = std::max(most, (size_t)(w * h) * esz);
+    }
+    void *tmp = nullptr;
+    CK(cudaMalloc(&tmp, most));
+    auto bail = [&](cudaError_t e, const char *what) {
+        cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        free_atlases(cb);
+        return cuda_fail(e, what);
+    };
+    cudaError_t e = cudaMemsetAsync(tmp, 0, most, s);
+    if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+    const cudaChannelFormatDesc cd = esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
+                                              : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
+    cb->atlas_arr.assign(nbr, nullptr);
+    cb->atlas_tex.assign(nbr, 0);
+    for (int i = 0; i < nbr; ++i) {
+        const int *dm = cb->tmpl[i].dim;
+        const size_t w = (size_t)dm[0] << lg[i], h = (size_t)((dm[2] + (1 << lg[i]) - 1) >> lg[i]) * dm[1];
+        cudaArray_t arr = nullptr;
+        if ((e = cudaMallocArray(&arr, &cd, w, h, cudaArrayTextureGather)) != cudaSuccess)
+            return bail(e, "cudaMallocArray (slice atlas)");
+        cb->atlas_arr[i] = arr;
+        const char *src = static_cast<const char *>(cb->d_pool) + (size_t)cb->loff[3 * (size_t)i] * esz;
+        if ((e = launch_atlas_pack(src, (int)esz, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, s)) != cudaSuccess)
+            return bail(e, "atlas pack launch");
+        if ((e = cudaMemcpy2DToArrayAsync(arr, 0, 0, tmp, w * esz, w * esz, h, cudaMemcpyDeviceToDevice, s)) !=
+            cudaSuccess)
+            return bail(e, "cudaMemcpy2DToArrayAsync (slice atlas)");
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = arr;
+        cudaTextureDesc td{};
+        td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        cudaTextureObject_t t = 0;
+        if ((e = cudaCreateTextureObject(&t, &rd, &td, nullptr)) != cudaSuccess)
+            return bail(e, "cudaCreateTextureObject (slice atlas)");
+        cb->atlas_tex[i] = t;
+        cb->atlas_bytes += w * h * esz;
+        cb->tmpl[i].atlas = t;
+        cb->tmpl[i].alog = lg[i];
+    }
+    e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        free_atlases(cb);
+        return cuda_fail(e, "slice atlas build");
+    }
+    return VR_OK;
+}
+
 int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
     const int nbr = (int)cb->tmpl.size();
     unsigned int *d_range = cb->d_bs + 2 * (size_t)nbr;
@@ -409,10 +505,13 @@ int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
         CK(cudaStreamSynchronize(s));
         for (int i = 0; i < nbr; ++i) cb->tmpl[i].exp2 = e[i];
     }
+    if (cb->layouts & 8) return build_atlases(c, cb, s);
+    free_atlases(cb);
     return VR_OK;
 }
 
 void free_cube(Cube *cb) {
+    free_atlases(cb);
     if (cb->d_src) cudaFree(cb->d_src);
     if (cb->d_pool) cudaFree(cb->d_pool);
     if (cb->d_tmpl) cudaFree(cb->d_tmpl);
@@ -897,7 +996,8 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    if (mask < 1 || mask > 7 || !(mask & 1)) return arg_fail("layout mask must be 1..7 and keep bit 0 (x contiguous)");
+    if (mask < 1 || mask > 15 || !(mask & 1))
+        return arg_fail("layout mask must be 1..15 and keep bit 0 (x contiguous)");
     if (cb->streamed && mask != 1) return fail(VR_ERR_UNSUPPORTED, "streamed bricks are stored x-contiguous only");
     if (cb->layouts == mask) return VR_OK;
     cb->layouts = mask;

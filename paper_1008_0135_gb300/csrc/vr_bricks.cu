@@ -3,6 +3,8 @@
 //
 // Bricking follows the object-space partition of Section 2.2 (each part rendered on its own);
 // the ghost layer makes every trilinear stencil of a sample a brick owns local to that brick.
+#include <algorithm>
+
 #include "vr_internal.cuh"
 
 namespace vr {
@@ -121,6 +123,37 @@ cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const
     if (nbricks <= 0) return cudaSuccess;
     dim3 grid(64, nbricks);
     k_brick_maxabs<<<grid, 256, 0, s>>>(cube, nx, ny, nz, bricks, maxbits, range);
+    return cudaGetLastError();
+}
+
+// Slice atlas: element (x, y, z) of the x-contiguous brick goes to atlas column
+// (z & (2^alog - 1)) dx + x, row (z >> alog) dy + y.  Raw bits are moved (codes stay codes).
+template <typename T>
+__global__ void k_atlas_pack(const T *__restrict__ src, int dx, int dy, int dz, int alog, char *atlas,
+                             size_t pitch) {
+    const long long n = (long long)dx * dy * dz;
+    const int cm = (1 << alog) - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % dx);
+        const long long r = i / dx;
+        const int y = (int)(r % dy), z = (int)(r / dy);
+        const size_t row = (size_t)(z >> alog) * dy + y, col = (size_t)(z & cm) * dx + x;
+        reinterpret_cast<T *>(atlas + row * pitch)[col] = src[i];
+    }
+}
+
+cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz, int alog, void *atlas,
+                              size_t pitch, cudaStream_t s) {
+    const long long n = (long long)dx * dy * dz;
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    if (esz == 4)
+        k_atlas_pack<unsigned int><<<grid, 256, 0, s>>>(static_cast<const unsigned int *>(brick), dx, dy, dz,
+                                                        alog, static_cast<char *>(atlas), pitch);
+    else
+        k_atlas_pack<unsigned short><<<grid, 256, 0, s>>>(static_cast<const unsigned short *>(brick), dx, dy,
+                                                          dz, alog, static_cast<char *>(atlas), pitch);
     return cudaGetLastError();
 }
 

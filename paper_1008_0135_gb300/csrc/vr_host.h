@@ -55,9 +55,13 @@ struct Cube {
     size_t pool_bytes = 0;
     unsigned int *d_bs = nullptr;     // per brick: max |v| bits, exponent, min, max (4 words)
     std::vector<float> vlo, vhi;      // per-brick value range of the stored region
-    // brick layouts kept in the pool: bit a = a copy whose axis a is contiguous (x always kept)
+    // brick layouts kept in the pool: bit a = a copy whose axis a is contiguous (x always kept);
+    // bit 3 = a slice-atlas texture of every brick besides the pool
     int layouts = 1;
     std::vector<long long> loff;      // element offset of brick b in layout a: loff[3 b + a]
+    std::vector<cudaArray_t> atlas_arr;          // per brick (layout bit 3)
+    std::vector<unsigned long long> atlas_tex;   // texture objects over them
+    size_t atlas_bytes = 0;
     // streamed cubes: bricks are produced on the host and cached in HBM on demand
     bool streamed = false;
     uint64_t proc_seed = 0;           // procedural cube: generator seed
@@ -130,14 +134,18 @@ struct vr_ctx {
 
 namespace vrh {
 
-// Per-frame choice of brick layout and warp orientation: the stored layout whose contiguous
-// world axis is most aligned with an image axis, and warps running along that image axis, so
-// the 32 rays of a warp gather from neighbouring addresses.
+// Per-frame choice of brick layout and warp orientation.  Linear copies: the one whose
+// contiguous world axis is most aligned with an image axis, and warps running along that image
+// axis, so the 32 rays of a warp load neighbouring addresses.  Slice atlases (when kept, always
+// preferred): warps along the image axis closer to the z-slices' plane, so a warp's gathers
+// stay within few slices; the linear copy for kernels that read linear bricks follows the
+// same image axis.
 struct FrameLayout {
-    int layout;                       // contiguous world axis of the chosen copy (0 x, 1 y, 2 z)
+    int layout;                       // contiguous world axis of the linear copy (0 x, 1 y, 2 z)
     int lanes_y;                      // warps along image y (1) or image x (0)
     int tw, th;                       // ray-cast tile size in pixels
     float align;                      // |cos| between that image axis and the contiguous axis
+    int atlas;                        // 1: the ray caster gathers from the slice atlases
 };
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb);
 // Empty-space skipping: prefix counts of table entries with non-zero opacity, and whether a

@@ -35,7 +35,10 @@ struct FrameConsts {
     int nx, ny, nz;                // cube size
     int lanes_y;                   // 0: a warp's 32 lanes run along image x (tiles 32x8);
                                    // 1: along image y (tiles 8x32)
-    int stencil_cache;             // 1: rays reuse shared stencil corners (poorly aligned layout)
+    int fetch;                     // how a sample's 8 stencil corners are read: 0 = 8 loads from
+                                   // the linear brick, 1 = the same with the stencil cache (rays
+                                   // keep shared corners; poorly aligned layout), 2 = 2 gathers
+                                   // from the brick's slice-atlas texture
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
 };
 
@@ -53,6 +56,11 @@ struct DrawBrick {
     long long data_off;            // element offset of the stored brick in the pool
     long long frag_off;            // fragment offset (pixels) of the brick's sub-image
     long long bytes;               // stored bytes of the brick
+    unsigned long long atlas;      // texture object over the brick's slice atlas (0: none): a 2D
+                                   // array whose tile (z & (2^alog - 1), z >> alog) of dim[0] x
+                                   // dim[1] texels holds stored slice z (FP32 values or 16-bit codes)
+    int alog;
+    int pad_;
 };
 
 struct TileItem {                  // one ray-cast work item
@@ -75,6 +83,10 @@ cudaError_t launch_minmax(const float *v, long long n, unsigned int *enc_minmax,
 cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                 int nbricks, unsigned int *maxbits, unsigned int *range,
                                 cudaStream_t s);
+// Packs one x-contiguous stored brick (dx*dy*dz elements of esz = 4 or 2 bytes) into a
+// pitch-linear slice atlas of (2^alog dx) x (ceil(dz / 2^alog) dy) elements, row pitch `pitch` bytes.
+cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz, int alog, void *atlas,
+                              size_t pitch, cudaStream_t s);
 cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                int nbricks, const unsigned int *maxbits, int storage, void *pool,
                                int *exps, cudaStream_t s);

@@ -201,6 +201,47 @@ struct Strides {
     int x, y, z;
 };
 
+// A brick's slice atlas (see DrawBrick::atlas): where its stored slice z starts.
+struct Atlas {
+    unsigned long long tex;
+    int alog, dx, dy;
+};
+
+template <int S>
+__device__ __forceinline__ float code_value(unsigned int c);
+template <>
+__device__ __forceinline__ float code_value<0>(unsigned int c) { return __uint_as_float(c); }
+template <>
+__device__ __forceinline__ float code_value<1>(unsigned int c) {
+    return __half2float(__ushort_as_half((unsigned short)c));
+}
+template <>
+__device__ __forceinline__ float code_value<2>(unsigned int c) { return __uint_as_float(c << 16); }
+
+// The 2x2 footprint (ix..ix+1, iy..iy+1) of slice iz and of slice iz+1, two texture gathers.
+// A gather at unnormalised (x, y) returns the texels at floor(x - 1/2) and the next one on
+// each axis, ordered ((x0,y1), (x1,y1), (x1,y0), (x0,y0)); x = ix + 1 selects exactly ix.  The
+// texels are returned unfiltered, so the corners are the stored values themselves.
+template <int S>
+__device__ __forceinline__ void fetch8_atlas(const Atlas &a, int ix, int iy, int iz, float v[8]) {
+    const int cm = (1 << a.alog) - 1, iz1 = iz + 1;
+    const float x0 = (float)((iz & cm) * a.dx + ix + 1), y0 = (float)((iz >> a.alog) * a.dy + iy + 1);
+    const float x1 = (float)((iz1 & cm) * a.dx + ix + 1), y1 = (float)((iz1 >> a.alog) * a.dy + iy + 1);
+    if constexpr (S == 0) {
+        const float4 g0 = tex2Dgather<float4>(a.tex, x0, y0, 0);
+        const float4 g1 = tex2Dgather<float4>(a.tex, x1, y1, 0);
+        v[0] = g0.w; v[1] = g0.z; v[2] = g0.x; v[3] = g0.y;
+        v[4] = g1.w; v[5] = g1.z; v[6] = g1.x; v[7] = g1.y;
+    } else {
+        const uint4 g0 = tex2Dgather<uint4>(a.tex, x0, y0, 0);
+        const uint4 g1 = tex2Dgather<uint4>(a.tex, x1, y1, 0);
+        v[0] = code_value<S>(g0.w); v[1] = code_value<S>(g0.z);
+        v[2] = code_value<S>(g0.x); v[3] = code_value<S>(g0.y);
+        v[4] = code_value<S>(g1.w); v[5] = code_value<S>(g1.z);
+        v[6] = code_value<S>(g1.x); v[7] = code_value<S>(g1.y);
+    }
+}
+
 template <int S>
 __device__ __forceinline__ void fetch8(const void *src, int i0, const Strides &t, float v[8]) {
     v[0] = ldv<S>(src, i0);             v[1] = ldv<S>(src, i0 + t.x);
@@ -295,10 +336,11 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 // ----------------------------------------------------------------------------------------------
 // One brick segment of a ray: n lattice samples from the anchor q, composited front to back
 // until the segment's transmittance reaches the threshold.  Returns the samples composited.
-// MASK: a spectral-channel mask is set (its own instantiation, so unmasked frames carry none of
-// its registers or branches).
-template <int S, bool CACHE, bool CLAMP, bool MASK>
-__device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, int mx, int my, int mz,
+// F: how the stencil is read (FrameConsts::fetch).  MASK: a spectral-channel mask is set (its own
+// instantiation, so unmasked frames carry none of its registers or branches).
+template <int S, int F, bool CLAMP, bool MASK>
+__device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, const Atlas &atl,
+                                           int mx, int my, int mz,
                                            float scale, float qx, float qy, float qz, const float d[3],
                                            int n, const FrameConsts &fc, const float4 *s_lut,
                                            int org_z, float vcode,
@@ -314,7 +356,9 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, i
         Cell cl;
         cell_of<CLAMP>(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
                        mx, my, mz, cl);
-        if (CACHE)
+        if (F == 2)
+            fetch8_atlas<S>(atl, cl.ix, cl.iy, cl.iz, v);
+        else if (F == 1)
             fetch8_cached<S>(src, st, cl, px, py, pz, v);
         else
             fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
@@ -327,10 +371,10 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, i
     return j;
 }
 
-// CACHE: a ray keeps the stencil corners its next cell shares with the last one (fewer
-// gathers, more instructions; pays off when a warp's gathers scatter over many cache lines);
-// otherwise all eight corners are gathered for every sample.
-template <int S, int MODE, bool CACHE, bool MASK>
+// F = 1: a ray keeps the stencil corners its next cell shares with the last one (fewer loads,
+// more instructions; pays off when a warp's loads scatter over many cache lines); F = 0: all
+// eight corners are loaded for every sample; F = 2: two gathers from the slice atlas.
+template <int S, int MODE, int F, bool MASK>
 __global__ void VR_RAYCAST_BOUNDS
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
@@ -359,6 +403,7 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
         const Strides st{b.str[0], b.str[1], b.str[2]};
         const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
         const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
+        const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
         if (MODE == 0) {
             float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
             if (hit) {
@@ -378,9 +423,9 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                                     min(e0.iz, e1.iz) >= 0 && max(e0.iz, e1.iz) <= mz;
                 const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
                 const int j = inside
-                    ? dvr_segment<S, CACHE, false, MASK>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                    ? dvr_segment<S, F, false, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
                                                    b.org[2], vcode, c0, c1, c2, T)
-                    : dvr_segment<S, CACHE, true, MASK>(src, st, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
+                    : dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
                                                   b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
@@ -401,7 +446,10 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                     const int iz = clampi((int)flz - b.org[2], 0, mz);
                     const int i0 = ix * st.x + iy * st.y + iz * st.z;
                     float v[8];
-                    fetch8<S>(src, i0, st, v);
+                    if (F == 2)
+                        fetch8_atlas<S>(atl, ix, iy, iz, v);
+                    else
+                        fetch8<S>(src, i0, st, v);
                     if (MASK)
                         mask_channels(v, iz, b.org[2], fc.nz, fc.chmask,
                                       S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2));
@@ -629,31 +677,35 @@ __global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts,
     glut[i] = (float)acc;
 }
 
-template <int S, int MODE, bool CACHE, bool MASK>
+template <int S, int MODE, int F, bool MASK>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static bool attr = false;
     const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, CACHE, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, F, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(2 * sizeof(float4) * kMaxLut));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_raycast<S, MODE, CACHE, MASK><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
+    k_raycast<S, MODE, F, MASK><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
     return cudaGetLastError();
 }
 
 template <int S>
 cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                         int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
-    if (fc.chmask) {     // masked frames: the uncached stencil (same values, fewer instantiations)
-        if (fc.mode != 0) return launch_rc<S, 1, false, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-        return launch_rc<S, 0, false, true>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+#define VR_RC(MODE, F, MASK) launch_rc<S, MODE, F, MASK>(fc, lut, db, items, nitems, pool, frags, ctr, s)
+    const bool atlas = fc.fetch == 2;
+    if (fc.chmask) {     // masked frames: no stencil cache (same values, fewer instantiations)
+        if (fc.mode != 0) return atlas ? VR_RC(1, 2, true) : VR_RC(1, 0, true);
+        return atlas ? VR_RC(0, 2, true) : VR_RC(0, 0, true);
     }
-    if (fc.mode != 0) return launch_rc<S, 1, false, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    if (fc.stencil_cache) return launch_rc<S, 0, true, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
-    return launch_rc<S, 0, false, false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+    if (fc.mode != 0) return atlas ? VR_RC(1, 2, false) : VR_RC(1, 0, false);
+    if (atlas) return VR_RC(0, 2, false);
+    if (fc.fetch == 1) return VR_RC(0, 1, false);
+    return VR_RC(0, 0, false);
+#undef VR_RC
 }
 
 }  // namespace

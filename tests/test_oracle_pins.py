@@ -162,6 +162,26 @@ def _slab64(o, d, n):
     return (t0, t1) if t1 > t0 else None
 
 
+def test_table_kink_flag_marks_samples_on_table_entries(orc):
+    """Bit 3 of the flags: a composited sample's table coordinate x = (v - vmin)/(vmax - vmin)
+    (N - 1) within 1e-4 of an entry.  A constant cube whose value sits on entry 10 of a
+    32-entry table flags every pixel with samples; half-way between entries flags none; the
+    bit changes nothing else."""
+    rng = np.random.default_rng(5)
+    shape = (9, 8, 7)
+    lut = synth.random_lut(1, n=32, alpha_max=0.2)
+    cam = synth.random_camera(rng, shape, 20, 18)
+    on = synth.constant_cube(shape, -3.0 + 11.0 * 10.0 / 31.0)
+    half = synth.constant_cube(shape, -3.0 + 11.0 * 10.5 / 31.0)
+    o1, f1, _ = orc.render(on, lut, (-3, 8), cam, step=0.5, tau=1.0)
+    o2, f2, _ = orc.render(half, lut, (-3, 8), cam, step=0.5, tau=1.0)
+    hit = (f1 & 2) == 0
+    assert hit.sum() > 100
+    assert np.all(f1[hit] & 8) and not np.any(f1[~hit] & 8)
+    assert not np.any(f2 & 8)
+    assert np.all((f1 & ~np.uint8(8)) == (f2 & ~np.uint8(8)))
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
 def test_constant_cube_alpha_closed_form(orc, seed):
     rng = np.random.default_rng(seed)

@@ -234,6 +234,25 @@ def test_error_statuses(ctx):
         ctx.set_transfer_function(synth.ramp_lut(), 5.0, 5.0)
     with pytest.raises(P.VrError):
         ctx.load_cube(cube, sub_origin=(0, 0, 0), sub_extent=(17, 1, 1))
+    with pytest.raises(P.VrError) as e:
+        ctx.set_brick_layouts(cid, 16)
+    assert e.value.status == -1
+    ctx.free_cube(cid)
+
+
+def test_slice_atlas_refuses_bricks_beyond_the_gather_limit(ctx):
+    """A 4002 x 4 x 4002 stored brick would need a 64 x 4002 = 256128 texel wide atlas, beyond
+    the device's 2D-gather limit: the bricking is refused (VR_ERR_UNSUPPORTED), and the same
+    bricking without atlases is fine."""
+    import torch
+    import paper_1008_0135_gb300 as P
+    cid = ctx.load_cube(torch.zeros((4000, 2, 4000), device="cuda"))
+    ctx.set_brick_layouts(cid, 9)
+    with pytest.raises(P.VrError) as e:
+        ctx.set_bricking(cid, (4000, 2, 4000))
+    assert e.value.status == -7 and "slice atlas" in str(e.value)
+    ctx.set_brick_layouts(cid, 1)
+    ctx.set_bricking(cid, (4000, 2, 4000))
     ctx.free_cube(cid)
 
 
@@ -280,16 +299,18 @@ def test_16bit_bricks(ctx, orc, storage):
 
 
 # ---------------------------------------------------------------------------------------------
-# brick layouts: the gathered addresses change, the arithmetic does not
+# brick layouts: the gathered addresses change, the arithmetic does not.  Mask 7 keeps x-, y- and
+# z-contiguous copies; 9 and 15 add slice atlases (texture gathers) that every frame then reads.
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_brick_layouts_give_identical_images(ctx, orc, storage):
+@pytest.mark.parametrize("storage,layouts", [("f32", 7), ("f16", 7), ("f32", 9), ("f16", 15),
+                                             ("bf16", 9)])
+def test_brick_layouts_give_identical_images(ctx, orc, storage, layouts):
     cube = synth.pr1_cube(seed=2)
     lut = synth.ramp_lut(alpha=0.5)
     one = ctx.load_cube(cube)
     ctx.set_bricking(one, (24, 32, 20), 1, storage)
     many = ctx.load_cube(cube)
-    ctx.set_brick_layouts(many, 7)
+    ctx.set_brick_layouts(many, layouts)
     ctx.set_bricking(many, (24, 32, 20), 1, storage)
     rng = np.random.default_rng(21)
     cams = [synth.pr1_camera(W=100, H=90), synth.random_camera(rng, (64, 64, 64), 90, 110),
@@ -345,8 +366,8 @@ def test_empty_space_skipping_is_exact(ctx, orc, storage):
 # ---------------------------------------------------------------------------------------------
 # spectral-channel masks and render windows (Section 2.3)
 # ---------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_channel_mask_and_window(ctx, orc, storage):
+@pytest.mark.parametrize("storage,layouts", [("f32", 7), ("f16", 7), ("f32", 9), ("bf16", 9)])
+def test_channel_mask_and_window(ctx, orc, storage, layouts):
     rng = np.random.default_rng(77)
     cube = synth.pr1_cube(seed=8)
     mask = (rng.uniform(size=64) > 0.3).astype(np.uint8)
@@ -354,7 +375,7 @@ def test_channel_mask_and_window(ctx, orc, storage):
     lut = synth.ramp_lut(alpha=0.4)
     lut[:20, 3] = 0.05                        # vmin itself visible: masked slices show
     cid = ctx.load_cube(cube)
-    ctx.set_brick_layouts(cid, 7)
+    ctx.set_brick_layouts(cid, layouts)
     ctx.set_bricking(cid, (16, 32, 24), 1, storage)
     q = "f32" if storage == "f32" else storage
     try:

@@ -27,7 +27,7 @@ def setup():
     ctx = P.Context(0)
     cube = synth.pr1_cube(seed=0)
     cid = ctx.load_cube(cube)
-    ctx.set_brick_layouts(cid, 7)
+    ctx.set_brick_layouts(cid, 15)
     ctx.set_bricking(cid, (32, 32, 32), 1, "f32")
     ctx.set_transfer_function(synth.ramp_lut(alpha=0.5), -3.0, 20.0)
     yield torch, ctx, _abi.lib(), cid
