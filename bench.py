@@ -340,7 +340,7 @@ def empty_space_leg(ctx, device, steps=16):
     cid = ctx.load_cube(cube)
     del cube
     torch.cuda.empty_cache()
-    ctx.set_brick_layouts(cid, 7)
+    ctx.set_brick_layouts(cid, 9)
     ctx.set_bricking(cid, cfg["brick"], 1, "f32")
     x = np.linspace(cfg["vrange"][0], cfg["vrange"][1], 256)
     out = torch.empty((cfg["H"], cfg["W"], 4), dtype=torch.float32, device=device)
@@ -407,7 +407,7 @@ def run_ours(args, dist):
         cube_np = cube.cpu().numpy()
     del cube
     torch.cuda.empty_cache()
-    ctx.set_brick_layouts(cid, 7)          # x-, y- and z-contiguous copies of every brick
+    ctx.set_brick_layouts(cid, 9)          # slice atlases (gathers) + the x-contiguous copy
     ctx.set_bricking(cid, cfg["brick"], 1, "f32")
     out = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     peak, psrc = peaks()
@@ -427,6 +427,7 @@ def run_ours(args, dist):
                    f"{cfg['step']}, 256^3 bricks + ghost 1, FP32 bricks, ERT 0.99",
                    "cube_xyz": [nx, ny, nz], "frame": [W, H], "bricks": list(cfg["brick"]),
                    "l2": "inputs larger than L2 (12.1 GB cube); no flush",
+                   "brick_layouts": "slice-atlas textures (2 gathers per sample) + x-contiguous copy",
                    "parallelism": f"replicas x{dist.world}"},
         "ms_per_frame": round(t_max / args.steps, 4),
         "samples_per_frame": st["samples"] // max(args.steps, 1),
