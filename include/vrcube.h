@@ -150,15 +150,23 @@ int vr_compute_minmax(vr_ctx *ctx, int cube_id, float *vmin, float *vmax);
  * per brick, a power-of-two scale 2^e with e chosen from the brick's stored max |v| (FP16:
  * max|v| 2^-e <= 2^14; BF16: <= 1), the codes being round-to-nearest-even of v 2^-e.
  * Synchronous.  Errors: VR_ERR_ARG (sizes < 1, ghost != 1, storage), VR_ERR_NOT_FOUND,
- * VR_ERR_OOM, VR_ERR_CUDA. */
+ * VR_ERR_UNSUPPORTED (bricks larger than a streamed cube's cache slots; slice atlases kept and
+ * a brick's atlas beyond the device's 2D-gather size), VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_bricking(vr_ctx *ctx, int cube_id, int bx, int by, int bz, int ghost, int storage);
 
-/* Brick layouts kept for a cube: bit a of `mask` keeps a copy of every brick whose axis a
+/* Brick layouts kept for a cube (how the stored bricks of Section 2.2's parts are laid out for
+ * the ray caster of Section 2.4).  Bits 0-2 of `mask` keep a copy of every brick whose axis a
  * (0 x, 1 y, 2 z) is the contiguous one in memory; bit 0 is always kept.  Each frame reads the
  * copy whose contiguous axis is most aligned with an image axis and runs its warps along that
- * image axis, so the 32 rays of a warp gather neighbouring addresses (each extra layout costs
- * one more copy of the pool in HBM).  A bricked cube is rebuilt.  Streamed cubes keep the
- * x-contiguous copy only.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED,
+ * image axis, so the 32 rays of a warp load neighbouring addresses (each extra layout costs one
+ * more copy of the pool in HBM).  Bit 3 also keeps a slice atlas of every brick: a 2D texture
+ * array whose tiles are the brick's z-slices, from which a sample's 8 stencil voxels are read
+ * by two texture gathers (exact texels; images identical to the linear copies).  When atlases
+ * are kept every DVR and MIP frame reads them; the adjoint reads a linear copy.  An atlas must
+ * fit the device's 2D-gather size (32768 texels a side; 258^3 stored bricks need 8256 x 2322).
+ * A bricked cube is rebuilt.  Streamed cubes keep the x-contiguous copy only.
+ * Mask 1..15 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
+ * (streamed cube with mask != 1; atlas beyond the gather size, raised by the rebuild),
  * VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_brick_layouts(vr_ctx *ctx, int cube_id, int mask);
 
