@@ -62,6 +62,9 @@ extern "C" {
 /* render modes */
 #define VR_DVR 0
 #define VR_MIP 1
+/* early-termination scope (vr_set_termination) */
+#define VR_TERM_SEGMENT 0
+#define VR_TERM_GLOBAL 1
 
 typedef struct vr_ctx vr_ctx;
 
@@ -193,6 +196,22 @@ int vr_set_camera(vr_ctx *ctx, const float view[16], int proj, float param, int 
  * reaches tau (test: transmittance <= 1 - tau after compositing a sample); tau >= 1 disables
  * it.  Errors: VR_ERR_ARG (mode, step <= 0, tau <= 0). */
 int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold);
+
+/* Scope of DVR early ray termination (Section 2.4: a ray stops once its accumulated value
+ * reaches its maximum; Section 2.5: the parts' sub-images are composited in depth order).
+ * VR_TERM_SEGMENT (default): every brick ray-casts its own segment of a ray from full
+ * transmittance and stops it at tau; the bricks' sub-images (fragments) are then composited
+ * front to back, so each brick works independently, as on the paper's cluster.
+ * VR_TERM_GLOBAL (occlusion skipping): bricks are ray-cast in waves of equal front-to-back
+ * key, nearest first, into one accumulator per pixel (colour, transmittance); a ray continues
+ * from the transmittance the nearer bricks left and stops once the whole ray's opacity reaches
+ * tau, so samples behind opaque pixels are skipped and a brick whose rays are all occluded
+ * costs no sampling.  The image is the unbricked ray's (global termination); it differs from
+ * VR_TERM_SEGMENT's by at most 1 - tau per channel.  No fragments are written (stats count
+ * none).  Not available for streamed cubes (vr_render_frame returns VR_ERR_UNSUPPORTED),
+ * vr_render_frame_noalloc or vr_render_backward (both VR_ERR_UNSUPPORTED); MIP ignores it.
+ * Errors: VR_ERR_ARG. */
+int vr_set_termination(vr_ctx *ctx, int mode);
 
 /* Renders one frame of cube `cube_id` with the current table, camera and parameters.
  * out: W*H*4 floats (DVR) or W*H floats (MIP) in host (VR_HOST) or device (VR_DEVICE) memory.

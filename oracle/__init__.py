@@ -38,6 +38,7 @@ class Args(C.Structure):
         ("quant", C.c_int32), ("ghost", C.c_int32), ("nthreads", C.c_int32),
         ("procedural", C.c_int32), ("proc_seed", C.c_uint64),
         ("channels", C.c_void_p), ("win_lo", C.c_int64 * 3), ("win_hi", C.c_int64 * 3),
+        ("term_global", C.c_int32),
     ]
 
 
@@ -86,10 +87,14 @@ class Procedural:
         self.shape_xyz = tuple(int(v) for v in shape_xyz)
 
 
+TERM = {"segment": 0, "global": 1}
+
+
 def _args(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, quant="f32",
-          ghost=1, nthreads=0, channels=None, window=None):
+          ghost=1, nthreads=0, channels=None, window=None, term="segment"):
     lut = np.ascontiguousarray(lut, dtype=np.float32)
     a = Args()
+    a.term_global = TERM[term]
     if isinstance(cube, Procedural):
         nx, ny, nz = cube.shape_xyz
         a.vox = None
@@ -131,16 +136,18 @@ def _pix(pix):
 
 
 def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, quant="f32",
-           pix=None, ghost=1, nthreads=0, channels=None, window=None):
+           pix=None, ghost=1, nthreads=0, channels=None, window=None, term="segment"):
     """Returns (out, flags, nsamples).  out: (npix, 4) premultiplied RGBA for DVR, (npix,) for
     MIP; float64.  pix: flat pixel indices (row*W + col) or None for the whole frame.
     channels: per-z 0/1 enable mask; window: ((x0,y0,z0), (x1,y1,z1)) voxel box.
+    term: DVR early termination per brick segment ("segment") or of the whole ray ("global";
+    the bricking then only sets the 16-bit scales).
     flags per pixel: bit 0 early-termination decision within 2e-4 (relative) of the threshold,
     bit 1 no samples, bit 2 broken sample partition (never expected), bit 3 a composited DVR
     sample's table coordinate within 1e-4 of a table entry (the image's derivative with respect
     to that sample's value jumps there)."""
     a, keep = _args(cube, lut, vrange, cam, mode, step, tau, brick, quant, ghost, nthreads,
-                    channels, window)
+                    channels, window, term)
     pixa, pp = _pix(pix)
     npix = cam["W"] * cam["H"] if pix is None else len(pixa)
     stride = 4 if mode == "dvr" else 1

@@ -58,6 +58,7 @@ typedef struct {
     uint64_t proc_seed;
     const uint8_t *channels;        /* per spectral channel z: 0 = disabled (NULL: all enabled) */
     int64_t win_lo[3], win_hi[3];   /* render window [lo, hi) in voxels (hi <= lo: whole cube) */
+    int32_t term_global;            /* DVR early termination: 0 per brick segment, 1 whole ray */
 } orc_args;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -577,7 +578,10 @@ static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, i
         if (cx < 0 || cy < 0 || cz < 0) { *flag |= FLAG_PARTITION_ERROR; continue; }
         if (cx != seg[0] || cy != seg[1] || cz != seg[2]) {  /* a new brick segment */
             seg[0] = cx; seg[1] = cy; seg[2] = cz;
-            Tseg = 1.0; stopped = 0;
+            /* per-segment termination restarts from full transmittance in every brick (the
+             * parts are ray-cast independently, Section 2.5); global termination keeps the
+             * whole ray's transmittance and its stop (Section 2.4) */
+            if (!a->term_global) { Tseg = 1.0; stopped = 0; }
         }
         if (stopped) continue;
         int e = exps ? exps[cx + r.nb[0] * (cy + r.nb[1] * cz)] : 0;

@@ -190,6 +190,13 @@ class Context:
         _check(self._L.vr_set_render_params(self._h, self.mode, float(step), float(tau)),
                "vr_set_render_params")
 
+    def set_termination(self, scope: str = "segment"):
+        """Early-termination scope for DVR: "segment" (each brick's ray segment stops on its own;
+        fragments composited afterwards) or "global" (occlusion skipping: bricks in front-to-back
+        waves into per-pixel accumulators, rays stop once the whole ray is opaque)."""
+        _check(self._L.vr_set_termination(self._h, {"segment": 0, "global": 1}[scope]),
+               "vr_set_termination")
+
     def set_channel_mask(self, mask=None):
         """0/1 per spectral channel (cube z); None switches every channel on."""
         if mask is None:

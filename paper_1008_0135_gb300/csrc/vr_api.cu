@@ -201,10 +201,12 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
             } else if (cam.proj == VR_PERSP && behind > 0) {
                 x0 = 0; y0 = 0; x1 = W; y1 = H;     // straddles the eye plane: whole frame
             } else {
-                x0 = (int)std::max(0.0, std::floor(mnx) - 1.0);
-                y0 = (int)std::max(0.0, std::floor(mny) - 1.0);
-                x1 = (int)std::min((double)W, std::ceil(mxx) + 1.0);
-                y1 = (int)std::min((double)H, std::ceil(mxy) + 1.0);
+                // clamped to the frame in double first: the int conversion of an
+                // out-of-range double is undefined
+                x0 = (int)std::min((double)W, std::max(0.0, std::floor(mnx) - 1.0));
+                y0 = (int)std::min((double)H, std::max(0.0, std::floor(mny) - 1.0));
+                x1 = (int)std::max(0.0, std::min((double)W, std::ceil(mxx) + 1.0));
+                y1 = (int)std::max(0.0, std::min((double)H, std::ceil(mxy) + 1.0));
                 if (x1 <= x0 || y1 <= y0) cull = true;
             }
         }
@@ -229,7 +231,17 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     wl.db.reserve(order.size());
     const FrameLayout fl = frame_layout(c, cb);
     long long frag = 0;
+    // waves: bricks of one front-to-back key share no ray (the key grows at every brick a ray
+    // enters), so a wave's bricks can update the pixels' accumulators concurrently
+    wl.wave_start.clear();
+    bool first = true;
+    long long wkey = 0;
     for (auto &o : order) {
+        if (first || o.first != wkey) {
+            wl.wave_start.push_back((int)wl.items.size());
+            wkey = o.first;
+            first = false;
+        }
         DrawBrick d = cand[o.second];
         d.frag_off = frag;
         frag += (long long)d.rect[2] * d.rect[3];
@@ -241,6 +253,7 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
             for (int tx = 0; tx < tw; ++tx) wl.items.push_back(TileItem{di, tx, ty});
         wl.db.push_back(d);
     }
+    wl.wave_start.push_back((int)wl.items.size());
     wl.frag_px = frag;
     // screen-tile bins in front-to-back order
     const int ntx = (W + kTile - 1) / kTile, nty = (H + kTile - 1) / kTile;
@@ -291,6 +304,7 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
     // it saves; with a poor alignment it pays
     fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
+    fc.accum = (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) ? 1 : 0;
     return fc;
 }
 
@@ -635,10 +649,12 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
             } else if (cam.proj == VR_PERSP && behind > 0) {
                 x0 = 0; y0 = 0; x1 = W; y1 = H;
             } else {
-                x0 = (int)std::max(0.0, std::floor(mnx) - 1.0);
-                y0 = (int)std::max(0.0, std::floor(mny) - 1.0);
-                x1 = (int)std::min((double)W, std::ceil(mxx) + 1.0);
-                y1 = (int)std::min((double)H, std::ceil(mxy) + 1.0);
+                // clamped to the frame in double first: the int conversion of an
+                // out-of-range double is undefined
+                x0 = (int)std::min((double)W, std::max(0.0, std::floor(mnx) - 1.0));
+                y0 = (int)std::min((double)H, std::max(0.0, std::floor(mny) - 1.0));
+                x1 = (int)std::max(0.0, std::min((double)W, std::ceil(mxx) + 1.0));
+                y1 = (int)std::max(0.0, std::min((double)H, std::ceil(mxy) + 1.0));
                 if (x1 <= x0 || y1 <= y0) cull = true;
             }
         }
@@ -992,6 +1008,13 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     return VR_OK;
 }
 
+int vr_set_termination(vr_ctx *c, int mode) {
+    if (!c) return arg_fail("null ctx");
+    if (mode != VR_TERM_SEGMENT && mode != VR_TERM_GLOBAL) return arg_fail("termination must be VR_TERM_SEGMENT or VR_TERM_GLOBAL");
+    c->term = mode;
+    return VR_OK;
+}
+
 int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
@@ -1108,16 +1131,22 @@ namespace vrh {
 // One frame of cube `cb` with the context's current table, camera and parameters.
 __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
-    if (cb->streamed) return render_streamed(c, cb, out, out_where, s);
+    if (cb->streamed) {
+        if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL)
+            return fail(VR_ERR_UNSUPPORTED, "global termination needs resident bricks (streamed cube)");
+        return render_streamed(c, cb, out, out_where, s);
+    }
     FrameConsts fc = make_consts(c, cb);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     WorkList wl;
     if ((rc = stage_frame(c, cb, wl, s, ev[0])) != VR_OK) return rc;
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
-    const size_t fbytes = (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
-    if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
     const size_t opix = (size_t)fc.cam.W * fc.cam.H;
+    // fragments, or with global termination one accumulator per pixel
+    const size_t fbytes = fc.accum ? opix * sizeof(float4)
+                                   : (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
+    if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
     const size_t ofl = opix * (c->mode == VR_DVR ? 4 : 1);
     float *dst = out;
     const bool direct = out_where == VR_DEVICE && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
@@ -1131,11 +1160,25 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
     const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
     const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
-    if (ev[1]) CK(cudaEventRecord(ev[1], s));
-    CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
-    if (ev[2]) CK(cudaEventRecord(ev[2], s));
-    CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
-    if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    if (fc.accum) {
+        // global termination: one ray-cast launch per front-to-back wave into the accumulator
+        float4 *acc = reinterpret_cast<float4 *>(c->d_frags.p);
+        CK(launch_accum_init(acc, (long long)opix, s));
+        if (ev[1]) CK(cudaEventRecord(ev[1], s));
+        for (size_t w = 0; w + 1 < wl.wave_start.size(); ++w) {
+            const int i0 = wl.wave_start[w], n = wl.wave_start[w + 1] - i0;
+            if (n > 0) CK(launch_raycast(fc, d_lut, d_db, d_items + i0, n, cb->d_pool, acc, c->d_ctr, s));
+        }
+        if (ev[2]) CK(cudaEventRecord(ev[2], s));
+        CK(launch_accum_finalize(acc, dst, (long long)opix, s));
+        if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    } else {
+        if (ev[1]) CK(cudaEventRecord(ev[1], s));
+        CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
+        if (ev[2]) CK(cudaEventRecord(ev[2], s));
+        CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
+        if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    }
     if (!direct) {
         CK(cudaMemcpyAsync(out, dst, ofl * sizeof(float),
                            out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
@@ -1144,7 +1187,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     c->frame_pending = true;
     if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
     c->frames++;
-    c->fragments += wl.frag_px;
+    c->fragments += fc.accum ? 0 : wl.frag_px;
     c->bricks_drawn += (int64_t)wl.db.size();
     if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
     return VR_OK;
@@ -1176,6 +1219,8 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
         g_last_error = "backward needs DVR mode and resident FP32 bricks";
         return VR_ERR_UNSUPPORTED;
     }
+    if (c->term != VR_TERM_SEGMENT)
+        return fail(VR_ERR_UNSUPPORTED, "backward replays per-segment termination (VR_TERM_SEGMENT)");
     if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
     if ((rc = set_dev(c)) != VR_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1282,6 +1327,8 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
     if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed cubes need the brick cache");
+    if (c->mode == VR_DVR && c->term != VR_TERM_SEGMENT)
+        return fail(VR_ERR_UNSUPPORTED, "the no-allocation path composites per-segment fragments (VR_TERM_SEGMENT)");
     int rc = check_ready(c, cb);
     if (rc) return rc;
     if ((rc = set_dev(c)) != VR_OK) return rc;

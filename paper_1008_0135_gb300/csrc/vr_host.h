@@ -78,6 +78,7 @@ struct WorkList {
     std::vector<DrawBrick> db;
     std::vector<TileItem> items;
     std::vector<int> tile_start, tile_list;
+    std::vector<int> wave_start;      // items of front-to-back key wave w: [wave_start[w], [w+1])
     long long frag_px = 0;
     // offsets inside the staged upload
     size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, off_mask = 0, bytes = 0;
@@ -101,6 +102,7 @@ struct vr_ctx {
     int mode = VR_DVR;
     float step = 0.5f;
     float tau = 0.99f;
+    int term = VR_TERM_SEGMENT;       // early termination per brick segment or global (waves)
     bool full_rect = false;
     bool timing = false;
     // Section 2.3 viewer controls: spectral channels switched off, sub-cube window

@@ -40,6 +40,8 @@ struct FrameConsts {
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
                                    // from the brick's slice-atlas texture
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
+    int accum;                     // DVR with global termination: rays continue from and write
+                                   // back a per-pixel accumulator (passed as the fragments)
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -93,6 +95,10 @@ cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const 
 cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
                            const TileItem *items, int nitems, const void *pool, void *frags,
                            Counters *ctr, cudaStream_t s);
+// Global termination: fill the W*H accumulator with (0, 0, 0, 1); turn it into premultiplied
+// RGBA (colour, 1 - transmittance) in `out` (W*H float4).
+cudaError_t launch_accum_init(float4 *acc, long long npix, cudaStream_t s);
+cudaError_t launch_accum_finalize(const float4 *acc, float *out, long long npix, cudaStream_t s);
 cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,
                              const int *tile_list, const void *frags, float *out, cudaStream_t s);
 cudaError_t launch_composite_backward(const FrameConsts &fc, const DrawBrick *db,

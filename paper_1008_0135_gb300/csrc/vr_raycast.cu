@@ -12,6 +12,9 @@
 // contracted), identical for every brick, so neighbouring bricks split each ray's samples
 // exactly, with no sample lost or counted twice.
 #include <math.h>
+
+#include <algorithm>
+
 #include "vr_internal.cuh"
 
 // Tuning knobs of the ray-cast kernel (build-time): unroll factor of the sample loop, and the
@@ -374,6 +377,11 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
 // F = 1: a ray keeps the stencil corners its next cell shares with the last one (fewer loads,
 // more instructions; pays off when a warp's loads scatter over many cache lines); F = 0: all
 // eight corners are loaded for every sample; F = 2: two gathers from the slice atlas.
+// MODE 0: DVR, one fragment (colour, transmittance) per (brick, pixel of its rectangle);
+// MODE 1: MIP, one maximum per (brick, pixel); MODE 2: DVR with global termination (occlusion
+// skipping): the ray continues from its pixel's accumulator (colour, transmittance) left by
+// the nearer bricks of earlier waves and writes it back; a ray that nearer bricks already made
+// opaque takes no sample, and a CTA whose rays all are exits before loading the table.
 template <int S, int MODE, int F, bool MASK>
 __global__ void VR_RAYCAST_BOUNDS
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
@@ -391,12 +399,29 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
     const int rx = fc.lanes_y ? it.tx * kRcShort + warp : it.tx * kRcLong + lane;
     const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + warp;
     const int rw = b.rect[2];
+    const bool inrect = rx < rw && ry < b.rect[3];
     int nsamp = 0;
-    if (rx < rw && ry < b.rect[3]) {
-        float o[3], d[3];
+    float o[3], d[3];
+    int k0 = 0, k1 = 0;
+    bool hit = false;
+    if (inrect) {
         ray_for_pixel(fc.cam, b.rect[0] + rx, b.rect[1] + ry, o, d);
-        int k0 = 0, k1 = 0;
-        const bool hit = box_krange(o, d, b.lo, b.hi, fc.step, k0, k1);
+        hit = box_krange(o, d, b.lo, b.hi, fc.step, k0, k1);
+    }
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+    float4 *acc = nullptr;
+    if constexpr (MODE == 2) {
+        if (hit) {
+            acc = static_cast<float4 *>(frags) + (long long)(b.rect[1] + ry) * fc.cam.W + (b.rect[0] + rx);
+            const float4 a = *acc;
+            c0 = a.x; c1 = a.y; c2 = a.z; T = a.w;
+            if (T <= fc.thr) hit = false;            // occluded by nearer bricks
+        }
+        if (!__syncthreads_or(hit)) return;          // block-uniform: no thread has a sample
+        load_table(lut, fc.nlut, s_lut);
+        __syncthreads();
+    }
+    if (inrect) {
         const long long fi = b.frag_off + (long long)ry * rw + rx;
         const void *src = static_cast<const char *>(pool) +
                           b.data_off * (S == 0 ? 4 : 2);
@@ -404,8 +429,7 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
         const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
         const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
         const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
-        if (MODE == 0) {
-            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+        if (MODE != 1) {
             if (hit) {
                 const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
                 const float qy = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
@@ -429,7 +453,10 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
                                                   b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
-            static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
+            if (MODE == 0)
+                static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
+            else if (nsamp > 0)                   // one brick of a wave per ray: no other writer
+                *acc = make_float4(c0, c1, c2, T);
         } else {
             float m = -INFINITY;
             if (hit) {
@@ -473,6 +500,20 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
             atomicAdd(&ctr->bricks_sampled, 1ull);
             atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)b.bytes);
         }
+    }
+}
+
+// Global termination: the per-pixel accumulator starts transparent (colour 0, transmittance 1)
+// and ends as premultiplied RGBA (colour, 1 - transmittance), like the composited image.
+__global__ void k_accum_init(float4 *__restrict__ acc, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc[i] = make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+}
+
+__global__ void k_accum_finalize(const float4 *__restrict__ acc, float4 *__restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float4 a = acc[i];
+        out[i] = make_float4(a.x, a.y, a.z, 1.0f - a.w);
     }
 }
 
@@ -681,7 +722,7 @@ template <int S, int MODE, int F, bool MASK>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static bool attr = false;
-    const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
+    const size_t smem = MODE != 1 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, F, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(2 * sizeof(float4) * kMaxLut));
@@ -697,6 +738,10 @@ cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBric
                         int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
 #define VR_RC(MODE, F, MASK) launch_rc<S, MODE, F, MASK>(fc, lut, db, items, nitems, pool, frags, ctr, s)
     const bool atlas = fc.fetch == 2;
+    if (fc.mode == 0 && fc.accum) {   // global termination: no stencil cache (fewer instantiations)
+        if (fc.chmask) return atlas ? VR_RC(2, 2, true) : VR_RC(2, 0, true);
+        return atlas ? VR_RC(2, 2, false) : VR_RC(2, 0, false);
+    }
     if (fc.chmask) {     // masked frames: no stencil cache (same values, fewer instantiations)
         if (fc.mode != 0) return atlas ? VR_RC(1, 2, true) : VR_RC(1, 0, true);
         return atlas ? VR_RC(0, 2, true) : VR_RC(0, 0, true);
@@ -717,6 +762,20 @@ cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawB
     if (fc.storage == 0) return launch_rc_s<0>(fc, lut, db, items, nitems, pool, frags, ctr, s);
     if (fc.storage == 1) return launch_rc_s<1>(fc, lut, db, items, nitems, pool, frags, ctr, s);
     return launch_rc_s<2>(fc, lut, db, items, nitems, pool, frags, ctr, s);
+}
+
+cudaError_t launch_accum_init(float4 *acc, long long npix, cudaStream_t s) {
+    if (npix <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((npix + 255) / 256, 152 * 32);
+    k_accum_init<<<grid, 256, 0, s>>>(acc, npix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum_finalize(const float4 *acc, float *out, long long npix, cudaStream_t s) {
+    if (npix <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((npix + 255) / 256, 152 * 32);
+    k_accum_finalize<<<grid, 256, 0, s>>>(acc, reinterpret_cast<float4 *>(out), npix);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,

@@ -344,6 +344,23 @@ def test_ert_bounds_and_off(orc):
     assert (glob[:, 3] >= 0).all() and np.any(glob[:, 3] >= 0.99)
 
 
+def test_global_termination_ignores_the_bricking(orc):
+    """term="global": the ray keeps its transmittance across bricks, so the bricked image is
+    the unbricked one sample for sample (bit-identical, FP64), for any brick size; and it takes
+    no more samples than per-segment termination."""
+    rng = np.random.default_rng(9)
+    cube = synth.pr1_cube(seed=3, n=32)
+    lut = synth.ramp_lut(alpha=0.8)
+    for _ in range(3):
+        cam = synth.random_camera(rng, (32, 32, 32), 40, 36)
+        b = tuple(int(x) for x in rng.integers(3, 17, 3))
+        ref, fr, nr = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.95)
+        g, fgl, ng = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.95, brick=b, term="global")
+        _, _, ns = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.95, brick=b)
+        assert np.array_equal(g, ref) and np.array_equal(fgl, fr) and ng == nr
+        assert ng <= ns
+
+
 def test_no_partition_errors_random(orc):
     rng = np.random.default_rng(3)
     cube = synth.pr1_cube(seed=1, n=24)

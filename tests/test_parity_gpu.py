@@ -426,3 +426,110 @@ def test_channel_mask_gradient(ctx, orc):
     finally:
         ctx.set_channel_mask(None)
         ctx.free_cube(cid)
+
+
+# ---------------------------------------------------------------------------------------------
+# global termination (occlusion skipping): front-to-back waves into per-pixel accumulators
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,layouts,brick", [("f32", 1, (16, 16, 16)), ("f32", 9, (24, 32, 20)),
+                                                   ("f16", 7, (16, 16, 16)), ("bf16", 9, (32, 16, 24))])
+def test_global_termination_matches_the_whole_ray(ctx, orc, storage, layouts, brick):
+    """The image is the oracle's with the whole ray's termination (bricking only sets the 16-bit
+    scales); it is within 1 - tau of per-segment termination and takes no more samples; with
+    an opaque table it takes far fewer."""
+    cube = synth.pr1_cube(seed=4)
+    lut = synth.ramp_lut(alpha=0.6)
+    cid = ctx.load_cube(cube)
+    ctx.set_brick_layouts(cid, layouts)
+    ctx.set_bricking(cid, brick, 1, storage)
+    rng = np.random.default_rng(31)
+    cams = [synth.pr1_camera(W=96, H=80), synth.random_camera(rng, (64, 64, 64), 90, 70),
+            dict(view=synth.look_at((30.0, 35.0, 28.0), (64.0, 10.0, 60.0)), proj=1, param=1.2,
+                 W=80, H=64)]                                   # eye inside the cube
+    fewer = 0
+    try:
+        for cam in cams:
+            for tau in (0.95, 1.0):
+                ctx.set_termination("global")
+                ctx.reset_stats()
+                g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=tau)
+                st_g = ctx.stats()
+                ctx.set_termination("segment")
+                ctx.reset_stats()
+                s = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=tau)
+                st_s = ctx.stats()
+                ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=tau, brick=brick,
+                                           quant=storage, term="global")
+                compare_dvr(g, ref, flags, tau)
+                assert st_g["fragments"] == 0 and st_g["samples"] <= st_s["samples"]
+                assert np.abs(g.astype(np.float64) - s).max() <= (1.0 - min(tau, 1.0)) + 2e-4
+                if tau >= 1.0:
+                    assert st_g["samples"] == st_s["samples"]
+                else:
+                    fewer += st_g["samples"] < 0.8 * st_s["samples"]
+        assert fewer >= 2
+    finally:
+        ctx.set_termination("segment")
+        ctx.free_cube(cid)
+
+
+def test_global_termination_with_mask_window_and_mip(ctx, orc):
+    rng = np.random.default_rng(41)
+    cube = synth.pr1_cube(seed=5)
+    mask = (rng.uniform(size=64) > 0.25).astype(np.uint8)
+    win = ((4, 6, 2), (60, 52, 58))
+    lut = synth.ramp_lut(alpha=0.5)
+    cid = ctx.load_cube(cube)
+    ctx.set_brick_layouts(cid, 9)
+    ctx.set_bricking(cid, (16, 16, 16), 1, "f32")
+    cam = synth.random_camera(rng, (64, 64, 64), 72, 64)
+    try:
+        ctx.set_termination("global")
+        ctx.set_channel_mask(mask)
+        ctx.set_window(*win)
+        g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.9)
+        ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.9, brick=(16, 16, 16),
+                                   channels=mask, window=win, term="global")
+        compare_dvr(g, ref, flags, 0.9)
+        m = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)    # MIP ignores the scope
+        rm, _, _ = orc.render(cube, lut, (-3, 20), cam, mode="mip32", step=0.5, brick=(16, 16, 16),
+                              channels=mask, window=win)
+        assert np.array_equal(m, rm.astype(np.float32))
+    finally:
+        ctx.set_termination("segment")
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+        ctx.free_cube(cid)
+
+
+def test_global_termination_refusals(ctx):
+    """The adjoint, the no-allocation path and streamed cubes need per-segment termination."""
+    import torch
+    import paper_1008_0135_gb300 as P
+    from paper_1008_0135_gb300 import _abi
+    cube = synth.pr1_cube(seed=6, n=32)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (16, 16, 16), 1, "f32")
+    cam = synth.pr1_camera(n=32, W=48, H=40)
+    lut = synth.ramp_lut(alpha=0.4)
+    vid = ctx.load_cube_procedural(7, (64, 64, 64))
+    ctx.set_bricking(vid, (32, 32, 32), 1, "f32")
+    try:
+        ctx.set_termination("global")
+        img = torch.from_numpy(render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)).cuda()
+        with pytest.raises(P.VrError) as e:
+            ctx.render_backward(cid, img.reshape(40, 48, 4).contiguous(),
+                                torch.zeros((256, 4), device="cuda"), None)
+        assert e.value.status == -7
+        out = torch.zeros((40, 48, 4), device="cuda")
+        rc = _abi.lib().vr_render_frame_noalloc(ctx._h, cid, out.data_ptr(),
+                                                torch.cuda.current_stream().cuda_stream)
+        assert rc == -7
+        with pytest.raises(P.VrError) as e:
+            ctx.render_frame(vid)
+        assert e.value.status == -7
+        assert _abi.lib().vr_set_termination(ctx._h, 5) == -1
+    finally:
+        ctx.set_termination("segment")
+        ctx.free_cube(cid)
+        ctx.free_cube(vid)
