@@ -195,6 +195,26 @@ def timed_frames(ctx, cid, cams, lut, vr, cfg, steps, warmup, dist, out, clocks=
     return ms, st, clk
 
 
+def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
+    """Occlusion skipping on the bench's cube with an opaque table (opacity = the ramp itself,
+    so a ray through the noise is opaque after a few hundred samples): per-segment termination
+    (every brick runs its own segment of a ray down to 1 - tau) against global termination
+    (bricks in front-to-back waves; a ray stops once the whole ray is opaque)."""
+    lut = synth.ramp_lut(alpha=1.0)
+    res = {"workload": cfg["name"] + f", {cfg['W']}x{cfg['H']} orbit, step {cfg['step']}, "
+                       f"ramp table with opacity = ramp (x10 the bench table), ERT {cfg['tau']}"}
+    for scope in ("segment", "global"):
+        ctx.set_termination(scope)
+        ms, st, _ = timed_frames(ctx, cid, cams, lut, cfg["vrange"], cfg, steps, warmup, dist, out)
+        t = dist.max(ms)
+        res[scope] = {"ms_per_frame": round(t / steps, 4),
+                      "samples_per_frame": int(st["samples"] // max(steps, 1)),
+                      "Gsamples_per_s": round(dist.sum(st["samples"]) / (t * 1e-3) / 1e9, 3)}
+    ctx.set_termination("segment")
+    res["speedup"] = round(res["segment"]["ms_per_frame"] / res["global"]["ms_per_frame"], 2)
+    return res
+
+
 def roofline(st, steps, peak, src, name):
     per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
     ms = st["ms_raycast"] / max(st["timed_frames"], 1)
@@ -445,6 +465,8 @@ def run_ours(args, dist):
             "unit": "Gsamples/s", "ms_per_frame": round(t16 / args.steps, 4),
             "roofline": roofline(st16, args.steps, peak, psrc, "k_raycast<f16,DVR>")}
         ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+        res["occlusion"] = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32),
+                                         args.warmup)
         # end to end through the C ABI with host buffers: table + camera in, frame out
         host_out = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
         lut_h = torch.from_numpy(lut).pin_memory()
