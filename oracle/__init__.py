@@ -71,6 +71,10 @@ def lib():
         L.orc_proc_noise.restype = C.c_double
         L.orc_proc_region.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, C.c_void_p,
                                       C.c_void_p, C.c_void_p]
+        L.orc_wavelet_bytes.argtypes = [C.c_int64] * 3
+        L.orc_wavelet_bytes.restype = C.c_int64
+        L.orc_wavelet_encode.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p]
+        L.orc_wavelet_decode.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p]
         _lib = L
     return _lib
 
@@ -272,6 +276,29 @@ def minmax(v):
     lo, hi = C.c_float(0), C.c_float(0)
     lib().orc_minmax(v.ctypes.data, v.size, C.byref(lo), C.byref(hi))
     return lo.value, hi.value
+
+
+WAVELET_RECORD = 544
+
+
+def wavelet_encode(cube):
+    """The 8-bit Haar-wavelet block store of a [z][y][x] FP32 cube (544 bytes per 8^3 block,
+    x-fastest block order; format in ``orc_wavelet_encode``)."""
+    cube = np.ascontiguousarray(cube, dtype=np.float32)
+    nz, ny, nx = cube.shape
+    out = np.zeros(int(lib().orc_wavelet_bytes(nx, ny, nz)), np.uint8)
+    lib().orc_wavelet_encode(cube.ctypes.data, nx, ny, nz, out.ctypes.data)
+    return out
+
+
+def wavelet_decode(store, shape_zyx):
+    """The FP32 cube a block store decodes to."""
+    store = np.ascontiguousarray(store, dtype=np.uint8)
+    nz, ny, nx = shape_zyx
+    assert store.size == int(lib().orc_wavelet_bytes(nx, ny, nz))
+    out = np.zeros((nz, ny, nx), np.float32)
+    lib().orc_wavelet_decode(store.ctypes.data, nx, ny, nz, out.ctypes.data)
+    return out
 
 
 def num_threads() -> int:

@@ -757,3 +757,144 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Lossy wavelet block store (Section 6: wavelet compression of the cube portions kept in GPU   */
+/* memory, decompressible with random access).  The format is the one the library documents:  */
+/* 8x8x8 blocks on a global grid (upper-face blocks repeat the edge voxels), three levels of    */
+/* the 3D Haar average/difference transform in binary32, int8 detail codes with one            */
+/* power-of-two step per subband, the block average in FP32, one 544-byte record per block.    */
+/* Written from that definition; every binary32 operation is a separate rounded step.          */
+/* ------------------------------------------------------------------------------------------ */
+#define WREC 544
+
+static float f_half(float v) { volatile float r = v * 0.5f; return r; }
+
+/* One line of n values at stride st: forward pairs (2i, 2i+1) -> (i, n/2 + i). */
+static void haar_line_fwd(float *w, int base, int st, int n) {
+    float tmp[8];
+    int h = n / 2;
+    for (int i = 0; i < h; ++i) {
+        float a = w[base + (2 * i) * st], b = w[base + (2 * i + 1) * st];
+        tmp[i] = f_half(f_add(a, b));
+        tmp[h + i] = f_half(f_sub(a, b));
+    }
+    for (int i = 0; i < n; ++i) w[base + i * st] = tmp[i];
+}
+
+/* One line, inverse: (i, n/2 + i) = (s, d) -> (2i, 2i+1) = (s + d, s - d). */
+static void haar_line_inv(float *w, int base, int st, int n) {
+    float tmp[8];
+    int h = n / 2;
+    for (int i = 0; i < h; ++i) {
+        float s = w[base + i * st], d = w[base + (h + i) * st];
+        tmp[2 * i] = f_add(s, d);
+        tmp[2 * i + 1] = f_sub(s, d);
+    }
+    for (int i = 0; i < n; ++i) w[base + i * st] = tmp[i];
+}
+
+/* Pyramid index x + 8y + 64z: -1 for the average, else 7 (level - 1) + (bx + 2by + 4bz) - 1. */
+static int w_subband(int x, int y, int z) {
+    for (int L = 1; L <= 3; ++L) {
+        int n = 8 >> (L - 1), h = n / 2;
+        if (x < n && y < n && z < n && (x >= h || y >= h || z >= h))
+            return 7 * (L - 1) + ((x >= h) + 2 * (y >= h) + 4 * (z >= h)) - 1;
+    }
+    return -1;
+}
+
+int64_t orc_wavelet_bytes(int64_t nx, int64_t ny, int64_t nz) {
+    return ((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 7) / 8) * (int64_t)WREC;
+}
+
+int orc_wavelet_encode(const float *vox, int64_t nx, int64_t ny, int64_t nz, uint8_t *store) {
+    int64_t bnx = (nx + 7) / 8, bny = (ny + 7) / 8, bnz = (nz + 7) / 8;
+    int64_t nb = bnx * bny * bnz;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t blk = 0; blk < nb; ++blk) {
+        int64_t bx = blk % bnx, by = (blk / bnx) % bny, bz = blk / (bnx * bny);
+        float w[512];
+        for (int z = 0; z < 8; ++z)
+            for (int y = 0; y < 8; ++y)
+                for (int x = 0; x < 8; ++x) {
+                    int64_t gx = clampi(8 * bx + x, 0, nx - 1), gy = clampi(8 * by + y, 0, ny - 1);
+                    int64_t gz = clampi(8 * bz + z, 0, nz - 1);
+                    w[x + 8 * y + 64 * z] = vox[gx + nx * (gy + ny * gz)];
+                }
+        for (int L = 1; L <= 3; ++L) {
+            int n = 8 >> (L - 1);
+            for (int v = 0; v < n; ++v)            /* along x: lines over (y, z) = (u, v) */
+                for (int u = 0; u < n; ++u) haar_line_fwd(w, 8 * u + 64 * v, 1, n);
+            for (int v = 0; v < n; ++v)            /* along y: lines over (x, z) */
+                for (int u = 0; u < n; ++u) haar_line_fwd(w, u + 64 * v, 8, n);
+            for (int v = 0; v < n; ++v)            /* along z: lines over (x, y) */
+                for (int u = 0; u < n; ++u) haar_line_fwd(w, u + 8 * v, 64, n);
+        }
+        /* per subband: the smallest e in [-126, 120] with max |c| <= 127 2^e */
+        float m[21];
+        for (int i = 0; i < 21; ++i) m[i] = 0.0f;
+        for (int p = 1; p < 512; ++p) {
+            int sb = w_subband(p & 7, (p >> 3) & 7, p >> 6);
+            float a = fabsf(w[p]);
+            if (a > m[sb]) m[sb] = a;
+        }
+        int e[21];
+        for (int i = 0; i < 21; ++i) {
+            if (m[i] == 0.0f) { e[i] = -128; continue; }
+            int k = -126;
+            while (k < 120 && m[i] > ldexpf(127.0f, k)) ++k;
+            e[i] = k;
+        }
+        uint8_t *rec = store + blk * WREC;
+        memset(rec, 0, WREC);
+        for (int p = 1; p < 512; ++p) {
+            int sb = w_subband(p & 7, (p >> 3) & 7, p >> 6);
+            int q = 0;
+            if (e[sb] != -128) {
+                volatile float t = ldexpf(w[p], -e[sb]);
+                q = (int)rintf(t);
+                if (q > 127) q = 127;
+                if (q < -127) q = -127;
+            }
+            rec[p] = (uint8_t)(int8_t)q;
+        }
+        memcpy(rec + 512, &w[0], 4);
+        for (int i = 0; i < 21; ++i) rec[516 + i] = (uint8_t)(int8_t)e[i];
+    }
+    return 0;
+}
+
+int orc_wavelet_decode(const uint8_t *store, int64_t nx, int64_t ny, int64_t nz, float *vox) {
+    int64_t bnx = (nx + 7) / 8, bny = (ny + 7) / 8, bnz = (nz + 7) / 8;
+    int64_t nb = bnx * bny * bnz;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t blk = 0; blk < nb; ++blk) {
+        int64_t bx = blk % bnx, by = (blk / bnx) % bny, bz = blk / (bnx * bny);
+        const uint8_t *rec = store + blk * WREC;
+        float w[512];
+        memcpy(&w[0], rec + 512, 4);
+        for (int p = 1; p < 512; ++p) {
+            int sb = w_subband(p & 7, (p >> 3) & 7, p >> 6);
+            int e = (int)(int8_t)rec[516 + sb];
+            int q = (int)(int8_t)rec[p];
+            w[p] = e == -128 ? 0.0f : ldexpf((float)q, e);
+        }
+        for (int L = 3; L >= 1; --L) {
+            int n = 8 >> (L - 1);
+            for (int v = 0; v < n; ++v)            /* along z */
+                for (int u = 0; u < n; ++u) haar_line_inv(w, u + 8 * v, 64, n);
+            for (int v = 0; v < n; ++v)            /* along y */
+                for (int u = 0; u < n; ++u) haar_line_inv(w, u + 64 * v, 8, n);
+            for (int v = 0; v < n; ++v)            /* along x */
+                for (int u = 0; u < n; ++u) haar_line_inv(w, 8 * u + 64 * v, 1, n);
+        }
+        for (int z = 0; z < 8; ++z)
+            for (int y = 0; y < 8; ++y)
+                for (int x = 0; x < 8; ++x) {
+                    int64_t gx = 8 * bx + x, gy = 8 * by + y, gz = 8 * bz + z;
+                    if (gx < nx && gy < ny && gz < nz) vox[gx + nx * (gy + ny * gz)] = w[x + 8 * y + 64 * z];
+                }
+    }
+    return 0;
+}

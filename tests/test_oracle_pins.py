@@ -514,3 +514,103 @@ def test_window_clips_the_lattice(orc, seed):
     whole, _, _ = orc.render(cube, lut, (-1, 3), cam, step=0.5, window=((0, 0, 0), shape))
     plain, _, _ = orc.render(cube, lut, (-1, 3), cam, step=0.5)
     assert np.array_equal(whole, plain)
+
+
+# ---------------------------------------------------------------------------------------------
+# wavelet block store (lossy compression of the cube kept in GPU memory)
+# ---------------------------------------------------------------------------------------------
+def _rec(store, i):
+    r = store[544 * i: 544 * (i + 1)]
+    return r[:512].view(np.int8), r[512:516].view(np.float32)[0], r[516:537].view(np.int8), r[537:]
+
+
+def test_wavelet_constant_block(orc):
+    """A constant block has no detail: every subband empty (-128), codes 0, average = value."""
+    c = np.full((8, 8, 8), -7.375, np.float32)
+    st = orc.wavelet_encode(c)
+    codes, avg, e, pad = _rec(st, 0)
+    assert st.size == 544 and avg == np.float32(-7.375)
+    assert np.all(e == -128) and not codes.any() and not pad.any()
+    assert np.array_equal(orc.wavelet_decode(st, c.shape), c)
+
+
+@pytest.mark.parametrize("k", [5, -3])
+def test_wavelet_delta_block_by_hand(orc, k):
+    """A single voxel 2^k at (0,0,0): each Haar level halves it per axis, so level L leaves the
+    value 2^(k - 3L) in every subband at the subband's first position, (bx, by, bz) * 8/2^L,
+    and 2^(k-9) as the average.  The step is the smallest 2^e with 2^j <= 127 2^e: e = j - 6, so
+    every code is 2^j / 2^(j-6) = 64 and the block decodes exactly."""
+    x = np.zeros((8, 8, 8), np.float32)
+    x[0, 0, 0] = 2.0 ** k
+    st = orc.wavelet_encode(x)
+    codes, avg, e, _ = _rec(st, 0)
+    want = np.zeros(512, np.int8)
+    want_e = np.zeros(21, np.int8)
+    for L in (1, 2, 3):
+        h = 8 >> L
+        for sb in range(1, 8):
+            bx, by, bz = sb & 1, (sb >> 1) & 1, sb >> 2
+            want[bx * h + 8 * by * h + 64 * bz * h] = 64
+            want_e[7 * (L - 1) + sb - 1] = (k - 3 * L) - 6
+    assert np.array_equal(codes, want) and np.array_equal(e, want_e)
+    assert avg == np.float32(2.0 ** (k - 9))
+    assert np.array_equal(orc.wavelet_decode(st, x.shape), x)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_wavelet_linear_ramp_by_hand(orc, axis):
+    """v = coordinate along one axis: level L's detail along that axis is -2^(L-2) everywhere in
+    its subband (a difference of averages 2^(L-1) apart, halved), all other subbands are empty,
+    the average is 3.5; steps 2^(L-8), codes -64; lossless."""
+    g = np.arange(8, dtype=np.float32)
+    x = np.broadcast_to(g.reshape([8 if a == 2 - axis else 1 for a in range(3)]), (8, 8, 8)).copy()
+    st = orc.wavelet_encode(x)
+    codes, avg, e, _ = _rec(st, 0)
+    sb = 1 << axis
+    for L in (1, 2, 3):
+        for s in range(1, 8):
+            assert e[7 * (L - 1) + s - 1] == ((L - 8) if s == sb else -128)
+    assert avg == np.float32(3.5)
+    assert set(np.unique(codes[1:]).tolist()) == {0, -64}
+    assert (codes == -64).sum() == 64 + 8 + 1
+    assert np.array_equal(orc.wavelet_decode(st, x.shape), x)
+
+
+def test_wavelet_error_within_half_steps(orc):
+    """Lossy bound: a voxel is the average plus, at each level, one coefficient of each of the
+    7 subbands with sign +-1, so its error is at most the sum of half a step over the block's
+    21 subbands, plus binary32 rounding in the 9 add/subtract stages (<= 9 ulp of 2 max|v|)."""
+    rng = np.random.default_rng(12)
+    shape = (19, 21, 27)                         # ragged: partial blocks on every axis
+    x = (rng.standard_normal(shape) * 2.0).astype(np.float32)
+    x[3:9, 4:12, 5:13] += 60.0 * rng.uniform(size=(6, 8, 8)).astype(np.float32)
+    x[16:, :, :8] = 0.0                          # whole blocks of zeros: empty subbands
+    st = orc.wavelet_encode(x)
+    y = orc.wavelet_decode(st, x.shape)
+    nb = ((27 + 7) // 8, (21 + 7) // 8, (19 + 7) // 8)
+    worst = 0.0
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                i = bx + nb[0] * (by + nb[1] * bz)
+                _, _, e, _ = _rec(st, i)
+                bound = sum(2.0 ** (int(v) - 1) for v in e if v != -128)
+                sl = np.s_[8 * bz:8 * bz + 8, 8 * by:8 * by + 8, 8 * bx:8 * bx + 8]
+                m = float(np.abs(x[sl]).max())
+                slack = 9 * 2.0 * m * 2.0 ** -23
+                err = float(np.abs(y[sl].astype(np.float64) - x[sl]).max())
+                assert err <= bound + slack, (bx, by, bz, err, bound)
+                worst = max(worst, err / max(bound, 1e-30))
+    assert 0.05 < worst <= 1.0 + 1e-6               # the bound is reached, not vacuous
+    assert np.array_equal(y[16:, :, :8], x[16:, :, :8])   # an all-zero block decodes exactly
+
+
+def test_wavelet_edge_blocks_repeat_the_border(orc):
+    """Blocks that stick out of the cube see the edge voxels repeated: the store of a 13x11x9
+    cube equals that of the same cube padded to 16x16x16 by edge replication."""
+    rng = np.random.default_rng(13)
+    x = rng.standard_normal((9, 11, 13)).astype(np.float32)
+    pad = np.pad(x, ((0, 7), (0, 5), (0, 3)), mode="edge")
+    assert np.array_equal(orc.wavelet_encode(x), orc.wavelet_encode(pad))
+    assert np.array_equal(orc.wavelet_decode(orc.wavelet_encode(x), x.shape),
+                          orc.wavelet_decode(orc.wavelet_encode(pad), pad.shape)[:9, :11, :13])
