@@ -80,9 +80,10 @@ typedef struct {
     double ms_composite;         /* device time of the compositing kernels (timing enabled) */
     double ms_frame;             /* device time from work-list upload to composite end */
     int64_t timed_frames;        /* frames that carried timing events */
-    int64_t bytes_streamed;      /* host -> device brick bytes copied by the residency cache */
+    int64_t bytes_streamed;      /* brick bytes the residency cache received (host copies, or
+                                    decoded on the device for compressed cubes) */
     int64_t cache_hits;          /* brick lookups served from the HBM cache */
-    int64_t cache_misses;        /* brick lookups that needed a copy */
+    int64_t cache_misses;        /* brick lookups that needed a copy or a decode */
 } vr_stats;
 
 /* Creates a context on CUDA device `device`.  cache_bytes bounds the HBM brick cache used for
@@ -121,7 +122,10 @@ int vr_load_cube(vr_ctx *ctx, const void *voxels, int dtype, int64_t nx, int64_t
  * The cube must be bricked (vr_set_bricking) before rendering.  Frames stream the bricks they
  * need through the context's HBM brick cache (cache_bytes of vr_create, LRU, pinned staging,
  * copies on a side stream); frames needing more bricks than the cache holds are ray-cast in
- * chunks.  Not offered for streamed cubes: min/max, update, backward, no-allocation frames.
+ * chunks.  The cache cuts its memory into slots of the largest brick it has seen; a frame
+ * whose bricks are larger re-cuts it (dropping its contents) once no serving frame holds a
+ * slot, else the frame returns VR_ERR_UNSUPPORTED.  Not offered for streamed cubes: min/max,
+ * update, backward, no-allocation frames.
  * Errors: VR_ERR_ARG (null, sizes < 1 or > 2^30). */
 int vr_load_cube_procedural(vr_ctx *ctx, uint64_t seed, int64_t nx, int64_t ny, int64_t nz,
                             int *cube_id);
@@ -153,9 +157,37 @@ int vr_compute_minmax(vr_ctx *ctx, int cube_id, float *vmin, float *vmax);
  * per brick, a power-of-two scale 2^e with e chosen from the brick's stored max |v| (FP16:
  * max|v| 2^-e <= 2^14; BF16: <= 1), the codes being round-to-nearest-even of v 2^-e.
  * Synchronous.  Errors: VR_ERR_ARG (sizes < 1, ghost != 1, storage), VR_ERR_NOT_FOUND,
- * VR_ERR_UNSUPPORTED (bricks larger than a streamed cube's cache slots; slice atlases kept and
- * a brick's atlas beyond the device's 2D-gather size), VR_ERR_OOM, VR_ERR_CUDA. */
+ * VR_ERR_UNSUPPORTED (slice atlases kept and a brick's atlas beyond the device's 2D-gather
+ * size; a compressed cube with a storage other than VR_F32), VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_bricking(vr_ctx *ctx, int cube_id, int bx, int by, int bz, int ghost, int storage);
+
+/* Lossy wavelet compression of a resident cube (Section 6: wavelet compression of the cube
+ * portions kept in GPU memory, with fast decompression and random access, to store and render
+ * larger cubes).  The cube's FP32 voxels are encoded into a block store in HBM and then
+ * released, with its brick pool and atlases: the cube then renders like a streamed cube, its
+ * bricks decoded on demand (on the device) into the brick cache, which must exist (cache_bytes
+ * > 0 at vr_create; else frames return VR_ERR_OOM, as for streamed cubes).  Bricking keeps its geometry and becomes
+ * VR_F32 (decoded bricks are FP32; other storages return VR_ERR_UNSUPPORTED).
+ * Format: the cube is cut into 8x8x8 blocks on a global grid (blocks at the upper faces repeat
+ * the edge voxels).  Each block takes three levels of the 3D Haar average/difference transform
+ * (s = (a + b)/2, d = (a - b)/2 in binary32, along x then y then z, each level on the previous
+ * level's averages); its 511 detail coefficients are rounded (to nearest even) to int8 codes in
+ * units of one power-of-two step per subband, the smallest 2^e (-126 <= e <= 120) with
+ * max |c| <= 127 2^e over the subband; the block average stays FP32.  One block is a 544-byte
+ * record (codes at [0, 512) indexed x + 8 y + 64 z in the pyramid layout, entry 0 unused; the
+ * average as FP32 at [512, 516); the 21 steps' exponents as int8 at [516, 537), index
+ * 7 (level - 1) + (bx + 2 by + 4 bz) - 1, -128 for an all-zero subband; zeros to 544); records
+ * in x-fastest block order: 1.0625 bytes per voxel.  Decoding inverts the transform (a = s + d,
+ * b = s - d, along z then y then x, finest level last), so a voxel's error is at most the sum
+ * of half a step over the 21 subbands that reach it, plus binary32 rounding.
+ * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED (streamed cube), VR_ERR_OOM,
+ * VR_ERR_CUDA.  Compressing a compressed cube does nothing. */
+int vr_compress_cube(vr_ctx *ctx, int cube_id);
+
+/* The block store of a compressed cube.  dst == NULL: *bytes = its size.  Otherwise copies it
+ * into host memory dst of *bytes >= that size (synchronous).  Errors: VR_ERR_ARG,
+ * VR_ERR_NOT_FOUND, VR_ERR_STATE (not compressed), VR_ERR_CUDA. */
+int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
 
 /* Brick layouts kept for a cube (how the stored bricks of Section 2.2's parts are laid out for
  * the ray caster of Section 2.4).  Bits 0-2 of `mask` keep a copy of every brick whose axis a

@@ -145,8 +145,23 @@ class Context:
         _check(self._L.vr_set_bricking(self._h, cube_id, bx, by, bz, ghost, STORAGE[storage]),
                "vr_set_bricking")
 
+    def compress_cube(self, cube_id: int):
+        """Encodes the cube into 8-bit Haar-wavelet blocks in HBM and releases its FP32 voxels and
+        bricks; frames then decode bricks on demand into the brick cache (vr_compress_cube)."""
+        _check(self._L.vr_compress_cube(self._h, cube_id), "vr_compress_cube")
+
+    def wavelet_store(self, cube_id: int):
+        """The compressed cube's block store as a uint8 numpy array (544 bytes per 8^3 block)."""
+        import numpy as np
+        n = C.c_size_t(0)
+        _check(self._L.vr_wavelet_store(self._h, cube_id, None, C.byref(n)), "vr_wavelet_store")
+        buf = np.empty(n.value, dtype=np.uint8)
+        _check(self._L.vr_wavelet_store(self._h, cube_id, buf.ctypes.data, C.byref(n)), "vr_wavelet_store")
+        return buf
+
     def set_brick_layouts(self, cube_id: int, mask: int):
-        """Keep x- (1), y- (2), z-contiguous (4) copies of the bricks (bit 0 always kept)."""
+        """Keep x- (1), y- (2), z-contiguous (4) copies of the bricks (bit 0 always kept) and
+        slice-atlas textures of them (8)."""
         _check(self._L.vr_set_brick_layouts(self._h, cube_id, int(mask)), "vr_set_brick_layouts")
 
     def brick_grid(self, cube_id: int):

@@ -67,6 +67,8 @@ SIGNATURES = {
     "vr_set_camera": (I, [VP, VP, I, F, I, I]),
     "vr_set_render_params": (I, [VP, I, F, F]),
     "vr_set_termination": (I, [VP, I]),
+    "vr_compress_cube": (I, [VP, I]),
+    "vr_wavelet_store": (I, [VP, I, VP, P(C.c_size_t)]),
     "vr_render_frame": (I, [VP, I, VP, I, VP]),
     "vr_render_frame_noalloc": (I, [VP, I, VP, VP]),
     "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),

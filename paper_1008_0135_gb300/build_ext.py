@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libvrcube.so")
-SOURCES = ["vr_bricks.cu", "vr_raycast.cu", "vr_api.cu", "vr_residency.cu", "vr_serve.cu"]
+SOURCES = ["vr_bricks.cu", "vr_raycast.cu", "vr_api.cu", "vr_residency.cu", "vr_serve.cu", "vr_wavelet.cu"]
 HEADERS = ["vr_internal.cuh", "vr_host.h", os.path.join("..", "..", "include", "vrcube.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-fvisibility=hidden",

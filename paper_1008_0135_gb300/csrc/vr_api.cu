@@ -526,6 +526,7 @@ int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
 
 void free_cube(Cube *cb) {
     free_atlases(cb);
+    if (cb->d_wstore) cudaFree(cb->d_wstore);
     if (cb->d_src) cudaFree(cb->d_src);
     if (cb->d_pool) cudaFree(cb->d_pool);
     if (cb->d_tmpl) cudaFree(cb->d_tmpl);
@@ -878,7 +879,7 @@ int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *
     if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed cubes have no resident voxels");
+    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed and compressed cubes have no resident voxels");
     int rc = set_dev(c);
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -906,7 +907,8 @@ int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
     if (!c || !vmin || !vmax) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "min/max of a streamed cube would generate all of it");
+    if (cb->streamed)
+        return fail(VR_ERR_UNSUPPORTED, "min/max of a streamed or compressed cube would produce all of it");
     int rc = set_dev(c);
     if (rc) return rc;
     unsigned int init[2] = {0xffffffffu, 0u}, res[2];
@@ -932,6 +934,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     if (bx < 1 || by < 1 || bz < 1) return arg_fail("brick size < 1");
     if (ghost != 1) return arg_fail("ghost must be 1");
     if (storage != VR_F32 && storage != VR_F16 && storage != VR_BF16) return arg_fail("bad storage");
+    if (cb->wavelet && storage != VR_F32) return fail(VR_ERR_UNSUPPORTED, "compressed cubes decode to FP32 bricks");
     int rc = set_dev(c);
     if (rc) return rc;
     if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
@@ -977,13 +980,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     if (cb->d_tmpl) { cudaFree(cb->d_tmpl); cb->d_tmpl = nullptr; }
     cb->bricked = false;
     if (cb->streamed) {                // bricks are produced on demand into the cache
-        cache_forget_cube(c, cube_id);
-        const size_t slot = cache_slot_bytes(c);
-        if (slot) {
-            size_t mx = 0;
-            for (auto &b : t) mx = std::max(mx, (size_t)b.bytes);
-            if (mx > slot) return fail(VR_ERR_UNSUPPORTED, "bricks larger than the cache's slots");
-        }
+        cache_forget_cube(c, cube_id);    // (a cache with smaller slots is re-cut by the next frame)
         cb->tmpl = std::move(t);
         cb->loff.clear();
         for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
@@ -1005,6 +1002,66 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     cb->storage = storage;
     if ((rc = build_bricks(c, cb, c->load_stream)) != VR_OK) return rc;
     cb->bricked = true;
+    return VR_OK;
+}
+
+int vr_compress_cube(vr_ctx *c, int cube_id) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (cb->wavelet) return VR_OK;
+    if (cb->streamed || !cb->d_src)
+        return fail(VR_ERR_UNSUPPORTED, "only resident cubes (with their FP32 voxels) can be compressed");
+    int rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    size_t nb = 1;
+    for (int a = 0; a < 3; ++a) nb *= (size_t)((cb->n[a] + 7) / 8);
+    const size_t bytes = nb * (size_t)kWaveletRecordBytes;
+    unsigned char *store = nullptr;
+    CK(cudaMalloc(&store, bytes));
+    cudaError_t e = launch_wavelet_encode(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], store,
+                                          c->load_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->load_stream);
+    if (e != cudaSuccess) {
+        cudaFree(store);
+        return cuda_fail(e, "wavelet encode");
+    }
+    // the FP32 voxels, the brick pool and the atlases go; frames in flight may still read them
+    CK(cudaDeviceSynchronize());
+    free_atlases(cb);
+    cudaFree(cb->d_src);
+    cb->d_src = nullptr;
+    if (cb->d_pool) { cudaFree(cb->d_pool); cb->d_pool = nullptr; }
+    if (cb->d_tmpl) { cudaFree(cb->d_tmpl); cb->d_tmpl = nullptr; }
+    if (cb->d_bs) { cudaFree(cb->d_bs); cb->d_bs = nullptr; }
+    cb->pool_bytes = 0;
+    cb->loff.clear();
+    cb->vlo.clear();
+    cb->vhi.clear();
+    cb->d_wstore = store;
+    cb->wstore_bytes = bytes;
+    cb->wavelet = true;
+    cb->streamed = true;
+    cb->layouts = 1;
+    if (!cb->bricked) return VR_OK;
+    cb->bricked = false;                 // brick records for the cache, FP32 bricks
+    return vr_set_bricking(c, cube_id, cb->B[0], cb->B[1], cb->B[2], cb->ghost, VR_F32);
+}
+
+int vr_wavelet_store(vr_ctx *c, int cube_id, void *dst, size_t *bytes) {
+    if (!c || !bytes) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (!cb->wavelet) return fail(VR_ERR_STATE, "cube is not compressed");
+    if (!dst) {
+        *bytes = cb->wstore_bytes;
+        return VR_OK;
+    }
+    if (*bytes < cb->wstore_bytes) return arg_fail("destination smaller than the block store");
+    int rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    CK(cudaMemcpy(dst, cb->d_wstore, cb->wstore_bytes, cudaMemcpyDeviceToHost));
+    *bytes = cb->wstore_bytes;
     return VR_OK;
 }
 

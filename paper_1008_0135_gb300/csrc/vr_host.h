@@ -64,6 +64,10 @@ struct Cube {
     size_t atlas_bytes = 0;
     // streamed cubes: bricks are produced on the host and cached in HBM on demand
     bool streamed = false;
+    // compressed cubes (also `streamed`): 8x8x8 wavelet blocks in HBM, bricks decoded on demand
+    bool wavelet = false;
+    unsigned char *d_wstore = nullptr;
+    size_t wstore_bytes = 0;
     uint64_t proc_seed = 0;           // procedural cube: generator seed
     int id = 0;
 };

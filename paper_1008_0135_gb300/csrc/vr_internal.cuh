@@ -95,6 +95,15 @@ cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const 
 cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawBrick *db,
                            const TileItem *items, int nitems, const void *pool, void *frags,
                            Counters *ctr, cudaStream_t s);
+// Wavelet block store: one record of kWaveletRecordBytes per 8x8x8 block of the cube, blocks
+// in x-fastest order over a ceil(n/8) grid (format in vr_wavelet.cu).
+constexpr int kWaveletRecordBytes = 544;
+cudaError_t launch_wavelet_encode(const float *cube, int nx, int ny, int nz, unsigned char *store,
+                                  cudaStream_t s);
+// Decodes the stored region of one brick (global voxels clamp(org + [0, dim)), x-contiguous
+// FP32) from the block store.
+cudaError_t launch_wavelet_decode(const unsigned char *store, int nx, int ny, int nz, const int org[3],
+                                  const int dim[3], float *dst, cudaStream_t s);
 // Global termination: fill the W*H accumulator with (0, 0, 0, 1); turn it into premultiplied
 // RGBA (colour, 1 - transmittance) in `out` (W*H float4).
 cudaError_t launch_accum_init(float4 *acc, long long npix, cudaStream_t s);

@@ -363,12 +363,35 @@ void cache_forget_cube(vr_ctx *c, int cube_id) {
         }
 }
 
-// Slots and staging sized for `slot_bytes` bricks (first streamed frame).  All or nothing: on
+// Slots and staging sized for `slot_bytes` bricks (first streamed frame).  A cache whose slots
+// are too small for a cube's bricks is re-cut, dropping its contents, once nothing holds a
+// slot: its copies and every frame that read a slot are waited for first.  All or nothing: on
 // failure everything this call allocated is released and the cache stays unsized.
 static int cache_size(vr_ctx *c, size_t slot_bytes) {
     BrickCache *k = c->cache;
     if (k->d_base && k->slot_bytes >= slot_bytes) return VR_OK;
-    if (k->d_base) return fail(VR_ERR_UNSUPPORTED, "streamed cubes with larger bricks than the cache's slots");
+    if (k->d_base) {
+        for (auto &s : k->slots)
+            if (s.held > 0) return fail(VR_ERR_UNSUPPORTED, "larger bricks than the cache's slots while frames hold bricks");
+        CK(cudaStreamSynchronize(k->copy));
+        for (auto &s : k->slots) {
+            if (s.used) CK(cudaEventSynchronize(s.last_use));
+            cudaEventDestroy(s.last_use);
+        }
+        for (auto &s : k->stage) {
+            if (s.pending) CK(cudaEventSynchronize(s.done));
+            cudaFreeHost(s.host);
+            cudaEventDestroy(s.done);
+        }
+        cudaFree(k->d_base);
+        k->d_base = nullptr;
+        k->slot_bytes = 0;
+        k->nslots = 0;
+        k->slots.clear();
+        k->stage.clear();
+        k->stage_next = 0;
+        k->where.clear();
+    }
     if (c->cache_bytes < slot_bytes)
         return fail(VR_ERR_OOM, "cache_bytes of vr_create is smaller than one brick");
     const size_t sb = align_up(slot_bytes, 256);
@@ -460,6 +483,26 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         s.chunk = chunk;
         s.lru = ++k->tick;
         misses[m].second = si;
+    }
+    if (cb->wavelet) {
+        // compressed cube: each missing brick is decoded from the HBM block store straight into
+        // its slot on the cache's stream, after the slot's previous reader
+        for (auto &mi : misses) {
+            Slot &s = k->slots[mi.second];
+            const DrawBrick &b = db[mi.first];
+            if (s.used) CK(cudaStreamWaitEvent(k->copy, s.last_use, 0));
+            CK(launch_wavelet_decode(cb->d_wstore, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], b.org, b.dim,
+                                     reinterpret_cast<float *>(k->d_base + (size_t)mi.second * k->slot_bytes),
+                                     k->copy));
+            s.cube = cb->id;
+            s.exp2 = 0;
+            k->where[key_of(cb->id, s.brick)] = mi.second;
+            db[mi.first].data_off = (long long)((size_t)mi.second * k->slot_bytes / esz);
+            db[mi.first].exp2 = 0;
+            k->misses++;
+            k->bytes += b.bytes;
+        }
+        return VR_OK;
     }
     // produce in parallel, at most one staging buffer per brick in flight
     const size_t nstage = k->stage.size();
@@ -649,10 +692,22 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     return VR_OK;
 }
 
-// Brick `brick` of a streamed cube as stored (generated on the calling thread).
+// Brick `brick` of a streamed cube as stored (generated on the calling thread; compressed
+// cubes: decoded on the device and copied back).
 int streamed_brick(Cube *cb, int64_t brick, void *data, int *exp2) {
     const DrawBrick &b = cb->tmpl[brick];
     int e = 0;
+    if (cb->wavelet) {
+        float *tmp = nullptr;
+        CK(cudaMalloc(&tmp, (size_t)b.bytes));
+        cudaError_t er = launch_wavelet_decode(cb->d_wstore, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], b.org,
+                                               b.dim, tmp, 0);
+        if (er == cudaSuccess) er = cudaMemcpy(data, tmp, (size_t)b.bytes, cudaMemcpyDeviceToHost);
+        cudaFree(tmp);
+        if (er != cudaSuccess) return cuda_fail(er, "wavelet brick decode");
+        *exp2 = 0;
+        return VR_OK;
+    }
     if (cb->storage == VR_F32) {
         gen_region(cb->proc_seed, cb->n, b.org, b.dim, static_cast<float *>(data));
     } else {
