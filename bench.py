@@ -215,6 +215,73 @@ def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
     return res
 
 
+def compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np, frames=16):
+    """The bench's cube compressed into 8-bit Haar-wavelet blocks in HBM (the FP32 voxels, brick
+    pool and atlases released), then rendered with its bricks decoded on demand into the brick
+    cache: store size, encode time, decoded-voxel error on sampled bricks, the first frame
+    (every brick decoded) and warm frames (bricks cached), and the image change against the
+    FP32 frame of the same view."""
+    import torch
+    ctx.set_transfer_function(lut, *vr)
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    ctx.set_camera_dict(cams[0])
+    ref = ctx.render_frame(cid, out).clone()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.compress_cube(cid)
+    enc_s = time.perf_counter() - t0
+    n_store = int(ctx.wavelet_store_bytes(cid))
+    nx, ny, nz = cfg["shape"]
+    res = {"workload": cfg["name"] + ": 8x8x8 Haar blocks, 3 levels, int8 codes, power-of-two "
+                                     "step per subband, decoded on demand into the brick cache",
+           "store_bytes": n_store, "fp32_bytes": 4 * nx * ny * nz,
+           "ratio_vs_fp32": round(4 * nx * ny * nz / n_store, 3), "encode_s": round(enc_s, 3)}
+    # decoded voxels against the FP32 cube on sampled bricks
+    nb, _ = ctx.brick_grid(cid)
+    total = nb[0] * nb[1] * nb[2]
+    errs, sq, cnt, peak = 0.0, 0.0, 0, 0.0
+    for b in np.linspace(0, total - 1, 6).astype(int):
+        dims, org, _, data = ctx.get_brick(cid, int(b))
+        zi = np.clip(org[2] + np.arange(dims[2]), 0, nz - 1)
+        yi = np.clip(org[1] + np.arange(dims[1]), 0, ny - 1)
+        xi = np.clip(org[0] + np.arange(dims[0]), 0, nx - 1)
+        want = cube_np[np.ix_(zi, yi, xi)]
+        d = data.astype(np.float64) - want
+        errs = max(errs, float(np.abs(d).max()))
+        sq += float((d * d).sum())
+        cnt += d.size
+        peak = max(peak, float(np.abs(want).max()))
+    rms = (sq / cnt) ** 0.5
+    res["voxel_error"] = {"max_abs": round(errs, 5), "rms": round(rms, 5),
+                          "psnr_db": round(20 * np.log10(peak / rms), 2), "bricks_sampled": 6}
+    ctx.reset_stats()
+    ctx.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    img = ctx.render_frame(cid, out)
+    e1.record()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    res["first_frame"] = {"ms": round(e0.elapsed_time(e1), 3), "bricks_decoded": st["cache_misses"],
+                          "bytes_decoded": st["bytes_streamed"]}
+    diff = (img - ref).abs()
+    res["image_change_vs_fp32"] = {"max_abs": round(float(diff.max()), 5),
+                                   "mean_abs": round(float(diff.mean()), 7)}
+    ctx.reset_stats()
+    e0.record()
+    for k in range(frames):
+        ctx.set_camera_dict(cams[k % len(cams)])
+        ctx.render_frame(cid, out)
+    e1.record()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    ctx.set_timing(False)
+    ms = e0.elapsed_time(e1) / frames
+    res["warm_frames"] = {"ms_per_frame": round(ms, 4), "Gsamples_per_s": round(st["samples"] / frames / (ms * 1e-3) / 1e9, 3),
+                          "cache_misses": st["cache_misses"], "frames": frames}
+    return res
+
+
 def roofline(st, steps, peak, src, name):
     per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
     ms = st["ms_raycast"] / max(st["timed_frames"], 1)
@@ -491,6 +558,7 @@ def run_ours(args, dist):
         if dist.rank == 0:
             res["adjoint"] = adjoint_leg(ctx, device)
             res["serving"] = serving_leg(ctx, cid, device)
+            res["compressed"] = compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np)
             ctx.free_cube(cid)
             cid = None
             res["empty_space"] = empty_space_leg(ctx, device)

@@ -150,6 +150,11 @@ class Context:
         bricks; frames then decode bricks on demand into the brick cache (vr_compress_cube)."""
         _check(self._L.vr_compress_cube(self._h, cube_id), "vr_compress_cube")
 
+    def wavelet_store_bytes(self, cube_id: int) -> int:
+        n = C.c_size_t(0)
+        _check(self._L.vr_wavelet_store(self._h, cube_id, None, C.byref(n)), "vr_wavelet_store")
+        return n.value
+
     def wavelet_store(self, cube_id: int):
         """The compressed cube's block store as a uint8 numpy array (544 bytes per 8^3 block)."""
         import numpy as np

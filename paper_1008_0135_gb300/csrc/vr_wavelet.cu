@@ -71,31 +71,6 @@ __device__ void haar_forward_level(float *a, float *b, int n, int lane) {
     }
 }
 
-// One level of the inverse on [0, n)^3: along z, then y, then x: a = s + d, b = s - d.
-__device__ void haar_inverse_level(float *a, float *b, int n, int lane) {
-    const int h = n >> 1;
-    for (int axis = 2; axis >= 0; --axis) {
-        const int st = axis == 0 ? 1 : (axis == 1 ? 8 : 64);
-        for (int t = lane; t < n * n * h; t += 32) {
-            const int i = t % h, r = t / h, u = r % n, v = r / n;
-            int base;
-            if (axis == 0) base = 8 * u + 64 * v;
-            else if (axis == 1) base = u + 64 * v;
-            else base = u + 8 * v;
-            const float s = a[base + i * st], d = a[base + (h + i) * st];
-            b[base + (2 * i) * st] = __fadd_rn(s, d);
-            b[base + (2 * i + 1) * st] = __fsub_rn(s, d);
-        }
-        __syncwarp();
-        for (int t = lane; t < n * n * n; t += 32) {
-            const int x = t % n, y = (t / n) % n, z = t / (n * n);
-            const int p = x + 8 * y + 64 * z;
-            a[p] = b[p];
-        }
-        __syncwarp();
-    }
-}
-
 // 2^k as a float for k in [-126, 127] (built from its bits: exact).
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
 
@@ -161,38 +136,103 @@ k_wavelet_encode(const float *__restrict__ cube, int nx, int ny, int nz, int bnx
     if (lane == 0) *reinterpret_cast<float *>(rec + 512) = a[0];
 }
 
+// Inverse of one level for one 2x2x2 group: c[a + 2b + 4c] holds the coarser average (c[0]) and
+// the 7 details of subbands (a, b, c); the separable inverse pairs along z, then y, then x
+// touch only these 8 values, so out[x + 2y + 4z] here is bit-identical to the whole-level
+// passes (same pairs, same binary32 operations, same order).
+__device__ __forceinline__ void inv_group(const float c[8], float out[8]) {
+    float t[8], u[8];
+#pragma unroll
+    for (int ab = 0; ab < 4; ++ab) {              // along z
+        t[ab] = __fadd_rn(c[ab], c[ab + 4]);
+        t[ab + 4] = __fsub_rn(c[ab], c[ab + 4]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {                 // along y: r = a + 4z -> index a + 4z (+ 2)
+        const int i0 = (r & 1) + 4 * (r >> 1);
+        u[i0] = __fadd_rn(t[i0], t[i0 + 2]);
+        u[i0 + 2] = __fsub_rn(t[i0], t[i0 + 2]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {                 // along x: r = y + 2z -> index 2y + 4z (+ 1)
+        const int i0 = 2 * r;
+        out[i0] = __fadd_rn(u[i0], u[i0 + 1]);
+        out[i0 + 1] = __fsub_rn(u[i0], u[i0 + 1]);
+    }
+}
+
+// Dequantised coefficient of pyramid position p (detail of subband slot sb) from shared codes.
+__device__ __forceinline__ float coef(const signed char *q, const float *step, int p, int slot) {
+    return __fmul_rn((float)q[p], step[slot]);
+}
+
+// One level for group (i, j, k) of half-size h = 4 >> (L - 1): the average comes from `avg`, the
+// details from the pyramid positions (i + a h, j + b h, k + c h).
+__device__ __forceinline__ void level_group(const signed char *q, const float *step, int L, int i, int j, int k,
+                                            float avg, float out[8]) {
+    const int h = 4 >> (L - 1);
+    float c[8];
+    c[0] = avg;
+#pragma unroll
+    for (int sb = 1; sb < 8; ++sb) {
+        const int p = (i + (sb & 1) * h) + 8 * (j + ((sb >> 1) & 1) * h) + 64 * (k + (sb >> 2) * h);
+        c[sb] = coef(q, step, p, 7 * (L - 1) + sb - 1);
+    }
+    inv_group(c, out);
+}
+
 // Decoder into one brick's stored region: elements (x, y, z) of a dx*dy*dz x-contiguous FP32
 // array holding global voxel clamp(org + (x, y, z)).  One warp per cube block that the
-// region's clamped coordinates touch: the block is decoded in shared memory and its voxels
-// are written to every element that maps to them.
+// region's clamped coordinates touch: levels 3 and 2 on a few lanes, level 1 as 64 independent
+// 2x2x2 groups (two per lane), the block's 512 voxels in shared memory, then written to every
+// element that maps to them.
 __global__ void __launch_bounds__(32 * kWarpsPerCta)
 k_wavelet_decode(const unsigned char *__restrict__ store, int nx, int ny, int nz, int bnx, int bny,
                  int ox, int oy, int oz, int dx, int dy, int dz, int b0x, int b0y, int b0z, int nbx, int nby,
                  long long nbl, float *__restrict__ dst) {
-    __shared__ float s_a[kWarpsPerCta][512];
-    __shared__ float s_b[kWarpsPerCta][512];
+    __shared__ __align__(16) signed char s_q[kWarpsPerCta][512];
+    __shared__ float s_step[kWarpsPerCta][21];
+    __shared__ float s_l3[kWarpsPerCta][8];
+    __shared__ float s_l2[kWarpsPerCta][64];
+    __shared__ float s_v[kWarpsPerCta][512];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long t = (long long)blockIdx.x * kWarpsPerCta + w;
     if (t >= nbl) return;                             // warp-uniform
     const int cbx = b0x + (int)(t % nbx), cby = b0y + (int)((t / nbx) % nby), cbz = b0z + (int)(t / ((long long)nbx * nby));
     const unsigned char *rec = store + (((long long)cbz * bny + cby) * bnx + cbx) * kWaveletRecordBytes;
-    float *a = s_a[w], *b = s_b[w];
-    for (int p = lane; p < 512; p += 32) {
-        const int sb = subband_of(p);
-        float c;
-        if (sb < 0) {
-            c = *reinterpret_cast<const float *>(rec + 512);
-        } else {
-            const int e = (int)(signed char)rec[516 + sb];
-            const int q = (int)(signed char)rec[p];
-            c = e == -128 ? 0.0f : __fmul_rn((float)q, pow2f(e));
-        }
-        a[p] = c;
+    reinterpret_cast<uint4 *>(s_q[w])[lane] = reinterpret_cast<const uint4 *>(rec)[lane];
+    if (lane < 21) {
+        const int e = (int)(signed char)rec[516 + lane];
+        s_step[w][lane] = e == -128 ? 0.0f : pow2f(e);
+    }
+    const float avg = *reinterpret_cast<const float *>(rec + 512);
+    __syncwarp();
+    const signed char *q = s_q[w];
+    const float *step = s_step[w];
+    float o[8];
+    if (lane == 0) {
+        level_group(q, step, 3, 0, 0, 0, avg, o);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) s_l3[w][v] = o[v];
     }
     __syncwarp();
-    haar_inverse_level(a, b, 2, lane);
-    haar_inverse_level(a, b, 4, lane);
-    haar_inverse_level(a, b, 8, lane);
+    if (lane < 8) {
+        const int i = lane & 1, j = (lane >> 1) & 1, k = lane >> 2;
+        level_group(q, step, 2, i, j, k, s_l3[w][i + 2 * j + 4 * k], o);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) s_l2[w][(2 * i + (v & 1)) + 4 * (2 * j + ((v >> 1) & 1)) + 16 * (2 * k + (v >> 2))] = o[v];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int gg = 0; gg < 2; ++gg) {
+        const int g = lane + 32 * gg;
+        const int i = g & 3, j = (g >> 2) & 3, k = g >> 4;
+        level_group(q, step, 1, i, j, k, s_l2[w][i + 4 * j + 16 * k], o);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) s_v[w][(2 * i + (v & 1)) + 8 * (2 * j + ((v >> 1) & 1)) + 64 * (2 * k + (v >> 2))] = o[v];
+    }
+    __syncwarp();
+    const float *a = s_v[w];
     // elements whose clamped global coordinate lies in this block, per axis [lo, hi)
     int lo[3], hi[3];
     const int org[3] = {ox, oy, oz}, dim[3] = {dx, dy, dz}, n[3] = {nx, ny, nz}, cb[3] = {cbx, cby, cbz};
@@ -208,6 +248,16 @@ k_wavelet_decode(const unsigned char *__restrict__ store, int nx, int ny, int nz
     }
     const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
     if (ex <= 0 || ey <= 0 || ez <= 0) return;
+    if (ex == 8 && ey == 8 && ez == 8 && lo[0] == 8 * cbx - ox && lo[1] == 8 * cby - oy && lo[2] == 8 * cbz - oz &&
+        8 * cbx + 8 <= nx && 8 * cby + 8 <= ny && 8 * cbz + 8 <= nz) {
+        // a block inside the cube whose voxels land once each, unclamped: element lo + v holds
+        // voxel v (blocks on an upper face hold padding beyond the cube: generic path)
+        float *d0 = dst + ((long long)lo[2] * dy + lo[1]) * dx + lo[0];
+#pragma unroll 4
+        for (int i = lane; i < 512; i += 32)
+            d0[((long long)(i >> 6) * dy + ((i >> 3) & 7)) * dx + (i & 7)] = a[i];
+        return;
+    }
     const int cnt = ex * ey * ez;
     for (int i = lane; i < cnt; i += 32) {
         const int x = lo[0] + i % ex, y = lo[1] + (i / ex) % ey, z = lo[2] + i / (ex * ey);
