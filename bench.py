@@ -37,7 +37,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "gass", "pr1"])
+    ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "hipass_slab", "gass", "pr1"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
     return ap.parse_args()
@@ -147,8 +147,8 @@ def kernel_traffic(name: str):
 def make_cube(cfg_name: str, device: str):
     if cfg_name == "hipass":
         return synth.hipass_cube(device=device), synth.HIPASS
-    if cfg_name == "hipass_small":
-        c = synth.HIPASS_SMALL
+    if cfg_name in ("hipass_small", "hipass_slab"):
+        c = synth.HIPASS_SMALL if cfg_name == "hipass_small" else synth.HIPASS_SLAB
         return synth.hipass_cube(seed=c["seed"], shape_xyz=c["shape"], n_sources=c["n_sources"],
                                  device=device), c
     if cfg_name == "gass":
@@ -513,7 +513,7 @@ def run_ours(args, dist):
         "config": {"workload": cfg["name"] + f", {W}x{H} perspective 64-view orbit, step "
                    f"{cfg['step']}, 256^3 bricks + ghost 1, FP32 bricks, ERT 0.99",
                    "cube_xyz": [nx, ny, nz], "frame": [W, H], "bricks": list(cfg["brick"]),
-                   "l2": "inputs larger than L2 (12.1 GB cube); no flush",
+                   "l2": f"inputs larger than L2 ({4 * nx * ny * nz / 1e9:.1f} GB cube); no flush",
                    "brick_layouts": "slice-atlas textures (2 gathers per sample) + x-contiguous copy",
                    "parallelism": f"replicas x{dist.world}"},
         "ms_per_frame": round(t_max / args.steps, 4),

@@ -382,22 +382,19 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
 // skipping): the ray continues from its pixel's accumulator (colour, transmittance) left by
 // the nearer bricks of earlier waves and writes it back; a ray that nearer bricks already made
 // opaque takes no sample, and a CTA whose rays all are exits before loading the table.
+// The 32 rays of one warp: strip `strip` (0..7) of work item `it`.  MODE 0 and 1 write their
+// fragments; MODE 2 (global termination) continues from and writes back the pixel's
+// accumulator, and skips when the whole CTA is occluded (so every thread of the CTA must call
+// it, once).  Adds the warp's samples to the counters.
 template <int S, int MODE, int F, bool MASK>
-__global__ void VR_RAYCAST_BOUNDS
-k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
-          const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
-          Counters *__restrict__ ctr) {
-    extern __shared__ float4 s_lut[];
-    if (MODE == 0) {
-        load_table(lut, fc.nlut, s_lut);
-        __syncthreads();
-    }
-    const TileItem it = items[blockIdx.x];
+__device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__restrict__ lut,
+                                         DrawBrick *__restrict__ dbs, const TileItem it, int strip, int lane,
+                                         const void *__restrict__ pool, void *__restrict__ frags,
+                                         Counters *__restrict__ ctr, float4 *s_lut) {
     const DrawBrick &b = dbs[it.db];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
-    const int rx = fc.lanes_y ? it.tx * kRcShort + warp : it.tx * kRcLong + lane;
-    const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + warp;
+    const int rx = fc.lanes_y ? it.tx * kRcShort + strip : it.tx * kRcLong + lane;
+    const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + strip;
     const int rw = b.rect[2];
     const bool inrect = rx < rw && ry < b.rect[3];
     int nsamp = 0;
@@ -500,6 +497,24 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
             atomicAdd(&ctr->bricks_sampled, 1ull);
             atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)b.bytes);
         }
+    }
+}
+
+template <int S, int MODE, int F, bool MASK>
+__global__ void VR_RAYCAST_BOUNDS
+k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
+          const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
+          Counters *__restrict__ ctr) {
+    extern __shared__ float4 s_lut[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (MODE == 2) {
+        rc_strip<S, MODE, F, MASK>(fc, lut, dbs, items[blockIdx.x], warp, lane, pool, frags, ctr, s_lut);
+    } else {
+        if (MODE == 0) {
+            load_table(lut, fc.nlut, s_lut);
+            __syncthreads();
+        }
+        rc_strip<S, MODE, F, MASK>(fc, lut, dbs, items[blockIdx.x], warp, lane, pool, frags, ctr, s_lut);
     }
 }
 

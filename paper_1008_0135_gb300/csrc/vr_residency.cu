@@ -236,7 +236,7 @@ struct Slot {
     uint64_t lru = 0;
     int exp2 = 0;
     int64_t chunk = -1;               // last chunk (global counter) that uses this slot
-    cudaEvent_t last_use = nullptr;   // recorded after the last ray-cast that read the slot
+    cudaEvent_t last_use = nullptr;   // completes after every ray-cast that read the slot so far
     bool used = false;
     int held = 0;                     // in-flight serving frames that need this brick
 };
@@ -670,6 +670,10 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
                           c->d_frags.p, c->d_ctr, s));
         for (size_t i = d0; i < d1; ++i) {
             Slot &sl = k->slots[k->where[key_of(cb->id, wl.db[i].brick)]];
+            // one event stands for every reader: frames of other streams may still read this
+            // slot, so the new record first waits for the previous one (which was enqueued
+            // earlier: no cycle); an eviction waiting on it then waits for all of them
+            if (sl.used) CK(cudaStreamWaitEvent(s, sl.last_use, 0));
             CK(cudaEventRecord(sl.last_use, s));
             sl.used = true;
         }

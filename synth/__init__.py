@@ -29,7 +29,7 @@ __all__ = [
     "ramp_lut", "shifted_ramp_lut", "constant_lut", "random_lut",
     "look_at", "orbit_view", "pr1_camera", "axis_ortho_camera", "random_camera",
     "sample_pixels", "poisson_arrivals",
-    "PR1", "HIPASS", "HIPASS_SMALL", "GASS", "DIFF", "orbit_camera",
+    "PR1", "HIPASS", "HIPASS_SMALL", "HIPASS_SLAB", "GASS", "DIFF", "orbit_camera",
 ]
 
 # ----------------------------------------------------------------------------------------------
@@ -43,6 +43,9 @@ HIPASS = dict(name="HIPASS-scale 1720x1720x1024", shape=(1720, 1720, 1024), seed
 # the HIPASS recipe at 768x768x512 (1.2 GB, still above L2): the case hardware counters are
 # captured on (a full-size capture would replay a 12 GB working set dozens of times)
 HIPASS_SMALL = dict(HIPASS, name="HIPASS-recipe 768x768x512", shape=(768, 768, 512), n_sources=1000)
+# the HIPASS recipe 256 channels deep (3.0 GB): the full cube's sky extent, so its rays are as
+# far apart as the full frame's (the case the sparse-ray counters are captured on)
+HIPASS_SLAB = dict(HIPASS, name="HIPASS-recipe 1720x1720x256", shape=(1720, 1720, 256), n_sources=5000)
 GASS = dict(name="GASS-scale 2048x2048x1600", shape=(2048, 2048, 1600), seed=2, W=1024,
             H=1024, step=0.5, tau=0.99, vrange=(-2.0, 8.0), brick=(256, 256, 256), ghost=1,
             n_views=64, fov_deg=60.0, eye_factor=1.5)
