@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "hipass_slab", "gass", "pr1"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
+    ap.add_argument("--leg", default=None, choices=["adjoint"],
+                    help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -614,6 +616,15 @@ def run_reference(args, dist):
 def main():
     args = parse()
     dist = Dist()
+    if args.leg == "adjoint":
+        import torch
+        import paper_1008_0135_gb300 as P
+        P.build()
+        torch.cuda.set_device(dist.local)
+        ctx = P.Context(dist.local)
+        print(json.dumps({"leg": "adjoint", **adjoint_leg(ctx, f"cuda:{dist.local}")}))
+        ctx.close()
+        return
     if args.impl == "reference":
         run_reference(args, dist)
     else:

@@ -634,15 +634,20 @@ __global__ void __launch_bounds__(256)
 k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const float *__restrict__ pool,
           const float4 *__restrict__ frags, const float4 *__restrict__ gfrag,
-          float *__restrict__ glut_partial, float *__restrict__ gvox) {
+          float *__restrict__ glut_partial, float *__restrict__ gvox, int ncopies) {
     extern __shared__ float4 s_lut[];
-    float *s_g = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);
+    // ncopies (1, 2, 4 or 8) table-gradient accumulators, lane l adding into copy l mod ncopies:
+    // neighbouring rays mostly hit the same entries, and same-address shared atomics of one
+    // warp serialise; copies sit 8 floats apart in bank position
+    const int gstride = 4 * fc.nlut + 8;
+    float *s_g0 = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);
     load_table(lut, fc.nlut, s_lut);
-    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) s_g[i] = 0.0f;
+    for (int i = threadIdx.x; i < ncopies * gstride; i += blockDim.x) s_g0[i] = 0.0f;
     __syncthreads();
     const TileItem it = items[blockIdx.x];
     const DrawBrick &b = dbs[it.db];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s_g = s_g0 + (lane & (ncopies - 1)) * gstride;
     // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
     const int rx = fc.lanes_y ? it.tx * kRcShort + warp : it.tx * kRcLong + lane;
     const int ry = fc.lanes_y ? it.ty * kRcLong + lane : it.ty * kRcShort + warp;
@@ -720,7 +725,11 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
     }
     __syncthreads();
     float *dst = glut_partial + (long long)blockIdx.x * 4 * fc.nlut;
-    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) dst[i] = s_g[i];
+    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) {
+        float v = s_g0[i];
+        for (int c = 1; c < ncopies; ++c) v += s_g0[c * gstride + i];
+        dst[i] = v;
+    }
 }
 
 // Final reduction of the per-CTA table-gradient partials, accumulated in FP64.
@@ -820,12 +829,16 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(48 * kMaxLut));
+                                             (int)(48 * kMaxLut + 32));
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const size_t smem = 48 * (size_t)fc.nlut;     // table + differences (32 B) + gradient accumulators (16 B)
-    k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
+    // table + differences (32 B per entry) + gradient accumulators (16 B per entry and copy): as
+    // many copies (up to 8) as keep the block within 64 KB
+    int ncopies = 8;
+    while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * (16 * (size_t)fc.nlut + 32) > (64u << 10)) ncopies >>= 1;
+    const size_t smem = 32 * (size_t)fc.nlut + ncopies * (16 * (size_t)fc.nlut + 32);
+    k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
     return cudaGetLastError();
 }
 

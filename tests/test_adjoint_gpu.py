@@ -17,10 +17,10 @@ def ctx():
     c.close()
 
 
-def _setup(ctx, seed, n=24, brick=(8, 8, 8), W=48, H=40):
+def _setup(ctx, seed, n=24, brick=(8, 8, 8), W=48, H=40, nlut=32):
     rng = np.random.default_rng(seed)
     cube = synth.pr1_cube(seed=seed, n=n, amp=(1.0, 4.0))
-    lut = synth.random_lut(seed, n=32, alpha_max=0.4)
+    lut = synth.random_lut(seed, n=nlut, alpha_max=0.4)
     cam = synth.random_camera(rng, (n, n, n), W, H)
     cid = ctx.load_cube(cube)
     ctx.set_bricking(cid, brick, 1, "f32")
@@ -37,9 +37,15 @@ def _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau):
     return glut.cpu().numpy().astype(np.float64), gvox.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("seed,tau,layouts", [(0, 0.95, 1), (1, 1.0, 1), (2, 0.9, 7), (3, 0.9, 9)])
-def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau, layouts):
-    rng, cube, lut, cam, cid = _setup(ctx, seed)
+# the table gradient accumulates in 8 shared-memory copies for small tables, 1 for 2048 entries;
+# an opacity above 1 (transmittance can turn negative) is followed as written
+@pytest.mark.parametrize("seed,tau,layouts,nlut,over", [(0, 0.95, 1, 32, False), (1, 1.0, 1, 32, False),
+                                                        (2, 0.9, 7, 32, False), (3, 0.9, 9, 32, False),
+                                                        (4, 0.95, 1, 2048, False), (5, 0.95, 1, 32, True)])
+def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau, layouts, nlut, over):
+    rng, cube, lut, cam, cid = _setup(ctx, seed, nlut=nlut)
+    if over:
+        lut[7, 3] = 1.05
     if layouts != 1:
         ctx.set_brick_layouts(cid, layouts)
     vr = (-3.0, 8.0)
