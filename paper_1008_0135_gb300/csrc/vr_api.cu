@@ -402,8 +402,8 @@ void free_atlases(Cube *cb) {
 // Slice atlas of every brick (layout bit 3) from its x-contiguous copy in the pool: slice z
 // of a brick of dx x dy x dz stored elements becomes tile (z mod 2^alog, z div 2^alog) of a 2D
 // array of 2^alog dx x ceil(dz / 2^alog) dy texels, with 2^alog the smallest power of two whose
-// square is >= dz.  FP32 bricks keep their values, 16-bit bricks their codes (as 16-bit
-// unsigned texels).  The array must fit the device's limit for 2D gathers.
+// square is >= dz.  FP32 bricks keep their values, 16-bit bricks their codes (FP16 as half
+// texels, BF16 as 16-bit unsigned ones).  The array must fit the device's limit for 2D gathers.
 int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     free_atlases(cb);
     const int nbr = (int)cb->tmpl.size();
@@ -432,8 +432,11 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     };
     cudaError_t e = cudaMemsetAsync(tmp, 0, most, s);
     if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+    // FP32 values; FP16 codes as half texels (gathers widen them to float exactly); BF16 codes as
+    // 16-bit unsigned texels (widened in the kernel)
     const cudaChannelFormatDesc cd = esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
-                                              : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
+                                   : cb->storage == VR_F16 ? cudaCreateChannelDescHalf()
+                                                           : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
     cb->atlas_arr.assign(nbr, nullptr);
     cb->atlas_tex.assign(nbr, 0);
     for (int i = 0; i < nbr; ++i) {

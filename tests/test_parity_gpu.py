@@ -334,6 +334,31 @@ def test_brick_layouts_give_identical_images(ctx, orc, storage, layouts):
     ctx.free_cube(many)
 
 
+def test_fp16_atlas_keeps_subnormal_codes(ctx):
+    """A brick whose maximum (1000) sets the FP16 scale 2^-4 turns values of 1e-7..2e-6 into
+    subnormal codes; the slice atlas (half texels widened by the texture unit) must give the
+    same frames as the linear copy, bit for bit, so no code may be flushed to zero."""
+    rng = np.random.default_rng(99)
+    cube = (rng.uniform(1e-7, 2e-6, (32, 32, 32)) * rng.choice([-1.0, 1.0], (32, 32, 32))).astype(np.float32)
+    cube[16, 16, 16] = 1000.0
+    lut = synth.ramp_lut(alpha=0.5)
+    one = ctx.load_cube(cube)
+    ctx.set_bricking(one, (32, 32, 32), 1, "f16")
+    atl = ctx.load_cube(cube)
+    ctx.set_brick_layouts(atl, 9)
+    ctx.set_bricking(atl, (32, 32, 32), 1, "f16")
+    assert ctx.get_brick(one, 0)[2] == -4
+    codes = ctx.get_brick(one, 0)[3]
+    assert np.count_nonzero((codes & 0x7C00) == 0) > 1000         # subnormal (or zero) codes
+    rng2 = np.random.default_rng(3)
+    for cam in [synth.pr1_camera(n=32, W=64, H=64), synth.random_camera(rng2, (32, 32, 32), 48, 40)]:
+        a = render(ctx, one, lut, (-1e-5, 1e-5), cam, step=0.5, tau=1.0)
+        b = render(ctx, atl, lut, (-1e-5, 1e-5), cam, step=0.5, tau=1.0)
+        assert np.abs(a).max() > 0 and np.array_equal(a, b)
+    ctx.free_cube(one)
+    ctx.free_cube(atl)
+
+
 # ---------------------------------------------------------------------------------------------
 # empty-space skipping (a noise-suppressing table: zero opacity below a threshold)
 # ---------------------------------------------------------------------------------------------
