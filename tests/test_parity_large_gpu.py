@@ -3,6 +3,9 @@
 HIPASS-scale: 1720x1720x1024 (12.1 GB), 256^3 bricks, 1024^2 perspective orbit, step 1.
 GASS-scale:   2048x2048x1600 (26.8 GB), 256^3 bricks, 1024^2 perspective orbit, step 0.5,
               FP32 / FP16 / BF16 bricks, error against the FP64 oracle on 4096 sampled rays.
+Both keep the bench's brick layouts (slice atlases + the x-contiguous copy), so every frame
+here gathers from the atlases as the timed frames do; HIPASS also checks global termination
+with the occlusion leg's opaque table.
 The measured maximum errors are written to gpurun_out/large_errors.json when that folder exists.
 """
 import json
@@ -39,6 +42,7 @@ def _check_config(ctx, orc, cfg, cube_t, storages, views, n_rays, tag):
     cid = ctx.load_cube(cube_t)
     del cube_t
     torch.cuda.empty_cache()
+    ctx.set_brick_layouts(cid, 9)
     lut = synth.ramp_lut()
     vr = cfg["vrange"]
     for storage in storages:
@@ -64,6 +68,18 @@ def _check_config(ctx, orc, cfg, cube_t, storages, views, n_rays, tag):
                                        brick=cfg["brick"], pix=pix[:512])
                 assert np.array_equal(m[pix[:512]], m32.astype(np.float32))
                 ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+            # global termination (occlusion skipping) with an opaque table, as timed
+            if tag == "hipass" and storage == "f32" and j == views[0]:
+                opaque = synth.ramp_lut(alpha=1.0)
+                ctx.set_transfer_function(opaque, *vr)
+                ctx.set_termination("global")
+                g = ctx.render_frame(cid).cpu().numpy().reshape(-1, 4)
+                ctx.set_termination("segment")
+                ctx.set_transfer_function(lut, *vr)
+                refg, flg, _ = orc.render(cube, opaque, vr, cam, step=cfg["step"], tau=cfg["tau"],
+                                          brick=cfg["brick"], pix=pix, term="global")
+                errg = compare_dvr(g[pix], refg, flg, cfg["tau"])
+                _record(f"{tag} f32 global-termination view{j}", {"max_abs_err": errg, "rays": int(len(pix))})
     ctx.free_cube(cid)
 
 
