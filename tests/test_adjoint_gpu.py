@@ -123,3 +123,42 @@ def test_autograd_function_sums_views(ctx, orc):
     assert np.abs(lut.grad.cpu().numpy() - rl).max() <= 2e-4 * np.abs(rl).max()
     assert np.abs(vox.grad.cpu().numpy() - rv).max() <= 2e-4 * np.abs(rv).max()
     ctx.free_cube(cid)
+
+
+def test_adjoint_at_the_benchmark_size_on_sampled_pixels(ctx, orc):
+    """The differentiation workload as the bench times it (256^3 cube, 128^3 bricks, 512^2
+    views, step 0.5, ERT 0.99, ramp table): pixel gradients on 512 seeded pixels of two orbit
+    views (zero elsewhere), so the oracle traces only those rays; table and voxel gradients
+    against it."""
+    import torch
+    cfg = synth.DIFF
+    cube = synth.diff_cube(seed=cfg["seed"])
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+    lut = synth.ramp_lut()
+    vr = cfg["vrange"]
+    c = np.array(cfg["shape"], np.float64) / 2
+    rng = np.random.default_rng(31)
+    for j in (1, 6):
+        cam = dict(view=synth.orbit_view(45.0 * j, c, 1.5 * 0.5 * math.sqrt(3) * cfg["shape"][0]),
+                   proj=1, param=math.radians(60.0), W=cfg["W"], H=cfg["H"])
+        pix = synth.sample_pixels(700 + j, cam["W"], cam["H"], 512)
+        _, flags, _ = orc.render(cube, lut, vr, cam, step=cfg["step"], tau=cfg["tau"],
+                                 brick=cfg["brick"], pix=pix)
+        g = rng.standard_normal((len(pix), 4))
+        g[(flags & 9).astype(bool)] = 0.0
+        g = g.astype(np.float32).astype(np.float64)
+        full = np.zeros((cam["H"] * cam["W"], 4), np.float32)
+        full[pix] = g
+        render(ctx, cid, lut, vr, cam, step=cfg["step"], tau=cfg["tau"])
+        gl = torch.zeros((lut.shape[0], 4), device="cuda")
+        gv = torch.zeros(cube.shape, device="cuda")
+        ctx.render_backward(cid, torch.from_numpy(full.reshape(cam["H"], cam["W"], 4)).cuda(), gl, gv)
+        rl, rv = orc.render_grad(cube, lut, vr, cam, g, step=cfg["step"], tau=cfg["tau"],
+                                 brick=cfg["brick"], pix=pix)
+        gl = gl.cpu().numpy().astype(np.float64)
+        gv = gv.cpu().numpy().astype(np.float64)
+        assert np.abs(rl).max() > 0 and np.abs(rv).max() > 0
+        assert np.abs(gl - rl).max() <= 2e-4 * np.abs(rl).max(), np.abs(gl - rl).max()
+        assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max(), np.abs(gv - rv).max()
+    ctx.free_cube(cid)
