@@ -595,6 +595,11 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     for (auto &b : cb->tmpl) max_bytes = std::max(max_bytes, (size_t)b.bytes);
     if ((rc = cache_size(c, max_bytes)) != VR_OK) return rc;
     FrameConsts fc = make_consts(c, cb);
+    // timing (vr_set_timing): frame, ray casting (from the first chunk's residency to the last
+    // chunk's ray-cast, so it includes waits for bricks made resident during the frame) and
+    // compositing
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     WorkList wl;
     build_worklist(c, cb, wl);
     const size_t nd = wl.db.size();
@@ -624,6 +629,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     }
     if ((rc = ensure_host(c, wl.bytes)) != VR_OK) return rc;
     if ((rc = ensure(c->d_stage, wl.bytes, c)) != VR_OK) return rc;
+    if (ev[0]) CK(cudaEventRecord(ev[0], s));
     const size_t felem = c->mode == VR_DVR ? sizeof(float4) : sizeof(float);
     if ((rc = ensure(c->d_frags, std::max<size_t>((size_t)wl.frag_px * felem, 16), c)) != VR_OK) return rc;
     const size_t opix = (size_t)fc.cam.W * fc.cam.H, ofl = opix * (c->mode == VR_DVR ? 4 : 1);
@@ -643,6 +649,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     CK(cudaMemcpyAsync(d + wl.off_ts, h + wl.off_ts, wl.off_mask - wl.off_ts + c->chmask.size(),
                        cudaMemcpyHostToDevice, s));
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(d + wl.off_mask);
+    if (ev[1]) CK(cudaEventRecord(ev[1], s));
     for (size_t ch = 0; ch < nchunks; ++ch) {
         const size_t d0 = ch * per, d1 = std::min(nd, d0 + per);
         const int64_t chunk_id = ++k->chunk_counter;
@@ -650,6 +657,8 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
             // leave nothing in flight that reads the staging of this abandoned frame
             cudaStreamSynchronize(k->copy);
             cudaStreamSynchronize(s);
+            if (ev[0])
+                for (auto e : ev) c->ev_pool.push_back(e);
             return rc;
         }
         CK(cudaEventRecord(k->copies_done, k->copy));
@@ -678,17 +687,20 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
             sl.used = true;
         }
     }
+    if (ev[2]) CK(cudaEventRecord(ev[2], s));
     std::memcpy(h + wl.off_db, wl.db.data(), sizeof(DrawBrick) * nd);
     CK(cudaMemcpyAsync(d + wl.off_db, h + wl.off_db, sizeof(DrawBrick) * nd, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->upload_done, s));
     CK(launch_composite(fc, reinterpret_cast<const DrawBrick *>(d + wl.off_db),
                         reinterpret_cast<const int *>(d + wl.off_ts), reinterpret_cast<const int *>(d + wl.off_tl),
                         c->d_frags.p, dst, s));
+    if (ev[3]) CK(cudaEventRecord(ev[3], s));
     if (!direct)
         CK(cudaMemcpyAsync(out, dst, ofl * sizeof(float),
                            out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(c->frame_done, s));
     c->frame_pending = true;
+    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
     c->frames++;
     c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)nd;

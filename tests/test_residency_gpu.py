@@ -88,6 +88,25 @@ def test_cache_hits_and_chunked_frames_agree():
     assert small1["bytes_streamed"] > 0
 
 
+def test_streamed_frames_are_timed():
+    """vr_set_timing covers streamed frames too: frame, ray-cast (with residency) and compositing."""
+    import paper_1008_0135_gb300 as P
+    lut = synth.ramp_lut(alpha=0.3)
+    cam = dict(view=synth.look_at((150.0, 135.0, -300.0), (150.0, 135.0, 130.0)), proj=1,
+               param=math.radians(70.0), W=120, H=100)
+    with P.Context(0, cache_bytes=8 * F32_BRICK_BYTES) as ctx:
+        cid = ctx.load_cube_procedural(SEED, SMALL)
+        ctx.set_bricking(cid, BRICK, 1, "f32")
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+        render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+        st = ctx.stats()
+        ctx.set_timing(False)
+    assert st["timed_frames"] == 2
+    assert st["ms_frame"] >= st["ms_raycast"] + st["ms_composite"] - 1e-3 > 0
+
+
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_streamed_16bit_equals_resident_16bit(orc, storage):
     """Host-encoded streamed bricks equal device-encoded resident bricks of the same voxels."""
