@@ -234,13 +234,12 @@ int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold)
  * VR_TERM_SEGMENT (default): every brick ray-casts its own segment of a ray from full
  * transmittance and stops it at tau; the bricks' sub-images (fragments) are then composited
  * front to back, so each brick works independently, as on the paper's cluster.
- * VR_TERM_GLOBAL (occlusion skipping): bricks are ray-cast in waves of equal front-to-back
- * key, nearest first, into one accumulator per pixel (colour, transmittance); a ray continues
- * from the transmittance the nearer bricks left and stops once the whole ray's opacity reaches
- * tau, so samples behind opaque pixels are skipped and a brick whose rays are all occluded
- * costs no sampling.  The image is the unbricked ray's (global termination); it differs from
- * VR_TERM_SEGMENT's by at most 1 - tau per channel.  No fragments are written (stats count
- * none).  Not available for streamed cubes (vr_render_frame returns VR_ERR_UNSUPPORTED),
+ * VR_TERM_GLOBAL (occlusion skipping): one pass in which every pixel's ray walks the cube's
+ * bricks front to back, sampling each brick's segment exactly as the fragment path would (the
+ * same samples, owners and arithmetic), carrying one transmittance through them, and stops
+ * once the whole ray's opacity reaches tau, so samples behind opaque pixels are skipped.  The
+ * image is the unbricked ray's (global termination); it differs from VR_TERM_SEGMENT's by at
+ * most 1 - tau per channel.  No fragments are written (stats count none).  Not available for streamed cubes (vr_render_frame returns VR_ERR_UNSUPPORTED),
  * vr_render_frame_noalloc or vr_render_backward (both VR_ERR_UNSUPPORTED); MIP ignores it.
  * Errors: VR_ERR_ARG. */
 int vr_set_termination(vr_ctx *ctx, int mode);

@@ -212,8 +212,8 @@ class Context:
 
     def set_termination(self, scope: str = "segment"):
         """Early-termination scope for DVR: "segment" (each brick's ray segment stops on its own;
-        fragments composited afterwards) or "global" (occlusion skipping: bricks in front-to-back
-        waves into per-pixel accumulators, rays stop once the whole ray is opaque)."""
+        fragments composited afterwards) or "global" (occlusion skipping: each ray walks the bricks
+        front to back in one pass and stops once the whole ray is opaque)."""
         _check(self._L.vr_set_termination(self._h, {"segment": 0, "global": 1}[scope]),
                "vr_set_termination")
 

@@ -231,17 +231,7 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     wl.db.reserve(order.size());
     const FrameLayout fl = frame_layout(c, cb);
     long long frag = 0;
-    // waves: bricks of one front-to-back key share no ray (the key grows at every brick a ray
-    // enters), so a wave's bricks can update the pixels' accumulators concurrently
-    wl.wave_start.clear();
-    bool first = true;
-    long long wkey = 0;
     for (auto &o : order) {
-        if (first || o.first != wkey) {
-            wl.wave_start.push_back((int)wl.items.size());
-            wkey = o.first;
-            first = false;
-        }
         DrawBrick d = cand[o.second];
         d.frag_off = frag;
         frag += (long long)d.rect[2] * d.rect[3];
@@ -253,7 +243,6 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
             for (int tx = 0; tx < tw; ++tx) wl.items.push_back(TileItem{di, tx, ty});
         wl.db.push_back(d);
     }
-    wl.wave_start.push_back((int)wl.items.size());
     wl.frag_px = frag;
     // screen-tile bins in front-to-back order
     const int ntx = (W + kTile - 1) / kTile, nty = (H + kTile - 1) / kTile;
@@ -304,7 +293,6 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
     // it saves; with a poor alignment it pays
     fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
-    fc.accum = (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) ? 1 : 0;
     return fc;
 }
 
@@ -1188,6 +1176,92 @@ int vr_set_full_rect(vr_ctx *c, int full) {
 
 namespace vrh {
 
+// A DVR frame with global early termination: one launch in which every pixel's ray walks the
+// cube's bricks front to back (k_raymarch), no fragments.  Stages the table, every brick's
+// record (the frame's linear layout, atlas and skip flag) and the channel mask.
+static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
+    int rc;
+    FrameConsts fc = make_consts(c, cb);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
+    const FrameLayout fl = frame_layout(c, cb);
+    const size_t nb = cb->tmpl.size();
+    std::vector<int> apre;
+    alpha_prefix(c, apre);
+    size_t off = 0;
+    const size_t off_lut = off;
+    off = align_up(off + sizeof(float4) * c->lut.size(), 256);
+    const size_t off_b = off;
+    off = align_up(off + sizeof(DrawBrick) * nb, 256);
+    const size_t off_mask = off;
+    off = align_up(off + c->chmask.size(), 256);
+    if (c->frame_pending) {
+        CK(cudaEventSynchronize(c->upload_done));
+        CK(cudaStreamWaitEvent(s, c->frame_done, 0));
+    }
+    if ((rc = ensure_host(c, off)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_stage, off, c)) != VR_OK) return rc;
+    char *h = c->h_stage;
+    std::memcpy(h + off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
+    DrawBrick *hb = reinterpret_cast<DrawBrick *>(h + off_b);
+    int64_t drawn = 0;
+    for (size_t i = 0; i < nb; ++i) {
+        DrawBrick d = cb->tmpl[i];
+        if (!cb->loff.empty()) d.data_off = cb->loff[3 * i + fl.layout];
+        layout_strides(d.dim, fl.layout, d.str);
+        d.skip = skip_brick(c, cb, i, apre.data()) ? 1 : 0;
+        d.sampled = 0;
+        drawn += d.skip ? 0 : 1;
+        hb[i] = d;
+    }
+    if (!c->chmask.empty()) std::memcpy(h + off_mask, c->chmask.data(), c->chmask.size());
+    MarchGrid g{};
+    for (int a = 0; a < 3; ++a) {
+        g.nb[a] = (int)cb->nb[a];
+        g.B[a] = (float)cb->B[a];
+        g.n[a] = (float)cb->n[a];
+        g.clo[a] = 0.0f;
+        g.chi[a] = (float)cb->n[a];
+        if (c->has_window) {
+            g.clo[a] = (float)std::max<int64_t>(c->win_lo[a], 0);
+            g.chi[a] = (float)std::min<int64_t>(c->win_hi[a], cb->n[a]);
+        }
+    }
+    if (ev[0]) CK(cudaEventRecord(ev[0], s));
+    CK(cudaMemcpyAsync(c->d_stage.p, h, off, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->upload_done, s));
+    char *d = c->d_stage.p;
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(d + off_mask);
+    const size_t opix = (size_t)fc.cam.W * fc.cam.H;
+    float *dst = out;
+    const bool direct = out_where == VR_DEVICE && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    if (!direct) {
+        if ((rc = ensure(c->d_out, opix * 4, c)) != VR_OK) return rc;
+        dst = c->d_out.p;
+    }
+    if (ev[1]) CK(cudaEventRecord(ev[1], s));
+    const bool empty = g.chi[0] <= g.clo[0] || g.chi[1] <= g.clo[1] || g.chi[2] <= g.clo[2];
+    if (empty) {                       // an empty window: a transparent frame
+        CK(cudaMemsetAsync(dst, 0, opix * sizeof(float4), s));
+    } else {
+        CK(launch_raymarch(fc, reinterpret_cast<const float4 *>(d + off_lut), reinterpret_cast<DrawBrick *>(d + off_b),
+                           g, cb->d_pool, reinterpret_cast<float4 *>(dst), c->d_ctr, s));
+    }
+    if (ev[2]) CK(cudaEventRecord(ev[2], s));
+    if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    if (!direct) {
+        CK(cudaMemcpyAsync(out, dst, opix * sizeof(float4),
+                           out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaEventRecord(c->frame_done, s));
+    c->frame_pending = true;
+    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    c->frames++;
+    c->bricks_drawn += drawn;
+    if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
 // One frame of cube `cb` with the context's current table, camera and parameters.
 __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
@@ -1196,6 +1270,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
             return fail(VR_ERR_UNSUPPORTED, "global termination needs resident bricks (streamed cube)");
         return render_streamed(c, cb, out, out_where, s);
     }
+    if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) return render_global(c, cb, out, out_where, s);
     FrameConsts fc = make_consts(c, cb);
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
@@ -1203,9 +1278,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     if ((rc = stage_frame(c, cb, wl, s, ev[0])) != VR_OK) return rc;
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
     const size_t opix = (size_t)fc.cam.W * fc.cam.H;
-    // fragments, or with global termination one accumulator per pixel
-    const size_t fbytes = fc.accum ? opix * sizeof(float4)
-                                   : (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
+    const size_t fbytes = (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
     if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
     const size_t ofl = opix * (c->mode == VR_DVR ? 4 : 1);
     float *dst = out;
@@ -1220,25 +1293,11 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
     const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
     const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
-    if (fc.accum) {
-        // global termination: one ray-cast launch per front-to-back wave into the accumulator
-        float4 *acc = reinterpret_cast<float4 *>(c->d_frags.p);
-        CK(launch_accum_init(acc, (long long)opix, s));
-        if (ev[1]) CK(cudaEventRecord(ev[1], s));
-        for (size_t w = 0; w + 1 < wl.wave_start.size(); ++w) {
-            const int i0 = wl.wave_start[w], n = wl.wave_start[w + 1] - i0;
-            if (n > 0) CK(launch_raycast(fc, d_lut, d_db, d_items + i0, n, cb->d_pool, acc, c->d_ctr, s));
-        }
-        if (ev[2]) CK(cudaEventRecord(ev[2], s));
-        CK(launch_accum_finalize(acc, dst, (long long)opix, s));
-        if (ev[3]) CK(cudaEventRecord(ev[3], s));
-    } else {
-        if (ev[1]) CK(cudaEventRecord(ev[1], s));
-        CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
-        if (ev[2]) CK(cudaEventRecord(ev[2], s));
-        CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
-        if (ev[3]) CK(cudaEventRecord(ev[3], s));
-    }
+    if (ev[1]) CK(cudaEventRecord(ev[1], s));
+    CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
+    if (ev[2]) CK(cudaEventRecord(ev[2], s));
+    CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
+    if (ev[3]) CK(cudaEventRecord(ev[3], s));
     if (!direct) {
         CK(cudaMemcpyAsync(out, dst, ofl * sizeof(float),
                            out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
@@ -1247,7 +1306,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     c->frame_pending = true;
     if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
     c->frames++;
-    c->fragments += fc.accum ? 0 : wl.frag_px;
+    c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)wl.db.size();
     if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
     return VR_OK;

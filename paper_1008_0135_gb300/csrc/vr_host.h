@@ -82,7 +82,6 @@ struct WorkList {
     std::vector<DrawBrick> db;
     std::vector<TileItem> items;
     std::vector<int> tile_start, tile_list;
-    std::vector<int> wave_start;      // items of front-to-back key wave w: [wave_start[w], [w+1])
     long long frag_px = 0;
     // offsets inside the staged upload
     size_t off_lut = 0, off_db = 0, off_items = 0, off_ts = 0, off_tl = 0, off_mask = 0, bytes = 0;

@@ -40,8 +40,6 @@ struct FrameConsts {
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
                                    // from the brick's slice-atlas texture
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
-    int accum;                     // DVR with global termination: rays continue from and write
-                                   // back a per-pixel accumulator (passed as the fragments)
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -62,7 +60,17 @@ struct DrawBrick {
                                    // array whose tile (z & (2^alog - 1), z >> alog) of dim[0] x
                                    // dim[1] texels holds stored slice z (FP32 values or 16-bit codes)
     int alog;
-    int pad_;
+    int skip;                      // global termination: every sample of this brick adds nothing
+                                   // (its values map only to zero opacity), walk through it
+};
+
+// The brick grid a global-termination frame walks: nb bricks per axis of core size B over a
+// cube of size n (voxels; the last brick along an axis holds the remainder), rays clipped to
+// [clo, chi) (the cube, or the render window inside it).
+struct MarchGrid {
+    int nb[3];
+    float B[3], n[3];
+    float clo[3], chi[3];
 };
 
 struct TileItem {                  // one ray-cast work item
@@ -104,10 +112,11 @@ cudaError_t launch_wavelet_encode(const float *cube, int nx, int ny, int nz, uns
 // FP32) from the block store.
 cudaError_t launch_wavelet_decode(const unsigned char *store, int nx, int ny, int nz, const int org[3],
                                   const int dim[3], float *dst, cudaStream_t s);
-// Global termination: fill the W*H accumulator with (0, 0, 0, 1); turn it into premultiplied
-// RGBA (colour, 1 - transmittance) in `out` (W*H float4).
-cudaError_t launch_accum_init(float4 *acc, long long npix, cudaStream_t s);
-cudaError_t launch_accum_finalize(const float4 *acc, float *out, long long npix, cudaStream_t s);
+// Global early termination: every pixel's ray walks the brick grid front to back in one
+// launch; premultiplied RGBA into out (W*H float4).  bricks: every brick of the cube in grid
+// order (x fastest), with the frame's layout offsets, atlases and skip flags.
+cudaError_t launch_raymarch(const FrameConsts &fc, const float4 *lut, DrawBrick *bricks, const MarchGrid &g,
+                            const void *pool, float4 *out, Counters *ctr, cudaStream_t s);
 cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,
                              const int *tile_list, const void *frags, float *out, cudaStream_t s);
 cudaError_t launch_composite_backward(const FrameConsts &fc, const DrawBrick *db,
