@@ -18,13 +18,17 @@
 
 #include "vr_internal.cuh"
 
-// Tuning knobs of the ray-cast kernel (build-time): unroll factor of the sample loop, and the
-// blocks per SM the register allocation must allow (0: no constraint).
+// Tuning knobs of the ray-cast kernels (build-time): unroll factor of the DVR sample loop, the
+// blocks per SM the fragment kernel's register allocation must allow (0: no constraint), and
+// the same for the one-pass (global termination) kernel.
 #ifndef VR_SAMPLE_UNROLL
-#define VR_SAMPLE_UNROLL 2
+#define VR_SAMPLE_UNROLL 1
 #endif
 #ifndef VR_RAYCAST_MIN_BLOCKS
 #define VR_RAYCAST_MIN_BLOCKS 0
+#endif
+#ifndef VR_RAYMARCH_MIN_BLOCKS
+#define VR_RAYMARCH_MIN_BLOCKS 5
 #endif
 constexpr int kSampleUnroll = VR_SAMPLE_UNROLL;
 #if VR_RAYCAST_MIN_BLOCKS > 0
@@ -529,11 +533,12 @@ __device__ __forceinline__ int cell_k(int c, bool exit, float o, float d, float 
 // transmittance; it stops once the transmittance reaches the threshold after a sample (global
 // early termination), so bricks behind opaque pixels cost nothing.  Bricks whose values map
 // only to zero opacity are walked through without sampling (their samples add nothing).
-// Registers: the walk's state on top of the sample loop; bounded to 4 CTAs per SM (64
-// registers, a few spilled) and one (clamped) copy of the sample loop, measured fastest
-// (1.10 ms against 1.69 unbounded with both loop copies, HIPASS-scale opaque-table frames).
+// Registers: the walk's state on top of the sample loop; bounded to 5 CTAs per SM (48
+// registers, some spilled outside the sample loop) and one (clamped) copy of the sample loop,
+// measured fastest (HIPASS-scale opaque-table frames: 0.98 ms; 4 CTAs at 64 registers 1.07,
+// unbounded with both loop copies 1.69).
 template <int S, int F, bool MASK>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, VR_RAYMARCH_MIN_BLOCKS)
 k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ bricks,
            const MarchGrid g, const void *__restrict__ pool, float4 *__restrict__ out,
            Counters *__restrict__ ctr) {
@@ -839,14 +844,20 @@ __global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts,
 }
 
 // The unified L1 / shared memory of an SM serves the texture gathers as cache: ask for just the
-// shared memory that 5 resident CTAs need (the table), leaving the rest to L1 (measured on
-// HIPASS-scale frames: 25 % carveout 3.65 ms, the driver's default 3.75, 50 % 3.98).  `last`
-// remembers the kernel's current preference (the attribute is per kernel).
+// shared memory (the table) of the 256-thread CTAs the register file admits, leaving the rest
+// to L1 (measured on HIPASS-scale frames at 5 CTAs: 25 % carveout 3.65 ms, the driver's default
+// 3.75, 50 % 3.98).  Registers are allocated per warp in units of 256, 64 K per SM, at most 64
+// warps.  `last` remembers the kernel's current preference (the attribute is per kernel).
 cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, std::atomic<int> &last) {
-    const double need = 5.0 * (double)(smem_per_cta + 1024) / (228.0 * 1024.0);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    const int ctas = std::max(1, std::min(64, 65536 / std::max(per_warp, 256)) / 8);
+    const double need = ctas * (double)(smem_per_cta + 1024) / (228.0 * 1024.0);
     const int pct = std::min(100, std::max(0, (int)std::ceil(100.0 * need)));
     if (last.load(std::memory_order_relaxed) == pct) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
     if (e == cudaSuccess) last.store(pct, std::memory_order_relaxed);
     return e;
 }
