@@ -19,23 +19,22 @@
 #include "vr_internal.cuh"
 
 // Tuning knobs of the ray-cast kernels (build-time): unroll factor of the DVR sample loop, the
-// blocks per SM the fragment kernel's register allocation must allow (0: no constraint), and
-// the same for the one-pass (global termination) kernel.
+// blocks per SM the register allocation of the fragment kernel must allow for DVR frames read
+// through slice atlases and for MIP frames (0: no constraint), and the same for the one-pass
+// (global termination) kernel.
 #ifndef VR_SAMPLE_UNROLL
 #define VR_SAMPLE_UNROLL 1
 #endif
-#ifndef VR_RAYCAST_MIN_BLOCKS
-#define VR_RAYCAST_MIN_BLOCKS 0
+#ifndef VR_DVR_MIN_BLOCKS
+#define VR_DVR_MIN_BLOCKS 6
+#endif
+#ifndef VR_MIP_MIN_BLOCKS
+#define VR_MIP_MIN_BLOCKS 0
 #endif
 #ifndef VR_RAYMARCH_MIN_BLOCKS
 #define VR_RAYMARCH_MIN_BLOCKS 5
 #endif
 constexpr int kSampleUnroll = VR_SAMPLE_UNROLL;
-#if VR_RAYCAST_MIN_BLOCKS > 0
-#define VR_RAYCAST_BOUNDS __launch_bounds__(256, VR_RAYCAST_MIN_BLOCKS)
-#else
-#define VR_RAYCAST_BOUNDS __launch_bounds__(256)
-#endif
 
 namespace vr {
 namespace {
@@ -149,14 +148,36 @@ struct Cell {
     float fx, fy, fz;
 };
 
+// floor(x) as a float and as an int, for |x| < 2^22, on the FMA and integer pipes (floorf and
+// float <-> int conversions issue on the narrower conversion pipe, which the per-sample work
+// kept a third busy): x + 1.5 * 2^23 rounded toward -infinity lands on the float grid of
+// spacing 1, exactly at floor(x) + 1.5 * 2^23, so the difference is exact and the integer sits in
+// the low mantissa bits.  (For x = -0 the float floor is +0 where floorf gives -0; the fraction
+// x - floor is then -0 instead of +0: the same value.)
+constexpr float kFloorMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr int kFloorMagicBits = 0x4B400000;         // its bit pattern
+__device__ __forceinline__ int floor_split(float x, float &fl) {
+    const float t = __fadd_rd(x, kFloorMagic);
+    fl = __fsub_rn(t, kFloorMagic);
+    return __float_as_int(t) - kFloorMagicBits;
+}
+
+// An int n with |n| < 2^22 as a float, exactly, without a conversion instruction.
+__device__ __forceinline__ float small_int_float(int n) {
+    return __fsub_rn(__int_as_float(kFloorMagicBits + n), kFloorMagic);
+}
+
+// Brick-local coordinates are below 2^17 in magnitude (stored bricks span at most 65536 + 2
+// voxels per axis), well inside floor_split's range.
 template <bool CLAMP = true>
 __device__ __forceinline__ void cell_of(float x, float y, float z, int mx, int my, int mz, Cell &c) {
-    const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+    float flx, fly, flz;
+    const int jx = floor_split(x, flx), jy = floor_split(y, fly), jz = floor_split(z, flz);
     c.fx = __fsub_rn(x, flx); c.fy = __fsub_rn(y, fly); c.fz = __fsub_rn(z, flz);
     if (CLAMP) {
-        c.ix = clampi((int)flx, 0, mx); c.iy = clampi((int)fly, 0, my); c.iz = clampi((int)flz, 0, mz);
+        c.ix = clampi(jx, 0, mx); c.iy = clampi(jy, 0, my); c.iz = clampi(jz, 0, mz);
     } else {                          // caller has shown every index of the segment is in range
-        c.ix = (int)flx; c.iy = (int)fly; c.iz = (int)flz;
+        c.ix = jx; c.iy = jy; c.iz = jz;
     }
 }
 
@@ -181,9 +202,11 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
     if (scaled) val = __fmul_rn(val, scale);
     o.u = __fmul_rn(__fsub_rn(val, vmin), inv_range);
     const float uc = fminf(fmaxf(o.u, 0.0f), 1.0f);
-    const float xl = __fmul_rn(uc, lutmax);
-    o.li = min((int)xl, lmax);
-    o.lf = __fsub_rn(xl, (float)o.li);
+    const float xl = __fmul_rn(uc, lutmax);    // in [0, lutmax]: truncation = floor
+    float fl;
+    const int li = floor_split(xl, fl);
+    o.li = min(li, lmax);
+    o.lf = __fsub_rn(xl, fminf(fl, __fsub_rn(lutmax, 1.0f)));   // (float)lmax = lutmax - 1
     o.L0 = s_lut[tab_entry(o.li, lmax + 2)];
     o.D = s_lut[tab_diff(o.li, lmax + 2)];
     o.r = __fmaf_rn(o.lf, o.D.x, o.L0.x);
@@ -224,9 +247,9 @@ __device__ __forceinline__ float bf16_value(unsigned int c) { return __uint_as_f
 // texels are returned unfiltered, so the corners are the stored values themselves.
 template <int S>
 __device__ __forceinline__ void fetch8_atlas(const Atlas &a, int ix, int iy, int iz, float v[8]) {
-    const int cm = (1 << a.alog) - 1, iz1 = iz + 1;
-    const float x0 = (float)((iz & cm) * a.dx + ix + 1), y0 = (float)((iz >> a.alog) * a.dy + iy + 1);
-    const float x1 = (float)((iz1 & cm) * a.dx + ix + 1), y1 = (float)((iz1 >> a.alog) * a.dy + iy + 1);
+    const int cm = (1 << a.alog) - 1, iz1 = iz + 1;   // atlas coordinates < 32768
+    const float x0 = small_int_float((iz & cm) * a.dx + ix + 1), y0 = small_int_float((iz >> a.alog) * a.dy + iy + 1);
+    const float x1 = small_int_float((iz1 & cm) * a.dx + ix + 1), y1 = small_int_float((iz1 >> a.alog) * a.dy + iy + 1);
     if constexpr (S != 2) {           // FP32 texels, or FP16 ones the texture unit widens (exactly)
         const float4 g0 = tex2Dgather<float4>(a.tex, x0, y0, 0);
         const float4 g1 = tex2Dgather<float4>(a.tex, x1, y1, 0);
@@ -350,9 +373,10 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
     int px = -4, py = -4, pz = -4;        // no cell cached yet
     float v[8];
     int j = 0;
+    float jf = 0.0f;                      // j as a float (exact: n <= 2^24 + 1, checked by the host)
 #pragma unroll kSampleUnroll
-    for (; j < n; ++j) {
-        const float tj = __fmul_rn((float)j, fc.step);
+    for (; j < n; ++j, jf = __fadd_rn(jf, 1.0f)) {
+        const float tj = __fmul_rn(jf, fc.step);
         Cell cl;
         cell_of<CLAMP>(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
                        mx, my, mz, cl);
@@ -490,8 +514,17 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
     }
 }
 
+// Blocks per SM the registers of k_raycast<., MODE, F, .> must allow (1: no constraint beyond
+// one block): the kernel's speed follows its resident warps, and 40 registers (6 CTAs) hold the
+// atlas DVR loop without spills.
+template <int MODE, int F>
+constexpr int rc_min_blocks() {
+    return MODE == 0 ? (F == 2 && VR_DVR_MIN_BLOCKS > 0 ? VR_DVR_MIN_BLOCKS : 1)
+                     : (VR_MIP_MIN_BLOCKS > 0 ? VR_MIP_MIN_BLOCKS : 1);
+}
+
 template <int S, int MODE, int F, bool MASK>
-__global__ void VR_RAYCAST_BOUNDS
+__global__ void __launch_bounds__(256, rc_min_blocks<MODE, F>())
 k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const void *__restrict__ pool, void *__restrict__ frags,
           Counters *__restrict__ ctr) {
