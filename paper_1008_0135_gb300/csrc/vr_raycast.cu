@@ -34,6 +34,15 @@
 #ifndef VR_RAYMARCH_MIN_BLOCKS
 #define VR_RAYMARCH_MIN_BLOCKS 5
 #endif
+#ifndef VR_ADJ_COPIES
+#define VR_ADJ_COPIES 8
+#endif
+#ifndef VR_ADJ_SMEM_KB
+#define VR_ADJ_SMEM_KB 64
+#endif
+#ifndef VR_ADJ_MIN_BLOCKS
+#define VR_ADJ_MIN_BLOCKS 4
+#endif
 constexpr int kSampleUnroll = VR_SAMPLE_UNROLL;
 
 namespace vr {
@@ -756,15 +765,47 @@ k_composite_backward(const FrameConsts fc, const DrawBrick *__restrict__ dbs,
     }
 }
 
+// A ray's cell accumulator after one step along axis SH (up: +1): the corners of the face both
+// cells share move to their place in the new cell, the new far face starts empty.
+template <int SH>
+__device__ __forceinline__ void shift_face(float acc[8], bool up) {
+    float nacc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const bool hi = (c >> SH) & 1;
+        nacc[c] = up ? (hi ? 0.0f : acc[c ^ (1 << SH)]) : (hi ? acc[c ^ (1 << SH)] : 0.0f);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = nacc[c];
+}
+
+// Adds a ray's accumulated voxel gradients of cell (cx, cy, cz) (corner c = x + 2y + 4z) for
+// the corners in `mask` to the cube's gradient (ghost copies map back to their source voxel).
+__device__ __forceinline__ void flush_voxel_grads(float *__restrict__ gvox, const float acc[8], unsigned mask,
+                                                  int cx, int cy, int cz, const DrawBrick &b,
+                                                  const FrameConsts &fc) {
+    const int gx[2] = {clampi(b.org[0] + cx, 0, fc.nx - 1), clampi(b.org[0] + cx + 1, 0, fc.nx - 1)};
+    const int gy[2] = {clampi(b.org[1] + cy, 0, fc.ny - 1), clampi(b.org[1] + cy + 1, 0, fc.ny - 1)};
+    const int gz[2] = {clampi(b.org[2] + cz, 0, fc.nz - 1), clampi(b.org[2] + cz + 1, 0, fc.nz - 1)};
+    const long long sy = fc.nx, sz = (long long)fc.nx * fc.ny;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (((mask >> c) & 1u) && acc[c] != 0.0f)
+            atomicAdd(gvox + gz[c >> 2] * sz + gy[(c >> 1) & 1] * sy + gx[c & 1], acc[c]);
+}
+
 // Adjoint ray cast (FP32 bricks).  Each (brick, pixel) segment is replayed front to back with
 // the forward's arithmetic; from the stored segment colour C_b and transmittance T_b the
 // gradient of every sample follows without per-sample storage:
 //   dL/dc_j = gC T_{j-1} a_j
 //   dL/da_j = T_{j-1} [ gC.c_j - (gC.(C_b - C_{<=j}) + gT T_b) / T_j ]   (T_j = T_{j-1}(1-a_j))
 //   last composited sample: dL/da_j = T_{j-1} [ gC.c_j - gT ]
-// Table gradients accumulate per CTA in shared memory and are written as one partial per CTA;
-// voxel gradients scatter to the cube's voxels (ghost copies map back to their source voxel).
-__global__ void __launch_bounds__(256)
+// Table gradients accumulate per CTA in shared memory and are written as one partial per CTA.
+// Voxel gradients accumulate per ray for the 8 corners of its current cell and are added to the
+// cube's voxels when the ray leaves the cell (ghost copies map back to their source voxel); a
+// step into an adjacent cell keeps the shared face's 4 sums (before: 8 atomics per sample).
+// Bounded to 4 CTAs per SM (64 registers, a few spilled; 80 unbounded give 3 CTAs, 8 % slower).
+__global__ void __launch_bounds__(256, VR_ADJ_MIN_BLOCKS)
 k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const float *__restrict__ pool,
           const float4 *__restrict__ frags, const float4 *__restrict__ gfrag,
@@ -772,8 +813,11 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
     extern __shared__ float4 s_lut[];
     // ncopies (1, 2, 4 or 8) table-gradient accumulators, lane l adding into copy l mod ncopies:
     // neighbouring rays mostly hit the same entries, and same-address shared atomics of one
-    // warp serialise; copies sit 8 floats apart in bank position
-    const int gstride = 4 * fc.nlut + 8;
+    // warp serialise.  A copy holds one row per channel with the entries consecutive, so the
+    // lanes' different entries spread over all 32 banks (entry-major rows put channel c of
+    // every entry in one of 8 banks: the table-gradient pass 1.3 x slower)
+    const int cs = fc.nlut + 2;              // one row per channel: entries along the banks
+    const int gstride = 4 * cs + 8;
     float *s_g0 = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);
     load_table(lut, fc.nlut, s_lut);
     for (int i = threadIdx.x; i < ncopies * gstride; i += blockDim.x) s_g0[i] = 0.0f;
@@ -803,6 +847,9 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
             const int n = k1 - k0;
             const float dxdv = __fmul_rn(fc.lutmax, fc.inv_range);
             float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+            // voxel gradients of the ray's current cell, added to the cube when the ray leaves it
+            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            int ccx = -4, ccy = -4, ccz = -4;
             for (int j = 0; j < n; ++j) {
                 const float tj = __fmul_rn((float)j, fc.step);
                 DvrSample sm;
@@ -823,45 +870,59 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                 }
                 const float wa = Tb * sm.a;
                 const float gr = gf.x * wa, gg = gf.y * wa, gb = gf.z * wa;
-                float *g0 = s_g + 4 * sm.li;
                 const float w1 = sm.lf, w0 = 1.0f - sm.lf;
-                atomicAdd(g0 + 0, w0 * gr); atomicAdd(g0 + 4, w1 * gr);
-                atomicAdd(g0 + 1, w0 * gg); atomicAdd(g0 + 5, w1 * gg);
-                atomicAdd(g0 + 2, w0 * gb); atomicAdd(g0 + 6, w1 * gb);
-                atomicAdd(g0 + 3, w0 * ga); atomicAdd(g0 + 7, w1 * ga);
+                float *g0 = s_g + sm.li;
+                atomicAdd(g0, w0 * gr); atomicAdd(g0 + 1, w1 * gr);
+                atomicAdd(g0 + cs, w0 * gg); atomicAdd(g0 + cs + 1, w1 * gg);
+                atomicAdd(g0 + 2 * cs, w0 * gb); atomicAdd(g0 + 2 * cs + 1, w1 * gb);
+                atomicAdd(g0 + 3 * cs, w0 * ga); atomicAdd(g0 + 3 * cs + 1, w1 * ga);
                 if (gvox != nullptr && sm.u > 0.0f && sm.u < 1.0f) {
                     const float gx = gr * sm.D.x + gg * sm.D.y + gb * sm.D.z + ga * sm.D.w;
                     const float gv = gx * dxdv;
                     if (gv != 0.0f) {
                         const int ix = sm.ix, iy = sm.iy, iz = sm.iz;
-                        const int gx0 = clampi(b.org[0] + ix, 0, fc.nx - 1), gx1 = clampi(b.org[0] + ix + 1, 0, fc.nx - 1);
-                        const int gy0 = clampi(b.org[1] + iy, 0, fc.ny - 1), gy1 = clampi(b.org[1] + iy + 1, 0, fc.ny - 1);
+                        if (ix != ccx || iy != ccy || iz != ccz) {
+                            const int ddx = ix - ccx, ddy = iy - ccy, ddz = iz - ccz;
+                            const int ax = (ddx != 0) + (ddy != 0) + (ddz != 0);
+                            if (ax == 1 && ddx >= -1 && ddx <= 1 && ddy >= -1 && ddy <= 1 &&
+                                ddz >= -1 && ddz <= 1) {
+                                // one step along one axis: the face both cells share keeps accumulating
+                                const int sh = ddx != 0 ? 0 : (ddy != 0 ? 1 : 2);
+                                const int up = (ddx + ddy + ddz) > 0;
+                                const unsigned lowf = sh == 0 ? 0x55u : (sh == 1 ? 0x33u : 0x0Fu);
+                                flush_voxel_grads(gvox, acc, up ? lowf : (~lowf & 0xffu), ccx, ccy, ccz, b, fc);
+                                if (sh == 0) shift_face<0>(acc, up);
+                                else if (sh == 1) shift_face<1>(acc, up);
+                                else shift_face<2>(acc, up);
+                            } else {
+                                flush_voxel_grads(gvox, acc, 0xffu, ccx, ccy, ccz, b, fc);
+#pragma unroll
+                                for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+                            }
+                            ccx = ix; ccy = iy; ccz = iz;
+                        }
                         const int gz0 = clampi(b.org[2] + iz, 0, fc.nz - 1), gz1 = clampi(b.org[2] + iz + 1, 0, fc.nz - 1);
-                        const long long sy = fc.nx, sz = (long long)fc.nx * fc.ny;
                         const float ux = sm.fx, uy = sm.fy;
                         const float vx = 1.0f - ux, vy = 1.0f - uy;
-                        // a disabled channel's voxels do not reach the image: no gradient
                         const float uz = (fc.chmask && !fc.chmask[gz1]) ? 0.0f : sm.fz;
                         const float vz = (fc.chmask && !fc.chmask[gz0]) ? 0.0f : 1.0f - sm.fz;
-                        atomicAdd(gvox + gz0 * sz + gy0 * sy + gx0, gv * vx * vy * vz);
-                        atomicAdd(gvox + gz0 * sz + gy0 * sy + gx1, gv * ux * vy * vz);
-                        atomicAdd(gvox + gz0 * sz + gy1 * sy + gx0, gv * vx * uy * vz);
-                        atomicAdd(gvox + gz0 * sz + gy1 * sy + gx1, gv * ux * uy * vz);
-                        atomicAdd(gvox + gz1 * sz + gy0 * sy + gx0, gv * vx * vy * uz);
-                        atomicAdd(gvox + gz1 * sz + gy0 * sy + gx1, gv * ux * vy * uz);
-                        atomicAdd(gvox + gz1 * sz + gy1 * sy + gx0, gv * vx * uy * uz);
-                        atomicAdd(gvox + gz1 * sz + gy1 * sy + gx1, gv * ux * uy * uz);
+                        acc[0] += gv * vx * vy * vz; acc[1] += gv * ux * vy * vz;
+                        acc[2] += gv * vx * uy * vz; acc[3] += gv * ux * uy * vz;
+                        acc[4] += gv * vx * vy * uz; acc[5] += gv * ux * vy * uz;
+                        acc[6] += gv * vx * uy * uz; acc[7] += gv * ux * uy * uz;
                     }
                 }
                 if (T <= fc.thr) break;
             }
+            if (gvox != nullptr && ccx != -4) flush_voxel_grads(gvox, acc, 0xffu, ccx, ccy, ccz, b, fc);
         }
     }
     __syncthreads();
     float *dst = glut_partial + (long long)blockIdx.x * 4 * fc.nlut;
     for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) {
-        float v = s_g0[i];
-        for (int c = 1; c < ncopies; ++c) v += s_g0[c * gstride + i];
+        const int at = (i & 3) * cs + (i >> 2);   // entry i / 4, channel i % 4
+        float v = s_g0[at];
+        for (int c = 1; c < ncopies; ++c) v += s_g0[c * gstride + at];
         dst[i] = v;
     }
 }
@@ -1012,15 +1073,16 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     static std::atomic<bool> attr{false};
     if (!attr.load(std::memory_order_acquire)) {
         cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(48 * kMaxLut + 32));
+                                             (int)(48 * kMaxLut + 64));
         if (e != cudaSuccess) return e;
         attr.store(true, std::memory_order_release);
     }
     // table + differences (32 B per entry) + gradient accumulators (16 B per entry and copy): as
     // many copies (up to 8) as keep the block within 64 KB
-    int ncopies = 8;
-    while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * (16 * (size_t)fc.nlut + 32) > (64u << 10)) ncopies >>= 1;
-    const size_t smem = 32 * (size_t)fc.nlut + ncopies * (16 * (size_t)fc.nlut + 32);
+    int ncopies = VR_ADJ_COPIES;
+    const size_t per_copy = 16 * (size_t)fc.nlut + 64;
+    while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * per_copy > ((size_t)VR_ADJ_SMEM_KB << 10)) ncopies >>= 1;
+    const size_t smem = 32 * (size_t)fc.nlut + ncopies * per_copy;
     k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
     return cudaGetLastError();
 }
