@@ -244,10 +244,22 @@ int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold)
  * Errors: VR_ERR_ARG. */
 int vr_set_termination(vr_ctx *ctx, int mode);
 
+/* Host output mode of vr_render_frame with VR_HOST.  async = 0
+ * (the default): the call returns after the frame has been copied into `out`.  async = 1: it
+ * returns once the copy into `out` is queued on `cuda_stream`, so that the caller can prepare
+ * and queue the next frame while this one renders (an interactive viewer shows frame k - 1
+ * while frame k is drawn); the caller synchronises the stream, or an event recorded on it
+ * after the call, before it reads `out`, and keeps `out` alive and unchanged until then.  The
+ * copy overlaps the host only if `out` is page-locked (e.g. cudaMallocHost); a pageable `out`
+ * makes the copy synchronous, as with async = 0.  Frames still run one after another on the
+ * stream, and the library's own scratch is reused safely.  Errors: VR_ERR_ARG. */
+int vr_set_host_output_async(vr_ctx *ctx, int async);
+
 /* Renders one frame of cube `cube_id` with the current table, camera and parameters.
  * out: W*H*4 floats (DVR) or W*H floats (MIP) in host (VR_HOST) or device (VR_DEVICE) memory.
  * With VR_DEVICE the call returns once the work is queued on `cuda_stream`; with VR_HOST it
- * returns after the frame has been copied into `out`.
+ * returns after the frame has been copied into `out` (or once that copy is queued, see
+ * vr_set_host_output_async).
  * Steps: per-brick rendering rectangles and culling (host), one ray-cast launch over all
  * (brick, 16x16 pixel tile) work items writing one premultiplied fragment per brick and pixel,
  * one compositing launch blending each pixel's fragments front to back (Section 2.5).

@@ -217,6 +217,13 @@ class Context:
         _check(self._L.vr_set_termination(self._h, {"segment": 0, "global": 1}[scope]),
                "vr_set_termination")
 
+    def set_host_output_async(self, flag: bool = True):
+        """With a host ``out``, render_frame returns once the copy into it is queued on the
+        stream (read ``out`` after synchronising that stream or an event recorded after the
+        call); False restores the synchronous copy."""
+        _check(self._L.vr_set_host_output_async(self._h, 1 if flag else 0),
+               "vr_set_host_output_async")
+
     def set_channel_mask(self, mask=None):
         """0/1 per spectral channel (cube z); None switches every channel on."""
         if mask is None:

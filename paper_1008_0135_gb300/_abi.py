@@ -67,6 +67,7 @@ SIGNATURES = {
     "vr_set_camera": (I, [VP, VP, I, F, I, I]),
     "vr_set_render_params": (I, [VP, I, F, F]),
     "vr_set_termination": (I, [VP, I]),
+    "vr_set_host_output_async": (I, [VP, I]),
     "vr_compress_cube": (I, [VP, I]),
     "vr_wavelet_store": (I, [VP, I, VP, P(C.c_size_t)]),
     "vr_render_frame": (I, [VP, I, VP, I, VP]),

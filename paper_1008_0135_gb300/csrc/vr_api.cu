@@ -1063,6 +1063,13 @@ int vr_set_termination(vr_ctx *c, int mode) {
     return VR_OK;
 }
 
+int vr_set_host_output_async(vr_ctx *c, int async) {
+    if (!c) return arg_fail("null ctx");
+    if (async != 0 && async != 1) return arg_fail("async must be 0 or 1");
+    c->async_host_out = async != 0;
+    return VR_OK;
+}
+
 int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);

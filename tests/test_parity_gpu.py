@@ -558,3 +558,42 @@ def test_global_termination_refusals(ctx):
         ctx.set_termination("segment")
         ctx.free_cube(cid)
         ctx.free_cube(vid)
+
+
+# ---------------------------------------------------------------------------------------------
+# asynchronous host output (a viewer queues frame k while it reads frame k - 1)
+# ---------------------------------------------------------------------------------------------
+def test_async_host_output_pipelined_frames(ctx, pr1):
+    import torch
+    _, cid = pr1
+    lut = synth.ramp_lut()
+    ctx.set_transfer_function(lut, -3.0, 20.0)
+    ctx.set_render_params("dvr", 0.5, 0.99)
+    cams = [synth.pr1_camera(W=64 + 8 * k, H=48 + 4 * k) for k in range(4)]
+    want = []
+    for cam in cams:                                   # synchronous copies: the reference
+        ctx.set_camera_dict(cam)
+        h = np.empty((cam["H"], cam["W"], 4), np.float32)
+        ctx.render_frame(cid, h)
+        want.append(h)
+    bufs = [torch.full((c["H"], c["W"], 4), -1.0, dtype=torch.float32).pin_memory() for c in cams]
+    ev = [torch.cuda.Event() for _ in cams]
+    ctx.set_host_output_async(True)
+    try:
+        for k, cam in enumerate(cams):
+            ctx.set_camera_dict(cam)
+            ctx.render_frame(cid, bufs[k])                 # queued on the default stream
+            ev[k].record()
+            if k > 0:                                      # frame k - 1 is read while k renders
+                ev[k - 1].synchronize()
+                assert np.array_equal(bufs[k - 1].numpy(), want[k - 1])
+        ev[-1].synchronize()
+        assert np.array_equal(bufs[-1].numpy(), want[-1])
+    finally:
+        ctx.set_host_output_async(False)
+    assert _abi_status(ctx, 2) == -1
+
+
+def _abi_status(ctx, flag):
+    from paper_1008_0135_gb300 import _abi
+    return _abi.lib().vr_set_host_output_async(ctx._h, flag)
