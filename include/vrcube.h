@@ -199,10 +199,14 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * by two texture gathers (exact texels; images identical to the linear copies).  When atlases
  * are kept every DVR and MIP frame reads them; the adjoint reads a linear copy.  An atlas must
  * fit the device's 2D-gather size (32768 texels a side; 258^3 stored bricks need 8256 x 2322).
- * A bricked cube is rebuilt.  Streamed cubes keep the x-contiguous copy only.
+ * A bricked cube is rebuilt.  Streamed and compressed cubes (bricks made resident in the brick
+ * cache) take mask 1 or 9: with 9, each cache slot holding one of the cube's bricks also holds
+ * its slice atlas (a 2D array sized for the cube's largest brick, packed from the slot on the
+ * cache's stream when the brick becomes resident: as much device memory again as the slots
+ * in use, outside cache_bytes; an allocation failure fails the frame with VR_ERR_OOM).
  * Mask 1..15 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
- * (streamed cube with mask != 1; atlas beyond the gather size, raised by the rebuild),
- * VR_ERR_OOM, VR_ERR_CUDA. */
+ * (streamed or compressed cube with a mask other than 1 or 9; atlas beyond the gather size,
+ * raised by the rebuild, or for streamed cubes by the frame), VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_brick_layouts(vr_ctx *ctx, int cube_id, int mask);
 
 /* Transfer function (Section 2: value -> colour and opacity; Section 2.3: colour map sent by

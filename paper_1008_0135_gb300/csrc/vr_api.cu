@@ -42,7 +42,9 @@ void layout_strides(const int dim[3], int layout, int str[3]) {
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
     FrameLayout f{0, 0, kRcLong, kRcShort, 0.0f, 0};
     float best = -1.0f;
-    const bool atlas = !cb->streamed && !cb->atlas_tex.empty();
+    // resident cubes: atlases built with the pool; streamed and compressed cubes: atlases of the
+    // brick cache's slots, packed as bricks become resident
+    const bool atlas = cb->streamed ? (cb->layouts & 8) != 0 : !cb->atlas_tex.empty();
     // with atlases, the image axis is fixed first: the one with the smaller z component
     const int only = atlas ? (std::fabs(c->cam.R[5]) < std::fabs(c->cam.R[2]) ? 1 : 0) : -1;
     for (int i = 0; i < 2; ++i)              // image axis: camera right (row 0), up (row 1)
@@ -1076,7 +1078,8 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!cb) return VR_ERR_NOT_FOUND;
     if (mask < 1 || mask > 15 || !(mask & 1))
         return arg_fail("layout mask must be 1..15 and keep bit 0 (x contiguous)");
-    if (cb->streamed && mask != 1) return fail(VR_ERR_UNSUPPORTED, "streamed bricks are stored x-contiguous only");
+    if (cb->streamed && mask != 1 && mask != 9)
+        return fail(VR_ERR_UNSUPPORTED, "streamed bricks are cached x-contiguous, with or without slot atlases (mask 1 or 9)");
     if (cb->layouts == mask) return VR_OK;
     cb->layouts = mask;
     if (!cb->bricked || cb->streamed) return VR_OK;

@@ -239,6 +239,12 @@ struct Slot {
     cudaEvent_t last_use = nullptr;   // completes after every ray-cast that read the slot so far
     bool used = false;
     int held = 0;                     // in-flight serving frames that need this brick
+    // slice atlas of the slot (cubes whose layout mask asks for atlases): a 2D array sized for
+    // the largest brick of its storage kind, created on first use
+    cudaArray_t arr = nullptr;
+    cudaTextureObject_t tex = 0;
+    int arr_storage = -1, arr_w = 0, arr_h = 0, alog = 0;
+    bool atlas_ok = false;            // the atlas holds this slot's brick
 };
 
 struct Staging {
@@ -260,6 +266,8 @@ struct BrickCache {
     std::vector<Staging> stage;
     size_t stage_next = 0;
     Workers *workers = nullptr;
+    void *pack_tmp = nullptr;         // pitched staging of atlas packs (on the copy stream)
+    size_t pack_bytes = 0;
     int64_t hits = 0, misses = 0, bytes = 0, generated = 0;
     std::recursive_mutex mu;          // frames of the serving loop make bricks resident from
                                       // their own host threads
@@ -284,12 +292,16 @@ void cache_destroy(vr_ctx *c) {
     if (!k) return;
     if (k->copy) cudaStreamSynchronize(k->copy);
     delete k->workers;
-    for (auto &s : k->slots)
+    for (auto &s : k->slots) {
         if (s.last_use) cudaEventDestroy(s.last_use);
+        if (s.tex) cudaDestroyTextureObject(s.tex);
+        if (s.arr) cudaFreeArray(s.arr);
+    }
     for (auto &s : k->stage) {
         if (s.host) cudaFreeHost(s.host);
         if (s.done) cudaEventDestroy(s.done);
     }
+    if (k->pack_tmp) cudaFree(k->pack_tmp);
     if (k->d_base) cudaFree(k->d_base);
     if (k->copies_done) cudaEventDestroy(k->copies_done);
     if (k->copy) cudaStreamDestroy(k->copy);
@@ -377,6 +389,8 @@ static int cache_size(vr_ctx *c, size_t slot_bytes) {
         for (auto &s : k->slots) {
             if (s.used) CK(cudaEventSynchronize(s.last_use));
             cudaEventDestroy(s.last_use);
+            if (s.tex) cudaDestroyTextureObject(s.tex);
+            if (s.arr) cudaFreeArray(s.arr);
         }
         for (auto &s : k->stage) {
             if (s.pending) CK(cudaEventSynchronize(s.done));
@@ -440,6 +454,86 @@ static void produce_brick(vr_ctx *c, Cube *cb, const DrawBrick &b, void *dst, in
     (void)c;
 }
 
+// Slice atlases of cache slots (streamed and compressed cubes whose layout mask has bit 3):
+// every brick of a cube uses the tile layout of the cube's largest stored brick (2^alog
+// z-slices per atlas row), so any of its bricks fits a slot's array.
+struct SlotAtlasGeom {
+    int w = 0, h = 0, alog = 0;
+};
+
+static int slot_atlas_geom(vr_ctx *c, Cube *cb, SlotAtlasGeom &g) {
+    int mx[3] = {0, 0, 0};
+    for (auto &b : cb->tmpl)
+        for (int a = 0; a < 3; ++a) mx[a] = std::max(mx[a], b.dim[a]);
+    int l = 0;
+    while ((1ll << (2 * l)) < mx[2]) ++l;
+    const long long w = (long long)mx[0] << l, h = (long long)((mx[2] + (1 << l) - 1) >> l) * mx[1];
+    int gw = 0, gh = 0;
+    CK(cudaDeviceGetAttribute(&gw, cudaDevAttrMaxTexture2DGatherWidth, c->device));
+    CK(cudaDeviceGetAttribute(&gh, cudaDevAttrMaxTexture2DGatherHeight, c->device));
+    if (w > gw || h > gh) return fail(VR_ERR_UNSUPPORTED, "bricks too large for a slice atlas (2D gather limit)");
+    g.w = (int)w;
+    g.h = (int)h;
+    g.alog = l;
+    return VR_OK;
+}
+
+// Packs slot `si`'s brick `b` (already queued into the slot on the copy stream) into the slot's
+// atlas on the copy stream, creating or replacing the array first when it has another texel
+// type or is too small (after every reader and pending copy of the old one).
+static int slot_atlas_pack(vr_ctx *c, Cube *cb, int si, const DrawBrick &b, const SlotAtlasGeom &g) {
+    BrickCache *k = c->cache;
+    Slot &s = k->slots[si];
+    const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+    if (!s.arr || s.arr_storage != cb->storage || s.arr_w < g.w || s.arr_h < g.h) {
+        if (s.arr) {
+            if (s.used) CK(cudaEventSynchronize(s.last_use));
+            CK(cudaStreamSynchronize(k->copy));
+            cudaDestroyTextureObject(s.tex);
+            cudaFreeArray(s.arr);
+            s.tex = 0;
+            s.arr = nullptr;
+        }
+        const cudaChannelFormatDesc cd =
+            esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
+            : cb->storage == VR_F16 ? cudaCreateChannelDescHalf()
+                                    : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
+        if (cudaMallocArray(&s.arr, &cd, (size_t)g.w, (size_t)g.h, cudaArrayTextureGather) != cudaSuccess) {
+            s.arr = nullptr;
+            cudaGetLastError();
+            return fail(VR_ERR_OOM, "slice atlas of a cache slot: cudaMallocArray failed");
+        }
+        cudaResourceDesc rd{};
+        rd.resType = cudaResourceTypeArray;
+        rd.res.array.array = s.arr;
+        cudaTextureDesc td{};
+        td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        CK(cudaCreateTextureObject(&s.tex, &rd, &td, nullptr));
+        s.arr_storage = cb->storage;
+        s.arr_w = g.w;
+        s.arr_h = g.h;
+    }
+    const size_t need = (size_t)g.w * g.h * esz;
+    if (k->pack_bytes < need) {
+        CK(cudaStreamSynchronize(k->copy));
+        if (k->pack_tmp) cudaFree(k->pack_tmp);
+        k->pack_tmp = nullptr;
+        k->pack_bytes = 0;
+        CK(cudaMalloc(&k->pack_tmp, need));
+        k->pack_bytes = need;
+    }
+    const size_t w = (size_t)b.dim[0] << g.alog, h = (size_t)((b.dim[2] + (1 << g.alog) - 1) >> g.alog) * b.dim[1];
+    CK(launch_atlas_pack(k->d_base + (size_t)si * k->slot_bytes, (int)esz, b.dim[0], b.dim[1], b.dim[2], g.alog,
+                         k->pack_tmp, w * esz, k->copy));
+    CK(cudaMemcpy2DToArrayAsync(s.arr, 0, 0, k->pack_tmp, w * esz, w * esz, h, cudaMemcpyDeviceToDevice, k->copy));
+    s.alog = g.alog;
+    s.atlas_ok = true;
+    return VR_OK;
+}
+
 // Makes the bricks of wl.db[d0, d1) resident: hits keep their slot, misses get the least
 // recently used slot not needed by this chunk, are produced on the workers and copied on the
 // cache's stream after the slot's previous reader finished.  Fills data_off / exp2.
@@ -447,6 +541,10 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
                          int64_t chunk) {
     BrickCache *k = c->cache;
     const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+    const bool atlas = (cb->layouts & 8) != 0;
+    SlotAtlasGeom g;
+    int rc = VR_OK;
+    if (atlas && (rc = slot_atlas_geom(c, cb, g)) != VR_OK) return rc;
     std::vector<std::pair<size_t, int>> misses;   // (db index, slot)
     for (size_t i = d0; i < d1; ++i) {
         auto it = k->where.find(key_of(cb->id, db[i].brick));
@@ -456,6 +554,12 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
             s.chunk = chunk;
             db[i].data_off = (long long)((size_t)it->second * k->slot_bytes / esz);
             db[i].exp2 = s.exp2;
+            db[i].atlas = 0ull;
+            if (atlas) {
+                if (!s.atlas_ok && (rc = slot_atlas_pack(c, cb, it->second, db[i], g)) != VR_OK) return rc;
+                db[i].atlas = s.tex;
+                db[i].alog = s.alog;
+            }
             k->hits++;
         } else {
             misses.push_back({i, -1});
@@ -479,6 +583,7 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         Slot &s = k->slots[si];
         if (s.cube >= 0) k->where.erase(key_of(s.cube, s.brick));
         s.cube = -1;                  // not valid until its copy is issued
+        s.atlas_ok = false;
         s.brick = db[misses[m].first].brick;
         s.chunk = chunk;
         s.lru = ++k->tick;
@@ -499,8 +604,20 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
             k->where[key_of(cb->id, s.brick)] = mi.second;
             db[mi.first].data_off = (long long)((size_t)mi.second * k->slot_bytes / esz);
             db[mi.first].exp2 = 0;
+            db[mi.first].atlas = 0ull;
             k->misses++;
             k->bytes += b.bytes;
+            if (atlas) {
+                if ((rc = slot_atlas_pack(c, cb, mi.second, b, g)) != VR_OK) {
+                    k->where.erase(key_of(cb->id, s.brick));
+                    s.cube = -1;
+                    s.brick = -1;
+                    s.chunk = -1;
+                    return rc;
+                }
+                db[mi.first].atlas = s.tex;
+                db[mi.first].alog = s.alog;
+            }
         }
         return VR_OK;
     }
@@ -511,7 +628,6 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
     std::vector<size_t> st_of(misses.size());
     std::vector<std::string> errors(misses.size());
     size_t submitted = 0, issued = 0;
-    int rc = VR_OK;
     auto submit = [&](size_t m) -> int {
         const size_t si = (k->stage_next++) % nstage;
         Staging &sg = k->stage[si];
@@ -565,9 +681,21 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         k->where[key_of(cb->id, s.brick)] = si;
         db[misses[m].first].data_off = (long long)((size_t)si * k->slot_bytes / esz);
         db[misses[m].first].exp2 = exps[m];
+        db[misses[m].first].atlas = 0ull;
         k->misses++;
         k->bytes += b.bytes;
         ++issued;
+        if (atlas) {
+            if ((rc = slot_atlas_pack(c, cb, si, b, g)) != VR_OK) {
+                k->where.erase(key_of(cb->id, s.brick));
+                s.cube = -1;
+                s.brick = -1;
+                s.chunk = -1;
+                break;
+            }
+            db[misses[m].first].atlas = s.tex;
+            db[misses[m].first].alog = s.alog;
+        }
     }
     if (rc != VR_OK) {
         // let submitted producers finish (they write into staging we own), drop unfilled slots

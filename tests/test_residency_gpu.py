@@ -184,3 +184,30 @@ def test_fault_injection_leaves_the_context_usable(big_ctx):
             render(slow, sid, lut, (-3, 20), _cam(SMALL, W=200, H=200, seed=2), step=0.5)
         assert e.value.status == -4                                # VR_ERR_TIMEOUT
     ctx.free_cube(cid)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode", ["dvr", "mip"])
+def test_slot_atlases_give_identical_images(storage, mode):
+    """Mask 9 on a streamed cube: cache slots also hold slice atlases, read by texture gathers;
+    the image equals the one read from the slots' linear bricks, bit for bit, for a frame that
+    fits the cache and for one chunked through a cache of 5 slots (evictions re-pack atlases)."""
+    import paper_1008_0135_gb300 as P
+    lut = synth.ramp_lut(alpha=0.3)
+    cam = dict(view=synth.look_at((150.0, 135.0, -300.0), (150.0, 135.0, 130.0)), proj=1,
+               param=math.radians(70.0), W=120, H=100)
+    esz = 4 if storage == "f32" else 2
+    for slots in (64, 5):
+        with P.Context(0, cache_bytes=slots * 130 ** 3 * esz) as ctx:
+            cid = ctx.load_cube_procedural(SEED, SMALL)
+            ctx.set_bricking(cid, BRICK, 1, storage)
+            lin = render(ctx, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            ctx.set_brick_layouts(cid, 9)
+            at1 = render(ctx, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)   # packs hits
+            at2 = render(ctx, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            ctx.set_brick_layouts(cid, 1)
+            lin2 = render(ctx, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            assert np.array_equal(lin, at1) and np.array_equal(lin, at2) and np.array_equal(lin, lin2)
+            assert np.count_nonzero(lin) > 0
+            with pytest.raises(P.VrError):
+                ctx.set_brick_layouts(cid, 15)

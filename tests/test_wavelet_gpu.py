@@ -136,3 +136,26 @@ def test_compressed_cube_refusals(ctx):
     assert e.value.status == -5
     for i in (cid, vid, other):
         ctx.free_cube(i)
+
+
+def test_compressed_frames_with_slot_atlases(orc):
+    """Mask 9 on a compressed cube: decoded bricks are also packed into the cache slots' slice
+    atlases; frames (fitting the cache, and chunked through 4 slots) equal the linear slots'."""
+    cube = synth.pr1_cube(seed=4, n=48)
+    lut = synth.ramp_lut(alpha=0.4)
+    cam = synth.pr1_camera(n=48, W=64, H=64)
+    for cache in (64 * 18 ** 3 * 4, 4 * 18 ** 3 * 4 + 1024):
+        c = _ctx(cache)
+        try:
+            cid = c.load_cube(cube)
+            c.set_bricking(cid, (16, 16, 16), 1, "f32")
+            c.compress_cube(cid)
+            for mode in ["dvr", "mip"]:
+                c.set_brick_layouts(cid, 1)
+                lin = render(c, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+                c.set_brick_layouts(cid, 9)
+                at = render(c, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+                again = render(c, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+                assert np.array_equal(lin, at) and np.array_equal(lin, again)
+        finally:
+            c.close()
