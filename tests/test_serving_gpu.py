@@ -114,3 +114,27 @@ def test_pinned_host_outputs_and_errors(world):
             continue
         assert res["status"] == 0
         assert torch.equal(r["out"].cuda(), _alone(ctx, r))
+
+
+def test_slot_atlases_in_the_mix(world):
+    """The streamed cube with slice atlases in its cache slots (mask 9): frames of the mix pack
+    and gather slot atlases on several streams at once (24 slots for 27 bricks: evictions and
+    re-packs during the run); each result equals the frame alone, and the frame from the linear
+    slots."""
+    import torch
+    ctx, cubes = world
+    v = cubes["proc"][0]
+    ctx.set_brick_layouts(v, 9)
+    try:
+        reqs = _requests({"proc": cubes["proc"], "pr1": cubes["pr1"]}, 32, 400.0, 21, "cuda")
+        results, summary = ctx.serve(reqs, max_inflight=6)
+        torch.cuda.synchronize()
+        assert all(r["status"] == 0 for r in results), results
+        for r in reqs:
+            _same(r, _alone(ctx, r))
+        ctx.set_brick_layouts(v, 1)
+        for r in reqs:
+            if r["cube"] == v:
+                _same(r, _alone(ctx, r))
+    finally:
+        ctx.set_brick_layouts(v, 1)
