@@ -601,7 +601,7 @@ def run_reference(args, dist):
     del cube
     lut = synth.ramp_lut()
     cams = cameras(cfg, cfg.get("n_views", 64))
-    rays = 2048
+    rays = 16384                       # per step: large enough that the call's fixed cost is small
     total, t_all = 0, 0.0
     for k in range(args.warmup + args.steps):
         cam = cams[k % len(cams)]
