@@ -6,7 +6,7 @@ GASS-scale:   2048x2048x1600 (26.8 GB), 256^3 bricks, 1024^2 perspective orbit, 
 Both keep the bench's brick layouts (slice atlases + the x-contiguous copy), so every frame
 here gathers from the atlases as the timed frames do; HIPASS also checks global termination
 with the occlusion leg's opaque table.
-The measured maximum errors are written to gpurun_out/large_errors.json when that folder exists.
+The measured maximum errors are written as JSON to the file named by VR_LARGE_ERRORS, if set.
 """
 import json
 import os
@@ -23,9 +23,9 @@ RESULTS = {}
 
 def _record(key, val):
     RESULTS[key] = val
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if os.path.isdir(d):
-        with open(os.path.join(d, "large_errors.json"), "w") as f:
+    path = os.environ.get("VR_LARGE_ERRORS")
+    if path:
+        with open(path, "w") as f:
             json.dump(RESULTS, f, indent=1)
 
 
