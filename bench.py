@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "hipass_slab", "gass", "pr1"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="brick storage of the main leg (the headline line uses f32)")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
     ap.add_argument("--leg", default=None, choices=["adjoint"],
                     help="run one extra leg alone and print its JSON (for profiling)")
@@ -500,7 +502,7 @@ def run_ours(args, dist):
     del cube
     torch.cuda.empty_cache()
     ctx.set_brick_layouts(cid, 9)          # slice atlases (gathers) + the x-contiguous copy
-    ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+    ctx.set_bricking(cid, cfg["brick"], 1, args.storage)
     out = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     peak, psrc = peaks()
     clocks = Clocks(dev)
@@ -509,14 +511,14 @@ def run_ours(args, dist):
     t_max = dist.max(ms)
     samples_all = dist.sum(st["samples"])
     value = samples_all / (t_max * 1e-3) / 1e9
-    rl = roofline(st, args.steps, peak, psrc, "k_raycast<f32,DVR>")
+    rl = roofline(st, args.steps, peak, psrc, f"k_raycast<{args.storage},DVR>")
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gsamples/s", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded stand-in for the HIPASS cube; no dataset available)",
         "config": {"workload": cfg["name"] + f", {W}x{H} perspective 64-view orbit, step "
-                   f"{cfg['step']}, 256^3 bricks + ghost 1, FP32 bricks, ERT 0.99",
+                   f"{cfg['step']}, 256^3 bricks + ghost 1, {args.storage.upper()} bricks, ERT 0.99",
                    "cube_xyz": [nx, ny, nz], "frame": [W, H], "bricks": list(cfg["brick"]),
                    "l2": f"inputs larger than L2 ({4 * nx * ny * nz / 1e9:.1f} GB cube); no flush",
                    "brick_layouts": "slice-atlas textures (2 gathers per sample) + x-contiguous copy",
