@@ -210,7 +210,7 @@ __device__ __forceinline__ void interp_tf(const float v[8], const Cell &c, bool 
     float val = __fmaf_rn(c.fz, __fsub_rn(b1, b0), b0);
     if (scaled) val = __fmul_rn(val, scale);
     o.u = __fmul_rn(__fsub_rn(val, vmin), inv_range);
-    const float uc = fminf(fmaxf(o.u, 0.0f), 1.0f);
+    const float uc = __saturatef(o.u);          // clamp to [0, 1] (one instruction)
     const float xl = __fmul_rn(uc, lutmax);    // in [0, lutmax]: truncation = floor
     float fl;
     const int li = floor_split(xl, fl);
@@ -256,9 +256,12 @@ __device__ __forceinline__ float bf16_value(unsigned int c) { return __uint_as_f
 // texels are returned unfiltered, so the corners are the stored values themselves.
 template <int S>
 __device__ __forceinline__ void fetch8_atlas(const Atlas &a, int ix, int iy, int iz, float v[8]) {
-    const int cm = (1 << a.alog) - 1, iz1 = iz + 1;   // atlas coordinates < 32768
-    const float x0 = small_int_float((iz & cm) * a.dx + ix + 1), y0 = small_int_float((iz >> a.alog) * a.dy + iy + 1);
-    const float x1 = small_int_float((iz1 & cm) * a.dx + ix + 1), y1 = small_int_float((iz1 >> a.alog) * a.dy + iy + 1);
+    const int cm = (1 << a.alog) - 1, col = iz & cm;   // atlas coordinates < 32768
+    const float x0 = small_int_float(col * a.dx + ix + 1), y0 = small_int_float((iz >> a.alog) * a.dy + iy + 1);
+    // slice iz + 1: the next tile of the row, or the first tile of the next row
+    const bool wrap = col == cm;
+    const float x1 = __fadd_rn(x0, small_int_float(wrap ? -cm * a.dx : a.dx));
+    const float y1 = wrap ? __fadd_rn(y0, small_int_float(a.dy)) : y0;
     if constexpr (S != 2) {           // FP32 texels, or FP16 ones the texture unit widens (exactly)
         const float4 g0 = tex2Dgather<float4>(a.tex, x0, y0, 0);
         const float4 g1 = tex2Dgather<float4>(a.tex, x1, y1, 0);
