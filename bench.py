@@ -234,14 +234,17 @@ def compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np, frames=16):
     t0 = time.perf_counter()
     ctx.compress_cube(cid)
     enc_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     ctx.set_brick_layouts(cid, 9)      # cache slots also hold slice atlases of the decoded bricks
+    atlas_s = time.perf_counter() - t0
     n_store = int(ctx.wavelet_store_bytes(cid))
     nx, ny, nz = cfg["shape"]
     res = {"workload": cfg["name"] + ": 8x8x8 Haar blocks, 3 levels, int8 codes, power-of-two "
                                      "step per subband, decoded on demand into the brick cache "
                                      "(slots with slice atlases)",
            "store_bytes": n_store, "fp32_bytes": 4 * nx * ny * nz,
-           "ratio_vs_fp32": round(4 * nx * ny * nz / n_store, 3), "encode_s": round(enc_s, 3)}
+           "ratio_vs_fp32": round(4 * nx * ny * nz / n_store, 3), "encode_s": round(enc_s, 3),
+           "slot_atlas_setup_s": round(atlas_s, 3)}
     # decoded voxels against the FP32 cube on sampled bricks
     nb, _ = ctx.brick_grid(cid)
     total = nb[0] * nb[1] * nb[2]

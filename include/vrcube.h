@@ -203,7 +203,10 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * cache) take mask 1 or 9: with 9, each cache slot holding one of the cube's bricks also holds
  * its slice atlas (a 2D array sized for the cube's largest brick, packed from the slot on the
  * cache's stream when the brick becomes resident: as much device memory again as the slots
- * in use, outside cache_bytes; an allocation failure fails the frame with VR_ERR_OOM).
+ * in use, outside cache_bytes).  The arrays of as many slots as the cube has bricks are made
+ * by this call (and by vr_set_bricking of such a cube), so that frames only pack; the call
+ * then sizes the brick cache (VR_ERR_OOM without one, or when an array cannot be had; a frame
+ * that needs another array and cannot have it fails with VR_ERR_OOM too).
  * Mask 1..15 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
  * (streamed or compressed cube with a mask other than 1 or 9; atlas beyond the gather size,
  * raised by the rebuild, or for streamed cubes by the frame), VR_ERR_OOM, VR_ERR_CUDA. */

@@ -980,7 +980,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
         cb->ghost = ghost;
         cb->storage = storage;
         cb->bricked = true;
-        return VR_OK;
+        return (cb->layouts & 8) ? cache_prepare_atlases(c, cb) : VR_OK;
     }
     CK(cudaMalloc(&cb->d_pool, std::max<size_t>(off * esz, 16)));
     cb->pool_bytes = off * esz;
@@ -1082,7 +1082,13 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
         return fail(VR_ERR_UNSUPPORTED, "streamed bricks are cached x-contiguous, with or without slot atlases (mask 1 or 9)");
     if (cb->layouts == mask) return VR_OK;
     cb->layouts = mask;
-    if (!cb->bricked || cb->streamed) return VR_OK;
+    if (!cb->bricked) return VR_OK;
+    if (cb->streamed) {                // slot atlases: arrays made now, so that frames only pack
+        if (!(mask & 8)) return VR_OK;
+        int rc = set_dev(c);
+        if (rc) return rc;
+        return cache_prepare_atlases(c, cb);
+    }
     return vr_set_bricking(c, cube_id, cb->B[0], cb->B[1], cb->B[2], cb->ghost, cb->storage);
 }
 

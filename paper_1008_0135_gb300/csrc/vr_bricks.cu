@@ -143,6 +143,38 @@ __global__ void k_atlas_pack(const T *__restrict__ src, int dx, int dy, int dz, 
     }
 }
 
+// The same placement written straight into the atlas array through a surface (no staging, no
+// array copy).  Coordinates are in range by construction; the zero boundary mode makes any
+// write outside the array a no-op rather than a fault.
+template <typename T>
+__global__ void k_atlas_pack_surf(const T *__restrict__ src, int dx, int dy, int dz, int alog,
+                                  cudaSurfaceObject_t surf) {
+    const long long n = (long long)dx * dy * dz;
+    const int cm = (1 << alog) - 1;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % dx);
+        const long long r = i / dx;
+        const int y = (int)(r % dy), z = (int)(r / dy);
+        const int row = (z >> alog) * dy + y, col = (z & cm) * dx + x;
+        surf2Dwrite<T>(src[i], surf, col * (int)sizeof(T), row, cudaBoundaryModeZero);
+    }
+}
+
+cudaError_t launch_atlas_pack_surf(const void *brick, int esz, int dx, int dy, int dz, int alog,
+                                   unsigned long long surf, cudaStream_t s) {
+    const long long n = (long long)dx * dy * dz;
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    if (esz == 4)
+        k_atlas_pack_surf<unsigned int><<<grid, 256, 0, s>>>(static_cast<const unsigned int *>(brick), dx, dy, dz,
+                                                             alog, (cudaSurfaceObject_t)surf);
+    else
+        k_atlas_pack_surf<unsigned short><<<grid, 256, 0, s>>>(static_cast<const unsigned short *>(brick), dx, dy,
+                                                               dz, alog, (cudaSurfaceObject_t)surf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz, int alog, void *atlas,
                               size_t pitch, cudaStream_t s) {
     const long long n = (long long)dx * dy * dz;

@@ -197,6 +197,7 @@ void cache_reset_stats(vr_ctx *c);
 void cache_forget_cube(vr_ctx *c, int cube_id);
 int streamed_brick(Cube *cb, int64_t brick, void *data, int *exp2);
 size_t cache_slot_bytes(vr_ctx *c);   // 0 until the cache has been sized
+int cache_prepare_atlases(vr_ctx *c, Cube *cb);   // slot atlases for a cube with layout bit 3
 // admission accounting of the serving loop: bricks of a work-list not yet resident and the
 // cache slots no in-flight frame holds (VR_ERR_TIMEOUT while another frame is making bricks
 // resident), and holding / releasing a frame's bricks (false if busy and !wait)

@@ -97,6 +97,8 @@ cudaError_t launch_brick_maxabs(const float *cube, int nx, int ny, int nz, const
 // pitch-linear slice atlas of (2^alog dx) x (ceil(dz / 2^alog) dy) elements, row pitch `pitch` bytes.
 cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz, int alog, void *atlas,
                               size_t pitch, cudaStream_t s);
+cudaError_t launch_atlas_pack_surf(const void *brick, int esz, int dx, int dy, int dz, int alog,
+                                   unsigned long long surf, cudaStream_t s);
 cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                int nbricks, const unsigned int *maxbits, int storage, void *pool,
                                int *exps, cudaStream_t s);

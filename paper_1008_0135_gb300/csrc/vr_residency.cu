@@ -243,6 +243,7 @@ struct Slot {
     // the largest brick of its storage kind, created on first use
     cudaArray_t arr = nullptr;
     cudaTextureObject_t tex = 0;
+    cudaSurfaceObject_t surf = 0;     // packs write the array through it (0: staging + copy)
     int arr_storage = -1, arr_w = 0, arr_h = 0, alog = 0;
     bool atlas_ok = false;            // the atlas holds this slot's brick
 };
@@ -295,6 +296,7 @@ void cache_destroy(vr_ctx *c) {
     for (auto &s : k->slots) {
         if (s.last_use) cudaEventDestroy(s.last_use);
         if (s.tex) cudaDestroyTextureObject(s.tex);
+        if (s.surf) cudaDestroySurfaceObject(s.surf);
         if (s.arr) cudaFreeArray(s.arr);
     }
     for (auto &s : k->stage) {
@@ -390,6 +392,7 @@ static int cache_size(vr_ctx *c, size_t slot_bytes) {
             if (s.used) CK(cudaEventSynchronize(s.last_use));
             cudaEventDestroy(s.last_use);
             if (s.tex) cudaDestroyTextureObject(s.tex);
+            if (s.surf) cudaDestroySurfaceObject(s.surf);
             if (s.arr) cudaFreeArray(s.arr);
         }
         for (auto &s : k->stage) {
@@ -478,10 +481,9 @@ static int slot_atlas_geom(vr_ctx *c, Cube *cb, SlotAtlasGeom &g) {
     return VR_OK;
 }
 
-// Packs slot `si`'s brick `b` (already queued into the slot on the copy stream) into the slot's
-// atlas on the copy stream, creating or replacing the array first when it has another texel
-// type or is too small (after every reader and pending copy of the old one).
-static int slot_atlas_pack(vr_ctx *c, Cube *cb, int si, const DrawBrick &b, const SlotAtlasGeom &g) {
+// Gives slot `si` an atlas array for cube `cb`'s bricks, creating or replacing it when it has
+// another texel type or is too small (after every reader and pending copy of the old one).
+static int slot_atlas_alloc(vr_ctx *c, Cube *cb, int si, const SlotAtlasGeom &g) {
     BrickCache *k = c->cache;
     Slot &s = k->slots[si];
     const size_t esz = cb->storage == VR_F32 ? 4 : 2;
@@ -490,18 +492,27 @@ static int slot_atlas_pack(vr_ctx *c, Cube *cb, int si, const DrawBrick &b, cons
             if (s.used) CK(cudaEventSynchronize(s.last_use));
             CK(cudaStreamSynchronize(k->copy));
             cudaDestroyTextureObject(s.tex);
+            if (s.surf) cudaDestroySurfaceObject(s.surf);
             cudaFreeArray(s.arr);
             s.tex = 0;
+            s.surf = 0;
             s.arr = nullptr;
         }
         const cudaChannelFormatDesc cd =
             esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
             : cb->storage == VR_F16 ? cudaCreateChannelDescHalf()
                                     : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
-        if (cudaMallocArray(&s.arr, &cd, (size_t)g.w, (size_t)g.h, cudaArrayTextureGather) != cudaSuccess) {
+        // writable through a surface when the device allows it with gathers, else filled by copies
+        bool surf_ok = cudaMallocArray(&s.arr, &cd, (size_t)g.w, (size_t)g.h,
+                                       cudaArrayTextureGather | cudaArraySurfaceLoadStore) == cudaSuccess;
+        if (!surf_ok) {
             s.arr = nullptr;
             cudaGetLastError();
-            return fail(VR_ERR_OOM, "slice atlas of a cache slot: cudaMallocArray failed");
+            if (cudaMallocArray(&s.arr, &cd, (size_t)g.w, (size_t)g.h, cudaArrayTextureGather) != cudaSuccess) {
+                s.arr = nullptr;
+                cudaGetLastError();
+                return fail(VR_ERR_OOM, "slice atlas of a cache slot: cudaMallocArray failed");
+            }
         }
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
@@ -512,9 +523,29 @@ static int slot_atlas_pack(vr_ctx *c, Cube *cb, int si, const DrawBrick &b, cons
         td.readMode = cudaReadModeElementType;
         td.normalizedCoords = 0;
         CK(cudaCreateTextureObject(&s.tex, &rd, &td, nullptr));
+        if (surf_ok) CK(cudaCreateSurfaceObject(&s.surf, &rd));
         s.arr_storage = cb->storage;
         s.arr_w = g.w;
         s.arr_h = g.h;
+        s.atlas_ok = false;
+    }
+    return VR_OK;
+}
+
+// Packs slot `si`'s brick `b` (already queued into the slot on the copy stream) into the slot's
+// atlas on the copy stream.
+static int slot_atlas_pack(vr_ctx *c, Cube *cb, int si, const DrawBrick &b, const SlotAtlasGeom &g) {
+    BrickCache *k = c->cache;
+    Slot &s = k->slots[si];
+    const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+    int rc = slot_atlas_alloc(c, cb, si, g);
+    if (rc != VR_OK) return rc;
+    if (s.surf) {
+        CK(launch_atlas_pack_surf(k->d_base + (size_t)si * k->slot_bytes, (int)esz, b.dim[0], b.dim[1], b.dim[2],
+                                  g.alog, (unsigned long long)s.surf, k->copy));
+        s.alog = g.alog;
+        s.atlas_ok = true;
+        return VR_OK;
     }
     const size_t need = (size_t)g.w * g.h * esz;
     if (k->pack_bytes < need) {
@@ -833,6 +864,25 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)nd;
     if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
+// Set-up for a streamed or compressed cube whose cache slots keep slice atlases: sizes the cache
+// for its bricks and gives as many slots as it has bricks (at most all slots) an atlas array, so
+// that frames only pack.  Arrays already fit for its bricks are kept.
+int cache_prepare_atlases(vr_ctx *c, Cube *cb) {
+    int rc = cache_create(c);
+    if (rc) return rc;
+    BrickCache *k = c->cache;
+    std::lock_guard<std::recursive_mutex> lock(k->mu);
+    size_t max_bytes = 0;
+    for (auto &b : cb->tmpl) max_bytes = std::max(max_bytes, (size_t)b.bytes);
+    if ((rc = cache_size(c, max_bytes)) != VR_OK) return rc;
+    SlotAtlasGeom g;
+    if ((rc = slot_atlas_geom(c, cb, g)) != VR_OK) return rc;
+    const int n = (int)std::min<size_t>((size_t)k->nslots, cb->tmpl.size());
+    for (int i = 0; i < n; ++i)
+        if ((rc = slot_atlas_alloc(c, cb, i, g)) != VR_OK) return rc;
     return VR_OK;
 }
 
