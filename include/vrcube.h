@@ -246,8 +246,11 @@ int vr_set_render_params(vr_ctx *ctx, int mode, float step, float ert_threshold)
  * same samples, owners and arithmetic), carrying one transmittance through them, and stops
  * once the whole ray's opacity reaches tau, so samples behind opaque pixels are skipped.  The
  * image is the unbricked ray's (global termination); it differs from VR_TERM_SEGMENT's by at
- * most 1 - tau per channel.  No fragments are written (stats count none).  Not available for streamed cubes (vr_render_frame returns VR_ERR_UNSUPPORTED),
- * vr_render_frame_noalloc or vr_render_backward (both VR_ERR_UNSUPPORTED); MIP ignores it.
+ * most 1 - tau per channel.  No fragments are written (stats count none).  Streamed and
+ * compressed cubes: the frame's bricks (those the per-segment frame would draw) are made
+ * resident in the brick cache together, then walked the same way (VR_ERR_UNSUPPORTED when they
+ * do not all fit the cache).  Not available for vr_render_frame_noalloc or vr_render_backward
+ * (both VR_ERR_UNSUPPORTED); MIP ignores it.
  * Errors: VR_ERR_ARG. */
 int vr_set_termination(vr_ctx *ctx, int mode);
 

@@ -1282,8 +1282,7 @@ static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStr
 __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
     if (cb->streamed) {
-        if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL)
-            return fail(VR_ERR_UNSUPPORTED, "global termination needs resident bricks (streamed cube)");
+        if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) return render_streamed_global(c, cb, out, out_where, s);
         return render_streamed(c, cb, out, out_where, s);
     }
     if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) return render_global(c, cb, out, out_where, s);

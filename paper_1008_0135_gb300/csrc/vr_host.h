@@ -192,6 +192,7 @@ int ensure(DevBuf<T> &b, size_t n, vr_ctx *c) {
 int cache_create(vr_ctx *c);
 void cache_destroy(vr_ctx *c);
 int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s);
+int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s);
 void cache_stats(vr_ctx *c, vr_stats *st);
 void cache_reset_stats(vr_ctx *c);
 void cache_forget_cube(vr_ctx *c, int cube_id);

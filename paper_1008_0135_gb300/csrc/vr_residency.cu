@@ -867,6 +867,118 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     return VR_OK;
 }
 
+// DVR frame of a streamed or compressed cube with global early termination: the frame's bricks
+// (the work-list: visible, not skipped) are made resident together, then one ray-march launch
+// walks the whole brick grid as for a resident cube.  Bricks outside the work-list are walked
+// through without samples: no ray of the frame reaches them (their screen rectangle misses
+// the frame) or their values map to zero opacity, exactly as the fragment path leaves them out.
+int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
+    int rc = cache_create(c);
+    if (rc) return rc;
+    BrickCache *k = c->cache;
+    std::lock_guard<std::recursive_mutex> lock(k->mu);
+    size_t max_bytes = 0;
+    for (auto &b : cb->tmpl) max_bytes = std::max(max_bytes, (size_t)b.bytes);
+    if ((rc = cache_size(c, max_bytes)) != VR_OK) return rc;
+    FrameConsts fc = make_consts(c, cb);
+    WorkList wl;
+    build_worklist(c, cb, wl);
+    const size_t nd = wl.db.size(), nb = cb->tmpl.size();
+    if (nd > (size_t)k->nslots)
+        return fail(VR_ERR_UNSUPPORTED, "global termination needs every brick of the frame in the brick cache at once");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
+    size_t off = 0;
+    const size_t off_lut = off;
+    off = align_up(off + sizeof(float4) * c->lut.size(), 256);
+    const size_t off_b = off;
+    off = align_up(off + sizeof(DrawBrick) * nb, 256);
+    const size_t off_mask = off;
+    off = align_up(off + c->chmask.size(), 256);
+    if (c->frame_pending) {
+        CK(cudaEventSynchronize(c->upload_done));
+        CK(cudaStreamWaitEvent(s, c->frame_done, 0));
+    }
+    if ((rc = ensure_host(c, off)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_stage, off, c)) != VR_OK) return rc;
+    if (ev[0]) CK(cudaEventRecord(ev[0], s));
+    const int64_t chunk_id = ++k->chunk_counter;
+    if ((rc = make_resident(c, cb, wl.db, 0, nd, chunk_id)) != VR_OK) {
+        cudaStreamSynchronize(k->copy);
+        if (ev[0]) {
+            cudaStreamSynchronize(s);
+            for (auto e : ev) c->ev_pool.push_back(e);
+        }
+        return rc;
+    }
+    CK(cudaEventRecord(k->copies_done, k->copy));
+    CK(cudaStreamWaitEvent(s, k->copies_done, 0));
+    char *h = c->h_stage, *d = c->d_stage.p;
+    std::memcpy(h + off_lut, c->lut.data(), sizeof(float4) * c->lut.size());
+    DrawBrick *hb = reinterpret_cast<DrawBrick *>(h + off_b);
+    for (size_t i = 0; i < nb; ++i) {
+        hb[i] = cb->tmpl[i];
+        hb[i].skip = 1;
+        hb[i].sampled = 0;
+        hb[i].atlas = 0ull;
+    }
+    for (size_t i = 0; i < nd; ++i) {
+        DrawBrick b = wl.db[i];
+        b.skip = 0;
+        b.sampled = 0;
+        hb[b.brick] = b;
+    }
+    if (!c->chmask.empty()) std::memcpy(h + off_mask, c->chmask.data(), c->chmask.size());
+    MarchGrid g{};
+    for (int a = 0; a < 3; ++a) {
+        g.nb[a] = (int)cb->nb[a];
+        g.B[a] = (float)cb->B[a];
+        g.n[a] = (float)cb->n[a];
+        g.clo[a] = 0.0f;
+        g.chi[a] = (float)cb->n[a];
+        if (c->has_window) {
+            g.clo[a] = (float)std::max<int64_t>(c->win_lo[a], 0);
+            g.chi[a] = (float)std::min<int64_t>(c->win_hi[a], cb->n[a]);
+        }
+    }
+    CK(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->upload_done, s));
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(d + off_mask);
+    const size_t opix = (size_t)fc.cam.W * fc.cam.H;
+    float *dst = out;
+    const bool direct = out_where == VR_DEVICE && (reinterpret_cast<uintptr_t>(out) % 16 == 0);
+    if (!direct) {
+        if ((rc = ensure(c->d_out, opix * 4, c)) != VR_OK) return rc;
+        dst = c->d_out.p;
+    }
+    if (ev[1]) CK(cudaEventRecord(ev[1], s));
+    const bool empty = g.chi[0] <= g.clo[0] || g.chi[1] <= g.clo[1] || g.chi[2] <= g.clo[2];
+    if (empty || nd == 0) {            // nothing to sample: a transparent frame
+        CK(cudaMemsetAsync(dst, 0, opix * sizeof(float4), s));
+    } else {
+        CK(launch_raymarch(fc, reinterpret_cast<const float4 *>(d + off_lut), reinterpret_cast<DrawBrick *>(d + off_b),
+                           g, k->d_base, reinterpret_cast<float4 *>(dst), c->d_ctr, s));
+    }
+    for (size_t i = 0; i < nd; ++i) {  // every slot this frame read: its readers' event
+        Slot &sl = k->slots[k->where[key_of(cb->id, wl.db[i].brick)]];
+        if (sl.used) CK(cudaStreamWaitEvent(s, sl.last_use, 0));
+        CK(cudaEventRecord(sl.last_use, s));
+        sl.used = true;
+    }
+    if (ev[2]) CK(cudaEventRecord(ev[2], s));
+    if (ev[3]) CK(cudaEventRecord(ev[3], s));
+    if (!direct)
+        CK(cudaMemcpyAsync(out, dst, opix * sizeof(float4),
+                           out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    CK(cudaEventRecord(c->frame_done, s));
+    c->frame_pending = true;
+    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    c->frames++;
+    c->bricks_drawn += (int64_t)nd;
+    if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
+    return VR_OK;
+}
+
 // Set-up for a streamed or compressed cube whose cache slots keep slice atlases: sizes the cache
 // for its bricks and gives as many slots as it has bricks (at most all slots) an atlas array, so
 // that frames only pack.  Arrays already fit for its bricks are kept.

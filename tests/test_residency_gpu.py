@@ -211,3 +211,41 @@ def test_slot_atlases_give_identical_images(storage, mode):
             assert np.count_nonzero(lin) > 0
             with pytest.raises(P.VrError):
                 ctx.set_brick_layouts(cid, 15)
+
+
+@pytest.mark.parametrize("layouts", [1, 9])
+def test_global_termination_of_a_streamed_cube(orc, layouts):
+    """Occlusion skipping on a streamed cube: the frame's bricks made resident together, one
+    ray-march over the brick grid; the image equals the resident cube's global-termination frame
+    of the same voxels (bit for bit), repeats from cache hits, and a cache smaller than the
+    frame's bricks refuses (VR_ERR_UNSUPPORTED)."""
+    import paper_1008_0135_gb300 as P
+    vox = orc.proc_region(SEED, SMALL, (0, 0, 0), SMALL)
+    lut = synth.ramp_lut(alpha=1.0)                  # opaque: rays stop early
+    cams = [_cam(SMALL, W=96, H=80, seed=s) for s in (3, 8)]
+    cams.append(dict(view=synth.look_at((150.0, 135.0, -300.0), (150.0, 135.0, 130.0)), proj=1,
+                     param=math.radians(70.0), W=120, H=100))
+    with P.Context(0, cache_bytes=40 * F32_BRICK_BYTES) as ctx:
+        sid = ctx.load_cube_procedural(SEED, SMALL)
+        ctx.set_bricking(sid, BRICK, 1, "f32")
+        ctx.set_brick_layouts(sid, layouts)
+        rid = ctx.load_cube(vox)
+        ctx.set_brick_layouts(rid, layouts)
+        ctx.set_bricking(rid, BRICK, 1, "f32")
+        ctx.set_termination("global")
+        try:
+            for cam in cams:
+                a = render(ctx, sid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                b = render(ctx, rid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                again = render(ctx, sid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                assert np.array_equal(a, b) and np.array_equal(a, again)
+                assert np.count_nonzero(a) > 0
+        finally:
+            ctx.set_termination("segment")
+    with P.Context(0, cache_bytes=5 * F32_BRICK_BYTES) as small:
+        sid = small.load_cube_procedural(SEED, SMALL)
+        small.set_bricking(sid, BRICK, 1, "f32")
+        small.set_termination("global")
+        with pytest.raises(P.VrError) as e:
+            render(small, sid, lut, (-3, 20), cams[2], step=0.5, tau=0.99)
+        assert e.value.status == -7
