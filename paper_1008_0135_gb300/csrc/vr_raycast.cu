@@ -18,11 +18,10 @@
 
 #include "vr_internal.cuh"
 
-// Tuning knobs (build-time; the defaults are the measured best on GB300): unroll factor of the
-// DVR sample loop; blocks per SM the register allocation must allow for the fragment kernel's
-// atlas DVR and MIP instantiations (0: no constraint), for the one-pass (global termination)
-// kernel and for the adjoint; and the adjoint's table-gradient copies with the shared-memory
-// bound (KB per block) they must fit in.
+// Tuning knobs of the ray-cast kernels (build-time): unroll factor of the DVR sample loop, the
+// blocks per SM the register allocation of the fragment kernel must allow for DVR frames read
+// through slice atlases and for MIP frames (0: no constraint), and the same for the one-pass
+// (global termination) kernel.
 #ifndef VR_SAMPLE_UNROLL
 #define VR_SAMPLE_UNROLL 1
 #endif
