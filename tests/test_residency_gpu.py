@@ -249,3 +249,31 @@ def test_global_termination_of_a_streamed_cube(orc, layouts):
         with pytest.raises(P.VrError) as e:
             render(small, sid, lut, (-3, 20), cams[2], step=0.5, tau=0.99)
         assert e.value.status == -7
+
+
+def test_async_host_output_of_streamed_frames():
+    """Asynchronous host output for streamed frames (DVR and MIP, chunked through 5 slots):
+    the queued copies, read after an event, equal the synchronous frames."""
+    import torch
+    import paper_1008_0135_gb300 as P
+    lut = synth.ramp_lut(alpha=0.3)
+    cam = dict(view=synth.look_at((150.0, 135.0, -300.0), (150.0, 135.0, 130.0)), proj=1,
+               param=math.radians(70.0), W=120, H=100)
+    with P.Context(0, cache_bytes=5 * F32_BRICK_BYTES) as ctx:
+        cid = ctx.load_cube_procedural(SEED, SMALL)
+        ctx.set_bricking(cid, BRICK, 1, "f32")
+        for mode in ["dvr", "mip"]:
+            want = render(ctx, cid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+            shape = (cam["H"], cam["W"], 4) if mode == "dvr" else (cam["H"], cam["W"])
+            bufs = [torch.full(shape, -1.0).pin_memory() for _ in range(2)]
+            ev = [torch.cuda.Event() for _ in range(2)]
+            ctx.set_host_output_async(True)
+            try:
+                for k in range(2):
+                    ctx.render_frame(cid, bufs[k])
+                    ev[k].record()
+                for k in range(2):
+                    ev[k].synchronize()
+                    assert np.array_equal(bufs[k].numpy().reshape(want.shape), want)
+            finally:
+                ctx.set_host_output_async(False)
