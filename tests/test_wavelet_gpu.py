@@ -159,3 +159,31 @@ def test_compressed_frames_with_slot_atlases(orc):
                 assert np.array_equal(lin, at) and np.array_equal(lin, again)
         finally:
             c.close()
+
+
+def test_compressed_cube_global_termination(orc):
+    """Occlusion skipping on a compressed cube equals the resident cube of the oracle-decoded
+    voxels under the same termination, bit for bit (slot atlases and linear slots)."""
+    cube = synth.pr1_cube(seed=4, n=48)
+    dec = orc.wavelet_decode(orc.wavelet_encode(cube), cube.shape).astype(np.float32)
+    lut = synth.ramp_lut(alpha=1.0)
+    cam = synth.pr1_camera(n=48, W=64, H=64)
+    c = _ctx(64 * 18 ** 3 * 4)
+    try:
+        cid = c.load_cube(cube)
+        c.set_bricking(cid, (16, 16, 16), 1, "f32")
+        c.compress_cube(cid)
+        rid = c.load_cube(dec)
+        c.set_bricking(rid, (16, 16, 16), 1, "f32")
+        c.set_termination("global")
+        try:
+            for mask in (1, 9):
+                c.set_brick_layouts(cid, mask)
+                c.set_brick_layouts(rid, mask)
+                a = render(c, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                b = render(c, rid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                assert np.array_equal(a, b) and np.count_nonzero(a) > 0
+        finally:
+            c.set_termination("segment")
+    finally:
+        c.close()
