@@ -498,14 +498,19 @@ def run_ours(args, dist):
     cams = cameras(cfg, cfg.get("n_views", 64))
     W, H = cfg["W"], cfg["H"]
     ctx = P.Context(dev, cache_bytes=64 << 30)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     cid = ctx.load_cube(cube)
+    load_s = time.perf_counter() - t_setup
     cube_np = None
     if dist.rank == 0 and not args.no_extras:
         cube_np = cube.cpu().numpy()
     del cube
     torch.cuda.empty_cache()
     ctx.set_brick_layouts(cid, 9)          # slice atlases (gathers) + the x-contiguous copy
+    t_setup = time.perf_counter()
     ctx.set_bricking(cid, cfg["brick"], 1, args.storage)
+    brick_s = time.perf_counter() - t_setup
     out = torch.empty((H, W, 4), dtype=torch.float32, device=device)
     peak, psrc = peaks()
     clocks = Clocks(dev)
@@ -531,6 +536,9 @@ def run_ours(args, dist):
         "roofline": rl,
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
+        "setup": {"load_cube_s": round(load_s, 3), "bricking_s": round(brick_s, 3),
+                  "what": "cube copied in from device memory; bricking = bricks with ghost voxels, "
+                          "their value ranges and the slice atlases (one-time)"},
     }
     if not args.no_extras:
         ctx.set_bricking(cid, cfg["brick"], 1, "f16")   # same layouts as the FP32 leg

@@ -414,8 +414,10 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     }
     void *tmp = nullptr;
     CK(cudaMalloc(&tmp, most));
+    std::vector<cudaSurfaceObject_t> surfs;   // kept until the packs that write through them ran
     auto bail = [&](cudaError_t e, const char *what) {
         cudaStreamSynchronize(s);
+        for (auto sf : surfs) cudaDestroySurfaceObject(sf);
         cudaFree(tmp);
         free_atlases(cb);
         return cuda_fail(e, what);
@@ -433,18 +435,34 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
         const int *dm = cb->tmpl[i].dim;
         const size_t w = (size_t)dm[0] << lg[i], h = (size_t)((dm[2] + (1 << lg[i]) - 1) >> lg[i]) * dm[1];
         cudaArray_t arr = nullptr;
-        if ((e = cudaMallocArray(&arr, &cd, w, h, cudaArrayTextureGather)) != cudaSuccess)
-            return bail(e, "cudaMallocArray (slice atlas)");
+        // written by the pack kernel through a surface where the device allows surface stores on
+        // a gather array; else packed into staging and copied (the copy engine's array writes)
+        const bool surf_ok = cudaMallocArray(&arr, &cd, w, h, cudaArrayTextureGather | cudaArraySurfaceLoadStore) ==
+                             cudaSuccess;
+        if (!surf_ok) {
+            arr = nullptr;
+            cudaGetLastError();
+            if ((e = cudaMallocArray(&arr, &cd, w, h, cudaArrayTextureGather)) != cudaSuccess)
+                return bail(e, "cudaMallocArray (slice atlas)");
+        }
         cb->atlas_arr[i] = arr;
-        const char *src = static_cast<const char *>(cb->d_pool) + (size_t)cb->loff[3 * (size_t)i] * esz;
-        if ((e = launch_atlas_pack(src, (int)esz, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, s)) != cudaSuccess)
-            return bail(e, "atlas pack launch");
-        if ((e = cudaMemcpy2DToArrayAsync(arr, 0, 0, tmp, w * esz, w * esz, h, cudaMemcpyDeviceToDevice, s)) !=
-            cudaSuccess)
-            return bail(e, "cudaMemcpy2DToArrayAsync (slice atlas)");
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
         rd.res.array.array = arr;
+        const char *src = static_cast<const char *>(cb->d_pool) + (size_t)cb->loff[3 * (size_t)i] * esz;
+        if (surf_ok) {
+            cudaSurfaceObject_t sf = 0;
+            if ((e = cudaCreateSurfaceObject(&sf, &rd)) != cudaSuccess) return bail(e, "cudaCreateSurfaceObject");
+            surfs.push_back(sf);
+            e = launch_atlas_pack_surf(src, (int)esz, dm[0], dm[1], dm[2], lg[i], (unsigned long long)sf, s);
+            if (e != cudaSuccess) return bail(e, "atlas pack launch");
+        } else {
+            if ((e = launch_atlas_pack(src, (int)esz, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, s)) != cudaSuccess)
+                return bail(e, "atlas pack launch");
+            if ((e = cudaMemcpy2DToArrayAsync(arr, 0, 0, tmp, w * esz, w * esz, h, cudaMemcpyDeviceToDevice, s)) !=
+                cudaSuccess)
+                return bail(e, "cudaMemcpy2DToArrayAsync (slice atlas)");
+        }
         cudaTextureDesc td{};
         td.addressMode[0] = td.addressMode[1] = cudaAddressModeClamp;
         td.filterMode = cudaFilterModePoint;
@@ -459,6 +477,7 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
         cb->tmpl[i].alog = lg[i];
     }
     e = cudaStreamSynchronize(s);
+    for (auto sf : surfs) cudaDestroySurfaceObject(sf);
     cudaFree(tmp);
     if (e != cudaSuccess) {
         free_atlases(cb);
