@@ -138,3 +138,36 @@ def test_slot_atlases_in_the_mix(world):
                 _same(r, _alone(ctx, r))
     finally:
         ctx.set_brick_layouts(v, 1)
+
+
+def test_soak_mixed_requests_with_evictions():
+    """A longer soak: 240 requests over a resident FP32 cube, a resident FP16 cube, a streamed
+    FP32 cube with slot atlases and a streamed FP16 cube through a 10-slot cache (evictions and
+    re-packs all the time), up to 8 frames in flight, device and pinned host outputs; every
+    result equals the frame alone."""
+    import torch
+    import paper_1008_0135_gb300 as P
+    with P.Context(0, cache_bytes=10 * 130 ** 3 * 4) as ctx:
+        a = ctx.load_cube(synth.pr1_cube(seed=0))
+        ctx.set_bricking(a, (32, 32, 32), 1, "f32")
+        b = ctx.load_cube(synth.pr1_cube(seed=3, n=96))
+        ctx.set_brick_layouts(b, 9)
+        ctx.set_bricking(b, (32, 48, 40), 1, "f16")
+        v = ctx.load_cube_procedural(4, (300, 270, 260))
+        ctx.set_bricking(v, (128, 128, 128), 1, "f32")
+        ctx.set_brick_layouts(v, 9)
+        w = ctx.load_cube_procedural(5, (200, 150, 130))
+        ctx.set_bricking(w, (64, 64, 64), 1, "f16")
+        cubes = {"pr1": (a, (64, 64, 64)), "b96": (b, (96, 96, 96)), "proc": (v, (300, 270, 260)),
+                 "proc16": (w, (200, 150, 130))}
+        reqs = _requests(cubes, 240, 2000.0, 31, "cuda")
+        for i, r in enumerate(reqs):
+            if i % 3 == 0:
+                r["out"] = torch.zeros(r["out"].shape, pin_memory=True)
+        results, summary = ctx.serve(reqs, max_inflight=8)
+        torch.cuda.synchronize()
+        assert all(r["status"] == 0 for r in results), [r for r in results if r["status"] != 0][:3]
+        assert summary["completed"] == 240 and summary["max_concurrent"] >= 2
+        for r in reqs:
+            out = r["out"] if r["out"].is_cuda else r["out"].cuda()
+            _same(dict(r, out=out), _alone(ctx, r))
