@@ -373,6 +373,7 @@ typedef struct {
     double arrival_ms;           /* arrival time, ms after the loop starts (non-decreasing) */
     float *out;                  /* caller's frame buffer (device or pinned host memory) */
     int out_where;               /* VR_DEVICE or VR_HOST */
+    int termination;             /* as vr_set_termination: VR_TERM_SEGMENT (0) or VR_TERM_GLOBAL */
 } vr_request;
 
 typedef struct {
@@ -399,7 +400,8 @@ typedef struct {
  * holds enough slots that no frame in flight needs for the bricks the request still lacks (a
  * request needing more than the whole cache runs alone, in chunks).  Admitted frames run
  * concurrently, one CUDA stream per slot; each result equals what vr_render_frame gives for
- * the same request.  Blocks until every request has completed or failed.  res[i] receives
+ * the same request (with its termination scope; a global-termination frame of a streamed cube
+ * whose bricks exceed the cache fails alone with VR_ERR_UNSUPPORTED).  Blocks until every request has completed or failed.  res[i] receives
  * request i's status and times; sum (nullable) the latency percentiles and throughput.
  * Host outputs should be pinned (a pageable copy serialises the loop).  Errors: VR_ERR_ARG
  * (null, max_inflight, unordered arrivals, request without table or output),

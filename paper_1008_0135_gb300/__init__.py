@@ -269,8 +269,9 @@ class Context:
 
     def serve(self, requests, max_inflight: int = 4):
         """Runs the continuous-batching request loop (vr_serve).  ``requests``: dicts with cube,
-        cam (view/proj/param/W/H), mode, step, tau, lut (n x 4), vrange, arrival_ms and out (a
-        CUDA tensor or pinned host tensor), in arrival order.  Returns (results, summary)."""
+        cam (view/proj/param/W/H), mode, step, tau, lut (n x 4), vrange, arrival_ms, out (a
+        CUDA tensor or pinned host tensor) and optionally termination ("segment" or "global"),
+        in arrival order.  Returns (results, summary)."""
         n = len(requests)
         arr = (_abi.VrRequest * max(n, 1))()
         keep = []
@@ -291,6 +292,7 @@ class Context:
             q.arrival_ms = float(r.get("arrival_ms", 0.0))
             ptr, loc = _buffer(r["out"])
             q.out, q.out_where = ptr, loc
+            q.termination = {"segment": 0, "global": 1}[r.get("termination", "segment")]
         cfg = _abi.VrServeConfig(int(max_inflight))
         res = (_abi.VrRequestResult * max(n, 1))()
         summ = _abi.VrServeSummary()

@@ -31,7 +31,7 @@ class VrRequest(C.Structure):
         ("width", C.c_int), ("height", C.c_int), ("mode", C.c_int), ("step", C.c_float),
         ("ert_threshold", C.c_float), ("lut", C.c_void_p), ("nlut", C.c_int),
         ("vmin", C.c_float), ("vmax", C.c_float), ("arrival_ms", C.c_double),
-        ("out", C.c_void_p), ("out_where", C.c_int),
+        ("out", C.c_void_p), ("out_where", C.c_int), ("termination", C.c_int),
     ]
 
 

@@ -186,6 +186,7 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
             int st = vr_set_transfer_function(fc, q.lut, q.nlut, q.vmin, q.vmax);
             if (st == VR_OK) st = vr_set_camera(fc, q.view, q.proj, q.param, q.width, q.height);
             if (st == VR_OK) st = vr_set_render_params(fc, q.mode, q.step, q.ert_threshold);
+            if (st == VR_OK) st = vr_set_termination(fc, q.termination);
             if (st == VR_OK) st = check_ready(fc, cb);
             std::vector<int64_t> bricks;
             if (st == VR_OK && cb->streamed) {

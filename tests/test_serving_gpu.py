@@ -51,7 +51,11 @@ def _alone(ctx, r):
     ctx.set_transfer_function(r["lut"], *r["vrange"])
     ctx.set_camera_dict(r["cam"])
     ctx.set_render_params(r["mode"], r["step"], r["tau"])
-    return ctx.render_frame(r["cube"])
+    ctx.set_termination(r.get("termination", "segment"))
+    try:
+        return ctx.render_frame(r["cube"])
+    finally:
+        ctx.set_termination("segment")
 
 
 def test_each_result_is_the_same_alone_and_in_the_mix(world):
@@ -171,3 +175,22 @@ def test_soak_mixed_requests_with_evictions():
         for r in reqs:
             out = r["out"] if r["out"].is_cuda else r["out"].cuda()
             _same(dict(r, out=out), _alone(ctx, r))
+
+
+def test_global_termination_requests_in_the_mix(world):
+    """Requests that ask for global termination (occlusion skipping) run beside per-segment ones
+    (the same cubes, opaque and transparent tables); each result equals the frame alone with
+    its own termination scope."""
+    import torch
+    ctx, cubes = world
+    reqs = _requests({"pr1": cubes["pr1"], "b96": cubes["b96"]}, 40, 400.0, 41, "cuda")
+    opaque = synth.ramp_lut(alpha=1.0)
+    for i, r in enumerate(reqs):
+        if i % 2 == 0:
+            r["termination"] = "global"
+            r["lut"] = opaque
+    results, summary = ctx.serve(reqs, max_inflight=6)
+    torch.cuda.synchronize()
+    assert all(r["status"] == 0 for r in results), results
+    for r in reqs:
+        _same(r, _alone(ctx, r))
