@@ -464,6 +464,33 @@ def empty_space_leg(ctx, device, steps=16):
         res[name] = {"ms_per_frame": round(e0.elapsed_time(e1) / steps, 3),
                      "bricks_drawn_per_frame": round(st["bricks_drawn"] / steps, 1),
                      "Gsamples_per_s": round(st["samples"] / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2)}
+    # the GASS-scale configuration itself: the ramp table, FP32 / FP16 / BF16 bricks
+    frames = {}
+    ctx.set_transfer_function(synth.ramp_lut(), *cfg["vrange"])
+    for storage in ("f32", "f16", "bf16"):
+        ctx.set_bricking(cid, cfg["brick"], 1, storage)
+        for j in range(3):
+            ctx.set_camera_dict(cams[j])
+            ctx.render_frame(cid, out)
+        torch.cuda.synchronize()
+        ctx.reset_stats()
+        ctx.set_timing(True)
+        e0.record()
+        for k in range(steps):
+            ctx.set_camera_dict(cams[(3 + 4 * k) % 64])
+            ctx.render_frame(cid, out)
+        e1.record()
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        ctx.set_timing(False)
+        ms = e0.elapsed_time(e1) / steps
+        alg = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
+        rc_ms = st["ms_raycast"] / max(st["timed_frames"], 1)
+        frames[storage] = {"ms_per_frame": round(ms, 3),
+                           "Gsamples_per_s": round(st["samples"] / (ms * steps * 1e-3) / 1e9, 2),
+                           "raycast_GB_per_s": round(alg / (rc_ms * 1e-3) / 1e9, 1)}
+    res["gass_frames"] = dict(frames, table=f"ramp over [{cfg['vrange'][0]}, {cfg['vrange'][1]}], "
+                                            f"step {cfg['step']}, slice atlases")
     ctx.free_cube(cid)
     res["workload"] = (f"GASS-scale 2048x2048x1600, {cfg['W']}x{cfg['H']} orbit, step "
                        f"{cfg['step']}, table with zero opacity below 3.0 (noise sd 0.5)")

@@ -202,9 +202,9 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * A bricked cube is rebuilt.  Streamed and compressed cubes (bricks made resident in the brick
  * cache) take mask 1 or 9: with 9, each cache slot holding one of the cube's bricks also holds
  * its slice atlas (a 2D array sized for the cube's largest brick, packed from the slot on the
- * cache's stream when the brick becomes resident: as much device memory again as the slots
- * in use, outside cache_bytes).  The arrays of as many slots as the cube has bricks are made
- * by this call (and by vr_set_bricking of such a cube), so that frames only pack; the call
+ * cache's stream when the brick becomes resident).  The arrays of as many slots as the cube
+ * has bricks (at most all slots: up to as much device memory again as cache_bytes, outside
+ * it) are made by this call (and by vr_set_bricking of such a cube), so that frames only pack; the call
  * then sizes the brick cache (VR_ERR_OOM without one, or when an array cannot be had; a frame
  * that needs another array and cannot have it fails with VR_ERR_OOM too).
  * Mask 1..15 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
