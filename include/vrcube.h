@@ -197,7 +197,7 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * more copy of the pool in HBM).  Bit 3 also keeps a slice atlas of every brick: a 2D texture
  * array whose tiles are the brick's z-slices, from which a sample's 8 stencil voxels are read
  * by two texture gathers (exact texels; images identical to the linear copies).  When atlases
- * are kept every DVR and MIP frame reads them; the adjoint reads a linear copy.  An atlas must
+ * are kept every DVR and MIP frame reads them, and so does the adjoint's replay.  An atlas must
  * fit the device's 2D-gather size (32768 texels a side; 258^3 stored bricks need 8256 x 2322).
  * A bricked cube is rebuilt.  Streamed and compressed cubes (bricks made resident in the brick
  * cache) take mask 1 or 9: with 9, each cache slot holding one of the cube's bricks also holds

@@ -300,12 +300,16 @@ __device__ __forceinline__ void dvr_sample(const void *src, const Strides &t, in
                                            float scale, float x, float y, float z, float vmin,
                                            float inv_range, float lutmax, int lmax,
                                            const float4 *s_lut, const unsigned char *chmask,
-                                           int org_z, int nz, float vcode, DvrSample &o) {
+                                           int org_z, int nz, float vcode, DvrSample &o,
+                                           const Atlas *atl = nullptr) {
     Cell c;
     cell_of(x, y, z, mx, my, mz, c);
     o.ix = c.ix; o.iy = c.iy; o.iz = c.iz;
     float v[8];
-    fetch8<S>(src, c.ix * t.x + c.iy * t.y + c.iz * t.z, t, v);
+    if (atl)                          // the same texels from the brick's slice atlas
+        fetch8_atlas<S>(*atl, c.ix, c.iy, c.iz, v);
+    else
+        fetch8<S>(src, c.ix * t.x + c.iy * t.y + c.iz * t.z, t, v);
     if (chmask) mask_channels(v, c.iz, org_z, nz, chmask, vcode);
     interp_tf(v, c, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, o);
 }
@@ -808,6 +812,9 @@ __device__ __forceinline__ void flush_voxel_grads(float *__restrict__ gvox, cons
 // cube's voxels when the ray leaves the cell (ghost copies map back to their source voxel); a
 // step into an adjacent cell keeps the shared face's 4 sums (before: 8 atomics per sample).
 // Bounded to 4 CTAs per SM (64 registers, a few spilled; 80 unbounded give 3 CTAs, 8 % slower).
+// ATLAS: the replay reads the stencils from the bricks' slice atlases (the forward's texels)
+// instead of the linear copy.
+template <bool ATLAS>
 __global__ void __launch_bounds__(256, VR_ADJ_MIN_BLOCKS)
 k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const float *__restrict__ pool,
@@ -853,13 +860,14 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
             // voxel gradients of the ray's current cell, added to the cube when the ray leaves it
             float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             int ccx = -4, ccy = -4, ccz = -4;
+            const Atlas atl{ATLAS ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
             for (int j = 0; j < n; ++j) {
                 const float tj = __fmul_rn((float)j, fc.step);
                 DvrSample sm;
                 dvr_sample<0>(src, st, mx, my, mz, 1.0f, __fmaf_rn(tj, d[0], qx),
                               __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz), fc.vmin,
                               fc.inv_range, fc.lutmax, fc.nlut - 2, s_lut, fc.chmask, b.org[2],
-                              fc.nz, fc.vmin, sm);
+                              fc.nz, fc.vmin, sm, ATLAS ? &atl : nullptr);
                 const float Tb = T;
                 over(sm, c0, c1, c2, T);
                 const bool last = (T <= fc.thr) || (j == n - 1);
@@ -1075,8 +1083,11 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     if (nitems <= 0) return cudaSuccess;
     static std::atomic<bool> attr{false};
     if (!attr.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(48 * kMaxLut + 64));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(48 * kMaxLut + 64));
         if (e != cudaSuccess) return e;
         attr.store(true, std::memory_order_release);
     }
@@ -1086,7 +1097,10 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     const size_t per_copy = 16 * (size_t)fc.nlut + 64;
     while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * per_copy > ((size_t)VR_ADJ_SMEM_KB << 10)) ncopies >>= 1;
     const size_t smem = 32 * (size_t)fc.nlut + ncopies * per_copy;
-    k_adjoint<<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
+    if (fc.fetch == 2)
+        k_adjoint<true><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
+    else
+        k_adjoint<false><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
     return cudaGetLastError();
 }
 
