@@ -305,8 +305,10 @@ int vr_render_frame_noalloc(vr_ctx *ctx, int cube_id, float *out, void *cuda_str
  * grad_out: W*H*4 floats dL/d(output RGBA), device memory.
  * grad_lut: n*4 floats, device memory, overwritten with dL/d(table).
  * grad_voxels: nx*ny*nz floats, device memory, dL/d(voxel) ADDED to its contents (NULL: skip).
- * The forward fragments are recomputed; each ray segment is then replayed front to back from
- * its stored final colour and transmittance (no per-sample state is kept).  The early
+ * The forward fragments are those of the last vr_render_frame when no call that can change a
+ * frame (cube, bricking, table, camera, parameters, termination, mask, window) came between
+ * it and this call, else they are recomputed; each ray segment is then replayed front to back
+ * from its stored final colour and transmittance (no per-sample state is kept).  The early
  * termination stops of the forward pass are held fixed.  Ordered on `cuda_stream`.
  * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_UNSUPPORTED (MIP or 16-bit
  * bricks), VR_ERR_OOM, VR_ERR_CUDA. */

@@ -823,6 +823,7 @@ void vr_destroy(vr_ctx *c) {
 
 int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz, int where,
                  const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !voxels || !cube_id) return arg_fail("null argument");
     if (dtype != VR_F32) return arg_fail("dtype must be VR_F32");
     if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
@@ -864,6 +865,7 @@ int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t n
 }
 
 int vr_load_cube_procedural(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int *cube_id) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !cube_id) return arg_fail("null argument");
     if (nx <= 0 || ny <= 0 || nz <= 0) return arg_fail("non-positive size");
     if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return arg_fail("size too large");
@@ -887,6 +889,7 @@ int vr_set_fault_injection(vr_ctx *c, int kind, int64_t after) {
 }
 
 int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *stream) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !voxels) return arg_fail("null argument");
     if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
     Cube *cb = find_cube(c, cube_id);
@@ -904,6 +907,7 @@ int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *
 }
 
 int vr_free_cube(vr_ctx *c, int cube_id) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -940,6 +944,7 @@ int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
 }
 
 int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, int storage) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1018,6 +1023,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
 }
 
 int vr_compress_cube(vr_ctx *c, int cube_id) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1078,6 +1084,7 @@ int vr_wavelet_store(vr_ctx *c, int cube_id, void *dst, size_t *bytes) {
 }
 
 int vr_set_termination(vr_ctx *c, int mode) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (mode != VR_TERM_SEGMENT && mode != VR_TERM_GLOBAL) return arg_fail("termination must be VR_TERM_SEGMENT or VR_TERM_GLOBAL");
     c->term = mode;
@@ -1092,6 +1099,7 @@ int vr_set_host_output_async(vr_ctx *c, int async) {
 }
 
 int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1112,6 +1120,7 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
 }
 
 int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !rgba) return arg_fail("null argument");
     if (n < 2 || n > kMaxLut) return arg_fail("table size must be 2..4096");
     if (!(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax)) return arg_fail("need vmax > vmin");
@@ -1126,6 +1135,7 @@ int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, fl
 }
 
 int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int width, int height) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !view) return arg_fail("null argument");
     if (proj != VR_ORTHO && proj != VR_PERSP) return arg_fail("bad projection");
     if (width < 1 || height < 1 || width > 16384 || height > 16384) return arg_fail("bad frame size");
@@ -1160,6 +1170,7 @@ int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int wi
 }
 
 int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (mode != VR_DVR && mode != VR_MIP) return arg_fail("bad mode");
     if (!(step > 0.0f) || !std::isfinite(step)) return arg_fail("step must be > 0");
@@ -1171,6 +1182,7 @@ int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
 }
 
 int vr_set_channel_mask(vr_ctx *c, const unsigned char *mask, int64_t n) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (!mask || n == 0) {
         c->chmask.clear();
@@ -1183,6 +1195,7 @@ int vr_set_channel_mask(vr_ctx *c, const unsigned char *mask, int64_t n) {
 }
 
 int vr_set_window(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (!lo || !hi) {
         c->has_window = false;
@@ -1202,6 +1215,7 @@ int vr_set_timing(vr_ctx *c, int enable) {
 }
 
 int vr_set_full_rect(vr_ctx *c, int full) {
+    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     c->full_rect = full != 0;
     return VR_OK;
@@ -1313,6 +1327,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
     const size_t opix = (size_t)fc.cam.W * fc.cam.H;
     const size_t fbytes = (size_t)wl.frag_px * (c->mode == VR_DVR ? sizeof(float4) : sizeof(float));
+    c->frag_valid = false;
     if ((rc = ensure(c->d_frags, std::max<size_t>(fbytes, 16), c)) != VR_OK) return rc;
     const size_t ofl = opix * (c->mode == VR_DVR ? 4 : 1);
     float *dst = out;
@@ -1329,6 +1344,11 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
     if (ev[1]) CK(cudaEventRecord(ev[1], s));
     CK(launch_raycast(fc, d_lut, d_db, d_items, (int)wl.items.size(), cb->d_pool, c->d_frags.p, c->d_ctr, s));
+    if (c->mode == VR_DVR) {          // these fragments serve a backward pass of the same frame
+        c->frag_valid = true;
+        c->frag_cube = cb->id;
+        c->frag_gen = c->state_gen;
+    }
     if (ev[2]) CK(cudaEventRecord(ev[2], s));
     CK(launch_composite(fc, d_db, d_ts, d_tl, c->d_frags.p, dst, s));
     if (ev[3]) CK(cudaEventRecord(ev[3], s));
@@ -1382,8 +1402,13 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     if ((rc = stage_frame(c, cb, wl, s, nullptr)) != VR_OK) return rc;
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
     const size_t nfr = (size_t)std::max<long long>(wl.frag_px, 1);
+    const char *frags_before = c->d_frags.p;
     if ((rc = ensure(c->d_frags, nfr * sizeof(float4), c)) != VR_OK) return rc;
     if ((rc = ensure(c->d_gfrag, nfr, c)) != VR_OK) return rc;
+    // the last frame's fragments are this frame's when nothing that changes a frame was called
+    // since and no other frame wrote them (the common render-then-backward step)
+    const bool reuse = c->frag_valid && c->frag_cube == cb->id && c->frag_gen == c->state_gen &&
+                       c->d_frags.p == frags_before;
     const int nitems = (int)wl.items.size();
     if ((rc = ensure(c->d_gpart, (size_t)std::max(nitems, 1) * 4 * fc.nlut, c)) != VR_OK) return rc;
     char *d = c->d_stage.p;
@@ -1392,7 +1417,13 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
     const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
     const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
-    CK(launch_raycast(fc, d_lut, d_db, d_items, nitems, cb->d_pool, c->d_frags.p, c->d_ctr, s));
+    if (!reuse) {
+        c->frag_valid = false;
+        CK(launch_raycast(fc, d_lut, d_db, d_items, nitems, cb->d_pool, c->d_frags.p, c->d_ctr, s));
+        c->frag_valid = true;
+        c->frag_cube = cb->id;
+        c->frag_gen = c->state_gen;
+    }
     CK(launch_composite_backward(fc, d_db, d_ts, d_tl, reinterpret_cast<const float4 *>(c->d_frags.p),
                                  reinterpret_cast<const float4 *>(grad_out), c->d_gfrag.p, s));
     if (nitems > 0) {

@@ -135,6 +135,12 @@ struct vr_ctx {
     bool async_host_out = false;      // serving slots: no host sync after a VR_HOST copy
     int fault_kind = 0;               // host-side fault injection (tests)
     int64_t fault_after = -1;
+    // d_frags holds the DVR fragments of cube frag_cube for render state state_gen: every call
+    // that can change a frame bumps state_gen; every other write of d_frags clears frag_valid.
+    // vr_render_backward reuses them instead of ray-casting the frame again.
+    uint64_t state_gen = 0, frag_gen = 0;
+    int frag_cube = -1;
+    bool frag_valid = false;
 };
 
 namespace vrh {

@@ -790,6 +790,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     if ((rc = ensure(c->d_stage, wl.bytes, c)) != VR_OK) return rc;
     if (ev[0]) CK(cudaEventRecord(ev[0], s));
     const size_t felem = c->mode == VR_DVR ? sizeof(float4) : sizeof(float);
+    c->frag_valid = false;             // d_frags now holds this streamed frame's fragments
     if ((rc = ensure(c->d_frags, std::max<size_t>((size_t)wl.frag_px * felem, 16), c)) != VR_OK) return rc;
     const size_t opix = (size_t)fc.cam.W * fc.cam.H, ofl = opix * (c->mode == VR_DVR ? 4 : 1);
     const bool direct = out_where == VR_DEVICE && (reinterpret_cast<uintptr_t>(out) % 16 == 0);

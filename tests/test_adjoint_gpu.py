@@ -162,3 +162,34 @@ def test_adjoint_at_the_benchmark_size_on_sampled_pixels(ctx, orc):
         assert np.abs(gl - rl).max() <= 2e-4 * np.abs(rl).max(), np.abs(gl - rl).max()
         assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max(), np.abs(gv - rv).max()
     ctx.free_cube(cid)
+
+
+@pytest.mark.parametrize("layouts", [1, 9])
+def test_backward_reuses_the_frames_fragments_only_when_valid(ctx, layouts):
+    """vr_render_backward right after the frame it differentiates reuses that frame's fragments;
+    after any call that can change a frame, or another frame, it ray-casts again.  All three
+    orders give the same gradients (to the atomics' summation order)."""
+    import torch
+    rng, cube, lut, cam, cid = _setup(ctx, 21)
+    ctx.set_brick_layouts(cid, layouts)
+    other = synth.random_camera(rng, cube.shape, cam["W"], cam["H"])
+    g = torch.from_numpy(rng.standard_normal((cam["H"], cam["W"], 4)).astype(np.float32)).cuda()
+
+    def grads():
+        glut = torch.zeros((lut.shape[0], 4), device="cuda")
+        gvox = torch.zeros(cube.shape, device="cuda")
+        ctx.render_backward(cid, g, glut, gvox)
+        return glut.cpu().numpy(), gvox.cpu().numpy()
+
+    render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    a = grads()                                      # reuses the frame's fragments
+    ctx.set_camera_dict(cam)                         # a setter: the next backward ray-casts
+    b = grads()
+    render(ctx, cid, lut, (-3, 20), other, step=0.5, tau=0.99)
+    ctx.set_camera_dict(cam)                         # another frame's fragments are held
+    c = grads()
+    for x, y in ((a, b), (a, c)):
+        for u, v in zip(x, y):
+            assert np.allclose(u, v, rtol=1e-5, atol=1e-6 * np.abs(u).max())
+    assert np.abs(a[0]).max() > 0
+    ctx.free_cube(cid)
