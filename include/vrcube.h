@@ -101,6 +101,8 @@ void vr_destroy(vr_ctx *ctx);
  * sub_origin / sub_extent: optional (both NULL or both set) voxel box [origin, origin+extent)
  *   inside the given array; the loaded cube has the extent's dimensions.
  * cube_id: receives the new cube's id.  The voxels are copied; the cube has no bricking yet.
+ *   A device source is read after all work already queued on the device (the call
+ *   synchronises the device first), so writes still in flight on the caller's streams land.
  * Errors: VR_ERR_ARG (null pointers, non-positive sizes, box outside the array, dtype),
  *   VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_load_cube(vr_ctx *ctx, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz,

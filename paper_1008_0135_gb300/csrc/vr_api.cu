@@ -847,6 +847,13 @@ int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t n
     cudaError_t e = cudaMalloc(&cb->d_src, bytes);
     if (e != cudaSuccess) { delete cb; return cuda_fail(e, "cudaMalloc(cube)"); }
     cudaMemcpyKind kind = where == VR_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // a device source is read after all work already queued on the device (the caller's
+    // writes to it may still be in flight on any of its streams: the copy runs on the
+    // library's own non-blocking stream, which orders after none of them)
+    if (where == VR_DEVICE && (e = cudaDeviceSynchronize()) != cudaSuccess) {
+        free_cube(cb);
+        return cuda_fail(e, "cudaDeviceSynchronize (device cube source)");
+    }
     // 3D copy of the box: rows of ext[0] floats
     cudaMemcpy3DParms p{};
     p.srcPtr = make_cudaPitchedPtr(const_cast<void *>(voxels), sizeof(float) * nx, nx, ny);

@@ -598,3 +598,17 @@ def test_async_host_output_pipelined_frames(ctx, pr1):
 def _abi_status(ctx, flag):
     from paper_1008_0135_gb300 import _abi
     return _abi.lib().vr_set_host_output_async(ctx._h, flag)
+
+
+def test_device_cube_source_is_read_after_queued_writes(ctx):
+    """vr_load_cube from device memory sees every write already queued on the caller's stream
+    (the library copies on its own stream): a chain of in-place adds still running at the call
+    is complete in the loaded cube."""
+    import torch
+    x = torch.zeros((256, 512, 512), device="cuda")        # 256 MB: the adds take a while
+    for _ in range(24):
+        x.add_(1.0)
+    cid = ctx.load_cube(x)
+    vmin, vmax = ctx.compute_minmax(cid)
+    assert vmin == 24.0 and vmax == 24.0
+    ctx.free_cube(cid)
