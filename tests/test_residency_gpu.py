@@ -277,3 +277,36 @@ def test_async_host_output_of_streamed_frames():
                     assert np.array_equal(bufs[k].numpy().reshape(want.shape), want)
             finally:
                 ctx.set_host_output_async(False)
+
+
+@pytest.mark.parametrize("term", ["segment", "global"])
+def test_streamed_atlas_frames_with_mask_and_window(orc, term):
+    """A streamed cube with slot atlases, a spectral-channel mask and a render window, per-segment
+    and global termination, DVR and MIP: every frame equals the resident cube's of the same
+    voxels with the same settings, bit for bit."""
+    import paper_1008_0135_gb300 as P
+    vox = orc.proc_region(SEED, SMALL, (0, 0, 0), SMALL)
+    lut = synth.ramp_lut(alpha=0.6)
+    rng = np.random.default_rng(7)
+    mask = (rng.uniform(size=SMALL[2]) > 0.3).astype(np.uint8)
+    cams = [_cam(SMALL, W=96, H=80, seed=s) for s in (2, 9)]
+    with P.Context(0, cache_bytes=40 * F32_BRICK_BYTES) as ctx:
+        sid = ctx.load_cube_procedural(SEED, SMALL)
+        ctx.set_bricking(sid, BRICK, 1, "f32")
+        ctx.set_brick_layouts(sid, 9)
+        rid = ctx.load_cube(vox)
+        ctx.set_brick_layouts(rid, 9)
+        ctx.set_bricking(rid, BRICK, 1, "f32")
+        ctx.set_channel_mask(mask)
+        ctx.set_window((20, 31, 11), (260, 240, 250))
+        ctx.set_termination(term)
+        try:
+            for cam in cams:
+                for mode in ["dvr", "mip"]:
+                    a = render(ctx, sid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+                    b = render(ctx, rid, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.99)
+                    assert np.array_equal(a, b) and np.count_nonzero(a) > 0
+        finally:
+            ctx.set_termination("segment")
+            ctx.set_window()
+            ctx.set_channel_mask()
