@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick storage of the main leg (the headline line uses f32)")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
-    ap.add_argument("--leg", default=None, choices=["adjoint"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -203,7 +203,8 @@ def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
     """Occlusion skipping on the bench's cube with an opaque table (opacity = the ramp itself,
     so a ray through the noise is opaque after a few hundred samples): per-segment termination
     (every brick runs its own segment of a ray down to 1 - tau) against global termination
-    (bricks in front-to-back waves; a ray stops once the whole ray is opaque)."""
+    (one pass in which each ray walks the bricks front to back and stops once the whole ray is
+    opaque)."""
     lut = synth.ramp_lut(alpha=1.0)
     res = {"workload": cfg["name"] + f", {cfg['W']}x{cfg['H']} orbit, step {cfg['step']}, "
                        f"ramp table with opacity = ramp (x10 the bench table), ERT {cfg['tau']}"}
@@ -680,6 +681,29 @@ def main():
         torch.cuda.set_device(dist.local)
         ctx = P.Context(dist.local)
         print(json.dumps({"leg": "adjoint", **adjoint_leg(ctx, f"cuda:{dist.local}")}))
+        ctx.close()
+        return
+    if args.leg in ("occlusion", "compressed"):
+        import torch
+        import paper_1008_0135_gb300 as P
+        P.build()
+        torch.cuda.set_device(dist.local)
+        device = f"cuda:{dist.local}"
+        cube, cfg = make_cube(args.config, device)
+        ctx = P.Context(dist.local, cache_bytes=64 << 30)
+        cid = ctx.load_cube(cube)
+        cube_np = cube.cpu().numpy() if args.leg == "compressed" else None
+        del cube
+        torch.cuda.empty_cache()
+        ctx.set_brick_layouts(cid, 9)
+        ctx.set_bricking(cid, cfg["brick"], 1, "f32")
+        out = torch.empty((cfg["H"], cfg["W"], 4), dtype=torch.float32, device=device)
+        cams = cameras(cfg, cfg.get("n_views", 64))
+        if args.leg == "occlusion":
+            res = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
+        else:
+            res = compressed_leg(ctx, cid, cfg, cams, synth.ramp_lut(), cfg["vrange"], out, cube_np)
+        print(json.dumps({"leg": args.leg, **res}))
         ctx.close()
         return
     if args.impl == "reference":
