@@ -612,3 +612,36 @@ def test_device_cube_source_is_read_after_queued_writes(ctx):
     vmin, vmax = ctx.compute_minmax(cid)
     assert vmin == 24.0 and vmax == 24.0
     ctx.free_cube(cid)
+
+
+@pytest.mark.parametrize("layouts", [1, 9])
+def test_maximum_table_and_frame_sizes(ctx, orc, pr1, layouts):
+    """The largest table the library takes (4096 entries, two shared-memory arrays of 64 KB per
+    block) and the widest / tallest frames (16384 pixels) against the oracle; one past each
+    limit is refused."""
+    import paper_1008_0135_gb300 as P
+    cube, cid = pr1
+    ctx.set_brick_layouts(cid, layouts)
+    try:
+        # smooth across its 4096 entries: the 1e-4 bar covers FP32 rounding of the sampled value
+        # times the table's slope, and a random table of 4096 entries has slopes of ~180 colour
+        # units per data unit (measured 1.3e-4 there)
+        t = np.arange(4096) / 4095.0
+        lut = np.stack([0.5 + 0.5 * np.sin(6 * np.pi * t), t * t, 1.0 - t, 0.3 * t], 1).astype(np.float32)
+        cam = synth.pr1_camera(W=96, H=64)
+        g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+        ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=0.99, brick=(32, 32, 32))
+        compare_dvr(g, ref, flags, 0.99)
+        for W, H in ((16384, 2), (2, 16384)):
+            cam = synth.pr1_camera(W=W, H=H)
+            g = render(ctx, cid, synth.ramp_lut(), (-3, 20), cam, step=0.5, tau=0.99)
+            pix = np.arange(0, W * H, 97)
+            ref, flags, _ = orc.render(cube, synth.ramp_lut(), (-3, 20), cam, step=0.5, tau=0.99,
+                                       brick=(32, 32, 32), pix=pix)
+            compare_dvr(g[pix], ref, flags, 0.99)
+        with pytest.raises(P.VrError):
+            ctx.set_transfer_function(synth.random_lut(31, n=4097), -3.0, 20.0)
+        with pytest.raises(P.VrError):
+            ctx.set_camera_dict(synth.pr1_camera(W=16385, H=2))
+    finally:
+        ctx.set_brick_layouts(cid, 1)
