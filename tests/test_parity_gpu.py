@@ -645,3 +645,25 @@ def test_maximum_table_and_frame_sizes(ctx, orc, pr1, layouts):
             ctx.set_camera_dict(synth.pr1_camera(W=16385, H=2))
     finally:
         ctx.set_brick_layouts(cid, 1)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 17, 9), (13, 1, 1), (6, 1, 11)])
+def test_degenerate_cube_extents(ctx, orc, shape):
+    """Cubes one voxel thin along some axes (the stencil clamps to the edge there): DVR within
+    the bar and MIP bit-exact against the oracle, bricked into 1- to 4-voxel bricks."""
+    rng = np.random.default_rng(sum(shape))
+    nx, ny, nz = shape
+    cube = rng.uniform(-1, 3, (nz, ny, nx)).astype(np.float32)
+    lut = synth.random_lut(5, n=48, alpha_max=0.6)
+    for k in range(3):
+        cam = synth.random_camera(rng, shape, 24, 20)
+        brick = tuple(int(x) for x in rng.integers(1, 5, 3))
+        cid = ctx.load_cube(cube)
+        ctx.set_bricking(cid, brick, 1, "f32")
+        g = render(ctx, cid, lut, (-1, 3), cam, step=0.3, tau=0.99)
+        ref, flags, _ = orc.render(cube, lut, (-1, 3), cam, step=0.3, tau=0.99, brick=brick)
+        compare_dvr(g, ref, flags, 0.99)
+        m = render(ctx, cid, lut, (-1, 3), cam, mode="mip", step=0.3)
+        m32, _, _ = orc.render(cube, lut, (-1, 3), cam, mode="mip32", step=0.3, brick=brick)
+        assert np.array_equal(m, m32.astype(np.float32))
+        ctx.free_cube(cid)
