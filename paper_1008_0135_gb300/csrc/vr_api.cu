@@ -1238,7 +1238,8 @@ namespace vrh {
 static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
     FrameConsts fc = make_consts(c, cb);
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    FrameTiming tm(c);
+    cudaEvent_t *ev = tm.ev;
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     const FrameLayout fl = frame_layout(c, cb);
     const size_t nb = cb->tmpl.size();
@@ -1311,7 +1312,7 @@ static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStr
     }
     CK(cudaEventRecord(c->frame_done, s));
     c->frame_pending = true;
-    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    tm.queue();
     c->frames++;
     c->bricks_drawn += drawn;
     if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
@@ -1327,7 +1328,8 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     }
     if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) return render_global(c, cb, out, out_where, s);
     FrameConsts fc = make_consts(c, cb);
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    FrameTiming tm(c);
+    cudaEvent_t *ev = tm.ev;
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     WorkList wl;
     if ((rc = stage_frame(c, cb, wl, s, ev[0])) != VR_OK) return rc;
@@ -1365,7 +1367,7 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
     }
     CK(cudaEventRecord(c->frame_done, s));
     c->frame_pending = true;
-    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    tm.queue();
     c->frames++;
     c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)wl.db.size();

@@ -172,6 +172,26 @@ void eye_f32(const Cam &c, float o[3]);
 void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl);
 FrameConsts make_consts(vr_ctx *c, Cube *cb);
 int timing_events(vr_ctx *c, cudaEvent_t ev[4]);
+
+// The timing events of one frame (vr_set_timing): taken from the context's pool, handed to
+// the pending list once the frame is queued, and put back in the pool by the destructor when
+// the frame fails before that.
+struct FrameTiming {
+    vr_ctx *c;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool queued = false;
+    explicit FrameTiming(vr_ctx *ctx) : c(ctx) {}
+    FrameTiming(const FrameTiming &) = delete;
+    FrameTiming &operator=(const FrameTiming &) = delete;
+    ~FrameTiming() {
+        if (!queued && ev[0])
+            for (auto e : ev) c->ev_pool.push_back(e);
+    }
+    void queue() {
+        if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+        queued = true;
+    }
+};
 int collect_timing(vr_ctx *c);
 int stage_frame(vr_ctx *c, Cube *cb, WorkList &wl, cudaStream_t s, cudaEvent_t ev0);
 int check_ready(vr_ctx *c, Cube *cb);

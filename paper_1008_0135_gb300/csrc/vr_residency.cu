@@ -757,7 +757,8 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
     // timing (vr_set_timing): frame, ray casting (from the first chunk's residency to the last
     // chunk's ray-cast, so it includes waits for bricks made resident during the frame) and
     // compositing
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    FrameTiming tm(c);
+    cudaEvent_t *ev = tm.ev;
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     WorkList wl;
     build_worklist(c, cb, wl);
@@ -817,8 +818,6 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
             // leave nothing in flight that reads the staging of this abandoned frame
             cudaStreamSynchronize(k->copy);
             cudaStreamSynchronize(s);
-            if (ev[0])
-                for (auto e : ev) c->ev_pool.push_back(e);
             return rc;
         }
         CK(cudaEventRecord(k->copies_done, k->copy));
@@ -860,7 +859,7 @@ int render_streamed(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t
                            out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(c->frame_done, s));
     c->frame_pending = true;
-    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    tm.queue();
     c->frames++;
     c->fragments += wl.frag_px;
     c->bricks_drawn += (int64_t)nd;
@@ -887,7 +886,8 @@ int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaS
     const size_t nd = wl.db.size(), nb = cb->tmpl.size();
     if (nd > (size_t)k->nslots)
         return fail(VR_ERR_UNSUPPORTED, "global termination needs every brick of the frame in the brick cache at once");
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    FrameTiming tm(c);
+    cudaEvent_t *ev = tm.ev;
     if (c->timing && (rc = timing_events(c, ev)) != VR_OK) return rc;
     size_t off = 0;
     const size_t off_lut = off;
@@ -906,10 +906,7 @@ int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaS
     const int64_t chunk_id = ++k->chunk_counter;
     if ((rc = make_resident(c, cb, wl.db, 0, nd, chunk_id)) != VR_OK) {
         cudaStreamSynchronize(k->copy);
-        if (ev[0]) {
-            cudaStreamSynchronize(s);
-            for (auto e : ev) c->ev_pool.push_back(e);
-        }
+        if (ev[0]) cudaStreamSynchronize(s);   // its timing events go back to the pool
         return rc;
     }
     CK(cudaEventRecord(k->copies_done, k->copy));
@@ -973,7 +970,7 @@ int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaS
                            out_where == VR_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(c->frame_done, s));
     c->frame_pending = true;
-    if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});
+    tm.queue();
     c->frames++;
     c->bricks_drawn += (int64_t)nd;
     if (out_where == VR_HOST && !c->async_host_out) CK(cudaStreamSynchronize(s));
