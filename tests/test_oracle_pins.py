@@ -614,3 +614,205 @@ def test_wavelet_edge_blocks_repeat_the_border(orc):
     assert np.array_equal(orc.wavelet_encode(x), orc.wavelet_encode(pad))
     assert np.array_equal(orc.wavelet_decode(orc.wavelet_encode(x), x.shape),
                           orc.wavelet_decode(orc.wavelet_encode(pad), pad.shape)[:9, :11, :13])
+
+
+# ---------------------------------------------------------------------------------------------
+# 16-bit bricks: a sample reads the voxels as stored in the brick that owns it
+# ---------------------------------------------------------------------------------------------
+def _ceil_log2(m):
+    """ceil(log2 m) of a positive float from numpy's exact frexp (m = f 2^e, f in [0.5, 1))."""
+    f, e = np.frexp(np.float64(m))
+    return int(e) - 1 if f == 0.5 else int(e)
+
+
+def _round16(x32, quant):
+    """Round-to-nearest-even to binary16 (numpy cast) or bfloat16 (torch cast), as FP64."""
+    x32 = np.asarray(x32, np.float32)
+    if quant == "f16":
+        with np.errstate(over="ignore"):
+            return x32.astype(np.float16).astype(np.float64)
+    torch = pytest.importorskip("torch")
+    return torch.from_numpy(x32).to(torch.bfloat16).double().numpy()
+
+
+def _brick_exp_np(cube, b, cell, quant):
+    """The brick's scale exponent from numpy: max|v| over its core plus one ghost voxel per side
+    (clamped to the cube); FP16 maps it to at most 2^14, BF16 to at most 1."""
+    nz, ny, nx = cube.shape
+    lo = [max(0, cell[a] * b[a] - 1) for a in range(3)]
+    hi = [min((nx, ny, nz)[a], (cell[a] + 1) * b[a] + 1) for a in range(3)]
+    m = float(np.abs(cube[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]).max())
+    if m == 0.0:
+        return 0
+    return _ceil_log2(m) - 14 if quant == "f16" else _ceil_log2(m)
+
+
+def _composite_np(rgba, tau, seg):
+    """Front-to-back over with per-segment termination (seg: segment id of every sample)."""
+    thr = float(np.float32(1.0) - np.float32(min(tau, 1.0)))
+    C, T, Tseg, cur, stop = np.zeros(3), 1.0, 1.0, None, False
+    for m in range(len(rgba)):
+        if seg[m] != cur:
+            cur, Tseg, stop = seg[m], 1.0, False
+        if stop:
+            continue
+        a = rgba[m, 3]
+        C += T * a * rgba[m, :3]
+        T *= 1 - a
+        Tseg *= 1 - a
+        stop = Tseg <= thr
+    return np.array([*C, 1 - T])
+
+
+def _quant_brute(cube, lut, vrange, cam, step, tau, b, quant, owner_rule=True):
+    """Every pixel of the frame from scipy trilinear interpolation of a copy of the cube rounded
+    with the exponent of the brick that owns the sample (owner_rule) or, for comparison, with
+    each voxel's home-brick exponent."""
+    nz, ny, nx = cube.shape
+    shape = (nx, ny, nz)
+    nb = [-(-shape[a] // b[a]) for a in range(3)]
+    exps = {}
+    for cz in range(nb[2]):
+        for cy in range(nb[1]):
+            for cx in range(nb[0]):
+                exps[(cx, cy, cz)] = _brick_exp_np(cube, b, (cx, cy, cz), quant)
+    rounded = {}
+
+    def at_exp(e):
+        if e not in rounded:
+            rounded[e] = np.ldexp(_round16(np.ldexp(cube, -e).astype(np.float32), quant), e)
+        return rounded[e]
+
+    if not owner_rule:
+        z, y, x = np.meshgrid(np.arange(nz) // b[2], np.arange(ny) // b[1], np.arange(nx) // b[0],
+                              indexing="ij")
+        home = np.empty(cube.shape, np.float64)
+        for (cx, cy, cz), e in exps.items():
+            sel = (x == cx) & (y == cy) & (z == cz)
+            home[sel] = at_exp(e)[sel]
+    o, d, k = orc_rays_cached(cam, shape, step)
+    out = np.zeros((cam["W"] * cam["H"], 4))
+    for p in range(len(out)):
+        if k[p, 1] <= k[p, 0]:
+            continue
+        ks = np.arange(k[p, 0], k[p, 1])
+        own = ORC.sample_owners(shape, cam, p, step, b)
+        pos = o[p].astype(np.float64)[None, :] + (ks[:, None] * float(step)) * d[p].astype(np.float64)
+        coords = np.stack([pos[:, 2] - 0.5, pos[:, 1] - 0.5, pos[:, 0] - 0.5])
+        v = np.empty(len(ks))
+        for m in range(len(ks)):
+            src = at_exp(exps[tuple(int(c) for c in own[m])]) if owner_rule else home
+            v[m] = map_coordinates(src, coords[:, m:m + 1], order=1, mode="nearest")[0]
+        u = np.clip((v - vrange[0]) / (vrange[1] - vrange[0]), 0, 1) * (len(lut) - 1)
+        rgba = np.stack([np.interp(u, np.arange(len(lut)), lut[:, c].astype(np.float64))
+                         for c in range(4)], 1)
+        out[p] = _composite_np(rgba, tau, [tuple(r) for r in own])
+    return out
+
+
+ORC = None
+
+
+def orc_rays_cached(cam, shape, step):
+    return ORC.rays(cam, shape, step=step)
+
+
+@pytest.mark.parametrize("quant", ["f16", "bf16"])
+def test_16bit_samples_read_the_owner_bricks_copy(orc, quant):
+    """Reading 10 (16-bit storage): a sample reads the 8 voxels of its stencil as stored in the
+    brick that owns it, ghost copies included, each rounded with that brick's exponent.  Two
+    bricks along x; brick 1 holds one bright voxel away from the shared face, so its exponent
+    is 2 (FP16 codes of its faint voxels are subnormal), brick 0's is -29: the face voxels x = 7
+    and x = 8 round differently in the two copies.  The oracle equals the owner-rule reference
+    and (FP16) differs from the home-brick rule."""
+    global ORC
+    ORC = orc
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 16, 6, 5
+    cube = (rng.uniform(-3e-5, 3e-5, (nz, ny, nx))).astype(np.float32)
+    cube[2, 3, 13] = 60000.0
+    b = (8, 8, 8)
+    assert _brick_exp_np(cube, b, (1, 0, 0), "f16") == 2
+    assert _brick_exp_np(cube, b, (0, 0, 0), "f16") == -29
+    lut = synth.random_lut(4, n=24, alpha_max=0.3)
+    vr = (-2.0 ** -15, 2.0 ** -15)           # binary32 values (the table range is binary32)
+    e_home = e_owner = 0.0
+    for trial in range(3):
+        cam = synth.random_camera(rng, (nx, ny, nz), 12, 9)
+        out, flags, _ = orc.render(cube, lut, vr, cam, step=0.5, tau=0.97, brick=b, quant=quant)
+        ref = _quant_brute(cube, lut, vr, cam, 0.5, 0.97, b, quant)
+        ok = (flags & 1) == 0
+        assert ok.sum() > 40
+        e_owner = max(e_owner, float(np.abs(out[ok] - ref[ok]).max()))
+        if quant == "f16":
+            alt = _quant_brute(cube, lut, vr, cam, 0.5, 0.97, b, quant, owner_rule=False)
+            e_home = max(e_home, float(np.abs(out[ok] - alt[ok]).max()))
+    assert e_owner < 1e-12
+    if quant == "f16":
+        assert e_home > 1e-4       # the home-brick rule is a different image: the pin can tell
+
+
+# ---------------------------------------------------------------------------------------------
+# FP32-order MIP at non-zero fractions
+# ---------------------------------------------------------------------------------------------
+def test_mip32_single_sample_by_hand(orc):
+    """Reading 9: one sample at p = (1.25, 1.0, 1.25) of a 2x2x2 cube (fractions 0.75, 0.5, 0.75),
+    interpolated as a + f (b - a) along x, then y, then z, each operation rounded to binary32.
+    Values chosen so that other orders (z first, or b + (1 - f)(a - b)) round differently."""
+    cube = np.array([1.0 / 3, 7.1, -2.3, 1e3 + 1.0 / 7,
+                     0.3, -5.0 / 3, 11.0 / 13, 2.0 ** -9 + 3.0], np.float32)
+    c = cube.reshape(2, 2, 2)                       # [z][y][x]
+    view = synth.look_at((1.25, 1.0, -8.75), (1.25, 1.0, 0.0))
+    cam = dict(view=view, proj=0, param=1.0, W=1, H=1)
+    o, d, k = orc.rays(cam, (2, 2, 2), step=10.0)
+    assert o[0].tolist() == [1.25, 1.0, -8.75] and d[0].tolist() == [0.0, 0.0, 1.0]
+    assert k[0].tolist() == [1, 2]                  # t = 10: p = (1.25, 1.0, 1.25)
+    f32 = np.float32
+    fx, fy, fz = f32(0.75), f32(0.5), f32(0.75)
+
+    def lerp(a, b, f):
+        return f32(f32(a) + f32(f32(f) * f32(f32(b) - f32(a))))
+
+    x00 = lerp(c[0, 0, 0], c[0, 0, 1], fx)
+    x10 = lerp(c[0, 1, 0], c[0, 1, 1], fx)
+    x01 = lerp(c[1, 0, 0], c[1, 0, 1], fx)
+    x11 = lerp(c[1, 1, 0], c[1, 1, 1], fx)
+    expect = lerp(lerp(x00, x10, fy), lerp(x01, x11, fy), fz)
+    z_first = lerp(lerp(lerp(c[0, 0, 0], c[1, 0, 0], fz), lerp(c[0, 1, 0], c[1, 1, 0], fz), fy),
+                   lerp(lerp(c[0, 0, 1], c[1, 0, 1], fz), lerp(c[0, 1, 1], c[1, 1, 1], fz), fy), fx)
+
+    def lerp_rev(a, b, f):
+        return f32(f32(b) + f32(f32(f32(1) - f32(f)) * f32(f32(a) - f32(b))))
+
+    rev = lerp_rev(lerp_rev(lerp_rev(c[0, 0, 0], c[0, 0, 1], fx), lerp_rev(c[0, 1, 0], c[0, 1, 1], fx), fy),
+                   lerp_rev(lerp_rev(c[1, 0, 0], c[1, 0, 1], fx), lerp_rev(c[1, 1, 0], c[1, 1, 1], fx), fy), fz)
+    assert expect != z_first and expect != rev
+    m32, _, _ = orc.render(cube.reshape(2, 2, 2), synth.ramp_lut(), (-3, 20), cam, mode="mip32", step=10.0)
+    assert np.float32(m32[0]) == expect
+    # the FP64 MIP of the same sample: the trilinear weights written out
+    w = np.array([(1 - 0.75) * (1 - 0.5) * (1 - 0.75), 0.75 * 0.5 * 0.25, 0.25 * 0.5 * 0.25,
+                  0.75 * 0.5 * 0.25, 0.25 * 0.5 * 0.75, 0.75 * 0.5 * 0.75, 0.25 * 0.5 * 0.75,
+                  0.75 * 0.5 * 0.75])
+    w[1] = 0.75 * (1 - 0.5) * (1 - 0.75)
+    m64, _, _ = orc.render(cube.reshape(2, 2, 2), synth.ramp_lut(), (-3, 20), cam, mode="mip", step=10.0)
+    assert abs(m64[0] - float(w @ cube.astype(np.float64))) < 1e-12
+
+
+def test_mip32_equals_fp64_mip_to_rounding_at_random_views(orc):
+    """On random views every fraction is non-zero; the FP32-order MIP stays within FP32 rounding
+    of the FP64 MIP (a swapped weight or lerp would be off by O(1) of the data range)."""
+    rng = np.random.default_rng(31)
+    cube = rng.uniform(-1, 3, (11, 9, 13)).astype(np.float32)
+    shape = (13, 9, 11)
+    worst = 0.0
+    for _ in range(4):
+        cam = synth.random_camera(rng, shape, 16, 14)
+        step = float(rng.choice([0.37, 0.5, 0.71]))
+        m64, f, _ = orc.render(cube, synth.ramp_lut(), (-1, 3), cam, mode="mip", step=step, brick=(5, 4, 6))
+        m32, _, _ = orc.render(cube, synth.ramp_lut(), (-1, 3), cam, mode="mip32", step=step, brick=(5, 4, 6))
+        hit = (f & 2) == 0
+        assert hit.sum() > 40
+        worst = max(worst, float(np.abs(m32[hit] - m64[hit]).max()))
+    # positions rounded to binary32 (|p| < 40: 4e-6) times a slope below 4 per voxel, plus
+    # 7 lerps of values below 3 rounded to binary32
+    assert worst < 3e-5
