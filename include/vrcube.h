@@ -290,16 +290,22 @@ int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *c
  *   array that every GPU loading this library reserves until the process exits.  A frame whose
  *   scratch would exceed 64 MiB is rejected with VR_ERR_ARG (vr_last_error_message() gives the
  *   bytes needed); e.g. 512x512 frames of cubes with a few dozen bricks fit, 1024x1024 frames of
- *   a 12 GB cube do not.  The work-list is built in a static host arena as well.
- * Set-up: the first call on a device looks up that array's device address (cudaGetSymbolAddress
- *   with the device current), which may also load the library's GPU code on that device; make
+ *   a 12 GB cube do not.  The work-list is built in a static 64 MiB host arena, page-locked in
+ *   place (its own pages; nothing is allocated) so that its upload is asynchronous.
+ * Set-up: the first call in the process page-locks the host arena; the first call on a device
+ *   looks up that array's device address (cudaGetSymbolAddress with the device current), which
+ *   may also load the library's GPU code on that device, and creates one event there.  Make
  *   that first call before any stream capture.
  * Sharing: every call, from any context, uses the same array and leaves its contents behind;
  *   calls whose GPU work overlaps (e.g. on two streams without ordering between them) race on
  *   it and corrupt each other's frames.  Calls ordered on one stream are safe.  Host calls are
  *   serialised by a lock.
- * Returns when the work is queued on `cuda_stream`.  Errors: VR_ERR_ARG (null or misaligned
- * out, frame too large for the scratch), VR_ERR_NOT_FOUND, VR_ERR_STATE, VR_ERR_CUDA. */
+ * Returns when the work is queued on `cuda_stream`.  The host arena holds one work-list: a call
+ * first waits until the previous call's upload has run (that upload waits only for the work
+ * queued before it on its stream), at most 60 s (VR_ERR_TIMEOUT).  Errors: VR_ERR_ARG (null or
+ * misaligned out, frame too large for the scratch), VR_ERR_NOT_FOUND, VR_ERR_STATE,
+ * VR_ERR_UNSUPPORTED (streamed cubes, which need the brick cache; DVR with VR_TERM_GLOBAL),
+ * VR_ERR_TIMEOUT, VR_ERR_CUDA. */
 int vr_render_frame_noalloc(vr_ctx *ctx, int cube_id, float *out, void *cuda_stream);
 
 /* Gradient of a scalar image loss L with respect to the transfer-function table and the
@@ -316,6 +322,28 @@ int vr_render_frame_noalloc(vr_ctx *ctx, int cube_id, float *out, void *cuda_str
  * bricks), VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_render_backward(vr_ctx *ctx, int cube_id, const float *grad_out, float *grad_lut,
                        float *grad_voxels, void *cuda_stream);
+
+/* One view of a batch: the row-major world -> eye matrix, projection and its parameter (as in
+ * vr_set_camera; every view of a batch has the current camera's width and height). */
+typedef struct vr_view {
+    float view[16];
+    int proj;
+    float param;
+} vr_view;
+
+/* Gradient of a scalar loss over a batch of views (the fitting loop's render-many-views step)
+ * with respect to the table and the voxels, as vr_render_backward for each view in turn, with
+ * the table gradients of all views summed in FP64 on the device and rounded to FP32 once.
+ * views: n_views cameras; grad_out: n_views * H * W * 4 floats (view-major), device memory,
+ * 16-byte aligned; grad_lut: n*4 floats, device memory, overwritten with the batch's dL/d(table);
+ * grad_voxels: as for vr_render_backward (ADDED to; NULL: skip).  The views are replayed last to
+ * first, so the last view reuses the fragments of the last vr_render_frame when that frame was
+ * of the same camera and nothing else changed; the context's camera is the first view's
+ * afterwards.  Every view is validated before any work is queued.  Ordered on `cuda_stream`.
+ * Errors: as vr_render_backward. */
+int vr_render_backward_views(vr_ctx *ctx, int cube_id, int n_views, const vr_view *views,
+                             const float *grad_out, float *grad_lut, float *grad_voxels,
+                             void *cuda_stream);
 
 /* Spectral channels (Section 2.3: "enabling/disabling spectral channel(s), which are handled in
  * the same manner" as a colour-map change).  mask[z] = 0 switches channel z of the rendered

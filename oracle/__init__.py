@@ -38,7 +38,7 @@ class Args(C.Structure):
         ("quant", C.c_int32), ("ghost", C.c_int32), ("nthreads", C.c_int32),
         ("procedural", C.c_int32), ("proc_seed", C.c_uint64),
         ("channels", C.c_void_p), ("win_lo", C.c_int64 * 3), ("win_hi", C.c_int64 * 3),
-        ("term_global", C.c_int32),
+        ("term_global", C.c_int32), ("sig", C.c_void_p),
     ]
 
 
@@ -150,6 +150,24 @@ def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, q
     bit 1 no samples, bit 2 broken sample partition (never expected), bit 3 a composited DVR
     sample's table coordinate within 1e-4 of a table entry (the image's derivative with respect
     to that sample's value jumps there)."""
+    out, flags, ns, _ = _render(cube, lut, vrange, cam, mode, step, tau, brick, quant, pix, ghost,
+                                nthreads, channels, window, term, False)
+    return out, flags, ns
+
+
+def render_sig(cube, lut, vrange, cam, step=0.5, tau=0.99, brick=None, pix=None, channels=None,
+               window=None):
+    """DVR render plus, per pixel, a uint64 hash of its piecewise structure: the table interval
+    (or clamp side) of every composited sample and the number of composited samples.  Two inputs
+    with equal hashes at every pixel lie, almost surely, in one piece of the image as a function
+    of the table and the voxels (no table entry, clamp edge or termination stop between them).
+    Returns (out, flags, nsamples, sig)."""
+    return _render(cube, lut, vrange, cam, "dvr", step, tau, brick, "f32", pix, 1, 0, channels,
+                   window, "segment", True)
+
+
+def _render(cube, lut, vrange, cam, mode, step, tau, brick, quant, pix, ghost, nthreads, channels,
+            window, term, want_sig):
     a, keep = _args(cube, lut, vrange, cam, mode, step, tau, brick, quant, ghost, nthreads,
                     channels, window, term)
     pixa, pp = _pix(pix)
@@ -157,12 +175,15 @@ def render(cube, lut, vrange, cam, mode="dvr", step=0.5, tau=0.99, brick=None, q
     stride = 4 if mode == "dvr" else 1
     out = np.zeros((npix, stride), np.float64)
     flags = np.zeros(npix, np.uint8)
+    sig = np.zeros(npix, np.uint64) if want_sig else None
+    if want_sig:
+        a.sig = sig.ctypes.data
     ns = C.c_int64(0)
     rc = lib().orc_render(C.byref(a), pp, npix, out.ctypes.data, flags.ctypes.data, C.byref(ns))
     if rc != 0:
         raise ValueError(f"orc_render failed ({rc})")
     del keep
-    return (out if stride == 4 else out[:, 0]), flags, int(ns.value)
+    return (out if stride == 4 else out[:, 0]), flags, int(ns.value), sig
 
 
 def proc_region(seed, shape_xyz, lo, dim):

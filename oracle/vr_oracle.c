@@ -59,6 +59,12 @@ typedef struct {
     const uint8_t *channels;        /* per spectral channel z: 0 = disabled (NULL: all enabled) */
     int64_t win_lo[3], win_hi[3];   /* render window [lo, hi) in voxels (hi <= lo: whole cube) */
     int32_t term_global;            /* DVR early termination: 0 per brick segment, 1 whole ray */
+    uint64_t *sig;                  /* DVR, optional (NULL: none): per listed pixel, a hash of its
+                                       piecewise structure -- for every composited sample, the
+                                       table interval or the clamp side its value falls in, and
+                                       the number of composited samples (so the termination
+                                       stops) -- equal for two inputs only if, almost surely,
+                                       no piece boundary lies between them */
 } orc_args;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -537,7 +543,8 @@ enum { FLAG_ERT_FRAGILE = 1, FLAG_NO_SAMPLES = 2, FLAG_PARTITION_ERROR = 4, FLAG
 /* Traces one pixel.  If keep != NULL, the composited samples are stored there (capacity cap). */
 static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, int64_t pix,
                        int64_t *buf, double out[4], uint8_t *flag, int64_t *ns,
-                       smp *keep, int64_t cap, int64_t *nkeep) {
+                       smp *keep, int64_t cap, int64_t *nkeep, uint64_t *sig) {
+    uint64_t h = 0xCBF29CE484222325ULL;     /* FNV-1a over the pieces of the composited samples */
     rayinfo r;
     *flag = 0; *ns = 0;
     if (nkeep) *nkeep = 0;
@@ -598,6 +605,11 @@ static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, i
         Tseg *= (1.0 - al);
         ++*ns;
         if (keep && *nkeep < cap) keep[(*nkeep)++] = s;
+        if (sig) {
+            double u = (s.tri.v - (double)a->vmin) / ((double)a->vmax - (double)a->vmin);
+            uint64_t piece = u <= 0.0 ? 0 : (u >= 1.0 ? (uint64_t)a->nlut : (uint64_t)s.tf.i + 1);
+            h = (h ^ piece) * 0x100000001B3ULL;
+        }
         {
             double xr = (s.tri.v - (double)a->vmin) / ((double)a->vmax - (double)a->vmin) * (double)(a->nlut - 1);
             if (xr > -0.5 && xr < (double)a->nlut - 0.5 && fabs(xr - nearbyint(xr)) < TABLE_KINK_BAND)
@@ -607,6 +619,7 @@ static int pixel_trace(const orc_args *a, const cam32 *c, const int32_t *exps, i
         if (Tseg <= thr) stopped = 1;
     }
     if (*ns == 0) *flag |= FLAG_NO_SAMPLES;
+    if (sig) *sig = (h ^ (uint64_t)*ns) * 0x100000001B3ULL;
     out[0] = C[0]; out[1] = C[1]; out[2] = C[2]; out[3] = 1.0 - T;
     return 0;
 }
@@ -657,7 +670,8 @@ int orc_render(const orc_args *a, const int64_t *pix, int64_t npix, double *out,
         for (int64_t q = 0; q < npix; ++q) {
             int64_t p = pix ? pix[q] : q;
             int64_t ns;
-            pixel_trace(a, &c, exps, p, buf, out + q * stride, flags + q, &ns, NULL, 0, NULL);
+            pixel_trace(a, &c, exps, p, buf, out + q * stride, flags + q, &ns, NULL, 0, NULL,
+                        a->sig ? a->sig + q : NULL);
             total += ns;
         }
         free(buf);
@@ -688,7 +702,7 @@ int orc_render_grad(const orc_args *a, const int64_t *pix, int64_t npix, const d
         double out[4];
         uint8_t flag;
         int64_t ns, nk;
-        pixel_trace(a, &c, NULL, p, buf, out, &flag, &ns, keep, cap, &nk);
+        pixel_trace(a, &c, NULL, p, buf, out, &flag, &ns, keep, cap, &nk, NULL);
         const double *g = gout + 4 * q;
         double T_final = 1.0 - out[3];
         double gT = -g[3];                  /* A = 1 - T_final */

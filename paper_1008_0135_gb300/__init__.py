@@ -267,6 +267,22 @@ class Context:
                                           grad_lut.data_ptr(), gv, _stream_handle(stream)),
                "vr_render_backward")
 
+    def render_backward_views(self, cube_id: int, cams, grad_out, grad_lut, grad_voxels=None, stream=None):
+        """Gradient over a batch of views (dicts with view, proj, param; the current camera's
+        size): grad_out (V, H, W, 4) CUDA tensor; grad_lut (n, 4) overwritten with the batch's
+        table gradient (summed over the views in FP64 by the library); grad_voxels added to."""
+        n = len(cams)
+        arr = (_abi.VrView * max(n, 1))()
+        for i, cam in enumerate(cams):
+            view = np.ascontiguousarray(cam["view"], dtype=np.float32).reshape(16)
+            for j in range(16):
+                arr[i].view[j] = float(view[j])
+            arr[i].proj, arr[i].param = int(cam["proj"]), float(cam["param"])
+        gv = grad_voxels.data_ptr() if grad_voxels is not None else None
+        _check(self._L.vr_render_backward_views(self._h, cube_id, n, arr, grad_out.data_ptr(),
+                                                grad_lut.data_ptr(), gv, _stream_handle(stream)),
+               "vr_render_backward_views")
+
     def serve(self, requests, max_inflight: int = 4):
         """Runs the continuous-batching request loop (vr_serve).  ``requests``: dicts with cube,
         cam (view/proj/param/W/H), mode, step, tau, lut (n x 4), vrange, arrival_ms, out (a

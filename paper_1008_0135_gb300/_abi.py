@@ -40,6 +40,10 @@ class VrRequestResult(C.Structure):
                 ("latency_ms", C.c_double)]
 
 
+class VrView(C.Structure):
+    _fields_ = [("view", C.c_float * 16), ("proj", C.c_int), ("param", C.c_float)]
+
+
 class VrServeConfig(C.Structure):
     _fields_ = [("max_inflight", C.c_int)]
 
@@ -73,6 +77,7 @@ SIGNATURES = {
     "vr_render_frame": (I, [VP, I, VP, I, VP]),
     "vr_render_frame_noalloc": (I, [VP, I, VP, VP]),
     "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),
+    "vr_render_backward_views": (I, [VP, I, I, P(VrView), VP, VP, VP, VP]),
     "vr_set_channel_mask": (I, [VP, VP, I64]),
     "vr_set_window": (I, [VP, P(I64), P(I64)]),
     "vr_set_timing": (I, [VP, I]),

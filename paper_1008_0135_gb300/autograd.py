@@ -2,8 +2,9 @@
 
 ``render_views`` renders a batch of views of one cube with a transfer-function table that may
 require gradients, and optionally with voxels that require gradients (they are copied into the
-cube's bricks before rendering).  Backward calls vr_render_backward once per view: the library
-replays every ray from its stored segment colour and transmittance (no per-sample storage).
+cube's bricks before rendering).  Backward is one vr_render_backward_views call: the library
+replays every ray of every view from its stored segment colour and transmittance (no per-sample
+storage) and sums the views' table gradients in FP64.
 """
 from __future__ import annotations
 
@@ -34,15 +35,12 @@ class _RenderViews(torch.autograd.Function):
         vctx.set_transfer_function(fctx.lut_host, fctx.vrange[0], fctx.vrange[1])
         vctx.set_render_params("dvr", fctx.step, fctx.tau)
         n = fctx.lut_host.shape[0]
-        glut = torch.zeros((n, 4), dtype=torch.float32, device=fctx.dev)
-        total = torch.zeros_like(glut)
+        glut = torch.empty((n, 4), dtype=torch.float32, device=fctx.dev)
         need_vox = fctx.needs_input_grad[1] and fctx.vox_shape is not None
         gvox = torch.zeros(fctx.vox_shape, dtype=torch.float32, device=fctx.dev) if need_vox else None
-        for v, cam in enumerate(fctx.cams):
-            vctx.set_camera_dict(cam)
-            vctx.render_backward(fctx.cube_id, gout[v].contiguous(), glut, gvox)
-            total += glut
-        glut_out = total if fctx.needs_input_grad[0] else None
+        vctx.set_camera_dict(fctx.cams[-1])      # the batch's frame size; last view's fragments reused
+        vctx.render_backward_views(fctx.cube_id, fctx.cams, gout.contiguous(), glut, gvox)
+        glut_out = glut if fctx.needs_input_grad[0] else None
         return glut_out, gvox, None, None, None, None, None, None
 
 

@@ -5,6 +5,7 @@
 // view matrices); Section 2.4 the rendering rectangle of each part (here: the screen bounding
 // box of each brick's projected corners); Section 2.5 the depth-ordered compositing.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +13,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "vr_host.h"
@@ -298,6 +300,103 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     return fc;
 }
 
+// Camera constants of a view (validated): rotation rows and translation from the row-major
+// world -> eye matrix, half extents (orthographic) or tan(fov / 2) (perspective), each rounded
+// to binary32 once.
+int make_cam(const float view[16], int proj, float param, int width, int height, Cam &cam) {
+    if (proj != VR_ORTHO && proj != VR_PERSP) return arg_fail("bad projection");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384) return arg_fail("bad frame size");
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(view[i])) return arg_fail("non-finite view matrix");
+    if (!(param > 0.0f) || !std::isfinite(param)) return arg_fail("bad projection parameter");
+    if (proj == VR_PERSP && !(param < 3.14159f)) return arg_fail("fov must be < pi");
+    // the rotation part must be (close to) orthonormal: rays need a unit direction
+    double det = (double)view[0] * ((double)view[5] * view[10] - (double)view[6] * view[9]) -
+                 (double)view[1] * ((double)view[4] * view[10] - (double)view[6] * view[8]) +
+                 (double)view[2] * ((double)view[4] * view[9] - (double)view[5] * view[8]);
+    if (!(det > 0.5 && det < 2.0)) return arg_fail("view rotation is not a rotation");
+    std::memset(&cam, 0, sizeof(cam));
+    for (int r = 0; r < 3; ++r) {
+        for (int k = 0; k < 3; ++k) cam.R[3 * r + k] = view[4 * r + k];
+        cam.t[r] = view[4 * r + 3];
+    }
+    cam.proj = proj;
+    cam.W = width;
+    cam.H = height;
+    volatile float aspect = (float)width / (float)height;
+    volatile float hh = param * 0.5f;
+    volatile float hw = hh * aspect;
+    cam.half_h = hh;
+    cam.half_w = hw;
+    volatile float th = (float)std::tan((double)param * 0.5);
+    volatile float thw = th * aspect;
+    cam.th = th;
+    cam.th_w = thw;
+    return VR_OK;
+}
+
+// Preconditions of the gradient calls: DVR, resident FP32 bricks, per-segment termination.
+int backward_ready(vr_ctx *c, Cube *cb) {
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if (c->mode != VR_DVR || cb->storage != VR_F32 || cb->streamed)
+        return fail(VR_ERR_UNSUPPORTED, "backward needs DVR mode and resident FP32 bricks");
+    if (c->term != VR_TERM_SEGMENT)
+        return fail(VR_ERR_UNSUPPORTED, "backward replays per-segment termination (VR_TERM_SEGMENT)");
+    return VR_OK;
+}
+
+// The adjoint of the current camera's frame: composite backward, ray replay, and the table
+// gradient either reduced into grad_lut (FP64 sum rounded once) or, with acc, added to the FP64
+// accumulator of a batch of views (zeroed first when `first`).
+int backward_view(vr_ctx *c, Cube *cb, const float *grad_out, float *grad_lut, double *acc, bool first,
+                  float *grad_voxels, cudaStream_t s) {
+    int rc;
+    FrameConsts fc = make_consts(c, cb);
+    WorkList wl;
+    if ((rc = stage_frame(c, cb, wl, s, nullptr)) != VR_OK) return rc;
+    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
+    const size_t nfr = (size_t)std::max<long long>(wl.frag_px, 1);
+    const char *frags_before = c->d_frags.p;
+    if ((rc = ensure(c->d_frags, nfr * sizeof(float4), c)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_gfrag, nfr, c)) != VR_OK) return rc;
+    // the last frame's fragments are this frame's when nothing that changes a frame was called
+    // since and no other frame wrote them (the common render-then-backward step)
+    const bool reuse = c->frag_valid && c->frag_cube == cb->id && c->frag_gen == c->state_gen &&
+                       c->d_frags.p == frags_before;
+    const int nitems = (int)wl.items.size();
+    if ((rc = ensure(c->d_gpart, (size_t)std::max(nitems, 1) * 4 * fc.nlut, c)) != VR_OK) return rc;
+    char *d = c->d_stage.p;
+    const float4 *d_lut = reinterpret_cast<const float4 *>(d + wl.off_lut);
+    const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(d + wl.off_db);
+    const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
+    const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
+    const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
+    if (!reuse) {
+        c->frag_valid = false;
+        CK(launch_raycast(fc, d_lut, d_db, d_items, nitems, cb->d_pool, c->d_frags.p, c->d_ctr, s));
+        c->frag_valid = true;
+        c->frag_cube = cb->id;
+        c->frag_gen = c->state_gen;
+    }
+    CK(launch_composite_backward(fc, d_db, d_ts, d_tl, reinterpret_cast<const float4 *>(c->d_frags.p),
+                                 reinterpret_cast<const float4 *>(grad_out), c->d_gfrag.p, s));
+    if (nitems > 0)
+        CK(launch_adjoint(fc, d_lut, d_db, d_items, nitems, static_cast<const float *>(cb->d_pool),
+                          reinterpret_cast<const float4 *>(c->d_frags.p), c->d_gfrag.p, c->d_gpart.p,
+                          grad_voxels, s));
+    if (acc) {
+        CK(launch_lut_grad_accumulate(c->d_gpart.p, nitems, fc.nlut, acc, first, s));
+    } else if (nitems > 0) {
+        CK(launch_lut_grad_reduce(c->d_gpart.p, nitems, fc.nlut, grad_lut, s));
+    } else {
+        CK(cudaMemsetAsync(grad_lut, 0, sizeof(float) * 4 * fc.nlut, s));
+    }
+    CK(cudaEventRecord(c->frame_done, s));
+    c->frame_pending = true;
+    return VR_OK;
+}
+
 int timing_events(vr_ctx *c, cudaEvent_t ev[4]) {
     for (int i = 0; i < 4; ++i) {
         if (c->ev_pool.empty()) {
@@ -563,25 +662,53 @@ constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;    // 64 MiB per devic
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Host arena the work-list is built in (static storage: no heap use on this path).  Its
-// contents are consumed by cudaMemcpyAsync from pageable memory, which copies them out before
-// returning, so the arena can be reused by the next call.
-alignas(256) unsigned char g_noalloc_host[kNoAllocScratchBytes];
+// Host arena the work-list is built in (static storage: no heap use on this path).  It is
+// page-locked once (cudaHostRegister: the arena's own pages, nothing allocated), so the
+// work-list upload is an asynchronous copy that waits for nothing queued before it.  The arena
+// holds one work-list: a call first waits (bounded) until the previous call's upload has read
+// it; the event recorded after each upload lives one per device (an event belongs to a device).
+alignas(4096) unsigned char g_noalloc_host[kNoAllocScratchBytes];
 std::mutex g_noalloc_mu;
-void *g_noalloc_dev[256] = {nullptr};                          // device address, per device
+bool g_noalloc_pinned = false;
+constexpr int kNoAllocDevices = 256;
+void *g_noalloc_dev[kNoAllocDevices] = {nullptr};              // device address, per device
+cudaEvent_t g_noalloc_up[kNoAllocDevices] = {nullptr};         // "arena read", per device
+int g_noalloc_last = -1;                                       // device of the last upload
 
-// Device address of g_noalloc_scratch on the current device.  In host code the symbol's name
-// is only a stand-in; its address must be queried per device with that device current.
+// Device address of g_noalloc_scratch on the current device, and that device's upload event.
+// In host code the symbol's name is only a stand-in; its address must be queried per device
+// with that device current.
 int noalloc_scratch(int device, unsigned char **ptr) {
-    if (device < 0 || device >= 256) return arg_fail("device ordinal out of range");
+    if (device < 0 || device >= kNoAllocDevices) return arg_fail("device ordinal out of range");
+    if (!g_noalloc_pinned) {
+        cudaError_t e = cudaHostRegister(g_noalloc_host, kNoAllocScratchBytes, cudaHostRegisterPortable);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaHostRegister(no-allocation host arena)");
+        g_noalloc_pinned = true;
+    }
     if (!g_noalloc_dev[device]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        e = cudaEventCreateWithFlags(&g_noalloc_up[device], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreateWithFlags");
         g_noalloc_dev[device] = p;
     }
     *ptr = static_cast<unsigned char *>(g_noalloc_dev[device]);
     return VR_OK;
+}
+
+// Waits until the last upload has read the host arena (60 s bound, VR_ERR_TIMEOUT).
+int noalloc_arena_free() {
+    if (g_noalloc_last < 0) return VR_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t r = cudaEventQuery(g_noalloc_up[g_noalloc_last]);
+        if (r == cudaSuccess) return VR_OK;
+        if (r != cudaErrorNotReady) return cuda_fail(r, "cudaEventQuery");
+        if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > 60.0)
+            return fail(VR_ERR_TIMEOUT, "the previous work-list upload did not run within 60 s");
+        std::this_thread::yield();
+    }
 }
 
 struct StaticLayout {
@@ -1126,13 +1253,19 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     return vr_set_bricking(c, cube_id, cb->B[0], cb->B[1], cb->B[2], cb->ghost, cb->storage);
 }
 
+// The table, camera and parameter setters count a change of the frame (state_gen, which the
+// gradient calls compare before reusing a frame's fragments) only when the value changes:
+// setting the same table, camera or parameters again leaves the last frame's fragments valid.
 int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
-    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !rgba) return arg_fail("null argument");
     if (n < 2 || n > kMaxLut) return arg_fail("table size must be 2..4096");
     if (!(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax)) return arg_fail("need vmax > vmin");
     for (int i = 0; i < 4 * n; ++i)
         if (!std::isfinite(rgba[i])) return arg_fail("non-finite table entry");
+    const bool same = c->tf_set && (int)c->lut.size() == n && c->vmin == vmin && c->vmax == vmax &&
+                      std::memcmp(c->lut.data(), rgba, sizeof(float) * 4 * n) == 0;
+    if (same) return VR_OK;
+    c->state_gen++;
     c->lut.resize(n);
     std::memcpy(c->lut.data(), rgba, sizeof(float) * 4 * n);
     c->vmin = vmin;
@@ -1142,46 +1275,24 @@ int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, fl
 }
 
 int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int width, int height) {
-    if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !view) return arg_fail("null argument");
-    if (proj != VR_ORTHO && proj != VR_PERSP) return arg_fail("bad projection");
-    if (width < 1 || height < 1 || width > 16384 || height > 16384) return arg_fail("bad frame size");
-    for (int i = 0; i < 16; ++i)
-        if (!std::isfinite(view[i])) return arg_fail("non-finite view matrix");
-    if (!(param > 0.0f) || !std::isfinite(param)) return arg_fail("bad projection parameter");
-    if (proj == VR_PERSP && !(param < 3.14159f)) return arg_fail("fov must be < pi");
-    // the rotation part must be (close to) orthonormal: rays need a unit direction
-    double det = (double)view[0] * ((double)view[5] * view[10] - (double)view[6] * view[9]) -
-                 (double)view[1] * ((double)view[4] * view[10] - (double)view[6] * view[8]) +
-                 (double)view[2] * ((double)view[4] * view[9] - (double)view[5] * view[8]);
-    if (!(det > 0.5 && det < 2.0)) return arg_fail("view rotation is not a rotation");
-    Cam &cam = c->cam;
-    for (int r = 0; r < 3; ++r) {
-        for (int k = 0; k < 3; ++k) cam.R[3 * r + k] = view[4 * r + k];
-        cam.t[r] = view[4 * r + 3];
-    }
-    cam.proj = proj;
-    cam.W = width;
-    cam.H = height;
-    volatile float aspect = (float)width / (float)height;
-    volatile float hh = param * 0.5f;
-    volatile float hw = hh * aspect;
-    cam.half_h = hh;
-    cam.half_w = hw;
-    volatile float th = (float)std::tan((double)param * 0.5);
-    volatile float thw = th * aspect;
-    cam.th = th;
-    cam.th_w = thw;
+    Cam cam;
+    const int rc = make_cam(view, proj, param, width, height, cam);
+    if (rc != VR_OK) return rc;
+    if (c->cam_set && std::memcmp(&cam, &c->cam, sizeof(Cam)) == 0) return VR_OK;
+    c->state_gen++;
+    c->cam = cam;
     c->cam_set = true;
     return VR_OK;
 }
 
 int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
-    if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (mode != VR_DVR && mode != VR_MIP) return arg_fail("bad mode");
     if (!(step > 0.0f) || !std::isfinite(step)) return arg_fail("step must be > 0");
     if (!(tau > 0.0f) || std::isnan(tau)) return arg_fail("tau must be > 0");
+    if (c->mode == mode && c->step == step && c->tau == tau) return VR_OK;
+    c->state_gen++;
     c->mode = mode;
     c->step = step;
     c->tau = tau;
@@ -1395,56 +1506,45 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     if (!c || !grad_out || !grad_lut) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    int rc = check_ready(c, cb);
+    int rc = backward_ready(c, cb);
     if (rc) return rc;
-    if (c->mode != VR_DVR || cb->storage != VR_F32 || cb->streamed) {
-        g_last_error = "backward needs DVR mode and resident FP32 bricks";
-        return VR_ERR_UNSUPPORTED;
-    }
-    if (c->term != VR_TERM_SEGMENT)
-        return fail(VR_ERR_UNSUPPORTED, "backward replays per-segment termination (VR_TERM_SEGMENT)");
     if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
     if ((rc = set_dev(c)) != VR_OK) return rc;
+    return backward_view(c, cb, grad_out, grad_lut, nullptr, false, grad_voxels, static_cast<cudaStream_t>(stream));
+}
+
+int vr_render_backward_views(vr_ctx *c, int cube_id, int n_views, const vr_view *views, const float *grad_out,
+                             float *grad_lut, float *grad_voxels, void *stream) {
+    if (!c || !views || !grad_out || !grad_lut) return arg_fail("null argument");
+    if (n_views < 1) return arg_fail("n_views must be >= 1");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = backward_ready(c, cb);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(grad_out) % 16 != 0) return arg_fail("grad_out must be 16-byte aligned");
+    const int W = c->cam.W, H = c->cam.H;
+    Cam probe;
+    for (int v = 0; v < n_views; ++v)      // every view valid before any work is queued
+        if ((rc = make_cam(views[v].view, views[v].proj, views[v].param, W, H, probe)) != VR_OK) return rc;
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_gacc, (size_t)4 * c->lut.size(), c)) != VR_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    FrameConsts fc = make_consts(c, cb);
-    WorkList wl;
-    if ((rc = stage_frame(c, cb, wl, s, nullptr)) != VR_OK) return rc;
-    if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(c->d_stage.p + wl.off_mask);
-    const size_t nfr = (size_t)std::max<long long>(wl.frag_px, 1);
-    const char *frags_before = c->d_frags.p;
-    if ((rc = ensure(c->d_frags, nfr * sizeof(float4), c)) != VR_OK) return rc;
-    if ((rc = ensure(c->d_gfrag, nfr, c)) != VR_OK) return rc;
-    // the last frame's fragments are this frame's when nothing that changes a frame was called
-    // since and no other frame wrote them (the common render-then-backward step)
-    const bool reuse = c->frag_valid && c->frag_cube == cb->id && c->frag_gen == c->state_gen &&
-                       c->d_frags.p == frags_before;
-    const int nitems = (int)wl.items.size();
-    if ((rc = ensure(c->d_gpart, (size_t)std::max(nitems, 1) * 4 * fc.nlut, c)) != VR_OK) return rc;
-    char *d = c->d_stage.p;
-    const float4 *d_lut = reinterpret_cast<const float4 *>(d + wl.off_lut);
-    const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(d + wl.off_db);
-    const TileItem *d_items = reinterpret_cast<const TileItem *>(d + wl.off_items);
-    const int *d_ts = reinterpret_cast<const int *>(d + wl.off_ts);
-    const int *d_tl = reinterpret_cast<const int *>(d + wl.off_tl);
-    if (!reuse) {
-        c->frag_valid = false;
-        CK(launch_raycast(fc, d_lut, d_db, d_items, nitems, cb->d_pool, c->d_frags.p, c->d_ctr, s));
-        c->frag_valid = true;
-        c->frag_cube = cb->id;
-        c->frag_gen = c->state_gen;
+    const size_t per_view = (size_t)W * H * 4;
+    // last view first: its fragments are usually the last frame's (render the batch, then
+    // differentiate it), reused when the camera is unchanged
+    for (int v = n_views - 1; v >= 0; --v) {
+        Cam cam;
+        make_cam(views[v].view, views[v].proj, views[v].param, W, H, cam);
+        if (std::memcmp(&cam, &c->cam, sizeof(Cam)) != 0) {
+            c->state_gen++;
+            c->cam = cam;
+        }
+        rc = backward_view(c, cb, grad_out + (size_t)v * per_view, nullptr, c->d_gacc.p, v == n_views - 1,
+                           grad_voxels, s);
+        if (rc != VR_OK) return rc;
     }
-    CK(launch_composite_backward(fc, d_db, d_ts, d_tl, reinterpret_cast<const float4 *>(c->d_frags.p),
-                                 reinterpret_cast<const float4 *>(grad_out), c->d_gfrag.p, s));
-    if (nitems > 0) {
-        CK(launch_adjoint(fc, d_lut, d_db, d_items, nitems, static_cast<const float *>(cb->d_pool),
-                          reinterpret_cast<const float4 *>(c->d_frags.p), c->d_gfrag.p, c->d_gpart.p,
-                          grad_voxels, s));
-        CK(launch_lut_grad_reduce(c->d_gpart.p, nitems, fc.nlut, grad_lut, s));
-    } else {
-        CK(cudaMemsetAsync(grad_lut, 0, sizeof(float) * 4 * fc.nlut, s));
-    }
+    CK(launch_lut_grad_store(c->d_gacc.p, (int)c->lut.size(), grad_lut, s));
     CK(cudaEventRecord(c->frame_done, s));
-    c->frame_pending = true;
     return VR_OK;
 }
 
@@ -1532,11 +1632,14 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     FrameConsts fc = make_consts(c, cb);
     const size_t frag_elem = c->mode == VR_DVR ? sizeof(float4) : sizeof(float);
     StaticLayout L{};
+    if ((rc = noalloc_arena_free()) != VR_OK) return rc;
     if ((rc = build_worklist_static(c, cb, g_noalloc_host, kNoAllocScratchBytes, frag_elem, L)) != VR_OK) return rc;
     // fragments follow the staged work-list; the kernel writes every fragment it later reads,
     // and the per-brick "sampled" flags arrive zeroed with the work-list, so nothing left over
     // from an earlier call is read
     CK(cudaMemcpyAsync(dev, g_noalloc_host, L.bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(g_noalloc_up[c->device], s));
+    g_noalloc_last = c->device;
     const float4 *d_lut = reinterpret_cast<const float4 *>(dev + L.off_lut);
     const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(dev + L.off_db);
     const TileItem *d_items = reinterpret_cast<const TileItem *>(dev + L.off_items);

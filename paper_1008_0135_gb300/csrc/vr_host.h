@@ -119,6 +119,7 @@ struct vr_ctx {
     vrh::DevBuf<char> d_frags;        // bytes
     vrh::DevBuf<float4> d_gfrag;
     vrh::DevBuf<float> d_gpart;
+    vrh::DevBuf<double> d_gacc;         // FP64 table-gradient sum over the views of a batch
     vrh::DevBuf<float> d_out;
     cudaEvent_t upload_done = nullptr, frame_done = nullptr;
     bool frame_pending = false;
@@ -184,8 +185,9 @@ struct FrameTiming {
     FrameTiming(const FrameTiming &) = delete;
     FrameTiming &operator=(const FrameTiming &) = delete;
     ~FrameTiming() {
-        if (!queued && ev[0])
-            for (auto e : ev) c->ev_pool.push_back(e);
+        if (!queued)        // a failed timing_events may have taken only some of the four
+            for (auto e : ev)
+                if (e) c->ev_pool.push_back(e);
     }
     void queue() {
         if (ev[0]) c->ev_pending.push_back({ev[0], ev[1], ev[2], ev[3]});

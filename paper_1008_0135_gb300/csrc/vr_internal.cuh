@@ -131,5 +131,10 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
                            float *gvox, cudaStream_t s);
 cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, float *glut,
                                    cudaStream_t s);
+// Several views: acc (4 nlut doubles) = (first ? 0 : acc) + the view's partials, in FP64; then
+// glut = (float)acc after the last view.
+cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *acc, bool first,
+                                       cudaStream_t s);
+cudaError_t launch_lut_grad_store(const double *acc, int nlut, float *glut, cudaStream_t s);
 
 }  // namespace vr

@@ -948,12 +948,57 @@ __global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts,
     glut[i] = (float)acc;
 }
 
+// Several views' table gradients: each view's partials are added to one FP64 accumulator
+// (zeroed by the first view), which is rounded to FP32 once, after the last view.
+__global__ void k_lut_grad_accumulate(const float *__restrict__ partial, int nparts, int n,
+                                      double *__restrict__ acc, int first) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = first ? 0.0 : acc[i];
+    for (int p = 0; p < nparts; ++p) a += (double)partial[(long long)p * n + i];
+    acc[i] = a;
+}
+
+__global__ void k_lut_grad_store(const double *__restrict__ acc, int n, float *__restrict__ glut) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) glut[i] = (float)acc[i];
+}
+
+// Function attributes (the dynamic shared-memory limit, the carveout) are set per device: a
+// kernel's attributes on one GPU say nothing about another GPU of the same process.  Each
+// launcher remembers what it set in one slot per device ordinal (devices beyond kAttrDevices
+// are set on every launch).  Frames of the serving loop may launch from several host threads:
+// the slots are atomics, and setting an attribute twice is harmless.
+constexpr int kAttrDevices = 64;
+struct DeviceAttrs {
+    std::atomic<int> smem[kAttrDevices];     // dynamic shared-memory limit set (bytes), 0: not yet
+    std::atomic<int> carve[kAttrDevices];    // carveout percentage set, -1: not yet
+    DeviceAttrs() {
+        for (int i = 0; i < kAttrDevices; ++i) { smem[i].store(0); carve[i].store(-1); }
+    }
+};
+
+int current_device() {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+
+// Raises the kernel's dynamic shared-memory limit to `bytes` on the current device (once).
+cudaError_t ensure_smem_limit(const void *kernel, int bytes, DeviceAttrs &da) {
+    const int dev = current_device();
+    const bool cached = dev >= 0 && dev < kAttrDevices;
+    if (cached && da.smem[dev].load(std::memory_order_acquire) >= bytes) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && cached) da.smem[dev].store(bytes, std::memory_order_release);
+    return e;
+}
+
 // The unified L1 / shared memory of an SM serves the texture gathers as cache: ask for just the
 // shared memory (the table) of the 256-thread CTAs the register file admits, leaving the rest
 // to L1 (measured on HIPASS-scale frames at 5 CTAs: 25 % carveout 3.65 ms, the driver's default
 // 3.75, 50 % 3.98).  Registers are allocated per warp in units of 256, 64 K per SM, at most 64
-// warps.  `last` remembers the kernel's current preference (the attribute is per kernel).
-cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, std::atomic<int> &last) {
+// warps.  The kernel's current preference on this device is remembered in `da`.
+cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, DeviceAttrs &da) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
@@ -961,28 +1006,24 @@ cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, std::atomic<in
     const int ctas = std::max(1, std::min(64, 65536 / std::max(per_warp, 256)) / 8);
     const double need = ctas * (double)(smem_per_cta + 1024) / (228.0 * 1024.0);
     const int pct = std::min(100, std::max(0, (int)std::ceil(100.0 * need)));
-    if (last.load(std::memory_order_relaxed) == pct) return cudaSuccess;
+    const int dev = current_device();
+    const bool cached = dev >= 0 && dev < kAttrDevices;
+    if (cached && da.carve[dev].load(std::memory_order_relaxed) == pct) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    if (e == cudaSuccess) last.store(pct, std::memory_order_relaxed);
+    if (e == cudaSuccess && cached) da.carve[dev].store(pct, std::memory_order_relaxed);
     return e;
 }
 
 template <int S, int MODE, int F, bool MASK>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
-    // the shared-memory limit is raised once per instantiation (frames of the serving loop may
-    // launch from several host threads: an atomic flag, and setting it twice is harmless)
-    static std::atomic<bool> attr{false};
-    static std::atomic<int> carve{-1};
+    static DeviceAttrs da;
     const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
-    if (!attr.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(k_raycast<S, MODE, F, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(2 * sizeof(float4) * kMaxLut));
-        if (e != cudaSuccess) return e;
-        attr.store(true, std::memory_order_release);
-    }
+    const void *kern = reinterpret_cast<const void *>(k_raycast<S, MODE, F, MASK>);
+    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut), da);
+    if (e != cudaSuccess) return e;
     if (MODE == 0) {
-        cudaError_t e = set_carveout(reinterpret_cast<const void *>(k_raycast<S, MODE, F, MASK>), smem, carve);
+        e = set_carveout(kern, smem, da);
         if (e != cudaSuccess) return e;
     }
     k_raycast<S, MODE, F, MASK><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items, pool, frags, ctr);
@@ -1019,19 +1060,11 @@ cudaError_t launch_raycast(const FrameConsts &fc, const float4 *lut, const DrawB
 template <int S, int F, bool MASK>
 cudaError_t launch_march(const FrameConsts &fc, const float4 *lut, DrawBrick *bricks, const MarchGrid &g,
                          const void *pool, float4 *out, Counters *ctr, cudaStream_t s) {
-    static std::atomic<bool> attr{false};
-    static std::atomic<int> carve{-1};
-    if (!attr.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(k_raymarch<S, F, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(2 * sizeof(float4) * kMaxLut));
-        if (e != cudaSuccess) return e;
-        attr.store(true, std::memory_order_release);
-    }
-    {
-        cudaError_t e = set_carveout(reinterpret_cast<const void *>(k_raymarch<S, F, MASK>),
-                                     2 * sizeof(float4) * (size_t)fc.nlut, carve);
-        if (e != cudaSuccess) return e;
-    }
+    static DeviceAttrs da;
+    const void *kern = reinterpret_cast<const void *>(k_raymarch<S, F, MASK>);
+    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut), da);
+    if (e == cudaSuccess) e = set_carveout(kern, 2 * sizeof(float4) * (size_t)fc.nlut, da);
+    if (e != cudaSuccess) return e;
     const int tw = fc.lanes_y ? kRcShort : kRcLong, th = fc.lanes_y ? kRcLong : kRcShort;
     const long long ntiles = (long long)((fc.cam.W + tw - 1) / tw) * ((fc.cam.H + th - 1) / th);
     k_raymarch<S, F, MASK><<<(unsigned)ntiles, 256, 2 * sizeof(float4) * (size_t)fc.nlut, s>>>(
@@ -1081,16 +1114,11 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
                            const float4 *frags, const float4 *gfrag, float *glut_partial,
                            float *gvox, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    static std::atomic<bool> attr{false};
-    if (!attr.load(std::memory_order_acquire)) {
-        cudaError_t e = cudaFuncSetAttribute(k_adjoint<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(48 * kMaxLut + 64));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_adjoint<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(48 * kMaxLut + 64));
-        if (e != cudaSuccess) return e;
-        attr.store(true, std::memory_order_release);
-    }
+    static DeviceAttrs da_lin, da_atl;
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<false>), (int)(48 * kMaxLut + 64), da_lin);
+    if (e == cudaSuccess)
+        e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<true>), (int)(48 * kMaxLut + 64), da_atl);
+    if (e != cudaSuccess) return e;
     // table + differences (32 B per entry) + gradient accumulators (16 B per entry and copy): as
     // many copies (up to 8) as keep the block within 64 KB
     int ncopies = VR_ADJ_COPIES;
@@ -1108,6 +1136,19 @@ cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, f
                                    cudaStream_t s) {
     const int n = 4 * nlut;
     k_lut_grad_reduce<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, glut);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *acc, bool first,
+                                       cudaStream_t s) {
+    const int n = 4 * nlut;
+    k_lut_grad_accumulate<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, acc, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_grad_store(const double *acc, int nlut, float *glut, cudaStream_t s) {
+    const int n = 4 * nlut;
+    k_lut_grad_store<<<(n + 255) / 256, 256, 0, s>>>(acc, n, glut);
     return cudaGetLastError();
 }
 

@@ -166,8 +166,9 @@ def test_adjoint_at_the_benchmark_size_on_sampled_pixels(ctx, orc):
 
 @pytest.mark.parametrize("layouts", [1, 9])
 def test_backward_reuses_the_frames_fragments_only_when_valid(ctx, layouts):
-    """vr_render_backward right after the frame it differentiates reuses that frame's fragments;
-    after any call that can change a frame, or another frame, it ray-casts again.  All three
+    """vr_render_backward right after the frame it differentiates reuses that frame's fragments
+    (setting the same camera, table or parameters again changes nothing); after a change of
+    camera, or another frame, it ray-casts again.  All three
     orders give the same gradients (to the atomics' summation order)."""
     import torch
     rng, cube, lut, cam, cid = _setup(ctx, 21)
@@ -183,7 +184,8 @@ def test_backward_reuses_the_frames_fragments_only_when_valid(ctx, layouts):
 
     render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
     a = grads()                                      # reuses the frame's fragments
-    ctx.set_camera_dict(cam)                         # a setter: the next backward ray-casts
+    ctx.set_camera_dict(other)                       # the camera changed and back: the next
+    ctx.set_camera_dict(cam)                         # backward ray-casts
     b = grads()
     render(ctx, cid, lut, (-3, 20), other, step=0.5, tau=0.99)
     ctx.set_camera_dict(cam)                         # another frame's fragments are held
@@ -192,4 +194,120 @@ def test_backward_reuses_the_frames_fragments_only_when_valid(ctx, layouts):
         for u, v in zip(x, y):
             assert np.allclose(u, v, rtol=1e-5, atol=1e-6 * np.abs(u).max())
     assert np.abs(a[0]).max() > 0
+    ctx.free_cube(cid)
+
+
+def test_adjoint_finite_differences_at_the_differentiation_config(ctx, orc):
+    """The differentiation workload: 256^3 cube (seed 3), 128^3 bricks, 8 orbit views 45 degrees
+    apart at 512^2, step 0.5, ERT 0.99, ramp table; loss = squared difference against a target
+    rendered with the ramp shifted by +3, on 2048 seeded pixels per view (no weight elsewhere).
+    The GPU gradient, one autograd backward through vr_render_backward_views, against FP64
+    central differences (h = 1e-3) of the oracle's loss for 64 seeded table entries and 64
+    seeded voxels, relative tolerance 1e-3.  The image is piecewise smooth: a pixel that some
+    checked +-h perturbation moves across a table entry, clamp edge or termination stop (its
+    oracle piece signature changes), or whose gradient is ambiguous at the unperturbed input, gets
+    no weight in the loss, so every checked difference stays inside one piece."""
+    import torch
+    from paper_1008_0135_gb300.autograd import render_views
+    cfg = synth.DIFF
+    cube = synth.diff_cube(seed=cfg["seed"])
+    lut = synth.ramp_lut()
+    target_lut = synth.shifted_ramp_lut(shift=3.0, vrange=cfg["vrange"])
+    vr, step, tau, brick = cfg["vrange"], cfg["step"], cfg["tau"], cfg["brick"]
+    c = np.array(cfg["shape"], np.float64) / 2
+    dist = 1.5 * 0.5 * math.sqrt(3) * cfg["shape"][0]
+    cams = [dict(view=synth.orbit_view(45.0 * j, c, dist), proj=1, param=math.radians(60.0),
+                 W=cfg["W"], H=cfg["H"]) for j in range(cfg["n_views"])]
+    V, npx = len(cams), cfg["W"] * cfg["H"]
+    kw = dict(step=step, tau=tau, brick=brick)
+    S, tgt, sig0 = [], [], []
+    for v, cam in enumerate(cams):
+        pix = synth.sample_pixels(900 + v, cam["W"], cam["H"], 2048)
+        _, flags, _, sg = orc.render_sig(cube, lut, vr, cam, pix=pix, **kw)
+        keep = (flags & 9) == 0
+        t, _, _ = orc.render(cube, target_lut, vr, cam, pix=pix[keep], **kw)
+        S.append(pix[keep])
+        tgt.append(t)
+        sig0.append(sg[keep])
+    # the oracle's analytic gradient picks entries the loss depends on
+    rl, rv = np.zeros((lut.shape[0], 4)), np.zeros(cube.shape)
+    for v, cam in enumerate(cams):
+        out, _, _ = orc.render(cube, lut, vr, cam, pix=S[v], **kw)
+        a, b = orc.render_grad(cube, lut, vr, cam, 2.0 * (out - tgt[v]), pix=S[v], **kw)
+        rl += a
+        rv += b
+    rng = np.random.default_rng(cfg["seed"])
+    h = 1e-3
+    cand = np.argwhere(np.abs(rl) > 1e-3 * np.abs(rl).max())
+    lut_entries = cand[rng.choice(len(cand), 64, replace=False)]
+    cand = np.argwhere(np.abs(rv) > 1e-2 * np.abs(rv).max())
+    vox_entries = cand[rng.choice(len(cand), 64, replace=False)]
+    rays = [orc.rays(cam, cfg["shape"], step=step, pix=S[v]) for v, cam in enumerate(cams)]
+    excluded = [np.zeros(len(S[v]), bool) for v in range(V)]
+
+    def perturbed(cb, lt, sel_of_view):
+        """Oracle images of the selected loss pixels (index arrays into S per view); marks the
+        pixels whose piece signature differs from the unperturbed one."""
+        res = {}
+        for v, sel in sel_of_view.items():
+            out, _, _, sg = orc.render_sig(cb, lt, vr, cams[v], pix=S[v][sel], **kw)
+            excluded[v][sel[sg != sig0[v][sel]]] = True
+            res[v] = (sel, out)
+        return res
+
+    runs = []
+    everything = {v: np.arange(len(S[v])) for v in range(V)}
+    for i, ch in lut_entries:
+        lp, lm = lut.astype(np.float64).copy(), lut.astype(np.float64).copy()
+        lp[i, ch] += h
+        lm[i, ch] -= h
+        lp32, lm32 = lp.astype(np.float32), lm.astype(np.float32)
+        runs.append(("lut", (i, ch), float(lp32[i, ch]) - float(lm32[i, ch]),
+                     perturbed(cube, lp32, everything), perturbed(cube, lm32, everything)))
+    for z, y, x in vox_entries:
+        p = np.array([x + 0.5, y + 0.5, z + 0.5])
+        near = {}
+        for v, (o, d, _) in enumerate(rays):       # rays within the stencil's reach of the voxel
+            dd = np.linalg.norm(np.cross(p[None, :] - o.astype(np.float64), d.astype(np.float64)), axis=1)
+            sel = np.nonzero(dd < 2.0)[0]
+            if len(sel):
+                near[v] = sel
+        cp, cm = cube.copy(), cube.copy()
+        cp[z, y, x] = np.float32(float(cube[z, y, x]) + h)
+        cm[z, y, x] = np.float32(float(cube[z, y, x]) - h)
+        runs.append(("vox", (z, y, x), float(cp[z, y, x]) - float(cm[z, y, x]),
+                     perturbed(cp, lut, near), perturbed(cm, lut, near)))
+    kept = sum(int((~e).sum()) for e in excluded)
+    assert kept > 0.8 * sum(len(p) for p in S), kept
+    # GPU gradient of the loss over the kept pixels, through the autograd function
+    mask = np.zeros((V, npx), np.float32)
+    target = np.zeros((V, npx, 4), np.float32)
+    for v in range(V):
+        mask[v, S[v][~excluded[v]]] = 1.0
+        target[v, S[v]] = tgt[v]
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, brick, 1, "f32")
+    lut_t = torch.from_numpy(lut).cuda().requires_grad_(True)
+    vox_t = torch.from_numpy(cube).cuda().requires_grad_(True)
+    imgs = render_views(ctx, cid, lut_t, cams, vr, voxels=vox_t, step=step, tau=tau)
+    m = torch.from_numpy(mask).cuda().reshape(V, cfg["H"], cfg["W"], 1)
+    tt = torch.from_numpy(target).cuda().reshape(V, cfg["H"], cfg["W"], 4)
+    (((imgs - tt) ** 2) * m).sum().backward()
+    gl = lut_t.grad.cpu().numpy().astype(np.float64)
+    gv = vox_t.grad.cpu().numpy().astype(np.float64)
+    checked = {"lut": 0, "vox": 0}
+    for kind, idx, den, plus, minus in runs:
+        num = 0.0
+        for v, (sel, op) in plus.items():
+            om = minus[v][1]
+            w = ~excluded[v][sel]
+            t = tgt[v][sel][w]
+            num += float(((op[w] - t) ** 2).sum() - ((om[w] - t) ** 2).sum())
+        fd = num / den
+        g = gl[idx] if kind == "lut" else gv[idx]
+        if fd == 0.0 and g == 0.0:
+            continue                        # every pixel the entry reaches was left out
+        assert abs(g - fd) <= 1e-3 * abs(fd), (kind, idx, g, fd)
+        checked[kind] += 1
+    assert checked["lut"] >= 48 and checked["vox"] >= 48, checked
     ctx.free_cube(cid)

@@ -816,3 +816,32 @@ def test_mip32_equals_fp64_mip_to_rounding_at_random_views(orc):
     # positions rounded to binary32 (|p| < 40: 4e-6) times a slope below 4 per voxel, plus
     # 7 lerps of values below 3 rounded to binary32
     assert worst < 3e-5
+
+
+def test_piece_signature_changes_exactly_across_piece_boundaries(orc):
+    """render_sig's per-pixel hash: a constant cube on a table entry moved by +-h lands in two
+    different intervals (signatures differ); half-way between entries they are equal, and equal
+    to the unmoved cube's; a change of the termination stop (more opacity) changes it."""
+    rng = np.random.default_rng(8)
+    shape = (7, 6, 9)
+    lut = synth.random_lut(2, n=32, alpha_max=0.2)
+    cam = synth.random_camera(rng, shape, 16, 12)
+    vr = (-3.0, 8.0)
+    on = -3.0 + 11.0 * 10.0 / 31.0
+    half = -3.0 + 11.0 * 10.5 / 31.0
+    sig = {}
+    for name, v in (("on+", on + 1e-3), ("on-", on - 1e-3), ("half", half), ("half+", half + 1e-3),
+                    ("half-", half - 1e-3)):
+        _, f, _, s = orc.render_sig(synth.constant_cube(shape, v), lut, vr, cam, step=0.5, tau=1.0)
+        sig[name] = s
+    hit = (f & 2) == 0
+    assert hit.sum() > 30
+    assert np.all(sig["on+"][hit] != sig["on-"][hit])
+    assert np.array_equal(sig["half"], sig["half+"]) and np.array_equal(sig["half"], sig["half-"])
+    # termination: an opaque table stops every segment early, a faint one never
+    _, _, n1, s1 = orc.render_sig(synth.constant_cube(shape, half), synth.constant_lut([1, 1, 1, 0.6], 32),
+                                  vr, cam, step=0.5, tau=0.9)
+    _, _, n2, s2 = orc.render_sig(synth.constant_cube(shape, half), synth.constant_lut([1, 1, 1, 0.01], 32),
+                                  vr, cam, step=0.5, tau=0.9)
+    # (rays with only a few samples stop nowhere in either)
+    assert n1 < n2 and np.mean(s1[hit] != s2[hit]) > 0.5
