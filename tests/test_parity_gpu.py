@@ -667,3 +667,29 @@ def test_degenerate_cube_extents(ctx, orc, shape):
         m32, _, _ = orc.render(cube, lut, (-1, 3), cam, mode="mip32", step=0.3, brick=brick)
         assert np.array_equal(m, m32.astype(np.float32))
         ctx.free_cube(cid)
+
+
+def test_contexts_created_later_render_the_largest_table(ctx, pr1):
+    """Launch attributes (the 128 KB shared-memory limit a 4096-entry table needs, the carveout)
+    belong to a device and are remembered per device: two more contexts on the same device,
+    created after frames were rendered, render 4096-entry tables (fragment and one-pass kernels)
+    bit for bit like the first context."""
+    import paper_1008_0135_gb300 as P
+    cube, cid = pr1
+    t = np.arange(4096) / 4095.0
+    lut = np.stack([t, 1.0 - t, t * t, 0.2 * t], 1).astype(np.float32)
+    cam = synth.pr1_camera(W=80, H=72)
+    refs = {}
+    for term in ("segment", "global"):
+        ctx.set_termination(term)
+        refs[term] = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=0.99)
+    ctx.set_termination("segment")
+    with P.Context(0) as a, P.Context(0) as b:
+        for c in (a, b):
+            k = c.load_cube(cube)
+            c.set_bricking(k, (32, 32, 32), 1, "f32")
+            for term in ("segment", "global"):
+                c.set_termination(term)
+                g = render(c, k, lut, (-3, 20), cam, step=0.5, tau=0.99)
+                assert np.array_equal(g, refs[term]), term
+            c.free_cube(k)
