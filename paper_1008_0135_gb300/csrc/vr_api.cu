@@ -297,12 +297,6 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
     // it saves; with a poor alignment it pays
     fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
-    // DVR fragment frames read atlases with the slice-origin table when every brick's stored
-    // depth fits it (bricks of a cube share their size; the last ones are smaller)
-    if (fc.fetch == 2 && c->mode == VR_DVR && cb->B[2] + 2 * cb->ghost <= kMaxTabSlices) {
-        fc.fetch = 3;
-        fc.tab_slices = cb->B[2] + 2 * cb->ghost;
-    }
     return fc;
 }
 

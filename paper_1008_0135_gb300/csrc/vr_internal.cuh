@@ -13,8 +13,6 @@ constexpr int kTile = 16;          // compositing: 16x16 screen tiles
 constexpr int kRcLong = 32;        // ray-cast work item: 32x8 (or 8x32) pixels of a rectangle,
 constexpr int kRcShort = 8;        // one warp per 32-pixel row (or column)
 constexpr int kMaxLut = 4096;      // transfer-function entries (float4 each) held in shared memory
-constexpr int kMaxTabSlices = 2048; // bricks up to this many stored slices read their atlases
-                                    // with a per-block table of slice tile origins (fetch 3)
 
 // Camera constants in the FP32 decision arithmetic (computed once per frame on the host).
 struct Cam {
@@ -40,11 +38,8 @@ struct FrameConsts {
     int fetch;                     // how a sample's 8 stencil corners are read: 0 = 8 loads from
                                    // the linear brick, 1 = the same with the stencil cache (rays
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
-                                   // from the brick's slice-atlas texture, 3 = the same gathers
-                                   // with the slices' tile origins from a shared-memory table
+                                   // from the brick's slice-atlas texture
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
-    int tab_slices;                // fetch 3: entries of the slice-origin table (the largest
-                                   // stored brick depth of the frame, <= kMaxTabSlices)
 };
 
 // One brick of the current frame's work-list (front-to-back order).

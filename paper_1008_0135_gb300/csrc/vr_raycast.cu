@@ -278,39 +278,6 @@ __device__ __forceinline__ void fetch8_atlas(const Atlas &a, int ix, int iy, int
     }
 }
 
-// The same two gathers with the tile origins of the brick's slices from a per-block table in
-// shared memory (float2 (column + 1, row + 1) of slice z's tile, built once per block for its
-// brick): the coordinates are then the cell's float floors plus the table entries of slices iz
-// and iz + 1, two broadcast-like shared loads and four adds in place of the integer tile
-// arithmetic.  flx, fly: floor of the sample's local x, y (exact small integers).
-template <int S>
-__device__ __forceinline__ void fetch8_atlas_tab(unsigned long long tex, const float2 *toff, float flx,
-                                                 float fly, int iz, float v[8]) {
-    const float2 t0 = toff[iz], t1 = toff[iz + 1];
-    const float x0 = __fadd_rn(flx, t0.x), y0 = __fadd_rn(fly, t0.y);
-    const float x1 = __fadd_rn(flx, t1.x), y1 = __fadd_rn(fly, t1.y);
-    if constexpr (S != 2) {
-        const float4 g0 = tex2Dgather<float4>(tex, x0, y0, 0);
-        const float4 g1 = tex2Dgather<float4>(tex, x1, y1, 0);
-        v[0] = g0.w; v[1] = g0.z; v[2] = g0.x; v[3] = g0.y;
-        v[4] = g1.w; v[5] = g1.z; v[6] = g1.x; v[7] = g1.y;
-    } else {
-        const uint4 g0 = tex2Dgather<uint4>(tex, x0, y0, 0);
-        const uint4 g1 = tex2Dgather<uint4>(tex, x1, y1, 0);
-        v[0] = bf16_value(g0.w); v[1] = bf16_value(g0.z);
-        v[2] = bf16_value(g0.x); v[3] = bf16_value(g0.y);
-        v[4] = bf16_value(g1.w); v[5] = bf16_value(g1.z);
-        v[6] = bf16_value(g1.x); v[7] = bf16_value(g1.y);
-    }
-}
-
-// Table of slice tile origins (+1: a gather at ix + 1 returns texels ix, ix + 1) of a brick's atlas.
-__device__ __forceinline__ void load_slice_offsets(int dx, int dy, int dz, int alog, float2 *toff) {
-    const int cm = (1 << alog) - 1;
-    for (int z = threadIdx.x; z < dz; z += blockDim.x)
-        toff[z] = make_float2((float)((z & cm) * dx + 1), (float)((z >> alog) * dy + 1));
-}
-
 template <int S>
 __device__ __forceinline__ void fetch8(const void *src, int i0, const Strides &t, float v[8]) {
     v[0] = ldv<S>(src, i0);             v[1] = ldv<S>(src, i0 + t.x);
@@ -417,8 +384,7 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
                                            float scale, float qx, float qy, float qz, const float d[3],
                                            int n, const FrameConsts &fc, const float4 *s_lut,
                                            int org_z, float vcode,
-                                           float &c0, float &c1, float &c2, float &T,
-                                           const float2 *toff = nullptr) {
+                                           float &c0, float &c1, float &c2, float &T) {
     const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
     const int lmax = fc.nlut - 2;
     int px = -4, py = -4, pz = -4;        // no cell cached yet
@@ -429,30 +395,14 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
     for (; j < n; ++j, jf = __fadd_rn(jf, 1.0f)) {
         const float tj = __fmul_rn(jf, fc.step);
         Cell cl;
-        const float x = __fmaf_rn(tj, d[0], qx), y = __fmaf_rn(tj, d[1], qy), z = __fmaf_rn(tj, d[2], qz);
-        if (F == 3) {
-            // float floors (the tabled atlas coordinates need no integer x, y), the integer z
-            const float tx = __fadd_rd(x, kFloorMagic), ty = __fadd_rd(y, kFloorMagic), tz = __fadd_rd(z, kFloorMagic);
-            float flx = __fsub_rn(tx, kFloorMagic), fly = __fsub_rn(ty, kFloorMagic);
-            const float flz = __fsub_rn(tz, kFloorMagic);
-            cl.fx = __fsub_rn(x, flx); cl.fy = __fsub_rn(y, fly); cl.fz = __fsub_rn(z, flz);
-            int jz = __float_as_int(tz) - kFloorMagicBits;
-            if (CLAMP) {
-                flx = fminf(fmaxf(flx, 0.0f), (float)mx);
-                fly = fminf(fmaxf(fly, 0.0f), (float)my);
-                jz = clampi(jz, 0, mz);
-            }
-            cl.iz = jz;
-            fetch8_atlas_tab<S>(atl.tex, toff, flx, fly, jz, v);
-        } else {
-            cell_of<CLAMP>(x, y, z, mx, my, mz, cl);
-            if (F == 2)
-                fetch8_atlas<S>(atl, cl.ix, cl.iy, cl.iz, v);
-            else if (F == 1)
-                fetch8_cached<S>(src, st, cl, px, py, pz, v);
-            else
-                fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
-        }
+        cell_of<CLAMP>(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
+                       mx, my, mz, cl);
+        if (F == 2)
+            fetch8_atlas<S>(atl, cl.ix, cl.iy, cl.iz, v);
+        else if (F == 1)
+            fetch8_cached<S>(src, st, cl, px, py, pz, v);
+        else
+            fetch8<S>(src, cl.ix * st.x + cl.iy * st.y + cl.iz * st.z, st, v);
         if (MASK) mask_channels(v, cl.iz, org_z, fc.nz, fc.chmask, vcode);
         DvrSample sm;
         interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
@@ -486,7 +436,7 @@ template <int S, int MODE, int F, bool MASK>
 __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__restrict__ lut,
                                          DrawBrick *__restrict__ dbs, const TileItem it, int strip, int lane,
                                          const void *__restrict__ pool, void *__restrict__ frags,
-                                         Counters *__restrict__ ctr, float4 *s_lut, const float2 *toff) {
+                                         Counters *__restrict__ ctr, float4 *s_lut) {
     const DrawBrick &b = dbs[it.db];
     // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
     int rx, ry;
@@ -509,7 +459,7 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
         const Strides st{b.str[0], b.str[1], b.str[2]};
         const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
         const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
-        const Atlas atl{F >= 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
+        const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
         if (MODE == 0) {
             if (hit) {
                 const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
@@ -529,9 +479,9 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
                 const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
                 const int j = inside
                     ? dvr_segment<S, F, false, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                   b.org[2], vcode, c0, c1, c2, T, toff)
+                                                   b.org[2], vcode, c0, c1, c2, T)
                     : dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                  b.org[2], vcode, c0, c1, c2, T, toff);
+                                                  b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
             static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
@@ -551,7 +501,7 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
                     const int iz = clampi((int)flz - b.org[2], 0, mz);
                     const int i0 = ix * st.x + iy * st.y + iz * st.z;
                     float v[8];
-                    if (F >= 2)
+                    if (F == 2)
                         fetch8_atlas<S>(atl, ix, iy, iz, v);
                     else
                         fetch8<S>(src, i0, st, v);
@@ -586,7 +536,7 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
 // atlas DVR loop without spills.
 template <int MODE, int F>
 constexpr int rc_min_blocks() {
-    return MODE == 0 ? (F >= 2 && VR_DVR_MIN_BLOCKS > 0 ? VR_DVR_MIN_BLOCKS : 1)
+    return MODE == 0 ? (F == 2 && VR_DVR_MIN_BLOCKS > 0 ? VR_DVR_MIN_BLOCKS : 1)
                      : (VR_MIP_MIN_BLOCKS > 0 ? VR_MIP_MIN_BLOCKS : 1);
 }
 
@@ -597,18 +547,11 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
           Counters *__restrict__ ctr) {
     extern __shared__ float4 s_lut[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const TileItem it = items[blockIdx.x];
-    // F = 3: the brick's slice tile origins follow the table (2 nlut float4)
-    float2 *toff = reinterpret_cast<float2 *>(s_lut + 2 * fc.nlut);
     if (MODE == 0) {
         load_table(lut, fc.nlut, s_lut);
-        if (F == 3) {
-            const DrawBrick &b = dbs[it.db];
-            load_slice_offsets(b.dim[0], b.dim[1], b.dim[2], b.alog, toff);
-        }
         __syncthreads();
     }
-    rc_strip<S, MODE, F, MASK>(fc, lut, dbs, it, warp, lane, pool, frags, ctr, s_lut, toff);
+    rc_strip<S, MODE, F, MASK>(fc, lut, dbs, items[blockIdx.x], warp, lane, pool, frags, ctr, s_lut);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1076,10 +1019,9 @@ template <int S, int MODE, int F, bool MASK>
 cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                       int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
     static DeviceAttrs da;
-    const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut + (F == 3 ? sizeof(float2) * (size_t)fc.tab_slices : 0)
-                                  : 0;
+    const size_t smem = MODE == 0 ? 2 * sizeof(float4) * (size_t)fc.nlut : 0;
     const void *kern = reinterpret_cast<const void *>(k_raycast<S, MODE, F, MASK>);
-    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut + sizeof(float2) * kMaxTabSlices), da);
+    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut), da);
     if (e != cudaSuccess) return e;
     if (MODE == 0) {
         e = set_carveout(kern, smem, da);
@@ -1093,14 +1035,12 @@ template <int S>
 cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                         int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
 #define VR_RC(MODE, F, MASK) launch_rc<S, MODE, F, MASK>(fc, lut, db, items, nitems, pool, frags, ctr, s)
-    const bool atlas = fc.fetch >= 2;
+    const bool atlas = fc.fetch == 2;
     if (fc.chmask) {     // masked frames: no stencil cache (same values, fewer instantiations)
         if (fc.mode != 0) return atlas ? VR_RC(1, 2, true) : VR_RC(1, 0, true);
-        if (fc.fetch == 3) return VR_RC(0, 3, true);
         return atlas ? VR_RC(0, 2, true) : VR_RC(0, 0, true);
     }
     if (fc.mode != 0) return atlas ? VR_RC(1, 2, false) : VR_RC(1, 0, false);
-    if (fc.fetch == 3) return VR_RC(0, 3, false);
     if (atlas) return VR_RC(0, 2, false);
     if (fc.fetch == 1) return VR_RC(0, 1, false);
     return VR_RC(0, 0, false);
@@ -1136,7 +1076,7 @@ cudaError_t launch_march(const FrameConsts &fc, const float4 *lut, DrawBrick *br
 template <int S>
 cudaError_t launch_march_s(const FrameConsts &fc, const float4 *lut, DrawBrick *bricks, const MarchGrid &g,
                            const void *pool, float4 *out, Counters *ctr, cudaStream_t s) {
-    const bool atlas = fc.fetch >= 2;
+    const bool atlas = fc.fetch == 2;
     if (fc.chmask)
         return atlas ? launch_march<S, 2, true>(fc, lut, bricks, g, pool, out, ctr, s)
                      : launch_march<S, 0, true>(fc, lut, bricks, g, pool, out, ctr, s);
@@ -1186,7 +1126,7 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     const size_t per_copy = 16 * (size_t)fc.nlut + 64;
     while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * per_copy > ((size_t)VR_ADJ_SMEM_KB << 10)) ncopies >>= 1;
     const size_t smem = 32 * (size_t)fc.nlut + ncopies * per_copy;
-    if (fc.fetch >= 2)
+    if (fc.fetch == 2)
         k_adjoint<true><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
     else
         k_adjoint<false><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
