@@ -279,6 +279,49 @@ int vr_set_host_output_async(vr_ctx *ctx, int async);
  * VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT (streamed bricks did not arrive in time). */
 int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *cuda_stream);
 
+/* Object-space partition (Section 2.2, Fig. 3: each GPU gets a portion of the cube, cut along
+ * the current longest axis, and each node cuts its portion again for its GPUs).  After this
+ * call frames of the cube draw only the bricks of one part: at level L = 0 .. nlevels-1 the
+ * current part's brick grid is cut along its longest axis (in voxels; ties to the lower axis)
+ * into counts[L] consecutive slabs of whole brick layers, as even as the layer count allows, and
+ * part index[L] is kept (e.g. {3} and {r} for rank r of 3; {2, 2} and {node, gpu} for two
+ * nodes of two GPUs).  A part may be empty.  nlevels = 0 restores the whole cube.  The bricking
+ * is unchanged (a part's frame samples its bricks exactly as the whole cube's frame does).
+ * Global early termination (VR_TERM_GLOBAL) is refused for partitioned cubes: parts terminate
+ * per segment, as the paper's nodes do.  Errors: VR_ERR_ARG (nlevels outside 0..8, counts
+ * outside 1..65536, index outside 0..counts-1), VR_ERR_NOT_FOUND. */
+int vr_set_partition(vr_ctx *ctx, int cube_id, int nlevels, const int *counts, const int *index);
+
+/* The brick index range [lo, hi) per axis of the cube's part, and (axes, NULL to skip) the split
+ * axis (0 x, 1 y, 2 z) of each partition level.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND,
+ * VR_ERR_STATE (no bricking). */
+int vr_get_partition(vr_ctx *ctx, int cube_id, int lo[3], int hi[3], int *axes);
+
+/* The sub-image of the cube's part (Section 2.5, the frame portion a GPU generates): the frame
+ * of vr_render_frame restricted to the part's bricks, with DVR pixels holding premultiplied
+ * colour and the TRANSMITTANCE T of the part (not 1 - T: the parts' sub-images compose exactly
+ * from (C, T)), and MIP pixels -inf where the part has no sample.  out: W*H*4 (DVR) or W*H
+ * (MIP) floats in host or device memory.  DVR needs VR_TERM_SEGMENT.  Errors: as
+ * vr_render_frame, VR_ERR_UNSUPPORTED (global termination). */
+int vr_render_subimage(vr_ctx *ctx, int cube_id, float *out, int out_where, void *cuda_stream);
+
+/* Second compositing stage (Section 2.5, Fig. 4: the sub-images of sibling parts blended in
+ * depth order; the operator is associative, not commutative).  subs: the n = counts[level]
+ * sub-images of the sibling parts of `level` (the parts that share every partition index but
+ * index[level], in index order), restricted to frame rows [row0, row0 + rows): n * rows * W * 4
+ * (DVR, (C, T)) or n * rows * W (MIP) floats, part-major, 16-byte aligned device memory.  Each
+ * pixel blends them front to back in the order its ray crosses them: the siblings are
+ * consecutive slabs along the level's split axis, crossed in increasing index order when the
+ * ray's direction along that axis (the fragment kernel's FP32 ray of the current camera) is
+ * positive and in decreasing order when negative.  out: rows * W * 4 (or rows * W) floats,
+ * device memory: the parent part's sub-image rows, or, with final != 0, the frame's format
+ * (C, 1 - T; MIP -inf becomes vmin).  The camera, mode and table range must be those the
+ * sub-images were rendered with.  Ordered on `cuda_stream`.  Errors: VR_ERR_ARG (level outside
+ * the partition, n != counts[level], rows outside the frame, misaligned pointers),
+ * VR_ERR_NOT_FOUND, VR_ERR_STATE (no bricking or camera), VR_ERR_CUDA. */
+int vr_composite_subimages(vr_ctx *ctx, int cube_id, int level, int n, const float *subs, int row0,
+                           int rows, int final_, float *out, void *cuda_stream);
+
 /* Renders one frame like vr_render_frame, but allocates no memory at all, for callers that
  * cannot allocate device memory while they render (their GPU memory is owned by another
  * allocator or held to a fixed budget, or their frame loop must not pay the device-wide

@@ -261,6 +261,54 @@ class Context:
         _check(self._L.vr_render_frame(self._h, cube_id, ptr, loc, sh), "vr_render_frame")
         return out
 
+    # ------------------------------------------------------------------- sort-last partitions
+    def set_partition(self, cube_id: int, counts=(), index=()):
+        """Draw only one part of the cube: a recursive longest-axis split with counts[L] slabs at
+        level L, keeping slab index[L] (empty counts: the whole cube)."""
+        n = len(counts)
+        if len(index) != n:
+            raise ValueError("counts and index must have the same length")
+        ca = (C.c_int * max(n, 1))(*[int(v) for v in counts])
+        ia = (C.c_int * max(n, 1))(*[int(v) for v in index])
+        _check(self._L.vr_set_partition(self._h, cube_id, n, ca, ia), "vr_set_partition")
+
+    def partition(self, cube_id: int, nlevels: int = 8):
+        """(lo, hi, axes): the part's brick index ranges per axis and the split axis per level."""
+        lo, hi, ax = (C.c_int * 3)(), (C.c_int * 3)(), (C.c_int * 8)()
+        _check(self._L.vr_get_partition(self._h, cube_id, lo, hi, ax), "vr_get_partition")
+        return tuple(lo), tuple(hi), tuple(ax)[:nlevels]
+
+    def render_subimage(self, cube_id: int, out=None, stream=None):
+        """The part's sub-image: DVR (H, W, 4) premultiplied colour + transmittance; MIP (H, W)
+        with -inf where the part has no sample."""
+        if self.cam is None:
+            raise VrError(_abi.VR_ERR_STATE, "render_subimage: set a camera first")
+        W, H = self.cam
+        if out is None:
+            import torch
+            shape = (H, W, 4) if self.mode == VR_DVR else (H, W)
+            out = torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}")
+        ptr, loc = _buffer(out)
+        sh = _stream_handle(stream) if (loc == VR_DEVICE or stream is not None) else 0
+        _check(self._L.vr_render_subimage(self._h, cube_id, ptr, loc, sh), "vr_render_subimage")
+        return out
+
+    def composite_subimages(self, cube_id: int, level: int, subs, row0: int, final: bool, out=None,
+                            stream=None):
+        """Blends the sibling parts' sub-images of `level` (CUDA tensor (n, rows, W, 4) or
+        (n, rows, W)) for frame rows [row0, row0 + rows); returns (rows, W, 4) / (rows, W)."""
+        if not subs.is_contiguous():
+            raise ValueError("subs must be contiguous")
+        n, rows = int(subs.shape[0]), int(subs.shape[1])
+        if out is None:
+            import torch
+            out = torch.empty(tuple(subs.shape[1:]), dtype=torch.float32, device=subs.device)
+        _check(self._L.vr_composite_subimages(self._h, cube_id, int(level), n, subs.data_ptr(), int(row0),
+                                              rows, int(bool(final)), out.data_ptr(),
+                                              _stream_handle(stream)),
+               "vr_composite_subimages")
+        return out
+
     def render_backward(self, cube_id: int, grad_out, grad_lut, grad_voxels=None, stream=None):
         gv = grad_voxels.data_ptr() if grad_voxels is not None else None
         _check(self._L.vr_render_backward(self._h, cube_id, grad_out.data_ptr(),

@@ -76,6 +76,10 @@ SIGNATURES = {
     "vr_wavelet_store": (I, [VP, I, VP, P(C.c_size_t)]),
     "vr_render_frame": (I, [VP, I, VP, I, VP]),
     "vr_render_frame_noalloc": (I, [VP, I, VP, VP]),
+    "vr_set_partition": (I, [VP, I, I, P(I), P(I)]),
+    "vr_get_partition": (I, [VP, I, P(I), P(I), P(I)]),
+    "vr_render_subimage": (I, [VP, I, VP, I, VP]),
+    "vr_composite_subimages": (I, [VP, I, I, I, VP, I, I, I, VP, VP]),
     "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),
     "vr_render_backward_views": (I, [VP, I, I, P(VrView), VP, VP, VP, VP]),
     "vr_set_channel_mask": (I, [VP, VP, I64]),

@@ -77,7 +77,36 @@ void alpha_prefix(const vr_ctx *c, std::vector<int> &pre) {
 // stencil's range, so a brick whose stored values map only to entries of zero opacity adds
 // exactly nothing (every sample has a = 0: colour += T*0, T *= 1).  The range is widened for
 // the FP32 rounding of the mapping and, for 16-bit bricks, for the rounding of the codes.
+// Recursive longest-axis split (Section 2.2, Fig. 3): at every level the current part's brick
+// range is cut along its longest axis (in voxels; ties to the lower axis) into counts[L]
+// consecutive slabs of whole brick layers, as even as the layer count allows, and the path
+// keeps slab index[L].  A part may be empty when a level has more slabs than layers.
+PartBox partition_box(const Cube *cb) {
+    PartBox p{};
+    for (int a = 0; a < 3; ++a) { p.lo[a] = 0; p.hi[a] = (int)cb->nb[a]; }
+    for (int L = 0; L < cb->part_nlev; ++L) {
+        int axis = 0;
+        int64_t best = -1;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t ext = std::min<int64_t>((int64_t)p.hi[a] * cb->B[a], cb->n[a]) - (int64_t)p.lo[a] * cb->B[a];
+            if (ext > best) { best = ext; axis = a; }
+        }
+        const int64_t layers = p.hi[axis] - p.lo[axis], n = cb->part_counts[L], k = cb->part_index[L];
+        const int s0 = p.lo[axis] + (int)(layers * k / n), s1 = p.lo[axis] + (int)(layers * (k + 1) / n);
+        p.axis[L] = axis;
+        p.lo[axis] = s0;
+        p.hi[axis] = s1;
+    }
+    return p;
+}
+
 bool window_clip(const vr_ctx *c, const Cube *cb, const DrawBrick &b, float lo[3], float hi[3]) {
+    if (cb->part_nlev > 0) {                 // bricks outside the cube's part are not drawn
+        const PartBox p = partition_box(cb);
+        const int64_t ci[3] = {b.brick % cb->nb[0], (b.brick / cb->nb[0]) % cb->nb[1], b.brick / (cb->nb[0] * cb->nb[1])};
+        for (int a = 0; a < 3; ++a)
+            if (ci[a] < p.lo[a] || ci[a] >= p.hi[a]) return false;
+    }
     for (int a = 0; a < 3; ++a) {
         lo[a] = b.lo[a];
         hi[a] = b.hi[a];
@@ -297,6 +326,7 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
     // it saves; with a poor alignment it pays
     fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
+    fc.sub = c->subimage ? 1 : 0;
     return fc;
 }
 
@@ -1433,6 +1463,8 @@ static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStr
 // One frame of cube `cb` with the context's current table, camera and parameters.
 __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStream_t s) {
     int rc;
+    if (cb->part_nlev > 0 && c->mode == VR_DVR && c->term == VR_TERM_GLOBAL)
+        return fail(VR_ERR_UNSUPPORTED, "a partitioned cube's parts terminate per segment (VR_TERM_SEGMENT)");
     if (cb->streamed) {
         if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL) return render_streamed_global(c, cb, out, out_where, s);
         return render_streamed(c, cb, out, out_where, s);
@@ -1499,6 +1531,73 @@ int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *str
     if (rc) return rc;
     if ((rc = set_dev(c)) != VR_OK) return rc;
     return render_frame_impl(c, cb, out, out_where, static_cast<cudaStream_t>(stream));
+}
+
+int vr_set_partition(vr_ctx *c, int cube_id, int nlevels, const int *counts, const int *index) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (nlevels < 0 || nlevels > Cube::kMaxPartLevels) return arg_fail("nlevels must be 0..8");
+    if (nlevels > 0 && (!counts || !index)) return arg_fail("null counts or index");
+    for (int L = 0; L < nlevels; ++L)
+        if (counts[L] < 1 || counts[L] > 65536 || index[L] < 0 || index[L] >= counts[L])
+            return arg_fail("each level needs 1 <= counts <= 65536 and 0 <= index < counts");
+    c->state_gen++;
+    cb->part_nlev = nlevels;
+    for (int L = 0; L < nlevels; ++L) { cb->part_counts[L] = counts[L]; cb->part_index[L] = index[L]; }
+    return VR_OK;
+}
+
+int vr_get_partition(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes) {
+    if (!c || !lo || !hi) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (!cb->bricked) return fail(VR_ERR_STATE, "cube has no bricking");
+    const PartBox p = partition_box(cb);
+    for (int a = 0; a < 3; ++a) { lo[a] = p.lo[a]; hi[a] = p.hi[a]; }
+    if (axes)
+        for (int L = 0; L < cb->part_nlev; ++L) axes[L] = p.axis[L];
+    return VR_OK;
+}
+
+int vr_render_subimage(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
+    if (!c || !out) return arg_fail("null argument");
+    if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    int rc = check_ready(c, cb);
+    if (rc) return rc;
+    if (c->mode == VR_DVR && c->term == VR_TERM_GLOBAL)
+        return fail(VR_ERR_UNSUPPORTED, "sub-images composite per-segment fragments (VR_TERM_SEGMENT)");
+    if ((rc = set_dev(c)) != VR_OK) return rc;
+    c->subimage = true;
+    rc = render_frame_impl(c, cb, out, out_where, static_cast<cudaStream_t>(stream));
+    c->subimage = false;
+    return rc;
+}
+
+int vr_composite_subimages(vr_ctx *c, int cube_id, int level, int n, const float *subs, int row0, int rows,
+                           int final_, float *out, void *stream) {
+    if (!c || !subs || !out) return arg_fail("null argument");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (!cb->bricked) return fail(VR_ERR_STATE, "cube has no bricking");
+    if (!c->cam_set) return fail(VR_ERR_STATE, "no camera");
+    if (level < 0 || level >= cb->part_nlev) return arg_fail("level outside the cube's partition");
+    if (n != cb->part_counts[level]) return arg_fail("n must equal the partition's count at that level");
+    if (row0 < 0 || rows < 0 || row0 + rows > c->cam.H) return arg_fail("rows outside the frame");
+    if (reinterpret_cast<uintptr_t>(subs) % 16 != 0 || reinterpret_cast<uintptr_t>(out) % 16 != 0)
+        return arg_fail("subs and out must be 16-byte aligned device memory");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    const PartBox p = partition_box(cb);
+    FrameConsts fc{};
+    fc.cam = c->cam;
+    fc.mode = c->mode;
+    fc.vmin = c->vmin;
+    CK(launch_composite_parts(fc, p.axis[level], n, subs, row0, rows, final_ ? 1 : 0, out,
+                              static_cast<cudaStream_t>(stream)));
+    return VR_OK;
 }
 
 int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,

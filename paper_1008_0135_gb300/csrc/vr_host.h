@@ -70,7 +70,21 @@ struct Cube {
     size_t wstore_bytes = 0;
     uint64_t proc_seed = 0;           // procedural cube: generator seed
     int id = 0;
+    // object-space partition (Section 2.2): frames draw only the bricks of one part of a
+    // recursive longest-axis split; part_nlev = 0 draws the whole cube
+    static constexpr int kMaxPartLevels = 8;
+    int part_nlev = 0;
+    int part_counts[kMaxPartLevels] = {0};
+    int part_index[kMaxPartLevels] = {0};
 };
+
+// The part of a cube's brick grid that its partition selects: brick index ranges [lo, hi) per
+// axis and the split axis of every level (the longest axis, in voxels, of the parent part).
+struct PartBox {
+    int lo[3], hi[3];
+    int axis[Cube::kMaxPartLevels];
+};
+PartBox partition_box(const Cube *cb);
 
 template <typename T>
 struct DevBuf {
@@ -107,6 +121,7 @@ struct vr_ctx {
     float tau = 0.99f;
     int term = VR_TERM_SEGMENT;       // early termination per brick segment or global (waves)
     bool full_rect = false;
+    bool subimage = false;            // the frame being rendered is a part's sub-image (C, T)
     bool timing = false;
     // Section 2.3 viewer controls: spectral channels switched off, sub-cube window
     std::vector<unsigned char> chmask;   // per cube z; empty = every channel on

@@ -40,6 +40,8 @@ struct FrameConsts {
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
                                    // from the brick's slice-atlas texture
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
+    int sub;                       // 1: a part's sub-image -- DVR pixels keep the transmittance T
+                                   // (not 1 - T), MIP pixels without samples stay -inf
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -121,6 +123,12 @@ cudaError_t launch_raymarch(const FrameConsts &fc, const float4 *lut, DrawBrick 
                             const void *pool, float4 *out, Counters *ctr, cudaStream_t s);
 cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const int *tile_start,
                              const int *tile_list, const void *frags, float *out, cudaStream_t s);
+// Second-stage compositing of n sibling parts' sub-images (Section 2.5): rows [row0, row0 + rows)
+// of the frame, subs = n sub-images of those rows (part-major; DVR (C, T) float4, MIP float),
+// blended per pixel in the order its ray crosses the parts along `axis` (parts are consecutive
+// slabs along it).  final: write the frame's format ((C, 1 - T); MIP -inf -> vmin).
+cudaError_t launch_composite_parts(const FrameConsts &fc, int axis, int n, const float *subs, int row0, int rows,
+                                   int final_, float *out, cudaStream_t s);
 cudaError_t launch_composite_backward(const FrameConsts &fc, const DrawBrick *db,
                                       const int *tile_start, const int *tile_list,
                                       const float4 *frags, const float4 *gout, float4 *gfrag,

@@ -710,7 +710,7 @@ k_composite(const FrameConsts fc, const DrawBrick *__restrict__ dbs, const int *
                 T = __fmul_rn(T, f.w);         // fragment .w holds the segment's transmittance
             }
         }
-        reinterpret_cast<float4 *>(out)[pix] = make_float4(c0, c1, c2, 1.0f - T);
+        reinterpret_cast<float4 *>(out)[pix] = make_float4(c0, c1, c2, fc.sub ? T : 1.0f - T);
     } else {
         float m = -INFINITY;
         for (int e = s0; e < s1; ++e) {
@@ -721,7 +721,45 @@ k_composite(const FrameConsts fc, const DrawBrick *__restrict__ dbs, const int *
                 m = f > m ? f : m;
             }
         }
-        out[pix] = (m == -INFINITY) ? fc.vmin : m;
+        out[pix] = (m == -INFINITY && !fc.sub) ? fc.vmin : m;
+    }
+}
+
+// Sort-last second stage (Section 2.5): the sub-images of sibling parts, which are consecutive
+// slabs of the cube along `axis`, blended per pixel front to back.  A ray crosses the slabs in
+// increasing index order when its direction along the axis is positive, in decreasing order
+// when negative; with a zero component it meets one slab only, and the others' (0, T = 1) leave
+// the blend unchanged whatever the order.  The direction is the ray of that pixel in the
+// fragment kernel's own FP32 arithmetic.
+__global__ void __launch_bounds__(256)
+k_composite_parts(const FrameConsts fc, int axis, int n, const float *__restrict__ subs, int row0, int rows,
+                  int final_, float *__restrict__ out) {
+    const long long npx = (long long)rows * fc.cam.W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npx;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (fc.mode == 0) {
+            const int x = (int)(i % fc.cam.W), y = row0 + (int)(i / fc.cam.W);
+            float o[3], d[3];
+            ray_for_pixel(fc.cam, x, y, o, d);
+            const bool down = d[axis] < 0.0f;
+            float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+            for (int j = 0; j < n; ++j) {
+                const int k = down ? n - 1 - j : j;
+                const float4 f = reinterpret_cast<const float4 *>(subs)[(long long)k * npx + i];
+                c0 = __fmaf_rn(T, f.x, c0);
+                c1 = __fmaf_rn(T, f.y, c1);
+                c2 = __fmaf_rn(T, f.z, c2);
+                T = __fmul_rn(T, f.w);
+            }
+            reinterpret_cast<float4 *>(out)[i] = make_float4(c0, c1, c2, final_ ? 1.0f - T : T);
+        } else {
+            float m = -INFINITY;
+            for (int k = 0; k < n; ++k) {
+                const float f = subs[(long long)k * npx + i];
+                m = f > m ? f : m;
+            }
+            out[i] = (m == -INFINITY && final_) ? fc.vmin : m;
+        }
     }
 }
 
@@ -1098,6 +1136,15 @@ cudaError_t launch_composite(const FrameConsts &fc, const DrawBrick *db, const i
         k_composite<0><<<grid, 256, 0, s>>>(fc, db, tile_start, tile_list, frags, out);
     else
         k_composite<1><<<grid, 256, 0, s>>>(fc, db, tile_start, tile_list, frags, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_composite_parts(const FrameConsts &fc, int axis, int n, const float *subs, int row0, int rows,
+                                   int final_, float *out, cudaStream_t s) {
+    const long long npx = (long long)rows * fc.cam.W;
+    if (npx <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((npx + 255) / 256, 152 * 8);
+    k_composite_parts<<<grid, 256, 0, s>>>(fc, axis, n, subs, row0, rows, final_, out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,172 @@
+"""Sort-last rendering on the GPU: longest-axis parts (Section 2.2), their sub-images and the
+staged depth-ordered compositing (Section 2.5) equal the whole cube's frame, and the oracle."""
+import math
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import compare_dvr, gpu_ctx
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SHAPE = (96, 64, 40)                      # x, y, z
+BRICK = (16, 16, 16)                      # 6 x 4 x 3 bricks (the last z layer 8 deep)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    c = gpu_ctx()
+    rng = np.random.default_rng(42)
+    nx, ny, nz = SHAPE
+    cube = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    cube += synth.pr1_cube(seed=5, n=96, n_sources=12, sigma=(3.0, 8.0))[:nz, :ny, :nx]
+    cid = c.load_cube(cube)
+    c.set_bricking(cid, BRICK, 1, "f32")
+    yield c, cube, cid
+    c.close()
+
+
+def test_partition_boxes_follow_the_longest_axis(setup):
+    ctx, cube, cid = setup
+    for k, want in enumerate([(0, 2), (2, 4), (4, 6)]):   # x (96) is longest: 6 layers in 3
+        ctx.set_partition(cid, (3,), (k,))
+        lo, hi, ax = ctx.partition(cid, 1)
+        assert ax == (0,) and (lo[0], hi[0]) == want and lo[1:] == (0, 0) and hi[1:] == (4, 3)
+    # two nodes of two GPUs: x first (96), then each 48 x 64 x 40 half along y (64)
+    ctx.set_partition(cid, (2, 2), (1, 0))
+    lo, hi, ax = ctx.partition(cid, 2)
+    assert ax == (0, 1) and lo == (3, 0, 0) and hi == (6, 2, 3)
+    ctx.set_partition(cid, (8,), (7,))                 # more slabs than layers: some parts empty
+    lo, hi, _ = ctx.partition(cid, 1)
+    assert hi[0] - lo[0] in (0, 1)
+    ctx.set_partition(cid)
+    lo, hi, _ = ctx.partition(cid, 0)
+    assert lo == (0, 0, 0) and hi == (6, 4, 3)
+
+
+def _blend(ctx, cid):
+    def f(level, stack, row0, final):
+        return ctx.composite_subimages(cid, level, stack, row0, final)
+    return f
+
+
+def _sortlast_local(ctx, cid, counts):
+    from paper_1008_0135_gb300 import sortlast as SL
+    world = int(np.prod(counts))
+    subs = []
+    for r in range(world):
+        ctx.set_partition(cid, counts, SL.digits(r, counts))
+        subs.append(ctx.render_subimage(cid).clone())
+    ctx.set_partition(cid)
+    return SL.composite_parts_local(subs, counts, _blend(ctx, cid))
+
+
+CAMS = [
+    dict(view=synth.look_at((150.0, 90.0, -60.0), (48.0, 32.0, 20.0)), proj=1, param=math.radians(50.0), W=72, H=56),
+    dict(view=synth.look_at((48.0, 32.0, 20.0 - 140.0), (48.0, 32.0, 20.0)), proj=0, param=110.0, W=64, H=48),
+    # eye inside the cube's x range: rays cross the x slabs in both directions
+    dict(view=synth.look_at((40.0, 30.0, -90.0), (50.0, 34.0, 20.0)), proj=1, param=math.radians(80.0), W=80, H=60),
+]
+
+
+@pytest.mark.parametrize("counts", [(2,), (3,), (2, 2), (4,), (3, 2)])
+def test_sortlast_frame_equals_the_whole_cube(setup, orc, counts):
+    """Sub-images of every part composited in stages equal the whole cube's frame (DVR to FP32
+    re-association, 1e-6; MIP bit for bit) and the oracle within the 1e-4 bar."""
+    ctx, cube, cid = setup
+    lut = synth.random_lut(3, n=64, alpha_max=0.35)
+    ctx.set_transfer_function(lut, -3.0, 12.0)
+    for cam in CAMS:
+        ctx.set_camera_dict(cam)
+        for mode in ("dvr", "mip"):
+            ctx.set_render_params(mode, 0.5, 0.99)
+            whole = ctx.render_frame(cid).cpu().numpy()
+            parts = _sortlast_local(ctx, cid, counts).cpu().numpy()
+            if mode == "mip":
+                assert np.array_equal(parts, whole)
+                continue
+            assert np.abs(parts - whole).max() <= 1e-6
+            ref, flags, _ = orc.render(cube, lut, (-3.0, 12.0), cam, step=0.5, tau=0.99, brick=BRICK)
+            compare_dvr(parts.reshape(-1, 4), ref, flags, 0.99)
+
+
+def test_subimage_keeps_transmittance_and_refuses_global_termination(setup):
+    import paper_1008_0135_gb300 as P
+    ctx, cube, cid = setup
+    ctx.set_transfer_function(synth.ramp_lut(alpha=0.3), -3.0, 12.0)
+    ctx.set_camera_dict(CAMS[0])
+    ctx.set_render_params("dvr", 0.5, 0.99)
+    frame = ctx.render_frame(cid)
+    sub = ctx.render_subimage(cid)                      # whole cube: T in place of 1 - T
+    assert (sub[..., :3] == frame[..., :3]).all()
+    assert ((1.0 - sub[..., 3]) - frame[..., 3]).abs().max().item() <= 1e-7
+    ctx.set_partition(cid, (2,), (0,))
+    ctx.set_termination("global")
+    with pytest.raises(P.VrError):
+        ctx.render_frame(cid)
+    with pytest.raises(P.VrError):
+        ctx.render_subimage(cid)
+    ctx.set_termination("segment")
+    ctx.set_partition(cid)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from datetime import timedelta
+    import torch.distributed as dist
+    import paper_1008_0135_gb300 as P
+    from paper_1008_0135_gb300.sortlast import SortLast
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=120))
+    rng = np.random.default_rng(42)
+    nx, ny, nz = SHAPE
+    cube = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    cube += synth.pr1_cube(seed=5, n=96, n_sources=12, sigma=(3.0, 8.0))[:nz, :ny, :nx]
+    with P.Context(0) as ctx:
+        cid = ctx.load_cube(cube)
+        ctx.set_bricking(cid, BRICK, 1, "f32")
+        ctx.set_transfer_function(synth.random_lut(3, n=64, alpha_max=0.35), -3.0, 12.0)
+        ctx.set_camera_dict(CAMS[2])
+        ctx.set_render_params("dvr", 0.5, 0.99)
+        frame = SortLast(ctx, cid, (world,), rank).render().cpu().numpy()
+    q.put((rank, frame))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_processes_exchange_subimages_over_gloo(setup):
+    """Two ranks (processes sharing cuda:0; no kernel waits on the other's), each rendering one
+    half of the cube and exchanging sub-image bands over gloo, end with the frame the stages
+    give in one process, bit for bit."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx, cube, cid = setup
+    ctx.set_transfer_function(synth.random_lut(3, n=64, alpha_max=0.35), -3.0, 12.0)
+    ctx.set_camera_dict(CAMS[2])
+    ctx.set_render_params("dvr", 0.5, 0.99)
+    local = _sortlast_local(ctx, cid, (2,)).cpu().numpy()
+    mpc = mp.get_context("spawn")
+    q = mpc.Queue()
+    port = _free_port()
+    procs = [mpc.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert np.array_equal(got[r], local), r
