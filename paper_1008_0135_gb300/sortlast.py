@@ -127,10 +127,10 @@ class TorchExchange:
 
 
 def composite_frame(sub, counts: Sequence[int], rank: int, exchange,
-                    blend: Callable[[int, object, int, bool], object]):
+                    blend: Callable[[int, object, int, bool, List[int]], object]):
     """Stages 2 and 3 of a frame from this rank's sub-image ``sub`` ((H, W, 4) or (H, W)).
-    ``blend(level, stack, row0, final)`` composites a (n, rows, ...) stack of sibling bands;
-    returns the full frame."""
+    ``blend(level, stack, row0, final, members)`` composites a (n, rows, ...) stack of the
+    bands of sibling parts ``members`` (ranks, in part-index order); returns the full frame."""
     import torch
     path = digits(rank, counts)
     H = int(sub.shape[0])
@@ -148,7 +148,7 @@ def composite_frame(sub, counts: Sequence[int], rank: int, exchange,
         recv = exchange.all_to_all(level, members, send, [rows] * len(members), row_elems)
         stack = torch.stack([t.reshape((rows,) + tail) for t in recv]) if rows > 0 else \
             torch.empty((len(members), 0) + tail, dtype=sub.dtype, device=sub.device)
-        cur = blend(level, stack.contiguous(), mine[0], level == 0)
+        cur = blend(level, stack.contiguous(), mine[0], level == 0, members)
         r0, r1 = mine
     world = 1
     for c in counts:
@@ -164,7 +164,7 @@ def composite_frame(sub, counts: Sequence[int], rank: int, exchange,
 
 
 def composite_parts_local(subs: Sequence, counts: Sequence[int],
-                          blend: Callable[[int, object, int, bool], object]):
+                          blend: Callable[[int, object, int, bool, List[int]], object]):
     """The stages of composite_frame for every part at once, in one process: ``subs[r]`` is the
     sub-image of the part with rank r.  Each rank's band is blended from the same rows of the
     same siblings as over the network, so the frame is the distributed frame bit for bit."""
@@ -180,7 +180,7 @@ def composite_parts_local(subs: Sequence, counts: Sequence[int],
             _, r0, r1 = cur[r]
             a, b = bands(r0, r1, counts[level])[paths[r][level]]
             stack = torch.stack([cur[q][0][a - cur[q][1]:b - cur[q][1]] for q in members]).contiguous()
-            nxt[r] = (blend(level, stack, a, level == 0) if b > a else stack[0], a, b)
+            nxt[r] = (blend(level, stack, a, level == 0, members) if b > a else stack[0], a, b)
         cur = nxt
     frame = torch.empty_like(subs[0])
     for r in range(world):
@@ -201,7 +201,7 @@ class SortLast:
         """The full frame ((H, W, 4) premultiplied RGBA, or (H, W) MIP) on every rank."""
         sub = self.ctx.render_subimage(self.cube_id, stream=stream)
 
-        def blend(level, stack, row0, final):
+        def blend(level, stack, row0, final, members):
             if stack.shape[1] == 0:
                 return stack[0]
             return self.ctx.composite_subimages(self.cube_id, level, stack, row0, final, stream=stream)

@@ -87,7 +87,7 @@ def _rank(rank, counts, H, W, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=60))
     ex = S.TorchExchange(counts)
     frame = S.composite_frame(_subimage(rank, H, W), counts, rank, ex,
-                              lambda level, stack, row0, final: _over(stack))
+                              lambda level, stack, row0, final, members: _over(stack))
     q.put((rank, frame.numpy()))
     dist.barrier()
     dist.destroy_process_group()
@@ -112,7 +112,7 @@ def test_gloo_ranks_composite_the_frame(counts, H, W):
         assert p.exitcode == 0
     ref = _reference(counts, H, W).numpy()
     local = SL.composite_parts_local([_subimage(r, H, W) for r in range(world)], counts,
-                                     lambda level, stack, row0, final: _over(stack)).numpy()
+                                     lambda level, stack, row0, final, members: _over(stack)).numpy()
     assert np.array_equal(local, ref)
     for r in range(world):
         assert np.array_equal(got[r], ref), r

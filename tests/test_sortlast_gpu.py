@@ -49,8 +49,13 @@ def test_partition_boxes_follow_the_longest_axis(setup):
     assert lo == (0, 0, 0) and hi == (6, 4, 3)
 
 
-def _blend(ctx, cid):
-    def f(level, stack, row0, final):
+def _blend(ctx, cid, counts):
+    """The library's blend for one process holding every part: the split axis of a level
+    depends on the parent part, so the context takes the partition of one of the siblings."""
+    from paper_1008_0135_gb300 import sortlast as SL
+
+    def f(level, stack, row0, final, members):
+        ctx.set_partition(cid, counts, SL.digits(members[0], counts))
         return ctx.composite_subimages(cid, level, stack, row0, final)
     return f
 
@@ -62,8 +67,9 @@ def _sortlast_local(ctx, cid, counts):
     for r in range(world):
         ctx.set_partition(cid, counts, SL.digits(r, counts))
         subs.append(ctx.render_subimage(cid).clone())
+    frame = SL.composite_parts_local(subs, counts, _blend(ctx, cid, counts))
     ctx.set_partition(cid)
-    return SL.composite_parts_local(subs, counts, _blend(ctx, cid))
+    return frame
 
 
 CAMS = [
