@@ -220,6 +220,36 @@ def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
     return res
 
 
+def sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, steps, warmup):
+    """N > 1 ranks: the same orbit frames rendered sort-last (Sections 2.2 and 2.5): rank r
+    draws its slab of a longest-axis cut of the cube into a sub-image, the sub-images are
+    exchanged by screen band over NCCL (direct send) and blended in depth order by the library,
+    and every rank gathers the frame.  One frame is split over all ranks ("strong")."""
+    import torch
+    from paper_1008_0135_gb300.sortlast import SortLast
+    ctx.set_transfer_function(lut, *vr)
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    sl = SortLast(ctx, cid, (dist.world,), dist.rank, backend="nccl")
+    for w in range(warmup):
+        ctx.set_camera_dict(cams[w % len(cams)])
+        sl.render()
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        ctx.set_camera_dict(cams[(warmup + k) % len(cams)])
+        sl.render()
+    torch.cuda.synchronize()
+    t = dist.max(time.perf_counter() - t0)
+    samples = dist.sum(ctx.stats()["samples"])
+    ctx.set_partition(cid)
+    return {"value": round(samples / t / 1e9, 3), "unit": "Gsamples/s", "scaling": "strong",
+            "ms_per_frame": round(1e3 * t / steps, 4), "ranks": dist.world,
+            "what": "one frame per step split over all ranks: longest-axis slabs, sub-image bands "
+                    "exchanged over NCCL, staged depth-ordered compositing, frame gathered on every rank"}
+
+
 def compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np, frames=16):
     """The bench's cube compressed into 8-bit Haar-wavelet blocks in HBM (the FP32 voxels, brick
     pool and atlases released), then rendered with its bricks decoded on demand into the brick
@@ -549,6 +579,12 @@ def run_ours(args, dist):
     samples_all = dist.sum(st["samples"])
     value = samples_all / (t_max * 1e-3) / 1e9
     rl = roofline(st, args.steps, peak, psrc, f"k_raycast<{args.storage},DVR>")
+    sortlast = None
+    if dist.world > 1:
+        try:
+            sortlast = sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, min(args.steps, 32), args.warmup)
+        except Exception as e:                 # the replicas' line stands without it
+            sortlast = {"error": f"{type(e).__name__}: {e}"[:300]}
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gsamples/s", "n_gpus": dist.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
@@ -565,6 +601,7 @@ def run_ours(args, dist):
         "roofline": rl,
         "clocks": clk,
         "gpu_launches": 2 * args.steps,
+        "sortlast": sortlast,
         "setup": {"load_cube_s": round(load_s, 3), "bricking_s": round(brick_s, 3),
                   "what": "cube copied in from device memory; bricking = bricks with ghost voxels, "
                           "their value ranges and the slice atlases (one-time)"},

@@ -72,7 +72,9 @@ class TorchExchange:
     """The collectives of a frame over torch.distributed: one process group per sibling set
     (created once, by every rank, in the same order) and the world group for the gather."""
 
-    def __init__(self, counts: Sequence[int]):
+    def __init__(self, counts: Sequence[int], backend: str = None):
+        """backend: that of the groups this exchange creates ("nccl": CUDA tensors move
+        GPU to GPU; "gloo": host copies); None: the default group's."""
         import torch.distributed as dist
         self.dist = dist
         self.counts = list(counts)
@@ -81,7 +83,9 @@ class TorchExchange:
             world *= c
         if dist.get_world_size() != world:
             raise ValueError(f"the partition has {world} parts for {dist.get_world_size()} ranks")
-        self.host = dist.get_backend() == "gloo"          # gloo moves host tensors
+        backend = backend or dist.get_backend()
+        self.host = backend == "gloo"                     # gloo moves host tensors
+        self.world_group = dist.new_group(list(range(world)), backend=backend)
         self.groups: Dict[Tuple[int, Tuple[int, ...]], object] = {}
         for level in range(len(counts)):
             seen = set()
@@ -90,7 +94,7 @@ class TorchExchange:
                 if g in seen:
                     continue
                 seen.add(g)
-                self.groups[(level, g)] = dist.new_group(list(g)) if len(g) > 1 else None
+                self.groups[(level, g)] = dist.new_group(list(g), backend=backend) if len(g) > 1 else None
 
     def _to(self, t):
         return t.cpu() if self.host else t
@@ -122,7 +126,7 @@ class TorchExchange:
         pad[:mine.numel()] = mine.reshape(-1)
         src = self._to(pad)
         out = torch.empty(self.dist.get_world_size() * src.numel(), dtype=src.dtype, device=src.device)
-        self.dist.all_gather_into_tensor(out, src)
+        self.dist.all_gather_into_tensor(out, src, group=self.world_group)
         return out.to(dev)
 
 
@@ -192,10 +196,11 @@ def composite_parts_local(subs: Sequence, counts: Sequence[int],
 class SortLast:
     """Sort-last frames of one cube over the ranks of torch.distributed (one GPU each)."""
 
-    def __init__(self, ctx, cube_id: int, counts: Sequence[int], rank: int, exchange=None):
+    def __init__(self, ctx, cube_id: int, counts: Sequence[int], rank: int, exchange=None,
+                 backend: str = None):
         self.ctx, self.cube_id, self.counts, self.rank = ctx, cube_id, list(counts), rank
         ctx.set_partition(cube_id, self.counts, digits(rank, self.counts))
-        self.exchange = exchange if exchange is not None else TorchExchange(self.counts)
+        self.exchange = exchange if exchange is not None else TorchExchange(self.counts, backend)
 
     def render(self, stream=None):
         """The full frame ((H, W, 4) premultiplied RGBA, or (H, W) MIP) on every rank."""
