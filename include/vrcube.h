@@ -484,6 +484,36 @@ typedef struct {
 int vr_serve(vr_ctx *ctx, const vr_request *reqs, int n, const vr_serve_config *cfg,
              vr_request_result *res, vr_serve_summary *sum);
 
+/* The same loop as an online server a viewer submits to while frames run (the paper's server
+ * waiting for render requests, Section 2.3): vr_serve_open starts the loop on a host thread of
+ * its own; vr_serve_submit hands it one request, which arrives at that moment (its arrival_ms
+ * is ignored); vr_serve_poll returns finished requests; vr_serve_close waits for every submitted
+ * request, stops the thread and frees the server.  Admission, concurrency and results are
+ * those of vr_serve.  While a server is open its context's cubes must not be loaded, freed,
+ * re-bricked or partitioned, and no other call may use the context. */
+typedef struct vr_server vr_server;
+
+/* cfg->max_inflight frame slots (1..64).  *out: the server (owned by the library until
+ * vr_serve_close).  Errors: VR_ERR_ARG, VR_ERR_CUDA, VR_ERR_OOM. */
+int vr_serve_open(vr_ctx *ctx, const vr_serve_config *cfg, vr_server **out);
+
+/* Submits one request; the table is copied now, `out` must stay valid until the request's
+ * ticket is returned by vr_serve_poll (or the server is closed).  *ticket: its number, 0, 1, 2,
+ * ... in submission order.  Thread-safe.  Errors: VR_ERR_ARG (null, no table or output),
+ * VR_ERR_NOT_FOUND (cube), VR_ERR_STATE (the server is closing). */
+int vr_serve_submit(vr_server *srv, const vr_request *req, int64_t *ticket);
+
+/* Up to `cap` finished requests, in completion order: tickets[k] and results[k] (status, times
+ * in ms after vr_serve_open, latency from submission to completion); *n how many.  Waits up to
+ * wait_ms (0..60000) for the first one when none is ready.  Thread-safe.  Errors: VR_ERR_ARG. */
+int vr_serve_poll(vr_server *srv, int64_t *tickets, vr_request_result *results, int cap, int *n,
+                  int wait_ms);
+
+/* Waits until every submitted request has finished, stops the loop and frees the server;
+ * results not yet polled are dropped.  sum (nullable): percentiles and throughput of all its
+ * requests.  Errors: VR_ERR_ARG; VR_ERR_STATE when some request failed. */
+int vr_serve_close(vr_server *srv, vr_serve_summary *sum);
+
 /* Name of a status code (static string). */
 const char *vr_error_string(int status);
 

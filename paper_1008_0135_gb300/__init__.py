@@ -67,6 +67,64 @@ def _buffer(x):
     return a.ctypes.data, VR_HOST
 
 
+def _fill_request(q, r, keep):
+    q.cube_id = int(r["cube"])
+    view = np.ascontiguousarray(r["cam"]["view"], dtype=np.float32).reshape(16)
+    for j in range(16):
+        q.view[j] = float(view[j])
+    q.proj, q.param = int(r["cam"]["proj"]), float(r["cam"]["param"])
+    q.width, q.height = int(r["cam"]["W"]), int(r["cam"]["H"])
+    q.mode = MODES[r.get("mode", "dvr")]
+    q.step, q.ert_threshold = float(r.get("step", 0.5)), float(r.get("tau", 0.99))
+    lut = np.ascontiguousarray(r["lut"], dtype=np.float32)
+    keep.append(lut)
+    q.lut, q.nlut = lut.ctypes.data, lut.shape[0]
+    q.vmin, q.vmax = float(r["vrange"][0]), float(r["vrange"][1])
+    q.arrival_ms = float(r.get("arrival_ms", 0.0))
+    ptr, loc = _buffer(r["out"])
+    q.out, q.out_where = ptr, loc
+    q.termination = {"segment": 0, "global": 1}[r.get("termination", "segment")]
+
+
+def _result_dict(res):
+    return {k: getattr(res, k) for k, _ in _abi.VrRequestResult._fields_}
+
+
+class Server:
+    """The online serving loop (vr_serve_open / submit / poll / close).  Keep each request's
+    ``out`` alive until its ticket has been polled."""
+
+    def __init__(self, ctx, max_inflight: int = 4):
+        self._L = ctx._L
+        self._h = C.c_void_p()
+        cfg = _abi.VrServeConfig(int(max_inflight))
+        _check(self._L.vr_serve_open(ctx._h, C.byref(cfg), C.byref(self._h)), "vr_serve_open")
+
+    def submit(self, request: dict) -> int:
+        q = _abi.VrRequest()
+        keep = []
+        _fill_request(q, request, keep)
+        t = C.c_int64()
+        _check(self._L.vr_serve_submit(self._h, C.byref(q), C.byref(t)), "vr_serve_submit")
+        return t.value
+
+    def poll(self, wait_ms: int = 0, cap: int = 64):
+        """[(ticket, result dict)] of the requests finished since the last poll."""
+        tk = (C.c_int64 * cap)()
+        rs = (_abi.VrRequestResult * cap)()
+        n = C.c_int()
+        _check(self._L.vr_serve_poll(self._h, tk, rs, cap, C.byref(n), int(wait_ms)), "vr_serve_poll")
+        return [(tk[i], _result_dict(rs[i])) for i in range(n.value)]
+
+    def close(self) -> dict:
+        summ = _abi.VrServeSummary()
+        rc = self._L.vr_serve_close(self._h, C.byref(summ))
+        self._h = None
+        if rc not in (0, _abi.VR_ERR_STATE):
+            raise VrError(rc, "vr_serve_close")
+        return {k: getattr(summ, k) for k, _ in _abi.VrServeSummary._fields_}
+
+
 class Context:
     """One library context on one CUDA device (vr_create / vr_destroy)."""
 
@@ -340,32 +398,20 @@ class Context:
         arr = (_abi.VrRequest * max(n, 1))()
         keep = []
         for i, r in enumerate(requests):
-            q = arr[i]
-            q.cube_id = int(r["cube"])
-            view = np.ascontiguousarray(r["cam"]["view"], dtype=np.float32).reshape(16)
-            for j in range(16):
-                q.view[j] = float(view[j])
-            q.proj, q.param = int(r["cam"]["proj"]), float(r["cam"]["param"])
-            q.width, q.height = int(r["cam"]["W"]), int(r["cam"]["H"])
-            q.mode = MODES[r.get("mode", "dvr")]
-            q.step, q.ert_threshold = float(r.get("step", 0.5)), float(r.get("tau", 0.99))
-            lut = np.ascontiguousarray(r["lut"], dtype=np.float32)
-            keep.append(lut)
-            q.lut, q.nlut = lut.ctypes.data, lut.shape[0]
-            q.vmin, q.vmax = float(r["vrange"][0]), float(r["vrange"][1])
-            q.arrival_ms = float(r.get("arrival_ms", 0.0))
-            ptr, loc = _buffer(r["out"])
-            q.out, q.out_where = ptr, loc
-            q.termination = {"segment": 0, "global": 1}[r.get("termination", "segment")]
+            _fill_request(arr[i], r, keep)
         cfg = _abi.VrServeConfig(int(max_inflight))
         res = (_abi.VrRequestResult * max(n, 1))()
         summ = _abi.VrServeSummary()
         rc = self._L.vr_serve(self._h, arr, n, C.byref(cfg), res, C.byref(summ))
         if rc not in (0, _abi.VR_ERR_STATE):
             raise VrError(rc, "vr_serve")
-        results = [{k: getattr(res[i], k) for k, _ in _abi.VrRequestResult._fields_} for i in range(n)]
+        results = [_result_dict(res[i]) for i in range(n)]
         summary = {k: getattr(summ, k) for k, _ in _abi.VrServeSummary._fields_}
         return results, summary
+
+    def serve_online(self, max_inflight: int = 4) -> "Server":
+        """An online request loop (vr_serve_open): submit requests as they arrive, poll results."""
+        return Server(self, max_inflight)
 
     def stats(self) -> dict:
         s = _abi.VrStats()

@@ -92,6 +92,10 @@ SIGNATURES = {
     "vr_get_brick": (I, [VP, I, I64, P(I), P(I), P(I), VP]),
     "vr_serve": (I, [VP, P(VrRequest), I, P(VrServeConfig), P(VrRequestResult),
                      P(VrServeSummary)]),
+    "vr_serve_open": (I, [VP, P(VrServeConfig), P(VP)]),
+    "vr_serve_submit": (I, [VP, P(VrRequest), P(C.c_int64)]),
+    "vr_serve_poll": (I, [VP, P(C.c_int64), P(VrRequestResult), I, P(I), I]),
+    "vr_serve_close": (I, [VP, P(VrServeSummary)]),
     "vr_error_string": (C.c_char_p, [I]),
     "vr_last_error_message": (C.c_char_p, []),
 }

@@ -7,12 +7,21 @@
 // cache has room for the bricks it still needs without evicting bricks of frames in flight.
 // Admitted frames run concurrently on their slots' streams; each completes on its own event,
 // and its latency is measured from its arrival to the completion seen by the loop.
+//
+// One loop (ServeCore) serves two front ends: vr_serve replays a trace of requests with known
+// arrival times and returns when all are done; the online server (vr_serve_open / submit /
+// poll / close) runs the loop on a host thread of its own while the caller submits requests
+// whenever they arrive and collects the finished ones.
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
 #include <future>
+#include <memory>
+#include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "vr_host.h"
@@ -20,11 +29,20 @@
 namespace vrh {
 namespace {
 
+// One request as the loop keeps it: a copy of the caller's request with its own table.
+struct Req {
+    vr_request q{};
+    std::vector<float> lut;
+    double arrival_ms = 0.0;          // ms after the loop started
+    vr_request_result res{};
+    int64_t ticket = -1;
+};
+
 struct FrameSlot {
     vr_ctx *c = nullptr;              // frame context sharing the parent's cubes, counters, cache
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
-    int req = -1;                     // request in flight, -1 = free
+    Req *req = nullptr;               // request in flight, nullptr = free
     Cube *cube = nullptr;
     std::vector<int64_t> held;        // streamed bricks this frame holds in the cache
     bool loading = false;             // streamed frame: bricks still being made resident
@@ -63,30 +81,54 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
-}  // namespace
-}  // namespace vrh
+// Copies a request (and its table) for the loop; checks what can be checked before admission.
+int make_req(vr_ctx *c, const vr_request &src, Req &r) {
+    if (!src.out || !src.lut || src.nlut < 2 || src.nlut > kMaxLut) return arg_fail("request without output or table");
+    if (!find_cube(c, src.cube_id)) return VR_ERR_NOT_FOUND;
+    r.q = src;
+    r.lut.assign(src.lut, src.lut + (size_t)4 * src.nlut);
+    r.q.lut = r.lut.data();
+    r.res = vr_request_result{};
+    r.res.status = VR_ERR_STATE;
+    return VR_OK;
+}
 
-using namespace vrh;
+// The continuous-batching loop.  Single-threaded: only the thread that calls step() touches it.
+struct ServeCore {
+    vr_ctx *c = nullptr;
+    std::vector<FrameSlot> slots;
+    std::deque<Req *> queue;           // arrived, not yet admitted (arrival order)
+    // brick holds (+1 when a streamed frame is queued, -1 when it completes), applied in order
+    // whenever the cache lock is free: they only steer admission, never correctness
+    struct HoldOp {
+        Cube *cube;
+        std::vector<int64_t> bricks;
+        int delta;
+    };
+    std::deque<HoldOp> holds;
+    std::vector<double> lat;
+    std::vector<Req *> finished;       // completed or failed since the caller last took them
+    int inflight = 0, max_conc = 0;
+    int64_t failed = 0, done = 0;
+    std::chrono::steady_clock::time_point t0;
 
-#pragma GCC visibility push(default)
-extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve_config *cfg,
-                        vr_request_result *res, vr_serve_summary *sum) {
-    if (!c || (!reqs && n > 0) || !cfg || (!res && n > 0)) return arg_fail("null argument");
-    if (n < 0 || cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
-    for (int i = 0; i < n; ++i) {
-        if (!reqs[i].out || !reqs[i].lut || reqs[i].nlut < 2) return arg_fail("request without output or table");
-        if (!find_cube(c, reqs[i].cube_id)) return VR_ERR_NOT_FOUND;
-        if (i > 0 && reqs[i].arrival_ms < reqs[i - 1].arrival_ms) return arg_fail("requests must be in arrival order");
+    int open(vr_ctx *parent, int max_inflight) {
+        c = parent;
+        t0 = std::chrono::steady_clock::now();
+        slots.resize(max_inflight);
+        for (auto &sl : slots) {
+            sl.c = slot_context(c);
+            if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sl.c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&sl.c->frame_done, cudaEventDisableTiming) != cudaSuccess)
+                return fail(VR_ERR_CUDA, "could not create the frame slots' streams and events");
+        }
+        return VR_OK;
     }
-    int rc = set_dev(c);
-    if (rc) return rc;
-    bool any_streamed = false;
-    for (int i = 0; i < n; ++i) any_streamed |= find_cube(c, reqs[i].cube_id)->streamed;
-    if (any_streamed && (rc = cache_create(c)) != VR_OK) return rc;
-    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
-    // frame slots
-    std::vector<FrameSlot> slots(cfg->max_inflight);
-    auto cleanup = [&]() {
+
+    // Waits for every slot, returns the slots' statistics to the parent, releases the slots.
+    void close() {
         for (auto &sl : slots) {
             if (sl.loading && sl.load.valid()) sl.load.wait();
             if (sl.s) cudaStreamSynchronize(sl.s);
@@ -100,52 +142,32 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
             if (sl.done) cudaEventDestroy(sl.done);
             if (sl.s) cudaStreamDestroy(sl.s);
         }
-    };
-    for (auto &sl : slots) {
-        sl.c = slot_context(c);
-        if (cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.c->upload_done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.c->frame_done, cudaEventDisableTiming) != cudaSuccess) {
-            cleanup();
-            return fail(VR_ERR_CUDA, "could not create the frame slots' streams and events");
-        }
+        for (auto &h : holds) cache_hold(c, h.cube, h.bricks, h.delta, true);
+        holds.clear();
+        slots.clear();
     }
-    for (int i = 0; i < n; ++i) {
-        res[i] = vr_request_result{};
-        res[i].status = VR_ERR_STATE;
+
+    double now() const { return ms_since(t0); }
+
+    void finish(Req *r, int status) {
+        r->res.done_ms = now();
+        r->res.latency_ms = r->res.done_ms - r->arrival_ms;
+        r->res.status = status;
+        if (status == VR_OK) lat.push_back(r->res.latency_ms); else ++failed;
+        ++done;
+        finished.push_back(r);
     }
-    std::deque<int> queue;             // arrived, not yet admitted (arrival order)
-    std::vector<double> lat;
-    lat.reserve(n);
-    // brick holds (+1 when a streamed frame is queued, -1 when it completes), applied in order
-    // whenever the cache lock is free: they only steer admission, never correctness
-    struct HoldOp {
-        Cube *cube;
-        std::vector<int64_t> bricks;
-        int delta;
-    };
-    std::deque<HoldOp> holds;
-    int next = 0, finished = 0, inflight = 0, max_conc = 0;
-    int64_t failed = 0;
-    const auto t0 = std::chrono::steady_clock::now();
-    auto finish = [&](int ri, int status) {
-        vr_request_result &r = res[ri];
-        r.done_ms = ms_since(t0);
-        r.latency_ms = r.done_ms - reqs[ri].arrival_ms;
-        r.status = status;
-        if (status == VR_OK) lat.push_back(r.latency_ms); else ++failed;
-        ++finished;
-    };
-    while (finished < n) {
-        const double now = ms_since(t0);
-        while (next < n && reqs[next].arrival_ms <= now) queue.push_back(next++);
+
+    bool idle() const { return queue.empty() && inflight == 0; }
+
+    // One pass: cache holds, streamed frames now queued, completions, admissions.
+    bool step() {
         bool progress = false;
         while (!holds.empty() && cache_hold(c, holds.front().cube, holds.front().bricks, holds.front().delta, false))
             holds.pop_front();
         // streamed frames whose bricks are resident and whose kernels are now queued
         for (auto &sl : slots) {
-            if (sl.req < 0 || !sl.loading) continue;
+            if (!sl.req || !sl.loading) continue;
             if (sl.load.wait_for(std::chrono::seconds(0)) != std::future_status::ready) continue;
             const int st = sl.load.get();
             sl.loading = false;
@@ -153,7 +175,7 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
             if (st != VR_OK) {
                 finish(sl.req, st);
                 --inflight;
-                sl.req = -1;
+                sl.req = nullptr;
                 continue;
             }
             sl.held = std::move(sl.bricks);
@@ -162,13 +184,13 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
         }
         // completions
         for (auto &sl : slots) {
-            if (sl.req < 0 || sl.loading) continue;
+            if (!sl.req || sl.loading) continue;
             const cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
             finish(sl.req, q == cudaSuccess ? VR_OK : cuda_fail(q, "frame completion"));
             if (sl.cube && !sl.held.empty()) holds.push_back({sl.cube, std::move(sl.held), -1});
             sl.held.clear();
-            sl.req = -1;
+            sl.req = nullptr;
             --inflight;
             progress = true;
         }
@@ -177,13 +199,14 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
         for (size_t qi = 0; qi < queue.size();) {
             FrameSlot *free_slot = nullptr;
             for (auto &sl : slots)
-                if (sl.req < 0) { free_slot = &sl; break; }
+                if (!sl.req) { free_slot = &sl; break; }
             if (!free_slot) break;
-            const int ri = queue[qi];
-            const vr_request &q = reqs[ri];
+            Req *r = queue[qi];
+            const vr_request &q = r->q;
             vr_ctx *fc = free_slot->c;
             Cube *cb = find_cube(c, q.cube_id);
-            int st = vr_set_transfer_function(fc, q.lut, q.nlut, q.vmin, q.vmax);
+            int st = cb ? VR_OK : VR_ERR_NOT_FOUND;
+            if (st == VR_OK) st = vr_set_transfer_function(fc, q.lut, q.nlut, q.vmin, q.vmax);
             if (st == VR_OK) st = vr_set_camera(fc, q.view, q.proj, q.param, q.width, q.height);
             if (st == VR_OK) st = vr_set_render_params(fc, q.mode, q.step, q.ert_threshold);
             if (st == VR_OK) st = vr_set_termination(fc, q.termination);
@@ -204,21 +227,21 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
                 for (auto &d : wl.db) bricks.push_back(d.brick);
             }
             queue.erase(queue.begin() + qi);
-            res[ri].admit_ms = ms_since(t0);
+            r->res.admit_ms = now();
             progress = true;
             if (st == VR_OK && cb->streamed) {
                 // bricks are produced and copied from a host thread; the loop keeps serving
                 FrameSlot *sl = free_slot;
                 const int dev = c->device;
-                sl->load = std::async(std::launch::async, [sl, fc, cb, &q, dev]() {
+                sl->load = std::async(std::launch::async, [sl, fc, cb, r, dev]() {
                     if (cudaSetDevice(dev) != cudaSuccess) return (int)VR_ERR_CUDA;
-                    int r = render_frame_impl(fc, cb, q.out, q.out_where, sl->s);
-                    if (r == VR_OK && cudaEventRecord(sl->done, sl->s) != cudaSuccess) r = VR_ERR_CUDA;
-                    return r;
+                    int rr = render_frame_impl(fc, cb, r->q.out, r->q.out_where, sl->s);
+                    if (rr == VR_OK && cudaEventRecord(sl->done, sl->s) != cudaSuccess) rr = VR_ERR_CUDA;
+                    return rr;
                 });
                 sl->loading = true;
                 sl->bricks = std::move(bricks);
-                sl->req = ri;
+                sl->req = r;
                 sl->cube = cb;
                 ++inflight;
                 max_conc = std::max(max_conc, inflight);
@@ -227,36 +250,202 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
             if (st == VR_OK) st = render_frame_impl(fc, cb, q.out, q.out_where, free_slot->s);
             if (st == VR_OK) st = cudaEventRecord(free_slot->done, free_slot->s) == cudaSuccess ? VR_OK : VR_ERR_CUDA;
             if (st != VR_OK) {
-                finish(ri, st);
+                finish(r, st);
                 continue;
             }
-            free_slot->req = ri;
+            free_slot->req = r;
             free_slot->cube = cb;
             ++inflight;
             max_conc = std::max(max_conc, inflight);
         }
-        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        return progress;
     }
-    for (auto &h : holds) cache_hold(c, h.cube, h.bricks, h.delta, true);
-    const double wall = ms_since(t0);
-    cleanup();
-    if (sum) {
+
+    void summary(vr_serve_summary *sum, double wall) {
+        if (!sum) return;
         std::memset(sum, 0, sizeof(*sum));
-        std::sort(lat.begin(), lat.end());
+        std::vector<double> l = lat;
+        std::sort(l.begin(), l.end());
         auto pct = [&](double p) {
-            if (lat.empty()) return 0.0;
-            const size_t i = std::min(lat.size() - 1, (size_t)std::ceil(p * lat.size()) - (p > 0 ? 1 : 0));
-            return lat[i];
+            if (l.empty()) return 0.0;
+            const size_t i = std::min(l.size() - 1, (size_t)std::ceil(p * l.size()) - (p > 0 ? 1 : 0));
+            return l[i];
         };
-        sum->completed = (int64_t)lat.size();
+        sum->completed = (int64_t)l.size();
         sum->failed = failed;
         sum->wall_ms = wall;
         sum->p50_ms = pct(0.50);
         sum->p99_ms = pct(0.99);
-        sum->max_ms = lat.empty() ? 0.0 : lat.back();
-        sum->frames_per_s = wall > 0 ? 1e3 * (double)lat.size() / wall : 0.0;
+        sum->max_ms = l.empty() ? 0.0 : l.back();
+        sum->frames_per_s = wall > 0 ? 1e3 * (double)l.size() / wall : 0.0;
         sum->max_concurrent = max_conc;
     }
-    return failed ? VR_ERR_STATE : VR_OK;
+};
+
+int serve_prepare(vr_ctx *c, bool any_streamed) {
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (any_streamed && (rc = cache_create(c)) != VR_OK) return rc;
+    if (c->frame_pending) CK(cudaEventSynchronize(c->frame_done));
+    return VR_OK;
+}
+
+}  // namespace
+}  // namespace vrh
+
+using namespace vrh;
+
+// The online server: the loop on its own host thread, fed by vr_serve_submit.
+struct vr_server {
+    vr_ctx *c = nullptr;
+    ServeCore core;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;          // signals finished requests and closing
+    std::unordered_map<int64_t, std::unique_ptr<Req>> owned;
+    std::deque<Req *> submitted;         // not yet handed to the loop
+    std::deque<Req *> completed;         // finished, not yet polled
+    int64_t next_ticket = 0;
+    int64_t outstanding = 0;             // submitted, not yet finished
+    bool closing = false;
+
+    void run() {
+        cudaSetDevice(c->device);
+        for (;;) {
+            {
+                std::lock_guard<std::mutex> l(mu);
+                while (!submitted.empty()) {
+                    core.queue.push_back(submitted.front());
+                    submitted.pop_front();
+                }
+            }
+            const bool progress = core.step();
+            bool stop = false;
+            {
+                std::lock_guard<std::mutex> l(mu);
+                if (!core.finished.empty()) {
+                    for (Req *r : core.finished) completed.push_back(r);
+                    outstanding -= (int64_t)core.finished.size();
+                    core.finished.clear();
+                    cv.notify_all();
+                }
+                stop = closing && outstanding == 0 && submitted.empty() && core.idle();
+            }
+            if (stop) break;
+            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
+};
+
+#pragma GCC visibility push(default)
+extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve_config *cfg,
+                        vr_request_result *res, vr_serve_summary *sum) {
+    if (!c || (!reqs && n > 0) || !cfg || (!res && n > 0)) return arg_fail("null argument");
+    if (n < 0 || cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
+    std::vector<Req> rq(n);
+    bool any_streamed = false;
+    for (int i = 0; i < n; ++i) {
+        const int rc = make_req(c, reqs[i], rq[i]);
+        if (rc != VR_OK) return rc;
+        if (i > 0 && reqs[i].arrival_ms < reqs[i - 1].arrival_ms) return arg_fail("requests must be in arrival order");
+        rq[i].arrival_ms = reqs[i].arrival_ms;
+        any_streamed |= find_cube(c, reqs[i].cube_id)->streamed;
+    }
+    int rc = serve_prepare(c, any_streamed);
+    if (rc) return rc;
+    ServeCore core;
+    if ((rc = core.open(c, cfg->max_inflight)) != VR_OK) {
+        core.close();
+        return rc;
+    }
+    int next = 0;
+    while (core.done < n) {
+        const double now = core.now();
+        while (next < n && rq[next].arrival_ms <= now) core.queue.push_back(&rq[next++]);
+        const bool progress = core.step();
+        core.finished.clear();
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    const double wall = core.now();
+    core.close();
+    for (int i = 0; i < n; ++i) res[i] = rq[i].res;
+    core.summary(sum, wall);
+    return core.failed ? VR_ERR_STATE : VR_OK;
+}
+
+extern "C" int vr_serve_open(vr_ctx *c, const vr_serve_config *cfg, vr_server **out) {
+    if (!c || !cfg || !out) return arg_fail("null argument");
+    if (cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
+    *out = nullptr;
+    bool any_streamed = false;
+    for (auto &kv : c->cubes) any_streamed |= kv.second->streamed;
+    int rc = serve_prepare(c, any_streamed);
+    if (rc) return rc;
+    std::unique_ptr<vr_server> s(new vr_server());
+    s->c = c;
+    if ((rc = s->core.open(c, cfg->max_inflight)) != VR_OK) {
+        s->core.close();
+        return rc;
+    }
+    try {
+        s->th = std::thread([srv = s.get()]() { srv->run(); });
+    } catch (...) {
+        s->core.close();
+        return fail(VR_ERR_OOM, "could not start the serving thread");
+    }
+    *out = s.release();
+    return VR_OK;
+}
+
+extern "C" int vr_serve_submit(vr_server *s, const vr_request *req, int64_t *ticket) {
+    if (!s || !req || !ticket) return arg_fail("null argument");
+    std::unique_ptr<Req> r(new Req());
+    const int rc = make_req(s->c, *req, *r);
+    if (rc != VR_OK) return rc;
+    Req *p = r.get();
+    std::lock_guard<std::mutex> l(s->mu);
+    if (s->closing) return fail(VR_ERR_STATE, "the server is closing");
+    p->arrival_ms = s->core.now();
+    p->ticket = s->next_ticket++;
+    *ticket = p->ticket;
+    s->owned.emplace(p->ticket, std::move(r));
+    s->submitted.push_back(p);
+    ++s->outstanding;
+    return VR_OK;
+}
+
+extern "C" int vr_serve_poll(vr_server *s, int64_t *tickets, vr_request_result *results, int cap, int *n,
+                             int wait_ms) {
+    if (!s || !n || (cap > 0 && (!tickets || !results))) return arg_fail("null argument");
+    if (cap < 0 || wait_ms < 0 || wait_ms > 60000) return arg_fail("cap >= 0 and 0 <= wait_ms <= 60000");
+    std::unique_lock<std::mutex> l(s->mu);
+    if (s->completed.empty() && wait_ms > 0)
+        s->cv.wait_for(l, std::chrono::milliseconds(wait_ms), [s]() { return !s->completed.empty(); });
+    int k = 0;
+    while (k < cap && !s->completed.empty()) {
+        Req *r = s->completed.front();
+        s->completed.pop_front();
+        tickets[k] = r->ticket;
+        results[k] = r->res;
+        s->owned.erase(r->ticket);
+        ++k;
+    }
+    *n = k;
+    return VR_OK;
+}
+
+extern "C" int vr_serve_close(vr_server *s, vr_serve_summary *sum) {
+    if (!s) return arg_fail("null argument");
+    {
+        std::lock_guard<std::mutex> l(s->mu);
+        s->closing = true;
+    }
+    if (s->th.joinable()) s->th.join();
+    const double wall = s->core.now();
+    s->core.close();
+    s->core.summary(sum, wall);
+    const int rc = s->core.failed ? VR_ERR_STATE : VR_OK;
+    delete s;
+    return rc;
 }
 #pragma GCC visibility pop

@@ -194,3 +194,44 @@ def test_global_termination_requests_in_the_mix(world):
     assert all(r["status"] == 0 for r in results), results
     for r in reqs:
         _same(r, _alone(ctx, r))
+
+
+def test_online_server_takes_requests_while_frames_run(world):
+    """vr_serve_open / submit / poll / close: requests handed over one at a time while earlier
+    ones render (resident and streamed cubes, DVR and MIP), results collected as they finish;
+    every ticket comes back once, each result equals the frame rendered alone, and a request
+    submitted after others completed is still served by the same loop."""
+    import time
+
+    import torch
+    ctx, cubes = world
+    reqs = _requests(cubes, 48, 400.0, 23, "cuda")
+    srv = ctx.serve_online(max_inflight=5)
+    got = {}
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        while (time.perf_counter() - t0) * 1e3 < r["arrival_ms"]:
+            for t, res in srv.poll(wait_ms=0):
+                got[t] = res
+            time.sleep(0.0002)
+        tickets.append(srv.submit(r))
+    assert tickets == list(range(len(reqs)))
+    deadline = time.perf_counter() + 120
+    while len(got) < len(reqs) - 1 and time.perf_counter() < deadline:
+        for t, res in srv.poll(wait_ms=100):
+            assert t not in got
+            got[t] = res
+    late = _requests(cubes, 1, 1.0, 99, "cuda")[0]       # after the loop went idle
+    tickets.append(srv.submit(late))
+    while len(got) < len(reqs) + 1 and time.perf_counter() < deadline:
+        for t, res in srv.poll(wait_ms=100):
+            got[t] = res
+    summary = srv.close()
+    torch.cuda.synchronize()
+    assert sorted(got) == tickets
+    assert all(res["status"] == 0 for res in got.values()), got
+    assert summary["completed"] == len(reqs) + 1 and summary["failed"] == 0
+    for t, r in enumerate(reqs + [late]):
+        assert got[t]["latency_ms"] > 0 and got[t]["done_ms"] >= got[t]["admit_ms"]
+        _same(r, _alone(ctx, r))
