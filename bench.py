@@ -385,13 +385,13 @@ def adjoint_leg(ctx, device):
             "ms_per_batch_fwd_bwd": round(ms, 3), "ms_per_view_fwd_bwd": round(ms / len(cams), 3)}
 
 
-def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4):
+def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=60, seed=4):
     """Continuous batching through the online server (vr_serve_open / submit / poll): requests
     are submitted by this process at Poisson arrival times while earlier ones render, over three
     cubes -- the resident HIPASS-scale cube (1024^2 or 512^2 orbit views), a resident 256^3 cube
     (512^2 orbit views) and the 4096x4096x4800 virtual cube (322 GB as FP32, above HBM),
     streamed through the HBM brick cache: its 512^2 requests come from two viewers flying
-    across it (the eye moves 48 voxels sideways per request, so each frame needs some bricks the
+    across it (the eye moves 16 voxels sideways per request, so each frame needs some bricks the
     cache does not hold) and occasional jumps to a random region.  Rates are swept; latency is
     submission to completion, per request kind; cache misses and bytes streamed are counted
     inside each timed run."""
@@ -407,8 +407,8 @@ def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4
     luts = [synth.ramp_lut(), synth.shifted_ramp_lut(vrange=(-3.0, 100.0))]
     # two viewers strafing across the cube (the eye moves sideways, so each frame's frustum
     # takes in bricks at its leading edge that earlier frames did not need)
-    paths = [dict(eye=np.array([-200.0, 300.0, 1800.0]), step=np.array([0.0, 48.0, 0.0]), look=np.array([1.0, 0.05, 0.1])),
-             dict(eye=np.array([300.0, 2900.0, -200.0]), step=np.array([48.0, 0.0, 0.0]), look=np.array([0.08, -0.05, 1.0]))]
+    paths = [dict(eye=np.array([-200.0, 300.0, 1800.0]), step=np.array([0.0, 16.0, 0.0]), look=np.array([1.0, 0.05, 0.1])),
+             dict(eye=np.array([300.0, 2900.0, -200.0]), step=np.array([16.0, 0.0, 0.0]), look=np.array([0.08, -0.05, 1.0]))]
     fly = [0, 0]
 
     def virtual_cam():
@@ -421,9 +421,9 @@ def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4
             p = paths[v]
             eye = p["eye"] + fly[v] * p["step"]
             tgt = eye + p["look"] * 500.0
-            fly[v] = (fly[v] + 1) % 64
+            fly[v] += 1
             kind = "virtual_fly"
-        return dict(view=synth.look_at(eye, tgt), proj=1, param=math.radians(12.0), W=512, H=512), kind
+        return dict(view=synth.look_at(eye, tgt), proj=1, param=math.radians(8.0), W=512, H=512), kind
 
     def make_request(arrival_ms):
         u = rng.uniform()
@@ -431,7 +431,7 @@ def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4
             res = 1024 if rng.uniform() < 0.5 else 512
             cam = synth.orbit_camera(synth.HIPASS, int(rng.integers(0, 64)), W=res, H=res)
             cube, vr, step, kind = hip_cid, (-3.0, 100.0), 1.0, f"hipass{res}"
-        elif u < 0.75:
+        elif u < 0.85:
             c = np.array(diff["shape"], np.float64) / 2
             view = synth.orbit_view(45.0 * int(rng.integers(0, 8)), c, 1.5 * 0.5 * math.sqrt(3) * 256)
             cam = dict(view=view, proj=1, param=math.radians(60.0), W=512, H=512)
@@ -443,6 +443,16 @@ def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4
         return dict(cube=cube, cam=cam, mode="dvr", step=step, tau=0.99,
                     lut=luts[int(rng.integers(0, 2))], vrange=vr, arrival_ms=arrival_ms, out=out), kind
 
+    # each viewer's first view once, untimed (its whole frustum is a cold start)
+    t_cold = time.perf_counter()
+    for p in paths:
+        ctx.set_transfer_function(luts[0], -3.0, 100.0)
+        ctx.set_camera_dict(dict(view=synth.look_at(p["eye"], p["eye"] + p["look"] * 500.0), proj=1,
+                                 param=math.radians(8.0), W=512, H=512))
+        ctx.set_render_params("dvr", 1.0, 0.99)
+        ctx.render_frame(vcid)
+    torch.cuda.synchronize()
+    cold_s = time.perf_counter() - t_cold
     runs = []
     for ri, rate in enumerate(rates):
         arrivals = synth.poisson_arrivals(seed + ri, rate, n_req) * 1e3
@@ -480,10 +490,11 @@ def serving_leg(ctx, hip_cid, device, rates=(10.0, 20.0, 40.0), n_req=90, seed=4
     ctx.free_cube(dcid)
     ctx.free_cube(vcid)
     return {"workload": f"{n_req} Poisson requests per rate, submitted online while frames run: "
-                        "HIPASS-scale 1024^2/512^2 (40 %), 256^3 cube 512^2 (35 %), 4096x4096x4800 "
+                        "HIPASS-scale 1024^2/512^2 (40 %), 256^3 cube 512^2 (45 %), 4096x4096x4800 "
                         "virtual cube (322 GB, streamed through a 64 GB brick cache with slice-atlas "
-                        "slots) 512^2 fly-throughs and jumps (25 %); two tables",
-            "max_inflight": 4, "rates": runs,
+                        "slots) 512^2 views, 8 deg, of two viewers strafing 16 voxels per request and "
+                        "jumps to random regions (15 %); two tables",
+            "max_inflight": 4, "virtual_first_views_s": round(cold_s, 2), "rates": runs,
             "p50_ms": runs[0]["p50_ms"], "p99_ms": runs[0]["p99_ms"]}
 
 
