@@ -37,7 +37,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "hipass_slab", "gass", "pr1"])
+    ap.add_argument("--config", default="hipass", choices=["hipass", "hipass_small", "hipass_slab", "gass", "gass_slab",
+                                                           "pr1"])
     ap.add_argument("--no-extras", action="store_true", help="skip FP16, adjoint and CPU legs")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick storage of the main leg (the headline line uses f32)")
@@ -157,6 +158,9 @@ def make_cube(cfg_name: str, device: str):
                                  device=device), c
     if cfg_name == "gass":
         return synth.gass_cube(device=device), synth.GASS
+    if cfg_name == "gass_slab":
+        c = synth.GASS_SLAB
+        return synth.gass_cube(seed=c["seed"], shape_xyz=c["shape"], slab=c["slab"], device=device), c
     import torch
     return torch.from_numpy(synth.pr1_cube(seed=0)).to(device), dict(synth.PR1, n_views=64,
                                                                        fov_deg=60.0, eye_factor=1.5)

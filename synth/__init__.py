@@ -29,7 +29,7 @@ __all__ = [
     "ramp_lut", "shifted_ramp_lut", "constant_lut", "random_lut",
     "look_at", "orbit_view", "pr1_camera", "axis_ortho_camera", "random_camera",
     "sample_pixels", "poisson_arrivals",
-    "PR1", "HIPASS", "HIPASS_SMALL", "HIPASS_SLAB", "GASS", "DIFF", "orbit_camera",
+    "PR1", "HIPASS", "HIPASS_SMALL", "HIPASS_SLAB", "GASS", "GASS_SLAB", "DIFF", "orbit_camera",
 ]
 
 # ----------------------------------------------------------------------------------------------
@@ -49,6 +49,10 @@ HIPASS_SLAB = dict(HIPASS, name="HIPASS-recipe 1720x1720x256", shape=(1720, 1720
 GASS = dict(name="GASS-scale 2048x2048x1600", shape=(2048, 2048, 1600), seed=2, W=1024,
             H=1024, step=0.5, tau=0.99, vrange=(-2.0, 8.0), brick=(256, 256, 256), ghost=1,
             n_views=64, fov_deg=60.0, eye_factor=1.5)
+# the GASS recipe 256 channels deep (4.3 GB): the full cube's sky extent with its 200-voxel
+# emission slab, so its rays are as far apart and its bricks as varied as the full frame's
+# (the case DRAM counters of GASS frames are captured on)
+GASS_SLAB = dict(GASS, name="GASS-recipe 2048x2048x256", shape=(2048, 2048, 256), slab=(28, 228))
 DIFF = dict(name="Diff 256^3", shape=(256, 256, 256), seed=3, W=512, H=512, step=0.5, tau=0.99,
             vrange=(-3.0, 20.0), brick=(128, 128, 128), ghost=1, n_views=8)
 
