@@ -326,14 +326,31 @@ def compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np, frames=16):
     return res
 
 
+def traffic_entry(name: str):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    return json.load(open(p)).get(name) if os.path.exists(p) else None
+
+
 def roofline(st, steps, peak, src, name):
-    per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
-    ms = st["ms_raycast"] / max(st["timed_frames"], 1)
+    """The HBM roofline of the ray-cast launch, and beside it the ceiling that binds the texture
+    path: the texels its gathers deliver to registers (32 B per sample: two gathers of four
+    32-bit texels, FP16 texels widened alike) against the L1TEX writeback rate derived from ncu
+    (32 B per cycle per SM)."""
+    nl = max(st["timed_frames"], 1)
+    per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / nl
+    ms = st["ms_raycast"] / nl
     achieved = per_launch / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": kernel_traffic(name),
-            "peak_source": src, "kernel": name, "algorithmic_bytes_per_launch": int(per_launch),
-            "launch_ms": round(ms, 4)}
+    rl = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+          "frac": round(achieved / peak, 4), "traffic": kernel_traffic(name),
+          "peak_source": src, "kernel": name, "algorithmic_bytes_per_launch": int(per_launch),
+          "launch_ms": round(ms, 4)}
+    wb = traffic_entry("l1tex_texel_writeback_peak_gbs")
+    if wb:
+        tex = 32.0 * st["samples"] / nl / (ms * 1e-3) / 1e9
+        rl["l1tex"] = {"bound": "l1tex texel writeback", "achieved": round(tex, 1), "peak": wb["value"],
+                       "unit": "GB/s", "frac": round(tex / wb["value"], 4),
+                       "peak_source": "derived from ncu (profiles/traffic.json)"}
+    return rl
 
 
 def adjoint_leg(ctx, device):
@@ -564,9 +581,18 @@ def empty_space_leg(ctx, device, steps=16):
         rc_ms = st["ms_raycast"] / max(st["timed_frames"], 1)
         frames[storage] = {"ms_per_frame": round(ms, 3),
                            "Gsamples_per_s": round(st["samples"] / (ms * steps * 1e-3) / 1e9, 2),
-                           "raycast_GB_per_s": round(alg / (rc_ms * 1e-3) / 1e9, 1)}
+                           "raycast_GB_per_s_upper_bound": round(alg / (rc_ms * 1e-3) / 1e9, 1)}
+        g = traffic_entry("k_raycast<f32,DVR>@GASS")
+        if storage == "f32" and g:
+            dram = g["traffic_over_algorithmic"] * alg / (rc_ms * 1e-3) / 1e9
+            frames[storage]["raycast_dram_GB_per_s"] = round(dram, 1)
+            frames[storage]["hbm_frac_of_measured"] = round(dram / peaks()[0], 4)
     res["gass_frames"] = dict(frames, table=f"ramp over [{cfg['vrange'][0]}, {cfg['vrange'][1]}], "
-                                            f"step {cfg['step']}, slice atlases")
+                                            f"step {cfg['step']}, slice atlases",
+                              bytes="upper bound: stored bytes of every drawn brick / ray-cast time "
+                                    "(segments stop early, so a drawn brick is not read whole); "
+                                    "dram: that times the DRAM traffic / algorithmic bytes ratio of "
+                                    "the GASS-recipe slab capture (0.663)")
     ctx.free_cube(cid)
     res["workload"] = (f"GASS-scale 2048x2048x1600, {cfg['W']}x{cfg['H']} orbit, step "
                        f"{cfg['step']}, table with zero opacity below 3.0 (noise sd 0.5)")
