@@ -235,3 +235,49 @@ def test_online_server_takes_requests_while_frames_run(world):
     for t, r in enumerate(reqs + [late]):
         assert got[t]["latency_ms"] > 0 and got[t]["done_ms"] >= got[t]["admit_ms"]
         _same(r, _alone(ctx, r))
+
+
+def test_online_server_from_several_threads_and_its_errors(world):
+    """Submissions from four host threads at once each get their own ticket and result; poll
+    returns at most `cap` results per call; a request for an unknown cube is refused at submit;
+    results not polled before close are dropped without harm; a closed server takes nothing."""
+    import threading
+
+    import paper_1008_0135_gb300 as P
+    import torch
+    ctx, cubes = world
+    reqs = _requests({"pr1": cubes["pr1"], "b96": cubes["b96"]}, 32, 1e9, 31, "cuda")
+    srv = ctx.serve_online(max_inflight=4)
+    tickets = {}
+    lock = threading.Lock()
+
+    def worker(part):
+        for i in part:
+            t = srv.submit(reqs[i])
+            with lock:
+                tickets[t] = i
+
+    ths = [threading.Thread(target=worker, args=(list(range(k, 32, 4)),)) for k in range(4)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert sorted(tickets) == list(range(32))
+    bad = dict(reqs[0], cube=12345)
+    with pytest.raises(P.VrError):
+        srv.submit(bad)
+    got = {}
+    import time
+    deadline = time.perf_counter() + 120
+    while len(got) < 30 and time.perf_counter() < deadline:
+        batch = srv.poll(wait_ms=50, cap=3)
+        assert len(batch) <= 3
+        for t, res in batch:
+            got[t] = res
+    summary = srv.close()                       # the last results may never be polled
+    torch.cuda.synchronize()
+    assert summary["completed"] == 32 and summary["failed"] == 0
+    for t, res in got.items():
+        assert res["status"] == 0
+        r = reqs[tickets[t]]
+        _same(r, _alone(ctx, r))

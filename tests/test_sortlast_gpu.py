@@ -176,3 +176,47 @@ def test_two_processes_exchange_subimages_over_gloo(setup):
         assert p.exitcode == 0
     for r in range(2):
         assert np.array_equal(got[r], local), r
+
+
+def test_sortlast_with_16bit_bricks_mask_window_and_streamed_cube(setup, orc):
+    """Parts compose the whole frame for FP16 bricks with a channel mask and a render window
+    (DVR within 1e-6, MIP bit for bit), and for a streamed (procedural) cube, whose parts make
+    only their own bricks resident."""
+    import paper_1008_0135_gb300 as P
+    ctx, cube, cid = setup
+    lut = synth.random_lut(9, n=48, alpha_max=0.3)
+    ctx.set_transfer_function(lut, -3.0, 12.0)
+    ctx.set_bricking(cid, BRICK, 1, "f16")
+    try:
+        mask = np.ones(SHAPE[2], np.uint8)
+        mask[5:9] = 0
+        ctx.set_channel_mask(mask)
+        ctx.set_window((10, 4, 2), (90, 60, 37))
+        for cam in CAMS[:2]:
+            ctx.set_camera_dict(cam)
+            for mode in ("dvr", "mip"):
+                ctx.set_render_params(mode, 0.5, 0.99)
+                whole = ctx.render_frame(cid).cpu().numpy()
+                parts = _sortlast_local(ctx, cid, (3,)).cpu().numpy()
+                if mode == "mip":
+                    assert np.array_equal(parts, whole)
+                else:
+                    assert np.abs(parts - whole).max() <= 1e-6
+    finally:
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+        ctx.set_bricking(cid, BRICK, 1, "f32")
+    with P.Context(0, cache_bytes=40 * 66 ** 3 * 4) as sc:
+        shape = (200, 140, 120)
+        sid = sc.load_cube_procedural(4, shape)
+        sc.set_bricking(sid, (64, 64, 64), 1, "f32")
+        sc.set_transfer_function(lut, -3.0, 12.0)
+        cam = synth.random_camera(np.random.default_rng(5), shape, 64, 48, proj=1)
+        sc.set_camera_dict(cam)
+        sc.set_render_params("dvr", 0.5, 0.99)
+        whole = sc.render_frame(sid).cpu().numpy()
+        parts = _sortlast_local(sc, sid, (2, 2)).cpu().numpy()
+        assert np.abs(parts - whole).max() <= 1e-6
+        ref, flags, _ = orc.render(orc.Procedural(4, shape), lut, (-3.0, 12.0), cam, step=0.5, tau=0.99,
+                                   brick=(64, 64, 64))
+        compare_dvr(parts.reshape(-1, 4), ref, flags, 0.99)
