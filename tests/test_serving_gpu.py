@@ -277,6 +277,8 @@ def test_online_server_from_several_threads_and_its_errors(world):
     summary = srv.close()                       # the last results may never be polled
     torch.cuda.synchronize()
     assert summary["completed"] == 32 and summary["failed"] == 0
+    with pytest.raises(P.VrError):
+        srv.submit(reqs[0])
     for t, res in got.items():
         assert res["status"] == 0
         r = reqs[tickets[t]]
