@@ -19,6 +19,7 @@
 #include <deque>
 #include <future>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -342,7 +343,12 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
                         vr_request_result *res, vr_serve_summary *sum) {
     if (!c || (!reqs && n > 0) || !cfg || (!res && n > 0)) return arg_fail("null argument");
     if (n < 0 || cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
-    std::vector<Req> rq(n);
+    std::vector<Req> rq;
+    try {
+        rq.resize(n);
+    } catch (const std::bad_alloc &) {
+        return fail(VR_ERR_OOM, "no host memory for the requests");
+    }
     bool any_streamed = false;
     for (int i = 0; i < n; ++i) {
         const int rc = make_req(c, reqs[i], rq[i]);
@@ -381,7 +387,8 @@ extern "C" int vr_serve_open(vr_ctx *c, const vr_serve_config *cfg, vr_server **
     for (auto &kv : c->cubes) any_streamed |= kv.second->streamed;
     int rc = serve_prepare(c, any_streamed);
     if (rc) return rc;
-    std::unique_ptr<vr_server> s(new vr_server());
+    std::unique_ptr<vr_server> s(new (std::nothrow) vr_server());
+    if (!s) return fail(VR_ERR_OOM, "no host memory for the server");
     s->c = c;
     if ((rc = s->core.open(c, cfg->max_inflight)) != VR_OK) {
         s->core.close();
@@ -399,19 +406,23 @@ extern "C" int vr_serve_open(vr_ctx *c, const vr_serve_config *cfg, vr_server **
 
 extern "C" int vr_serve_submit(vr_server *s, const vr_request *req, int64_t *ticket) {
     if (!s || !req || !ticket) return arg_fail("null argument");
-    std::unique_ptr<Req> r(new Req());
-    const int rc = make_req(s->c, *req, *r);
-    if (rc != VR_OK) return rc;
-    Req *p = r.get();
-    std::lock_guard<std::mutex> l(s->mu);
-    if (s->closing) return fail(VR_ERR_STATE, "the server is closing");
-    p->arrival_ms = s->core.now();
-    p->ticket = s->next_ticket++;
-    *ticket = p->ticket;
-    s->owned.emplace(p->ticket, std::move(r));
-    s->submitted.push_back(p);
-    ++s->outstanding;
-    return VR_OK;
+    try {
+        std::unique_ptr<Req> r(new Req());
+        const int rc = make_req(s->c, *req, *r);
+        if (rc != VR_OK) return rc;
+        Req *p = r.get();
+        std::lock_guard<std::mutex> l(s->mu);
+        if (s->closing) return fail(VR_ERR_STATE, "the server is closing");
+        p->arrival_ms = s->core.now();
+        p->ticket = s->next_ticket++;
+        *ticket = p->ticket;
+        s->owned.emplace(p->ticket, std::move(r));
+        s->submitted.push_back(p);
+        ++s->outstanding;
+        return VR_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(VR_ERR_OOM, "no host memory for the request");
+    }
 }
 
 extern "C" int vr_serve_poll(vr_server *s, int64_t *tickets, vr_request_result *results, int cap, int *n,
