@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick storage of the main leg (the headline line uses f32)")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
-    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed", "serving"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed", "serving", "sortlast"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -252,6 +252,69 @@ def sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, steps, warmup):
             "ms_per_frame": round(1e3 * t / steps, 4), "ranks": dist.world,
             "what": "one frame per step split over all ranks: longest-axis slabs, sub-image bands "
                     "exchanged over NCCL, staged depth-ordered compositing, frame gathered on every rank"}
+
+
+def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8, counts_list=((2,), (4,), (8,))):
+    """Sort-last on one GPU, part by part (Sections 2.2, 2.5, 3): for N parts of a longest-axis cut
+    (equal layer counts, and cuts balanced by the view's estimated cost) every part's sub-image
+    of the same orbit views is rendered and timed alone (CUDA events around each part's frame),
+    then the staged composite of all parts is timed.  With one part per GPU the frame would take
+    the slowest part plus a rank's share of the compositing plus the exchange (each rank sends
+    and receives (N - 1)/N of a frame of (C, T) per stage, not timed here): the projection is
+    that sum without the exchange, its speedup over the whole frame, and the parts' imbalance
+    (slowest / mean), the paper's limit on speedup."""
+    import torch
+    from paper_1008_0135_gb300 import sortlast as SL
+    ctx.set_transfer_function(lut, *vr)
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        ev[0].record(st)
+        r = fn()
+        ev[1].record(st)
+        torch.cuda.synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    whole = []
+    for v in range(views):
+        ctx.set_camera_dict(cams[v * len(cams) // views])
+        ctx.render_frame(cid)                              # warm
+        whole.append(timed(lambda: ctx.render_frame(cid))[1])
+    res = {"whole_ms_per_frame": round(float(np.mean(whole)), 4), "views": views}
+    for counts in counts_list:
+        world = int(np.prod(counts))
+        for balanced in (False, True):
+            ctx.set_partition_balance(cid, balanced)
+            proj, imb, comp_share = [], [], []
+            for v in range(views):
+                ctx.set_camera_dict(cams[v * len(cams) // views])
+                subs, times = [], []
+                for r in range(world):
+                    ctx.set_partition(cid, counts, SL.digits(r, counts))
+                    ctx.render_subimage(cid)               # warm (and the cuts for this view)
+                    sub, ms = timed(lambda: ctx.render_subimage(cid))
+                    subs.append(sub)
+                    times.append(ms)
+
+                def blend(level, stack, row0, final, members):
+                    ctx.set_partition(cid, counts, SL.digits(members[0], counts))
+                    return ctx.composite_subimages(cid, level, stack, row0, final)
+
+                _, cms = timed(lambda: SL.composite_parts_local(subs, counts, blend))
+                proj.append(max(times) + cms / world)
+                imb.append(max(times) / (sum(times) / world))
+                comp_share.append(cms / world)
+            key = f"{world}_{'balanced' if balanced else 'equal'}"
+            res[key] = {"projected_ms_per_frame": round(float(np.mean(proj)), 4),
+                        "speedup_vs_whole": round(res["whole_ms_per_frame"] / float(np.mean(proj)), 2),
+                        "imbalance_slowest_over_mean": round(float(np.mean(imb)), 3),
+                        "composite_ms_per_rank": round(float(np.mean(comp_share)), 4),
+                        "exchange_bytes_per_rank": int(cfg["W"] * cfg["H"] * 16 * (world - 1) / world)}
+    ctx.set_partition(cid)
+    ctx.set_partition_balance(cid, False)
+    return res
 
 
 def compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np, frames=16):
@@ -723,6 +786,7 @@ def run_ours(args, dist):
                       "loop": "table + camera set, frame queued with an asynchronous copy into "
                               "one of two pinned host frames, previous frame read"}
         if dist.rank == 0:
+            res["sortlast_projection"] = sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr)
             res["adjoint"] = adjoint_leg(ctx, device)
             res["serving"] = serving_leg(ctx, cid, device)
             res["compressed"] = compressed_leg(ctx, cid, cfg, cams, lut, vr, out, cube_np)
@@ -790,7 +854,7 @@ def main():
         print(json.dumps({"leg": "adjoint", **adjoint_leg(ctx, f"cuda:{dist.local}")}))
         ctx.close()
         return
-    if args.leg in ("occlusion", "compressed", "serving"):
+    if args.leg in ("occlusion", "compressed", "serving", "sortlast"):
         import torch
         import paper_1008_0135_gb300 as P
         P.build()
@@ -810,6 +874,8 @@ def main():
             res = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
         elif args.leg == "serving":
             res = serving_leg(ctx, cid, device)
+        elif args.leg == "sortlast":
+            res = sortlast_projection_leg(ctx, cid, cfg, cams, synth.ramp_lut(), cfg["vrange"])
         else:
             res = compressed_leg(ctx, cid, cfg, cams, synth.ramp_lut(), cfg["vrange"], out, cube_np)
         print(json.dumps({"leg": args.leg, **res}))

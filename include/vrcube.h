@@ -292,6 +292,18 @@ int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *c
  * outside 1..65536, index outside 0..counts-1), VR_ERR_NOT_FOUND. */
 int vr_set_partition(vr_ctx *ctx, int cube_id, int nlevels, const int *counts, const int *index);
 
+/* How the partition's cuts are placed (Section 3: the slowest GPU sets the frame time, and a
+ * part's work depends on the view).  0 (the default): equal layer counts.  1: balanced for the
+ * current camera -- each cut falls where the cumulative estimated cost of the part's brick
+ * layers crosses k/counts[L] of its total, a brick's cost being the samples a full bundle of
+ * the frame's rays takes through it (its window-clipped core volume over a pixel's footprint
+ * at its depth times the step; 0 when skipped as empty space or outside the frame; early
+ * termination not modelled).  Balanced parts change with the camera, so every rank needs the
+ * whole cube (or the bricks any view can give it); the ranks agree on the cuts because they
+ * compute them from the same camera, table and bricking.  The no-allocation renderer refuses
+ * balanced partitions (VR_ERR_UNSUPPORTED).  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND. */
+int vr_set_partition_balance(vr_ctx *ctx, int cube_id, int balanced);
+
 /* The brick index range [lo, hi) per axis of the cube's part, and (axes, NULL to skip) the split
  * axis (0 x, 1 y, 2 z) of each partition level.  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND,
  * VR_ERR_STATE (no bricking). */

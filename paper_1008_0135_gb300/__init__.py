@@ -330,6 +330,11 @@ class Context:
         ia = (C.c_int * max(n, 1))(*[int(v) for v in index])
         _check(self._L.vr_set_partition(self._h, cube_id, n, ca, ia), "vr_set_partition")
 
+    def set_partition_balance(self, cube_id: int, balanced: bool):
+        """Cuts at equal layer counts (False) or balanced by the current camera's estimated cost."""
+        _check(self._L.vr_set_partition_balance(self._h, cube_id, int(bool(balanced))),
+               "vr_set_partition_balance")
+
     def partition(self, cube_id: int, nlevels: int = 8):
         """(lo, hi, axes): the part's brick index ranges per axis and the split axis per level."""
         lo, hi, ax = (C.c_int * 3)(), (C.c_int * 3)(), (C.c_int * 8)()

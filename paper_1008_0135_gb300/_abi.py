@@ -78,6 +78,7 @@ SIGNATURES = {
     "vr_render_frame_noalloc": (I, [VP, I, VP, VP]),
     "vr_set_partition": (I, [VP, I, I, P(I), P(I)]),
     "vr_get_partition": (I, [VP, I, P(I), P(I), P(I)]),
+    "vr_set_partition_balance": (I, [VP, I, I]),
     "vr_render_subimage": (I, [VP, I, VP, I, VP]),
     "vr_composite_subimages": (I, [VP, I, I, I, VP, I, I, I, VP, VP]),
     "vr_render_backward": (I, [VP, I, VP, VP, VP, VP]),

@@ -77,36 +77,7 @@ void alpha_prefix(const vr_ctx *c, std::vector<int> &pre) {
 // stencil's range, so a brick whose stored values map only to entries of zero opacity adds
 // exactly nothing (every sample has a = 0: colour += T*0, T *= 1).  The range is widened for
 // the FP32 rounding of the mapping and, for 16-bit bricks, for the rounding of the codes.
-// Recursive longest-axis split (Section 2.2, Fig. 3): at every level the current part's brick
-// range is cut along its longest axis (in voxels; ties to the lower axis) into counts[L]
-// consecutive slabs of whole brick layers, as even as the layer count allows, and the path
-// keeps slab index[L].  A part may be empty when a level has more slabs than layers.
-PartBox partition_box(const Cube *cb) {
-    PartBox p{};
-    for (int a = 0; a < 3; ++a) { p.lo[a] = 0; p.hi[a] = (int)cb->nb[a]; }
-    for (int L = 0; L < cb->part_nlev; ++L) {
-        int axis = 0;
-        int64_t best = -1;
-        for (int a = 0; a < 3; ++a) {
-            const int64_t ext = std::min<int64_t>((int64_t)p.hi[a] * cb->B[a], cb->n[a]) - (int64_t)p.lo[a] * cb->B[a];
-            if (ext > best) { best = ext; axis = a; }
-        }
-        const int64_t layers = p.hi[axis] - p.lo[axis], n = cb->part_counts[L], k = cb->part_index[L];
-        const int s0 = p.lo[axis] + (int)(layers * k / n), s1 = p.lo[axis] + (int)(layers * (k + 1) / n);
-        p.axis[L] = axis;
-        p.lo[axis] = s0;
-        p.hi[axis] = s1;
-    }
-    return p;
-}
-
 bool window_clip(const vr_ctx *c, const Cube *cb, const DrawBrick &b, float lo[3], float hi[3]) {
-    if (cb->part_nlev > 0) {                 // bricks outside the cube's part are not drawn
-        const PartBox p = partition_box(cb);
-        const int64_t ci[3] = {b.brick % cb->nb[0], (b.brick / cb->nb[0]) % cb->nb[1], b.brick / (cb->nb[0] * cb->nb[1])};
-        for (int a = 0; a < 3; ++a)
-            if (ci[a] < p.lo[a] || ci[a] >= p.hi[a]) return false;
-    }
     for (int a = 0; a < 3; ++a) {
         lo[a] = b.lo[a];
         hi[a] = b.hi[a];
@@ -138,6 +109,125 @@ bool skip_brick(const vr_ctx *c, const Cube *cb, size_t b, const int *pre) {
     const long i0 = std::max(0L, (long)std::floor(xl));
     const long i1 = std::min((long)n1, (long)std::floor(xh) + 1);
     return pre[i1 + 1] - pre[i0] == 0;
+}
+
+// Estimated ray-cast cost of brick bi for the current camera: the samples a full bundle of the
+// frame's rays takes through it, its (window-clipped) core volume over the volume one sample
+// stands for (a pixel's footprint at the brick's depth times the step); 0 when it is skipped
+// (empty space), clipped away or projects entirely outside the frame.  Early termination is
+// not modelled.
+double brick_cost(const vr_ctx *c, const Cube *cb, size_t bi, const int *apre) {
+    const DrawBrick &b = cb->tmpl[bi];
+    float lo[3], hi[3];
+    if (!window_clip(c, cb, b, lo, hi) || skip_brick(c, cb, bi, apre)) return 0.0;
+    const Cam &m = c->cam;
+    double vol = 1.0, ctr[3], diag2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        vol *= (double)hi[a] - lo[a];
+        ctr[a] = 0.5 * ((double)lo[a] + hi[a]);
+        diag2 += ((double)hi[a] - lo[a]) * ((double)hi[a] - lo[a]);
+    }
+    // projected extent (the corners' image-plane box) against the frame
+    double mnx = 1e300, mny = 1e300, mxx = -1e300, mxy = -1e300;
+    bool behind = false;
+    for (int k = 0; k < 8; ++k) {
+        const double q[3] = {(k & 1) ? hi[0] : lo[0], (k & 2) ? hi[1] : lo[1], (k & 4) ? hi[2] : lo[2]};
+        double e[3];
+        for (int r = 0; r < 3; ++r) e[r] = m.R[3 * r] * q[0] + m.R[3 * r + 1] * q[1] + m.R[3 * r + 2] * q[2] + m.t[r];
+        double sx, sy;
+        if (m.proj == VR_PERSP) {
+            if (e[2] > -1e-6) { behind = true; continue; }
+            sx = e[0] / (-e[2]) / m.th_w;
+            sy = e[1] / (-e[2]) / m.th;
+        } else {
+            sx = e[0] / m.half_w;
+            sy = e[1] / m.half_h;
+        }
+        mnx = std::min(mnx, sx); mxx = std::max(mxx, sx);
+        mny = std::min(mny, sy); mxy = std::max(mxy, sy);
+    }
+    if (!behind && (mxx < -1.0 || mnx > 1.0 || mxy < -1.0 || mny > 1.0)) return 0.0;
+    double pix;
+    if (m.proj == VR_PERSP) {
+        const double ez = m.R[6] * ctr[0] + m.R[7] * ctr[1] + m.R[8] * ctr[2] + m.t[2];
+        const double depth = std::max(-ez, 0.5 * std::sqrt(diag2));
+        pix = 2.0 * depth * m.th / m.H;
+    } else {
+        pix = 2.0 * m.half_h / m.H;
+    }
+    return vol / (pix * pix * (double)c->step);
+}
+
+// Recursive longest-axis split (Section 2.2, Fig. 3): at every level the current part's brick
+// range is cut along its longest axis (in voxels; ties to the lower axis) into counts[L]
+// consecutive slabs of whole brick layers and the path keeps slab index[L].  Equal split: as
+// even a layer count as possible.  Balanced split (Section 3: the slowest GPU sets the frame
+// time, and the work of a part depends on the view): the cuts fall where the cumulative
+// estimated cost of the part's layers for the current camera crosses k/counts[L] of its total,
+// each slab keeping at least one layer while layers last.  A part may be empty when a level has
+// more slabs than layers.
+PartBox partition_box(const vr_ctx *c, const Cube *cb) {
+    PartBox p{};
+    for (int a = 0; a < 3; ++a) { p.lo[a] = 0; p.hi[a] = (int)cb->nb[a]; }
+    std::vector<double> cost;
+    const bool balanced = cb->part_balance && c->cam_set && c->tf_set && cb->part_nlev > 0;
+    if (balanced) {
+        std::vector<int> apre;
+        alpha_prefix(c, apre);
+        cost.resize(cb->tmpl.size());
+        for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) cost[bi] = brick_cost(c, cb, bi, apre.data());
+    }
+    for (int L = 0; L < cb->part_nlev; ++L) {
+        int axis = 0;
+        int64_t best = -1;
+        for (int a = 0; a < 3; ++a) {
+            const int64_t ext = std::min<int64_t>((int64_t)p.hi[a] * cb->B[a], cb->n[a]) - (int64_t)p.lo[a] * cb->B[a];
+            if (ext > best) { best = ext; axis = a; }
+        }
+        const int64_t layers = p.hi[axis] - p.lo[axis], n = cb->part_counts[L], k = cb->part_index[L];
+        int s0 = p.lo[axis] + (int)(layers * k / n), s1 = p.lo[axis] + (int)(layers * (k + 1) / n);
+        if (balanced && layers > 0) {
+            // cost of each layer of the current part along the axis
+            std::vector<double> lc((size_t)layers, 0.0);
+            for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) {
+                const int64_t ci[3] = {(int64_t)bi % cb->nb[0], ((int64_t)bi / cb->nb[0]) % cb->nb[1],
+                                       (int64_t)bi / (cb->nb[0] * cb->nb[1])};
+                bool in = true;
+                for (int a = 0; a < 3; ++a) in = in && ci[a] >= p.lo[a] && ci[a] < p.hi[a];
+                if (in) lc[(size_t)(ci[axis] - p.lo[axis])] += cost[bi];
+            }
+            double total = 0.0;
+            for (double v : lc) total += v;
+            // cut j (1..n-1): the first layer boundary where the prefix cost reaches j/n of the
+            // total, kept strictly increasing while layers last
+            std::vector<int64_t> cut((size_t)n + 1, 0);
+            cut[(size_t)n] = layers;
+            double pre = 0.0;
+            int64_t li = 0;
+            for (int64_t j = 1; j < n; ++j) {
+                const double target = total * (double)j / (double)n;
+                while (li < layers && pre + lc[(size_t)li] * 0.5 < target) pre += lc[(size_t)li++];
+                const int64_t lo_ok = std::min<int64_t>(cut[(size_t)j - 1] + 1, layers);
+                cut[(size_t)j] = std::min<int64_t>(std::max<int64_t>(li, lo_ok), layers);
+            }
+            for (int64_t j = n - 1; j >= 1; --j)        // leave room for the later slabs
+                cut[(size_t)j] = std::min<int64_t>(cut[(size_t)j], std::max<int64_t>(layers - (n - j), 0));
+            s0 = p.lo[axis] + (int)cut[(size_t)k];
+            s1 = p.lo[axis] + (int)cut[(size_t)k + 1];
+            if (s1 < s0) s1 = s0;
+        }
+        p.axis[L] = axis;
+        p.lo[axis] = s0;
+        p.hi[axis] = s1;
+    }
+    return p;
+}
+
+bool in_part(const PartBox &p, const Cube *cb, int64_t brick) {
+    const int64_t ci[3] = {brick % cb->nb[0], (brick / cb->nb[0]) % cb->nb[1], brick / (cb->nb[0] * cb->nb[1])};
+    for (int a = 0; a < 3; ++a)
+        if (ci[a] < p.lo[a] || ci[a] >= p.hi[a]) return false;
+    return true;
 }
 
 Cube *find_cube(vr_ctx *c, int id) {
@@ -201,8 +291,11 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
     cand.reserve(cb->tmpl.size());
     std::vector<int> apre;
     alpha_prefix(c, apre);
+    const bool parted = cb->part_nlev > 0;      // bricks outside the cube's part are not drawn
+    const PartBox part = parted ? partition_box(c, cb) : PartBox{};
     for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) {
         DrawBrick b = cb->tmpl[bi];
+        if (parted && !in_part(part, cb, (int64_t)bi)) continue;
         if (!window_clip(c, cb, b, b.lo, b.hi)) continue;
         if (skip_brick(c, cb, bi, apre.data())) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
@@ -786,8 +879,12 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
     int apre_buf[kMaxLut + 1];
     apre_buf[0] = 0;
     for (size_t i = 0; i < c->lut.size(); ++i) apre_buf[i + 1] = apre_buf[i] + (c->lut[i].w != 0.0f ? 1 : 0);
+    // a partitioned cube draws its part (the equal split needs no heap; the balanced one does)
+    const bool parted = cb->part_nlev > 0;
+    const PartBox part = parted ? partition_box(c, cb) : PartBox{};
     for (size_t bi = 0; bi < nb; ++bi) {
         DrawBrick b = cb->tmpl[bi];
+        if (parted && !in_part(part, cb, (int64_t)bi)) continue;
         if (!window_clip(c, cb, b, b.lo, b.hi)) continue;
         if (skip_brick(c, cb, bi, apre_buf)) continue;
         int x0 = 0, y0 = 0, x1 = W, y1 = H;
@@ -1548,12 +1645,22 @@ int vr_set_partition(vr_ctx *c, int cube_id, int nlevels, const int *counts, con
     return VR_OK;
 }
 
+int vr_set_partition_balance(vr_ctx *c, int cube_id, int balanced) {
+    if (!c) return arg_fail("null ctx");
+    Cube *cb = find_cube(c, cube_id);
+    if (!cb) return VR_ERR_NOT_FOUND;
+    if (balanced != 0 && balanced != 1) return arg_fail("balanced must be 0 or 1");
+    if (cb->part_balance != balanced) c->state_gen++;
+    cb->part_balance = balanced;
+    return VR_OK;
+}
+
 int vr_get_partition(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes) {
     if (!c || !lo || !hi) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
     if (!cb->bricked) return fail(VR_ERR_STATE, "cube has no bricking");
-    const PartBox p = partition_box(cb);
+    const PartBox p = partition_box(c, cb);
     for (int a = 0; a < 3; ++a) { lo[a] = p.lo[a]; hi[a] = p.hi[a]; }
     if (axes)
         for (int L = 0; L < cb->part_nlev; ++L) axes[L] = p.axis[L];
@@ -1590,7 +1697,7 @@ int vr_composite_subimages(vr_ctx *c, int cube_id, int level, int n, const float
         return arg_fail("subs and out must be 16-byte aligned device memory");
     int rc = set_dev(c);
     if (rc) return rc;
-    const PartBox p = partition_box(cb);
+    const PartBox p = partition_box(c, cb);
     FrameConsts fc{};
     fc.cam = c->cam;
     fc.mode = c->mode;
@@ -1721,6 +1828,8 @@ int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
     if (cb->streamed) return fail(VR_ERR_UNSUPPORTED, "streamed cubes need the brick cache");
     if (c->mode == VR_DVR && c->term != VR_TERM_SEGMENT)
         return fail(VR_ERR_UNSUPPORTED, "the no-allocation path composites per-segment fragments (VR_TERM_SEGMENT)");
+    if (cb->part_nlev > 0 && cb->part_balance)
+        return fail(VR_ERR_UNSUPPORTED, "balanced partitions are computed on the heap; the no-allocation path takes equal ones");
     int rc = check_ready(c, cb);
     if (rc) return rc;
     if ((rc = set_dev(c)) != VR_OK) return rc;

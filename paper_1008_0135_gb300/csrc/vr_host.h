@@ -76,6 +76,7 @@ struct Cube {
     int part_nlev = 0;
     int part_counts[kMaxPartLevels] = {0};
     int part_index[kMaxPartLevels] = {0};
+    int part_balance = 0;             // 1: cuts balanced by the current camera's estimated cost
 };
 
 // The part of a cube's brick grid that its partition selects: brick index ranges [lo, hi) per
@@ -84,7 +85,8 @@ struct PartBox {
     int lo[3], hi[3];
     int axis[Cube::kMaxPartLevels];
 };
-PartBox partition_box(const Cube *cb);
+PartBox partition_box(const vr_ctx *c, const Cube *cb);
+bool in_part(const PartBox &p, const Cube *cb, int64_t brick);
 
 template <typename T>
 struct DevBuf {

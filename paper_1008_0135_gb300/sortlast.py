@@ -197,9 +197,10 @@ class SortLast:
     """Sort-last frames of one cube over the ranks of torch.distributed (one GPU each)."""
 
     def __init__(self, ctx, cube_id: int, counts: Sequence[int], rank: int, exchange=None,
-                 backend: str = None):
+                 backend: str = None, balanced: bool = False):
         self.ctx, self.cube_id, self.counts, self.rank = ctx, cube_id, list(counts), rank
         ctx.set_partition(cube_id, self.counts, digits(rank, self.counts))
+        ctx.set_partition_balance(cube_id, balanced)
         self.exchange = exchange if exchange is not None else TorchExchange(self.counts, backend)
 
     def render(self, stream=None):

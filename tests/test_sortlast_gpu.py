@@ -80,11 +80,14 @@ CAMS = [
 ]
 
 
-@pytest.mark.parametrize("counts", [(2,), (3,), (2, 2), (4,), (3, 2)])
-def test_sortlast_frame_equals_the_whole_cube(setup, orc, counts):
+@pytest.mark.parametrize("counts,balanced", [((2,), False), ((3,), False), ((2, 2), False), ((4,), False),
+                                             ((3, 2), False), ((3,), True), ((2, 2), True)])
+def test_sortlast_frame_equals_the_whole_cube(setup, orc, counts, balanced):
     """Sub-images of every part composited in stages equal the whole cube's frame (DVR to FP32
-    re-association, 1e-6; MIP bit for bit) and the oracle within the 1e-4 bar."""
+    re-association, 1e-6; MIP bit for bit) and the oracle within the 1e-4 bar, for equal and
+    camera-balanced cuts."""
     ctx, cube, cid = setup
+    ctx.set_partition_balance(cid, balanced)
     lut = synth.random_lut(3, n=64, alpha_max=0.35)
     ctx.set_transfer_function(lut, -3.0, 12.0)
     for cam in CAMS:
@@ -99,6 +102,36 @@ def test_sortlast_frame_equals_the_whole_cube(setup, orc, counts):
             assert np.abs(parts - whole).max() <= 1e-6
             ref, flags, _ = orc.render(cube, lut, (-3.0, 12.0), cam, step=0.5, tau=0.99, brick=BRICK)
             compare_dvr(parts.reshape(-1, 4), ref, flags, 0.99)
+    ctx.set_partition_balance(cid, False)
+
+
+def test_balanced_cuts_even_out_the_parts_work(setup):
+    """A perspective view from close to one end of the cube's longest axis: equal cuts give the
+    near slab most of the samples; camera-balanced cuts spread them (the slowest part renders
+    fewer samples), and the parts still tile the brick grid."""
+    ctx, cube, cid = setup
+    ctx.set_transfer_function(synth.ramp_lut(alpha=0.05), -3.0, 12.0)
+    cam = dict(view=synth.look_at((-25.0, 32.0, 20.0), (96.0, 32.0, 20.0)), proj=1, param=math.radians(70.0),
+               W=96, H=96)
+    ctx.set_camera_dict(cam)
+    ctx.set_render_params("dvr", 0.5, 1.0)
+    worst = {}
+    for balanced in (False, True):
+        ctx.set_partition_balance(cid, balanced)
+        per, spans = [], []
+        for k in range(3):
+            ctx.set_partition(cid, (3,), (k,))
+            lo, hi, _ = ctx.partition(cid, 1)
+            spans.append((lo[0], hi[0]))
+            ctx.reset_stats()
+            ctx.render_subimage(cid)
+            per.append(ctx.stats()["samples"])
+        assert spans[0][0] == 0 and spans[-1][1] == 6
+        assert all(spans[i][1] == spans[i + 1][0] for i in range(2))
+        worst[balanced] = max(per) / (sum(per) / 3.0)
+    ctx.set_partition(cid)
+    ctx.set_partition_balance(cid, False)
+    assert worst[True] < worst[False]
 
 
 def test_subimage_keeps_transmittance_and_refuses_global_termination(setup):
