@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="brick storage of the main leg (the headline line uses f32)")
     ap.add_argument("--cpu-rays", type=int, default=1 << 20)
+    ap.add_argument("--layouts", type=int, default=9,
+                    help="brick layout mask of the main leg (9: x-contiguous copy + slice atlases; "
+                         "19: x- and y-contiguous copies + their 16-byte-row copies, staged slabs)")
     ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed", "serving", "sortlast"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
@@ -699,7 +702,7 @@ def run_ours(args, dist):
         cube_np = cube.cpu().numpy()
     del cube
     torch.cuda.empty_cache()
-    ctx.set_brick_layouts(cid, 9)          # slice atlases (gathers) + the x-contiguous copy
+    ctx.set_brick_layouts(cid, args.layouts)   # default: slice atlases (gathers) + the x copy
     t_setup = time.perf_counter()
     ctx.set_bricking(cid, cfg["brick"], 1, args.storage)
     brick_s = time.perf_counter() - t_setup

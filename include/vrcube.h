@@ -84,6 +84,8 @@ typedef struct {
                                     decoded on the device for compressed cubes) */
     int64_t cache_hits;          /* brick lookups served from the HBM cache */
     int64_t cache_misses;        /* brick lookups that needed a copy or a decode */
+    int64_t kernel_errors;       /* bit 0: a staged ray cast gave up waiting for a slab's copies
+                                    (its bounded wait ran out; those samples read global memory) */
 } vr_stats;
 
 /* Creates a context on CUDA device `device`.  cache_bytes bounds the HBM brick cache used for

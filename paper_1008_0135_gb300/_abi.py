@@ -22,6 +22,7 @@ class VrStats(C.Structure):
         ("brick_bytes_sampled", C.c_int64), ("ms_raycast", C.c_double),
         ("ms_composite", C.c_double), ("ms_frame", C.c_double), ("timed_frames", C.c_int64),
         ("bytes_streamed", C.c_int64), ("cache_hits", C.c_int64), ("cache_misses", C.c_int64),
+        ("kernel_errors", C.c_int64),
     ]
 
 

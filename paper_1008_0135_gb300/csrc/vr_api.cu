@@ -41,6 +41,19 @@ void layout_strides(const int dim[3], int layout, int str[3]) {
     }
 }
 
+long long layout_strides_padded(const int dim[3], int a, int esz, int str[3]) {
+    const int per16 = 16 / esz;
+    const long long row = ((long long)dim[a] + per16 - 1) / per16 * per16;
+    int ord[3];
+    ord[0] = a;
+    for (int q = 0, k = 1; q < 3; ++q)
+        if (q != a) ord[k++] = q;
+    str[ord[0]] = 1;
+    str[ord[1]] = (int)row;
+    str[ord[2]] = (int)(row * dim[ord[1]]);
+    return row * dim[ord[1]] * dim[ord[2]];
+}
+
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb) {
     FrameLayout f{0, 0, kRcLong, kRcShort, 0.0f, 0};
     float best = -1.0f;
@@ -363,6 +376,11 @@ void build_worklist(vr_ctx *c, Cube *cb, WorkList &wl) {
         frag += (long long)d.rect[2] * d.rect[3];
         if (!cb->loff.empty()) d.data_off = cb->loff[3 * (size_t)d.brick + fl.layout];
         layout_strides(d.dim, fl.layout, d.str);
+        d.pad_off = -1;
+        if (!cb->loff_pad.empty() && cb->loff_pad[3 * (size_t)d.brick + fl.layout] >= 0) {
+            d.pad_off = cb->loff_pad[3 * (size_t)d.brick + fl.layout];
+            layout_strides_padded(d.dim, fl.layout, cb->storage == VR_F32 ? 4 : 2, d.pad_str);
+        }
         int tw = (d.rect[2] + fl.tw - 1) / fl.tw, th = (d.rect[3] + fl.th - 1) / fl.th;
         int di = (int)wl.db.size();
         for (int ty = 0; ty < th; ++ty)
@@ -420,6 +438,20 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // it saves; with a poor alignment it pays
     fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
     fc.sub = c->subimage ? 1 : 0;
+    // staged slabs: DVR frames of resident FP32 cubes that keep the padded copy of the frame
+    // layout; the march axis is the view's dominant axis other than the contiguous one
+    if ((cb->layouts & 16) && !cb->streamed && c->mode == VR_DVR && cb->storage == VR_F32 &&
+        !cb->loff_pad.empty() && cb->loff_pad[fl.layout] >= 0) {
+        const float fwd[3] = {-c->cam.R[6], -c->cam.R[7], -c->cam.R[8]};
+        int m = -1;
+        for (int a = 0; a < 3; ++a)
+            if (a != fl.layout && (m < 0 || std::fabs(fwd[a]) > std::fabs(fwd[m]))) m = a;
+        if (std::fabs(fwd[m]) > 0.3f) {
+            fc.fetch = 4;
+            fc.stage_m = m;
+            fc.stage_dir = fwd[m] > 0.0f ? 1 : -1;
+        }
+    }
     return fc;
 }
 
@@ -747,6 +779,17 @@ int build_bricks(vr_ctx *c, Cube *cb, cudaStream_t s) {
                               cb->storage, cb->d_pool, d_exps, s));
         CK(cudaStreamSynchronize(s));      // rec is rewritten for the next layout
     }
+    for (int a = 0; a < 3 && !cb->loff_pad.empty(); ++a) {
+        if (cb->loff_pad[a] < 0) continue;
+        for (int i = 0; i < nbr; ++i) {
+            rec[i].data_off = cb->loff_pad[3 * (size_t)i + a];
+            layout_strides_padded(rec[i].dim, a, cb->storage == VR_F32 ? 4 : 2, rec[i].str);
+        }
+        CK(cudaMemcpyAsync(cb->d_tmpl, rec.data(), sizeof(DrawBrick) * nbr, cudaMemcpyHostToDevice, s));
+        CK(launch_brick_build(cb->d_src, (int)cb->n[0], (int)cb->n[1], (int)cb->n[2], cb->d_tmpl, nbr, cb->d_bs,
+                              cb->storage, cb->d_pool, d_exps, s));
+        CK(cudaStreamSynchronize(s));
+    }
     if (cb->storage != VR_F32) {
         std::vector<int> e(nbr);
         CK(cudaMemcpyAsync(e.data(), d_exps, sizeof(int) * nbr, cudaMemcpyDeviceToHost, s));
@@ -979,6 +1022,11 @@ int build_worklist_static(vr_ctx *c, Cube *cb, unsigned char *arena, size_t cap,
         fo += (long long)d.rect[2] * d.rect[3];
         if (!cb->loff.empty()) d.data_off = cb->loff[3 * (size_t)d.brick + fl.layout];
         layout_strides(d.dim, fl.layout, d.str);
+        d.pad_off = -1;
+        if (!cb->loff_pad.empty() && cb->loff_pad[3 * (size_t)d.brick + fl.layout] >= 0) {
+            d.pad_off = cb->loff_pad[3 * (size_t)d.brick + fl.layout];
+            layout_strides_padded(d.dim, fl.layout, cb->storage == VR_F32 ? 4 : 2, d.pad_str);
+        }
         const int tw = (d.rect[2] + fl.tw - 1) / fl.tw, th = (d.rect[3] + fl.th - 1) / fl.th;
         for (int ty = 0; ty < th; ++ty)
             for (int tx = 0; tx < tw; ++tx) items[it++] = TileItem{i, tx, ty};
@@ -1239,6 +1287,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
             d.dim[a] = (int)(hi - lo + 2 * ghost);
         }
         d.brick = (int)bi;
+        d.pad_off = -1;
         const size_t elems = (size_t)d.dim[0] * d.dim[1] * d.dim[2];
         d.bytes = (long long)(elems * esz);
         layout_strides(d.dim, 0, d.str);
@@ -1253,6 +1302,19 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
             off = align_up(off + (size_t)t[bi].dim[0] * t[bi].dim[1] * t[bi].dim[2], 64);
         }
     }
+    // layout bit 4: padded copies of the kept linear layouts (resident cubes)
+    std::vector<long long> loff_pad;
+    if (!cb->streamed && (layouts & 16)) {
+        loff_pad.assign((size_t)nbr * 3, -1);
+        for (int a = 0; a < 3; ++a) {
+            if (!(layouts & (1 << a))) continue;
+            for (int64_t bi = 0; bi < nbr; ++bi) {
+                int ps[3];
+                loff_pad[3 * bi + a] = (long long)off;
+                off = align_up(off + (size_t)layout_strides_padded(t[bi].dim, a, (int)esz, ps), 64);
+            }
+        }
+    }
     for (int64_t bi = 0; bi < nbr; ++bi) t[bi].data_off = loff[3 * bi];
     if (cb->d_pool) { cudaFree(cb->d_pool); cb->d_pool = nullptr; }
     if (cb->d_tmpl) { cudaFree(cb->d_tmpl); cb->d_tmpl = nullptr; }
@@ -1261,6 +1323,7 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
         cache_forget_cube(c, cube_id);    // (a cache with smaller slots is re-cut by the next frame)
         cb->tmpl = std::move(t);
         cb->loff.clear();
+        cb->loff_pad.clear();
         for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
         cb->ghost = ghost;
         cb->storage = storage;
@@ -1275,9 +1338,12 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     CK(cudaMalloc(&cb->d_bs, sizeof(unsigned int) * 4 * nbr));
     cb->tmpl = std::move(t);
     cb->loff = std::move(loff);
+    cb->loff_pad = std::move(loff_pad);
     for (int a = 0; a < 3; ++a) { cb->B[a] = B[a]; cb->nb[a] = nb[a]; }
     cb->ghost = ghost;
     cb->storage = storage;
+    if (!cb->loff_pad.empty())          // row padding defined (it is copied, never sampled)
+        CK(cudaMemsetAsync(cb->d_pool, 0, std::max<size_t>(off * esz, 16), c->load_stream));
     if ((rc = build_bricks(c, cb, c->load_stream)) != VR_OK) return rc;
     cb->bricked = true;
     return VR_OK;
@@ -1315,6 +1381,7 @@ int vr_compress_cube(vr_ctx *c, int cube_id) {
     if (cb->d_bs) { cudaFree(cb->d_bs); cb->d_bs = nullptr; }
     cb->pool_bytes = 0;
     cb->loff.clear();
+    cb->loff_pad.clear();
     cb->vlo.clear();
     cb->vhi.clear();
     cb->d_wstore = store;
@@ -1364,8 +1431,8 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    if (mask < 1 || mask > 15 || !(mask & 1))
-        return arg_fail("layout mask must be 1..15 and keep bit 0 (x contiguous)");
+    if (mask < 1 || mask > 31 || !(mask & 1))
+        return arg_fail("layout mask must be 1..31 and keep bit 0 (x contiguous)");
     if (cb->streamed && mask != 1 && mask != 9)
         return fail(VR_ERR_UNSUPPORTED, "streamed bricks are cached x-contiguous, with or without slot atlases (mask 1 or 9)");
     if (cb->layouts == mask) return VR_OK;
@@ -1773,6 +1840,7 @@ int vr_get_stats(vr_ctx *c, vr_stats *st) {
     st->ms_composite = c->ms_composite;
     st->ms_frame = c->ms_frame;
     st->timed_frames = c->timed_frames;
+    st->kernel_errors = (int64_t)(h.pad & 0xffffffffull);
     cache_stats(c, st);
     return VR_OK;
 }

@@ -59,6 +59,9 @@ struct Cube {
     // bit 3 = a slice-atlas texture of every brick besides the pool
     int layouts = 1;
     std::vector<long long> loff;      // element offset of brick b in layout a: loff[3 b + a]
+    // layout bit 4: each kept linear copy again with its rows padded to 16 bytes (staged frames
+    // copy rows of it into shared memory): offset of brick b's padded copy along a
+    std::vector<long long> loff_pad;
     std::vector<cudaArray_t> atlas_arr;          // per brick (layout bit 3)
     std::vector<unsigned long long> atlas_tex;   // texture objects over them
     size_t atlas_bytes = 0;
@@ -177,6 +180,9 @@ struct FrameLayout {
     int atlas;                        // 1: the ray caster gathers from the slice atlases
 };
 FrameLayout frame_layout(const vr_ctx *c, const Cube *cb);
+// Strides of the copy of a dim[0] x dim[1] x dim[2] brick whose axis a is contiguous, its rows
+// padded to a multiple of 16 bytes (esz-byte elements); returns the copy's elements.
+long long layout_strides_padded(const int dim[3], int a, int esz, int str[3]);
 // Empty-space skipping: prefix counts of table entries with non-zero opacity, and whether a
 // brick's value range reaches only zero-opacity entries (its fragment would be a no-op).
 void alpha_prefix(const vr_ctx *c, std::vector<int> &pre);

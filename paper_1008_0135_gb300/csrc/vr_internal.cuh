@@ -38,10 +38,15 @@ struct FrameConsts {
     int fetch;                     // how a sample's 8 stencil corners are read: 0 = 8 loads from
                                    // the linear brick, 1 = the same with the stencil cache (rays
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
-                                   // from the brick's slice-atlas texture
+                                   // from the brick's slice-atlas texture, 4 = slabs of the
+                                   // brick staged in shared memory by bulk copies from the copy
+                                   // with 16-byte rows (DVR, FP32 bricks)
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
     int sub;                       // 1: a part's sub-image -- DVR pixels keep the transmittance T
                                    // (not 1 - T), MIP pixels without samples stay -inf
+    int stage_m, stage_dir;        // fetch 4: the march axis the slabs are staged along (the
+                                   // view's dominant axis other than the contiguous one) and the
+                                   // direction the rays cross it (+1 / -1)
 };
 
 // One brick of the current frame's work-list (front-to-back order).
@@ -64,6 +69,9 @@ struct DrawBrick {
     int alog;
     int skip;                      // global termination: every sample of this brick adds nothing
                                    // (its values map only to zero opacity), walk through it
+    long long pad_off;             // staged frames (fetch 4): element offset of the brick's copy
+    int pad_str[3];                // with 16-byte rows (the frame layout's contiguous axis) and
+                                   // its strides; -1 when the cube keeps no such copy
 };
 
 // The brick grid a global-termination frame walks: nb bricks per axis of core size B over a

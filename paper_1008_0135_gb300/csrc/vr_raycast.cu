@@ -555,6 +555,309 @@ k_raycast(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__res
 }
 
 // ----------------------------------------------------------------------------------------------
+// staged ray cast (fetch 4): the rays of a work item cross their brick along its march axis M (the
+// view's dominant axis other than the contiguous axis L of the brick copy); the block walks that
+// axis in chunks of kStageC lower-stencil indices, copies each chunk's slab of the brick -- the
+// bounding box of the tile's four corner rays across the chunk, widened by the stencil and a
+// margin -- into shared memory with one bulk copy per row of the padded copy, one chunk ahead
+// (two stages, an mbarrier each), and samples the stencils from there.  Each ray processes its
+// samples in order, stopping at a chunk's end; a stencil outside the staged slab (or a chunk
+// whose slab does not fit a stage, or a ray crossing M the other way) is read from global
+// memory instead, so every sample and every frame is exactly the linear path's.
+// ----------------------------------------------------------------------------------------------
+constexpr int kStageC = 8;              // lower-stencil indices per chunk along the march axis
+constexpr int kStageFloats = 7168;      // floats per stage (28 KB)
+constexpr int kStageSpin = 1 << 21;     // bound of a wait for a stage's copies (polls ~32 ns apart:
+                                        // ~0.1 s, against microseconds for a slab)
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Whether the phase of `bar` with parity `parity` has completed (no blocking).
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// One row of the slab: `bytes` (a multiple of 16) from 16-byte-aligned global `src` to
+// 16-byte-aligned shared `dst`, counted on `bar`.
+__device__ __forceinline__ void bulk_row(float *dst, const float *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// The slab a stage holds: stored-brick index ranges [lo, lo + n) per world axis, the floats per
+// shared row (its contiguous-axis extent, a multiple of 4) and the stage's bytes (0: nothing
+// staged; the chunk's stencils are read from global memory).
+struct StageBox {
+    int lo[3], n[3];
+    int row, bytes;
+};
+
+// Element a of a three-element register array by selects (a dynamic index would put the
+// array in local memory).
+__device__ __forceinline__ float pick3(const float v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+__device__ __forceinline__ int pick3(const int v[3], int a) { return a == 0 ? v[0] : (a == 1 ? v[1] : v[2]); }
+
+// Warp 0: the slab of chunk c (march-axis lower indices [c C, c C + C)) from the tile's four corner
+// rays, and its bulk copies into stage s.  Every lane takes a corner (lane & 3); lane 0 arms the
+// stage's barrier with the slab's bytes before any lane issues a row.
+__device__ __forceinline__ void stage_slab(const FrameConsts &fc, const DrawBrick &b, const TileItem &it, int M,
+                                           int L, int O, int c, int s, float *stage, const float *__restrict__ pool,
+                                           StageBox *box, unsigned long long *bar, bool off) {
+    const int lane = threadIdx.x & 31;
+    // the tile's pixel range inside the rectangle
+    const int tw = fc.lanes_y ? kRcShort : kRcLong, th = fc.lanes_y ? kRcLong : kRcShort;
+    const int px0 = it.tx * tw, py0 = it.ty * th;
+    const int px1 = min(px0 + tw, b.rect[2]) - 1, py1 = min(py0 + th, b.rect[3]) - 1;
+    const int cx = (lane & 1) ? px1 : px0, cy = (lane & 2) ? py1 : py0;
+    float o[3], d[3];
+    ray_for_pixel(fc.cam, b.rect[0] + cx, b.rect[1] + cy, o, d);
+    const int dimM = b.dim[M], dimL = b.dim[L], dimO = b.dim[O];
+    const int m0 = c * kStageC;
+    int lo_l = 0x7fffffff, hi_l = -0x7fffffff, lo_o = 0x7fffffff, hi_o = -0x7fffffff;
+    const float oM = pick3(o, M), dM = pick3(d, M), oL = pick3(o, L), dL = pick3(d, L), oO = pick3(o, O),
+                dO = pick3(d, O);
+    bool ok = dM != 0.0f;
+    for (int e = 0; e < 2 && ok; ++e) {
+        // the plane x_M = m0 (or m0 + C) of stored coordinates: x = p - org_c
+        const float v = (float)(m0 + e * kStageC) + b.org_c[M];
+        const float t = (v - oM) / dM;
+        ok = t >= 0.0f;
+        const float xl = fmaf(t, dL, oL) - b.org_c[L], xo = fmaf(t, dO, oO) - b.org_c[O];
+        const int fl = (int)floorf(xl), fo = (int)floorf(xo);
+        lo_l = min(lo_l, fl); hi_l = max(hi_l, fl);
+        lo_o = min(lo_o, fo); hi_o = max(hi_o, fo);
+    }
+#pragma unroll
+    for (int sh = 1; sh < 4; sh <<= 1) {
+        lo_l = min(lo_l, __shfl_xor_sync(0xffffffffu, lo_l, sh));
+        hi_l = max(hi_l, __shfl_xor_sync(0xffffffffu, hi_l, sh));
+        lo_o = min(lo_o, __shfl_xor_sync(0xffffffffu, lo_o, sh));
+        hi_o = max(hi_o, __shfl_xor_sync(0xffffffffu, hi_o, sh));
+    }
+    ok = __all_sync(0xffffffffu, ok) && !off && b.pad_off >= 0 && (unsigned)m0 <= (unsigned)(dimM - 1);
+    // the stencil's upper neighbour and a margin of one voxel for rounding, inside the brick;
+    // the contiguous axis from a 16-byte boundary, whole 16-byte pieces, within the padded row
+    const int prow = (dimL + 3) & ~3;
+    int l0 = max(lo_l - 1, 0) & ~3;
+    int l1 = min(hi_l + 2, dimL - 1);
+    int o0 = max(lo_o - 1, 0), o1 = min(hi_o + 2, dimO - 1);
+    const int nm = min(kStageC + 1, dimM - m0);
+    int row = ((l1 - l0 + 1) + 3) & ~3;
+    if (l0 + row > prow) row = prow - l0;
+    const int no = o1 - o0 + 1;
+    long long floats = (long long)nm * no * row;
+    // a stencil needs two indices along every axis of the slab
+    if (!ok || l1 < l0 + 1 || o1 < o0 + 1 || nm < 2 || row < 4 || floats > kStageFloats) floats = 0;
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            box->lo[a] = a == L ? l0 : (a == O ? o0 : m0);
+            box->n[a] = a == L ? row : (a == O ? no : nm);
+        }
+        box->row = row;
+        box->bytes = (int)(floats * 4);
+        if (floats > 0) mbar_expect_tx(bar, (unsigned)(floats * 4));
+    }
+    __syncwarp();
+    if (floats == 0) return;
+    const float *base = pool + b.pad_off + (long long)l0;
+    const int sM = b.pad_str[M], sO = b.pad_str[O];
+    for (int mi = 0; mi < nm; ++mi)
+        for (int oi = lane; oi < no; oi += 32)
+            bulk_row(stage + ((long long)mi * no + oi) * row,
+                     base + (long long)(m0 + mi) * sM + (long long)(o0 + oi) * sO, (unsigned)(row * 4), bar);
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(256, 3)
+k_raycast_staged(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ dbs,
+                 const TileItem *__restrict__ items, const float *__restrict__ pool, float4 *__restrict__ frags,
+                 Counters *__restrict__ ctr) {
+    extern __shared__ float4 s_lut[];
+    float *stages = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);      // 2 x kStageFloats
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ StageBox s_box[2];
+    __shared__ int s_rng[2][8];
+    __shared__ int s_err;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    load_table(lut, fc.nlut, s_lut);
+    if (tid == 0) {
+        mbar_init(&s_bar[0]);
+        mbar_init(&s_bar[1]);
+        mbar_fence_init();
+        s_err = 0;
+    }
+    const TileItem it = items[blockIdx.x];
+    DrawBrick &b = dbs[it.db];
+    const int L = b.pad_str[0] == 1 ? 0 : (b.pad_str[1] == 1 ? 1 : 2);
+    const int M = fc.stage_m, O = 3 - L - M;
+    int rx, ry;
+    thread_pixel(fc.lanes_y, it, warp, lane, rx, ry);
+    const int rw = b.rect[2];
+    const bool inrect = rx < rw && ry < b.rect[3];
+    float o[3], d[3];
+    int k0 = 0, k1 = 0;
+    bool hit = false;
+    if (inrect) {
+        ray_for_pixel(fc.cam, b.rect[0] + rx, b.rect[1] + ry, o, d);
+        hit = box_krange(o, d, b.lo, b.hi, fc.step, k0, k1);
+    }
+    const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
+    const int mM = b.dim[M] - 2;
+    float q[3] = {0.0f, 0.0f, 0.0f};
+    int n = 0;
+    if (hit) {
+        q[0] = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
+        q[1] = anchor(o[1], d[1], b.org_c[1], k0, fc.step);
+        q[2] = anchor(o[2], d[2], b.org_c[2], k0, fc.step);
+        n = k1 - k0;
+    }
+    const float dM = M == 0 ? d[0] : (M == 1 ? d[1] : d[2]);
+    const float qM = M == 0 ? q[0] : (M == 1 ? q[1] : q[2]);
+    const bool staged = hit && (fc.stage_dir > 0 ? dM > 0.2f : dM < -0.2f) && b.pad_off >= 0;
+    // chunks of the ray's first and last samples (the loop's own position arithmetic)
+    int cmin = 0x7fffffff, cmax = -1;
+    if (staged) {
+        const float tl = __fmul_rn((float)(n - 1), fc.step);
+        float fl;
+        const int i0 = clampi(floor_split(qM, fl), 0, mM);
+        const int i1 = clampi(floor_split(__fmaf_rn(tl, dM, qM), fl), 0, mM);
+        cmin = min(i0, i1) / kStageC;
+        cmax = max(i0, i1) / kStageC;
+    }
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, sh));
+        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, sh));
+    }
+    if (lane == 0) { s_rng[0][warp] = cmin; s_rng[1][warp] = cmax; }
+    __syncthreads();                    // table, barriers and the warps' chunk ranges
+    cmin = s_rng[0][0]; cmax = s_rng[1][0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) { cmin = min(cmin, s_rng[0][w]); cmax = max(cmax, s_rng[1][w]); }
+
+    const float *src = pool + (b.pad_off >= 0 ? b.pad_off : b.data_off);
+    const Strides gst = b.pad_off >= 0 ? Strides{b.pad_str[0], b.pad_str[1], b.pad_str[2]}
+                                       : Strides{b.str[0], b.str[1], b.str[2]};
+    const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
+    const int lmax = fc.nlut - 2;
+    float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+    int j = 0;
+    bool done = !hit;
+    if (hit && !staged) {               // every stencil of this ray from global memory
+        j = dvr_segment<0, 0, true, MASK>(src, gst, Atlas{0ull, 0, 0, 0}, mx, my, mz, 1.0f, q[0], q[1], q[2], d,
+                                          n, fc, s_lut, b.org[2], fc.vmin, c0, c1, c2, T);
+        done = true;
+    }
+    if (cmax >= cmin) {
+        const int nch = cmax - cmin + 1;
+        const int cbeg = fc.stage_dir > 0 ? cmin : cmax;
+        unsigned phases = 0u;           // bit s: the parity stage s waits for next
+        if (warp == 0) stage_slab(fc, b, it, M, L, O, cbeg, 0, stages, pool, &s_box[0], &s_bar[0], false);
+        __syncthreads();
+        for (int i = 0; i < nch; ++i) {
+            const int cs = i & 1, c = cbeg + i * fc.stage_dir;
+            if (i + 1 < nch && warp == 0)
+                stage_slab(fc, b, it, M, L, O, c + fc.stage_dir, cs ^ 1, stages + (cs ^ 1) * kStageFloats, pool,
+                           &s_box[cs ^ 1], &s_bar[cs ^ 1], s_err != 0);
+            StageBox bx = s_box[cs];
+            if (bx.bytes > 0) {         // this chunk's slab has landed
+                bool ok = false;
+                const unsigned par = (phases >> cs) & 1u;
+                for (int r = 0; r < kStageSpin && !ok; ++r) {
+                    ok = mbar_test_wait(&s_bar[cs], par);
+                    if (!ok) __nanosleep(32);
+                }
+                phases ^= 1u << cs;
+                if (!ok) {
+                    s_err = 1;
+                    atomicOr(reinterpret_cast<unsigned int *>(&ctr->pad), 1u);
+                    bx.bytes = 0;
+                }
+            }
+            const float *stage = stages + cs * kStageFloats;
+            int so[3];                  // shared-memory strides of the slab by world axis
+#pragma unroll
+            for (int a = 0; a < 3; ++a) so[a] = a == L ? 1 : (a == O ? bx.row : bx.row * pick3(bx.n, O));
+            const int mlo = c * kStageC, mhi = mlo + kStageC;
+            float jf = (float)j;
+            while (staged && !done && j < n) {
+                const float tj = __fmul_rn(jf, fc.step);
+                Cell cl;
+                cell_of<true>(__fmaf_rn(tj, d[0], q[0]), __fmaf_rn(tj, d[1], q[1]), __fmaf_rn(tj, d[2], q[2]),
+                              mx, my, mz, cl);
+                const int im = M == 0 ? cl.ix : (M == 1 ? cl.iy : cl.iz);
+                if (fc.stage_dir > 0 ? im >= mhi : im < mlo) break;   // the next chunk's sample
+                float v[8];
+                const int ux = cl.ix - bx.lo[0], uy = cl.iy - bx.lo[1], uz = cl.iz - bx.lo[2];
+                if (bx.bytes > 0 && ux >= 0 && ux < bx.n[0] - 1 && uy >= 0 && uy < bx.n[1] - 1 && uz >= 0 &&
+                    uz < bx.n[2] - 1) {
+                    const float *p = stage + ux * so[0] + uy * so[1] + uz * so[2];
+                    v[0] = p[0];                  v[1] = p[so[0]];
+                    v[2] = p[so[1]];              v[3] = p[so[1] + so[0]];
+                    v[4] = p[so[2]];              v[5] = p[so[2] + so[0]];
+                    v[6] = p[so[2] + so[1]];      v[7] = p[so[2] + so[1] + so[0]];
+                } else {
+                    fetch8<0>(src, cl.ix * gst.x + cl.iy * gst.y + cl.iz * gst.z, gst, v);
+                }
+                if (MASK) mask_channels(v, cl.iz, b.org[2], fc.nz, fc.chmask, fc.vmin);
+                DvrSample sm;
+                interp_tf(v, cl, false, 1.0f, vmin, inv_range, lutmax, lmax, s_lut, sm);
+                over(sm, c0, c1, c2, T);
+                ++j;
+                jf = __fadd_rn(jf, 1.0f);
+                if (T <= thr) done = true;
+            }
+            if (j >= n) done = true;
+            __syncthreads();            // the stage is read before it is refilled
+        }
+    }
+    if (hit && !done && j < n) {        // samples no chunk took (not expected): from global memory
+        for (float jf = (float)j; j < n; ++j, jf = __fadd_rn(jf, 1.0f)) {
+            const float tj = __fmul_rn(jf, fc.step);
+            Cell cl;
+            cell_of<true>(__fmaf_rn(tj, d[0], q[0]), __fmaf_rn(tj, d[1], q[1]), __fmaf_rn(tj, d[2], q[2]), mx, my,
+                          mz, cl);
+            float v[8];
+            fetch8<0>(src, cl.ix * gst.x + cl.iy * gst.y + cl.iz * gst.z, gst, v);
+            if (MASK) mask_channels(v, cl.iz, b.org[2], fc.nz, fc.chmask, fc.vmin);
+            DvrSample sm;
+            interp_tf(v, cl, false, 1.0f, vmin, inv_range, lutmax, lmax, s_lut, sm);
+            over(sm, c0, c1, c2, T);
+            if (T <= thr) { ++j; break; }
+        }
+    }
+    if (inrect) frags[b.frag_off + (long long)ry * rw + rx] = make_float4(c0, c1, c2, T);
+    const unsigned int tot = __reduce_add_sync(0xffffffffu, (unsigned int)(hit ? j : 0));
+    if (lane == 0 && tot > 0) {
+        atomicAdd(&ctr->samples, (unsigned long long)tot);
+        if (atomicExch(&b.sampled, 1) == 0) {
+            atomicAdd(&ctr->bricks_sampled, 1ull);
+            atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)b.bytes);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------------------------
 // global early termination (occlusion skipping): one pass, each ray walking the bricks
 // ----------------------------------------------------------------------------------------------
 // Lattice index at which a ray crosses the plane {axis = face}: the binary32 operations of
@@ -1069,9 +1372,25 @@ cudaError_t launch_rc(const FrameConsts &fc, const float4 *lut, const DrawBrick 
     return cudaGetLastError();
 }
 
+template <bool MASK>
+cudaError_t launch_staged(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
+                          int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
+    static DeviceAttrs da;
+    const size_t smem = 2 * sizeof(float4) * (size_t)fc.nlut + 2 * sizeof(float) * (size_t)kStageFloats;
+    const void *kern = reinterpret_cast<const void *>(k_raycast_staged<MASK>);
+    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut + 2 * sizeof(float) * kStageFloats), da);
+    if (e != cudaSuccess) return e;
+    k_raycast_staged<MASK><<<nitems, 256, smem, s>>>(fc, lut, const_cast<DrawBrick *>(db), items,
+                                                     static_cast<const float *>(pool), static_cast<float4 *>(frags), ctr);
+    return cudaGetLastError();
+}
+
 template <int S>
 cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBrick *db, const TileItem *items,
                         int nitems, const void *pool, void *frags, Counters *ctr, cudaStream_t s) {
+    if (S == 0 && fc.fetch == 4 && fc.mode == 0)
+        return fc.chmask ? launch_staged<true>(fc, lut, db, items, nitems, pool, frags, ctr, s)
+                         : launch_staged<false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
 #define VR_RC(MODE, F, MASK) launch_rc<S, MODE, F, MASK>(fc, lut, db, items, nitems, pool, frags, ctr, s)
     const bool atlas = fc.fetch == 2;
     if (fc.chmask) {     // masked frames: no stencil cache (same values, fewer instantiations)

@@ -693,3 +693,78 @@ def test_contexts_created_later_render_the_largest_table(ctx, pr1):
                 g = render(c, k, lut, (-3, 20), cam, step=0.5, tau=0.99)
                 assert np.array_equal(g, refs[term]), term
             c.free_cube(k)
+
+
+def _layouts_frame(ctx, cid, mask, lut, vr, cam, mode="dvr", step=0.5, tau=0.99):
+    ctx.set_brick_layouts(cid, mask)
+    return render(ctx, cid, lut, vr, cam, mode=mode, step=step, tau=tau)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_staged_slabs_equal_the_linear_path_and_the_oracle(ctx, orc, seed):
+    """Layout bit 4 keeps copies with 16-byte rows; DVR frames of FP32 bricks then read their
+    stencils from slabs of the brick staged in shared memory by bulk copies.  They are the linear
+    copies' frames bit for bit (the same voxels through the same arithmetic; stencils outside a
+    slab come from global memory) and within the oracle's bar: random cameras, ragged bricks,
+    tables of 2..4096 entries, a channel mask, a window, MIP frames (not staged) unchanged."""
+    rng = np.random.default_rng(300 + seed)
+    shape = tuple(int(v) for v in rng.integers(37, 71, 3))
+    nx, ny, nz = shape
+    cube = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    cube += synth.pr1_cube(seed=seed, n=max(shape), n_sources=6, sigma=(2.0, 5.0))[:nz, :ny, :nx]
+    brick = tuple(int(v) for v in rng.integers(9, 33, 3))
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, brick, 1, "f32")
+    nl = [2, 64, 256, 4096][seed]
+    t = np.arange(nl) / max(nl - 1, 1)
+    lut = np.stack([t, 1.0 - t, t * t, 0.25 * t], 1).astype(np.float32)
+    try:
+        for k in range(3):
+            cam = synth.random_camera(rng, shape, int(rng.integers(40, 97)), int(rng.integers(30, 81)))
+            lin = _layouts_frame(ctx, cid, 7, lut, (-3.0, 12.0), cam)
+            stg = _layouts_frame(ctx, cid, 7 | 16, lut, (-3.0, 12.0), cam)
+            assert np.array_equal(stg, lin), (k, np.abs(stg - lin).max())
+            if k == 0:
+                ref, flags, _ = orc.render(cube, lut, (-3.0, 12.0), cam, step=0.5, tau=0.99, brick=brick)
+                compare_dvr(stg, ref, flags, 0.99)
+            m_lin = _layouts_frame(ctx, cid, 7, lut, (-3.0, 12.0), cam, mode="mip")
+            m_stg = _layouts_frame(ctx, cid, 7 | 16, lut, (-3.0, 12.0), cam, mode="mip")
+            assert np.array_equal(m_lin, m_stg)
+        # a spectral-channel mask and a render window
+        mask = np.ones(nz, np.uint8)
+        mask[nz // 3:nz // 3 + 4] = 0
+        ctx.set_channel_mask(mask)
+        ctx.set_window((2, 3, 1), (nx - 4, ny - 2, nz - 3))
+        cam = synth.random_camera(rng, shape, 64, 48, proj=1)
+        lin = _layouts_frame(ctx, cid, 7, lut, (-3.0, 12.0), cam)
+        stg = _layouts_frame(ctx, cid, 7 | 16, lut, (-3.0, 12.0), cam)
+        assert np.array_equal(stg, lin)
+    finally:
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+        ctx.free_cube(cid)
+    assert ctx.stats()["kernel_errors"] == 0
+
+
+def test_staged_slabs_on_large_bricks_and_frames(ctx):
+    """64^3 bricks of a 192x160x128 cube in 384^2 perspective frames from around the cube: many
+    chunks per brick, slabs that overflow a stage near the eye (those chunks read global memory),
+    rays of a tile crossing the march axis both ways; frames equal to the linear copies'."""
+    rng = np.random.default_rng(77)
+    shape = (192, 160, 128)
+    nx, ny, nz = shape
+    cube = rng.standard_normal((nz, ny, nx)).astype(np.float32)
+    cid = ctx.load_cube(cube)
+    ctx.set_bricking(cid, (64, 64, 64), 1, "f32")
+    lut = synth.ramp_lut(alpha=0.02)
+    try:
+        c = np.array(shape, np.float64) / 2
+        for j, dist in ((0, 400.0), (3, 260.0), (5, 150.0)):
+            cam = dict(view=synth.orbit_view(360.0 * j / 8 + 10.0, c, dist), proj=1, param=math.radians(55.0),
+                       W=384, H=384)
+            lin = _layouts_frame(ctx, cid, 1 | 2, lut, (-3.0, 12.0), cam, step=0.7)
+            stg = _layouts_frame(ctx, cid, 1 | 2 | 16, lut, (-3.0, 12.0), cam, step=0.7)
+            assert np.array_equal(stg, lin), j
+    finally:
+        ctx.free_cube(cid)
+    assert ctx.stats()["kernel_errors"] == 0
