@@ -211,7 +211,12 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * it) are made by this call (and by vr_set_bricking of such a cube), so that frames only pack; the call
  * then sizes the brick cache (VR_ERR_OOM without one, or when an array cannot be had; a frame
  * that needs another array and cannot have it fails with VR_ERR_OOM too).
- * Mask 1..15 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
+ * Bit 4 (resident cubes) keeps, for each kept linear copy, another copy whose rows are padded
+ * to 16 bytes; DVR frames of FP32 bricks then stage slabs of each brick in shared memory (bulk
+ * copies of those rows) and read the stencils from there (frames identical to the linear
+ * copies'; measured slower than the gathers on the HIPASS- and GASS-scale frames, so opt-in),
+ * and take precedence over atlases for those frames.
+ * Mask 1..31 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
  * (streamed or compressed cube with a mask other than 1 or 9; atlas beyond the gather size,
  * raised by the rebuild, or for streamed cubes by the frame), VR_ERR_OOM, VR_ERR_CUDA. */
 int vr_set_brick_layouts(vr_ctx *ctx, int cube_id, int mask);
