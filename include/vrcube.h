@@ -214,7 +214,7 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * Bit 4 (resident cubes) keeps, for each kept linear copy, another copy whose rows are padded
  * to 16 bytes; DVR frames of FP32 bricks then stage slabs of each brick in shared memory (bulk
  * copies of those rows) and read the stencils from there (frames identical to the linear
- * copies'; measured slower than the gathers on the HIPASS- and GASS-scale frames, so opt-in),
+ * copies'; measured slower than the gathers on HIPASS-scale frames, so opt-in),
  * and take precedence over atlases for those frames.
  * Mask 1..31 with bit 0 set.  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
  * (streamed or compressed cube with a mask other than 1 or 9; atlas beyond the gather size,
