@@ -730,7 +730,8 @@ def run_ours(args, dist):
                    f"{cfg['step']}, 256^3 bricks + ghost 1, {args.storage.upper()} bricks, ERT 0.99",
                    "cube_xyz": [nx, ny, nz], "frame": [W, H], "bricks": list(cfg["brick"]),
                    "l2": f"inputs larger than L2 ({4 * nx * ny * nz / 1e9:.1f} GB cube); no flush",
-                   "brick_layouts": "slice-atlas textures (2 gathers per sample) + x-contiguous copy",
+                   "brick_layouts": ("slice-atlas textures (2 gathers per sample) + x-contiguous copy"
+                                     if args.layouts == 9 else f"layout mask {args.layouts}"),
                    "parallelism": f"replicas x{dist.world}"},
         "ms_per_frame": round(t_max / args.steps, 4),
         "samples_per_frame": st["samples"] // max(args.steps, 1),
