@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--layouts", type=int, default=9,
                     help="brick layout mask of the main leg (9: x-contiguous copy + slice atlases; "
                          "19: x- and y-contiguous copies + their 16-byte-row copies, staged slabs)")
+    ap.add_argument("--frame", type=int, default=0,
+                    help="frame edge in pixels of --leg runs (0: the config's); a smaller frame of a "
+                         "small cube spaces its rays as far apart as the full cube's (for profiling)")
     ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed", "serving", "sortlast"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
@@ -865,6 +868,8 @@ def main():
         torch.cuda.set_device(dist.local)
         device = f"cuda:{dist.local}"
         cube, cfg = make_cube(args.config, device)
+        if args.frame > 0:
+            cfg = dict(cfg, W=args.frame, H=args.frame)
         ctx = P.Context(dist.local, cache_bytes=64 << 30)
         cid = ctx.load_cube(cube)
         cube_np = cube.cpu().numpy() if args.leg == "compressed" else None

@@ -1537,6 +1537,25 @@ int vr_set_full_rect(vr_ctx *c, int full) {
 
 namespace vrh {
 
+// The brick grid a global-termination frame walks: the cube's bricks, rays clipped to the cube
+// or to the render window inside it.
+__attribute__((visibility("hidden"))) MarchGrid march_grid(const vr_ctx *c, const Cube *cb) {
+    MarchGrid g{};
+    for (int a = 0; a < 3; ++a) {
+        g.nb[a] = (int)cb->nb[a];
+        g.B[a] = (float)cb->B[a];
+        g.n[a] = (float)cb->n[a];
+        g.invB[a] = 1.0f / g.B[a];
+        g.clo[a] = 0.0f;
+        g.chi[a] = (float)cb->n[a];
+        if (c->has_window) {
+            g.clo[a] = (float)std::max<int64_t>(c->win_lo[a], 0);
+            g.chi[a] = (float)std::min<int64_t>(c->win_hi[a], cb->n[a]);
+        }
+    }
+    return g;
+}
+
 // A DVR frame with global early termination: one launch in which every pixel's ray walks the
 // cube's bricks front to back (k_raymarch), no fragments.  Stages the table, every brick's
 // record (the frame's linear layout, atlas and skip flag) and the channel mask.
@@ -1577,18 +1596,7 @@ static int render_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaStr
         hb[i] = d;
     }
     if (!c->chmask.empty()) std::memcpy(h + off_mask, c->chmask.data(), c->chmask.size());
-    MarchGrid g{};
-    for (int a = 0; a < 3; ++a) {
-        g.nb[a] = (int)cb->nb[a];
-        g.B[a] = (float)cb->B[a];
-        g.n[a] = (float)cb->n[a];
-        g.clo[a] = 0.0f;
-        g.chi[a] = (float)cb->n[a];
-        if (c->has_window) {
-            g.clo[a] = (float)std::max<int64_t>(c->win_lo[a], 0);
-            g.chi[a] = (float)std::min<int64_t>(c->win_hi[a], cb->n[a]);
-        }
-    }
+    const MarchGrid g = march_grid(c, cb);
     if (ev[0]) CK(cudaEventRecord(ev[0], s));
     CK(cudaMemcpyAsync(c->d_stage.p, h, off, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->upload_done, s));

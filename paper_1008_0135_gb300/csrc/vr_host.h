@@ -188,6 +188,8 @@ long long layout_strides_padded(const int dim[3], int a, int esz, int str[3]);
 void alpha_prefix(const vr_ctx *c, std::vector<int> &pre);
 bool skip_brick(const vr_ctx *c, const Cube *cb, size_t b, const int *pre);
 void layout_strides(const int dim[3], int layout, int str[3]);
+// The brick grid a global-termination frame walks (the render window clips the rays).
+MarchGrid march_grid(const vr_ctx *c, const Cube *cb);
 
 int set_dev(vr_ctx *c);
 Cube *find_cube(vr_ctx *c, int id);

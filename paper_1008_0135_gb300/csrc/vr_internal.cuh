@@ -80,6 +80,7 @@ struct DrawBrick {
 struct MarchGrid {
     int nb[3];
     float B[3], n[3];
+    float invB[3];                 // 1 / B (rounded): a first guess of a cell, settled exactly
     float clo[3], chi[3];
 };
 

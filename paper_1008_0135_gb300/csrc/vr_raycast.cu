@@ -51,30 +51,43 @@ namespace {
 // ----------------------------------------------------------------------------------------------
 // FP32 decision arithmetic: ray generation and slab clipping
 // ----------------------------------------------------------------------------------------------
-__device__ __forceinline__ void ray_for_pixel(const Cam &c, int i, int j, float o[3], float d[3]) {
+// Pixel (i, j)'s ray before the view rotation: the offset y = e - t of its origin from the
+// view translation (y2 = 0 - t2 for both projections, so only y0, y1 vary per pixel) and its
+// direction in world space.
+__device__ __forceinline__ void ray_eye(const Cam &c, int i, int j, float &y0, float &y1, float d[3]) {
     float sx = __fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn((float)i, 0.5f), (float)c.W), 2.0f), 1.0f);
     float sy = __fsub_rn(1.0f, __fmul_rn(__fdiv_rn(__fadd_rn((float)j, 0.5f), (float)c.H), 2.0f));
-    float e0, e1, e2, de0, de1, de2;
+    float e0, e1, de0, de1, de2;
     if (c.proj == 0) {
         e0 = __fmul_rn(sx, c.half_w);
         e1 = __fmul_rn(sy, c.half_h);
-        e2 = 0.0f;
         de0 = 0.0f; de1 = 0.0f; de2 = -1.0f;
     } else {
-        e0 = e1 = e2 = 0.0f;
+        e0 = e1 = 0.0f;
         float x = __fmul_rn(sx, c.th_w), y = __fmul_rn(sy, c.th), z = -1.0f;
         float n2 = __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
         float len = __fsqrt_rn(n2);
         de0 = __fdiv_rn(x, len); de1 = __fdiv_rn(y, len); de2 = __fdiv_rn(z, len);
     }
-    float y0 = __fsub_rn(e0, c.t[0]), y1 = __fsub_rn(e1, c.t[1]), y2 = __fsub_rn(e2, c.t[2]);
+    y0 = __fsub_rn(e0, c.t[0]);
+    y1 = __fsub_rn(e1, c.t[1]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {   // world = R^T (eye - t)
-        o[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], y0), __fmul_rn(c.R[3 + k], y1)),
-                         __fmul_rn(c.R[6 + k], y2));
+    for (int k = 0; k < 3; ++k)     // world = R^T (eye - t)
         d[k] = __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], de0), __fmul_rn(c.R[3 + k], de1)),
                          __fmul_rn(c.R[6 + k], de2));
-    }
+}
+
+// World coordinate k of the origin of a ray whose eye-space offset is (y0, y1, 0 - t2).
+__device__ __forceinline__ float ray_origin(const Cam &c, int k, float y0, float y1) {
+    const float y2 = __fsub_rn(0.0f, c.t[2]);
+    return __fadd_rn(__fadd_rn(__fmul_rn(c.R[k], y0), __fmul_rn(c.R[3 + k], y1)), __fmul_rn(c.R[6 + k], y2));
+}
+
+__device__ __forceinline__ void ray_for_pixel(const Cam &c, int i, int j, float o[3], float d[3]) {
+    float y0, y1;
+    ray_eye(c, i, j, y0, y1, d);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[k] = ray_origin(c, k, y0, y1);
 }
 
 // Lattice range [k0, k1) of the samples inside the half-open box [lo, hi), t >= 0.
@@ -378,7 +391,7 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 // until the segment's transmittance reaches the threshold.  Returns the samples composited.
 // F: how the stencil is read (FrameConsts::fetch).  MASK: a spectral-channel mask is set (its own
 // instantiation, so unmasked frames carry none of its registers or branches).
-template <int S, int F, bool CLAMP, bool MASK>
+template <int S, int F, bool CLAMP, bool MASK, bool ICOUNT = false>
 __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, const Atlas &atl,
                                            int mx, int my, int mz,
                                            float scale, float qx, float qy, float qz, const float d[3],
@@ -389,10 +402,13 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
     const int lmax = fc.nlut - 2;
     int px = -4, py = -4, pz = -4;        // no cell cached yet
     float v[8];
+    // the sample index as a float (exact: n <= 2^24 + 1, checked by the host), and as an int
+    // beside it where that takes fewer registers (ICOUNT)
+    const float nf = (float)n;
+    float jf = 0.0f;
     int j = 0;
-    float jf = 0.0f;                      // j as a float (exact: n <= 2^24 + 1, checked by the host)
 #pragma unroll kSampleUnroll
-    for (; j < n; ++j, jf = __fadd_rn(jf, 1.0f)) {
+    for (; ICOUNT ? j < n : jf < nf; ++j, jf = __fadd_rn(jf, 1.0f)) {
         const float tj = __fmul_rn(jf, fc.step);
         Cell cl;
         cell_of<CLAMP>(__fmaf_rn(tj, d[0], qx), __fmaf_rn(tj, d[1], qy), __fmaf_rn(tj, d[2], qz),
@@ -407,9 +423,9 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
         DvrSample sm;
         interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
         over(sm, c0, c1, c2, T);
-        if (T <= thr) return j + 1;
+        if (T <= thr) return (ICOUNT ? j : (int)jf) + 1;
     }
-    return j;
+    return ICOUNT ? j : (int)jf;
 }
 
 // F = 1: a ray keeps the stencil corners its next cell shares with the last one (fewer loads,
@@ -477,11 +493,12 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
                                     min(e0.iy, e1.iy) >= 0 && max(e0.iy, e1.iy) <= my &&
                                     min(e0.iz, e1.iz) >= 0 && max(e0.iz, e1.iz) <= mz;
                 const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
+                constexpr bool icount = MASK && S == 2;      // BF16 masked: an int count spills less
                 const int j = inside
-                    ? dvr_segment<S, F, false, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                   b.org[2], vcode, c0, c1, c2, T)
-                    : dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut,
-                                                  b.org[2], vcode, c0, c1, c2, T);
+                    ? dvr_segment<S, F, false, MASK, icount>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc,
+                                                             s_lut, b.org[2], vcode, c0, c1, c2, T)
+                    : dvr_segment<S, F, true, MASK, icount>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc,
+                                                            s_lut, b.org[2], vcode, c0, c1, c2, T);
                 nsamp = j;
             }
             static_cast<float4 *>(frags)[fi] = make_float4(c0, c1, c2, T);   // .w = transmittance
@@ -879,6 +896,22 @@ __device__ __forceinline__ int cell_k(int c, bool exit, float o, float d, float 
     return face_k(upper ? hi : lo, o, d, step);
 }
 
+// A march CTA's walk state while its rays sample a segment: one int slot per thread (256) for
+// each of the three exits, the three cells, the ray's end, the segment's end, the step bound,
+// the sample count, the ray's eye-space offset (two floats) and the pixel's index.  It sits in
+// shared memory after the table.
+enum MarchSlot { kWkX0, kWkC0 = kWkX0 + 3, kWkK1 = kWkC0 + 3, kWkEnd, kWkGuard, kWkSamp, kWkY0, kWkY1, kWkPix,
+                 kWkSlots };
+constexpr size_t kMarchStashBytes = (size_t)kWkSlots * 256 * sizeof(int);
+
+// This thread's first stash slot.  The thread index is read with a volatile move so that the
+// address is formed anew at each use instead of held in a register across the sample loop.
+__device__ __forceinline__ volatile int *march_stash(float4 *s_lut, int nlut) {
+    unsigned tid;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(tid));
+    return reinterpret_cast<volatile int *>(s_lut + 2 * nlut) + tid;
+}
+
 // One CTA = a 32x8 (8x32) pixel tile of the frame.  Each ray is clipped to the cube (and the
 // render window), then walks the brick grid front to back: its segment in brick b is
 // [max(k, enter), min over axes of exit), sampled with the per-brick anchor and stencil of
@@ -886,10 +919,11 @@ __device__ __forceinline__ int cell_k(int c, bool exit, float o, float d, float 
 // transmittance; it stops once the transmittance reaches the threshold after a sample (global
 // early termination), so bricks behind opaque pixels cost nothing.  Bricks whose values map
 // only to zero opacity are walked through without sampling (their samples add nothing).
-// Registers: the walk's state on top of the sample loop; bounded to 5 CTAs per SM (48
-// registers, some spilled outside the sample loop) and one (clamped) copy of the sample loop,
-// measured fastest (HIPASS-scale opaque-table frames: 0.98 ms; 4 CTAs at 64 registers 1.07,
-// unbounded with both loop copies 1.69).
+// Registers: the sample loop runs with the registers of the fragment kernel's loop plus the
+// index clamps; the walk's state rests in shared memory meanwhile (volatile stores and loads
+// around each segment, so no register holds it), the origin is rebuilt from the ray's two
+// eye-space offsets where a brick or a crossing needs it, and the pixel's index waits in
+// shared memory for the final write.
 template <int S, int F, bool MASK>
 __global__ void __launch_bounds__(256, VR_RAYMARCH_MIN_BLOCKS)
 k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ bricks,
@@ -898,92 +932,126 @@ k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__re
     extern __shared__ float4 s_lut[];
     load_table(lut, fc.nlut, s_lut);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tw = fc.lanes_y ? kRcShort : kRcLong;
-    const int ntx = (fc.cam.W + tw - 1) / tw;
-    const TileItem it{0, (int)(blockIdx.x % ntx), (int)(blockIdx.x / ntx)};
-    int px, py;
-    thread_pixel(fc.lanes_y, it, warp, lane, px, py);
     int nsamp = 0;
     float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
-    const bool inframe = px < fc.cam.W && py < fc.cam.H;
-    if (inframe) {
-        float o[3], d[3];
-        ray_for_pixel(fc.cam, px, py, o, d);
-        int K0 = 0, K1 = 0;
-        if (box_krange(o, d, g.clo, g.chi, fc.step, K0, K1)) {
-            // per axis: the cell owning sample K0 and the index where the ray leaves it
-            int c[3], kx[3];
-            bool ok = true;
+    float y0 = 0.0f, y1 = 0.0f, d[3] = {0.0f, 0.0f, 0.0f};
+    int K0 = 0, K1 = 0;
+    int c[3] = {0, 0, 0}, kx[3] = {0, 0, 0};
+    bool ok = false;
+    {
+        const int tw = fc.lanes_y ? kRcShort : kRcLong;
+        const int ntx = (fc.cam.W + tw - 1) / tw;
+        int px, py;
+        thread_pixel(fc.lanes_y, TileItem{0, (int)(blockIdx.x % ntx), (int)(blockIdx.x / ntx)},
+                     threadIdx.x >> 5, threadIdx.x & 31, px, py);
+        const bool inframe = px < fc.cam.W && py < fc.cam.H;
+        march_stash(s_lut, fc.nlut)[kWkPix * 256] = inframe ? py * fc.cam.W + px : -1;      // frames hold < 2^31 pixels
+        if (inframe) {
+            ray_eye(fc.cam, px, py, y0, y1, d);
+            float o[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
+            for (int a = 0; a < 3; ++a) o[a] = ray_origin(fc.cam, a, y0, y1);
+            ok = box_krange(o, d, g.clo, g.chi, fc.step, K0, K1);
+            // per axis: the cell owning sample K0 and the index where the ray leaves it
+#pragma unroll
+            for (int a = 0; a < 3 && ok; ++a) {
                 int ca;
                 if (d[a] == 0.0f) {
                     // the slab test's own comparisons: the cell with lo <= o < hi
-                    ca = clampi((int)floorf(__fdiv_rn(o[a], g.B[a])), 0, g.nb[a] - 1);
+                    ca = clampi((int)floorf(__fmul_rn(o[a], g.invB[a])), 0, g.nb[a] - 1);
                     for (int r = 0; r < g.nb[a]; ++r) {
                         if (ca > 0 && o[a] < fminf((float)ca * g.B[a], g.n[a])) --ca;
                         else if (ca < g.nb[a] - 1 && o[a] >= fminf((float)(ca + 1) * g.B[a], g.n[a])) ++ca;
                         else break;
                     }
+                    c[a] = ca;
+                    kx[a] = cell_k(ca, true, o[a], d[a], g.B[a], g.n[a], fc.step);
+                    ok = K0 < kx[a];
                 } else {
+                    // an estimate of the cell of sample K0 (any rounding), then settled on the cell
+                    // whose [enter, exit) holds K0 by the exact crossings (a step or two at most;
+                    // the moves only go one way, so the bound is never reached)
                     const float p = __fmaf_rn(__fmul_rn((float)K0, fc.step), d[a], o[a]);
-                    ca = clampi((int)floorf(__fdiv_rn(p, g.B[a])), 0, g.nb[a] - 1);
-                    // settle on the cell whose [enter, exit) holds K0 (a step or two at most)
-                    for (int r = 0; r < g.nb[a]; ++r) {
-                        const int step_dir = d[a] > 0.0f ? 1 : -1;
-                        if (cell_k(ca, true, o[a], d[a], g.B[a], g.n[a], fc.step) <= K0 &&
-                            (unsigned)(ca + step_dir) < (unsigned)g.nb[a]) ca += step_dir;
-                        else if (cell_k(ca, false, o[a], d[a], g.B[a], g.n[a], fc.step) > K0 &&
-                                 (unsigned)(ca - step_dir) < (unsigned)g.nb[a]) ca -= step_dir;
-                        else break;
+                    ca = clampi((int)floorf(__fmul_rn(p, g.invB[a])), 0, g.nb[a] - 1);
+                    const int step_dir = d[a] > 0.0f ? 1 : -1;
+                    int ex = 0, en = 0;
+                    bool settled = false;
+                    for (int r = 0; r <= g.nb[a] && !settled; ++r) {
+                        ex = cell_k(ca, true, o[a], d[a], g.B[a], g.n[a], fc.step);
+                        if (ex <= K0 && (unsigned)(ca + step_dir) < (unsigned)g.nb[a]) { ca += step_dir; continue; }
+                        en = cell_k(ca, false, o[a], d[a], g.B[a], g.n[a], fc.step);
+                        if (en > K0 && (unsigned)(ca - step_dir) < (unsigned)g.nb[a]) { ca -= step_dir; continue; }
+                        settled = true;
                     }
+                    c[a] = ca;
+                    kx[a] = ex;
+                    ok = settled && en <= K0 && K0 < ex;
                 }
-                c[a] = ca;
-                kx[a] = cell_k(ca, true, o[a], d[a], g.B[a], g.n[a], fc.step);
-                ok = ok && cell_k(ca, false, o[a], d[a], g.B[a], g.n[a], fc.step) <= K0 && K0 < kx[a];
-            }
-            int k = K0;
-            // at most one segment per brick crossed (each step leaves a cell on some axis)
-            for (int guard = g.nb[0] + g.nb[1] + g.nb[2] + 1; ok && k < K1 && guard > 0; --guard) {
-                const int kend = min(min(kx[0], kx[1]), min(kx[2], K1));
-                DrawBrick &b = bricks[((long long)c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]];
-                if (kend > k && !b.skip) {
-                    const void *src = static_cast<const char *>(pool) + b.data_off * (S == 0 ? 4 : 2);
-                    const Strides st{b.str[0], b.str[1], b.str[2]};
-                    const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
-                    const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
-                    const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
-                    const float qx = anchor(o[0], d[0], b.org_c[0], k, fc.step);
-                    const float qy = anchor(o[1], d[1], b.org_c[1], k, fc.step);
-                    const float qz = anchor(o[2], d[2], b.org_c[2], k, fc.step);
-                    const int n = kend - k;
-                    const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
-                    const int j = dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc,
-                                                                s_lut, b.org[2], vcode, c0, c1, c2, T);
-                    nsamp += j;
-                    if (j > 0 && b.sampled == 0 && atomicExch(&b.sampled, 1) == 0) {
-                        atomicAdd(&ctr->bricks_sampled, 1ull);
-                        atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)b.bytes);
-                    }
-                    if (T <= fc.thr) break;           // the whole ray is opaque
-                }
-                // leave the cells whose exit is here (several at an edge or corner)
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (kx[a] == kend && kend < K1) {
-                        c[a] += d[a] > 0.0f ? 1 : -1;
-                        if ((unsigned)c[a] >= (unsigned)g.nb[a]) ok = false;
-                        else kx[a] = cell_k(c[a], true, o[a], d[a], g.B[a], g.n[a], fc.step);
-                    }
-                }
-                k = kend;
             }
         }
-        out[(long long)py * fc.cam.W + px] = make_float4(c0, c1, c2, 1.0f - T);
     }
+    int k = K0;
+    // at most one segment per brick crossed (each step leaves a cell on some axis)
+    for (int guard = ok ? g.nb[0] + g.nb[1] + g.nb[2] + 1 : 0; guard > 0 && k < K1; --guard) {
+        int kend = min(min(kx[0], kx[1]), min(kx[2], K1));
+        const long long bi = ((long long)c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0];
+        if (kend > k && !bricks[bi].skip) {
+            const DrawBrick &b = bricks[bi];
+            const void *src = static_cast<const char *>(pool) + b.data_off * (S == 0 ? 4 : 2);
+            const Strides st{b.str[0], b.str[1], b.str[2]};
+            const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
+            const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
+            const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
+            const float qx = anchor(ray_origin(fc.cam, 0, y0, y1), d[0], b.org_c[0], k, fc.step);
+            const float qy = anchor(ray_origin(fc.cam, 1, y0, y1), d[1], b.org_c[1], k, fc.step);
+            const float qz = anchor(ray_origin(fc.cam, 2, y0, y1), d[2], b.org_c[2], k, fc.step);
+            const int n = kend - k;
+            const float vcode = S == 0 ? fc.vmin : ldexpf(fc.vmin, -b.exp2);
+            const int org_z = b.org[2];
+            volatile int *wk = march_stash(s_lut, fc.nlut);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                wk[(kWkX0 + a) * 256] = kx[a];
+                wk[(kWkC0 + a) * 256] = c[a];
+            }
+            wk[kWkK1 * 256] = K1; wk[kWkEnd * 256] = kend; wk[kWkGuard * 256] = guard;
+            wk[kWkSamp * 256] = nsamp;
+            wk[kWkY0 * 256] = __float_as_int(y0); wk[kWkY1 * 256] = __float_as_int(y1);
+            const int j = dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc,
+                                                        s_lut, org_z, vcode, c0, c1, c2, T);
+            wk = march_stash(s_lut, fc.nlut);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                kx[a] = wk[(kWkX0 + a) * 256];
+                c[a] = wk[(kWkC0 + a) * 256];
+            }
+            K1 = wk[kWkK1 * 256]; kend = wk[kWkEnd * 256]; guard = wk[kWkGuard * 256];
+            nsamp = wk[kWkSamp * 256] + j;
+            y0 = __int_as_float(wk[kWkY0 * 256]); y1 = __int_as_float(wk[kWkY1 * 256]);
+            DrawBrick &bw = bricks[((long long)c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]];
+            if (j > 0 && bw.sampled == 0 && atomicExch(&bw.sampled, 1) == 0) {
+                atomicAdd(&ctr->bricks_sampled, 1ull);
+                atomicAdd(&ctr->brick_bytes_sampled, (unsigned long long)bw.bytes);
+            }
+            if (T <= fc.thr) break;               // the whole ray is opaque
+        }
+        // leave the cells whose exit is here (several at an edge or corner)
+        bool out_of_grid = false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (kx[a] == kend && kend < K1) {
+                c[a] += d[a] > 0.0f ? 1 : -1;
+                if ((unsigned)c[a] >= (unsigned)g.nb[a]) out_of_grid = true;
+                else kx[a] = cell_k(c[a], true, ray_origin(fc.cam, a, y0, y1), d[a], g.B[a], g.n[a], fc.step);
+            }
+        }
+        if (out_of_grid) break;
+        k = kend;
+    }
+    const int pix = march_stash(s_lut, fc.nlut)[kWkPix * 256];
+    if (pix >= 0) out[pix] = make_float4(c0, c1, c2, 1.0f - T);
     const unsigned int tot = __reduce_add_sync(0xffffffffu, (unsigned int)nsamp);
-    if (lane == 0 && tot > 0) atomicAdd(&ctr->samples, (unsigned long long)tot);
+    if ((threadIdx.x & 31) == 0 && tot > 0) atomicAdd(&ctr->samples, (unsigned long long)tot);
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -1420,13 +1488,13 @@ cudaError_t launch_march(const FrameConsts &fc, const float4 *lut, DrawBrick *br
                          const void *pool, float4 *out, Counters *ctr, cudaStream_t s) {
     static DeviceAttrs da;
     const void *kern = reinterpret_cast<const void *>(k_raymarch<S, F, MASK>);
-    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut), da);
-    if (e == cudaSuccess) e = set_carveout(kern, 2 * sizeof(float4) * (size_t)fc.nlut, da);
+    cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut + kMarchStashBytes), da);
+    const size_t smem = 2 * sizeof(float4) * (size_t)fc.nlut + kMarchStashBytes;
+    if (e == cudaSuccess) e = set_carveout(kern, smem, da);
     if (e != cudaSuccess) return e;
     const int tw = fc.lanes_y ? kRcShort : kRcLong, th = fc.lanes_y ? kRcLong : kRcShort;
     const long long ntiles = (long long)((fc.cam.W + tw - 1) / tw) * ((fc.cam.H + th - 1) / th);
-    k_raymarch<S, F, MASK><<<(unsigned)ntiles, 256, 2 * sizeof(float4) * (size_t)fc.nlut, s>>>(
-        fc, lut, bricks, g, pool, out, ctr);
+    k_raymarch<S, F, MASK><<<(unsigned)ntiles, 256, smem, s>>>(fc, lut, bricks, g, pool, out, ctr);
     return cudaGetLastError();
 }
 

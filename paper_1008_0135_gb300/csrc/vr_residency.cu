@@ -927,18 +927,7 @@ int render_streamed_global(vr_ctx *c, Cube *cb, float *out, int out_where, cudaS
         hb[b.brick] = b;
     }
     if (!c->chmask.empty()) std::memcpy(h + off_mask, c->chmask.data(), c->chmask.size());
-    MarchGrid g{};
-    for (int a = 0; a < 3; ++a) {
-        g.nb[a] = (int)cb->nb[a];
-        g.B[a] = (float)cb->B[a];
-        g.n[a] = (float)cb->n[a];
-        g.clo[a] = 0.0f;
-        g.chi[a] = (float)cb->n[a];
-        if (c->has_window) {
-            g.clo[a] = (float)std::max<int64_t>(c->win_lo[a], 0);
-            g.chi[a] = (float)std::min<int64_t>(c->win_hi[a], cb->n[a]);
-        }
-    }
+    const MarchGrid g = march_grid(c, cb);
     CK(cudaMemcpyAsync(d, h, off, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->upload_done, s));
     if (!c->chmask.empty()) fc.chmask = reinterpret_cast<const unsigned char *>(d + off_mask);
