@@ -896,13 +896,21 @@ __device__ __forceinline__ int cell_k(int c, bool exit, float o, float d, float 
     return face_k(upper ? hi : lo, o, d, step);
 }
 
-// A march CTA's walk state while its rays sample a segment: one int slot per thread (256) for
+// Warps of a global-termination CTA: the CTA is a 32 x kMarchWarps (kMarchWarps x 32) tile of the
+// frame, one warp per row (column) of 32 rays.
+#ifndef VR_MARCH_WARPS
+#define VR_MARCH_WARPS 8
+#endif
+constexpr int kMarchWarps = VR_MARCH_WARPS;
+constexpr int kMarchThreads = 32 * kMarchWarps;
+
+// A march CTA's walk state while its rays sample a segment: one int slot per thread for
 // each of the three exits, the three cells, the ray's end, the segment's end, the step bound,
 // the sample count, the ray's eye-space offset (two floats) and the pixel's index.  It sits in
 // shared memory after the table.
 enum MarchSlot { kWkX0, kWkC0 = kWkX0 + 3, kWkK1 = kWkC0 + 3, kWkEnd, kWkGuard, kWkSamp, kWkY0, kWkY1, kWkPix,
                  kWkSlots };
-constexpr size_t kMarchStashBytes = (size_t)kWkSlots * 256 * sizeof(int);
+constexpr size_t kMarchStashBytes = (size_t)kWkSlots * kMarchThreads * sizeof(int);
 
 // This thread's first stash slot.  The thread index is read with a volatile move so that the
 // address is formed anew at each use instead of held in a register across the sample loop.
@@ -925,7 +933,7 @@ __device__ __forceinline__ volatile int *march_stash(float4 *s_lut, int nlut) {
 // eye-space offsets where a brick or a crossing needs it, and the pixel's index waits in
 // shared memory for the final write.
 template <int S, int F, bool MASK>
-__global__ void __launch_bounds__(256, VR_RAYMARCH_MIN_BLOCKS)
+__global__ void __launch_bounds__(kMarchThreads, VR_RAYMARCH_MIN_BLOCKS * 8 / kMarchWarps)
 k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__restrict__ bricks,
            const MarchGrid g, const void *__restrict__ pool, float4 *__restrict__ out,
            Counters *__restrict__ ctr) {
@@ -939,13 +947,14 @@ k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__re
     int c[3] = {0, 0, 0}, kx[3] = {0, 0, 0};
     bool ok = false;
     {
-        const int tw = fc.lanes_y ? kRcShort : kRcLong;
+        const int tw = fc.lanes_y ? kMarchWarps : kRcLong;
         const int ntx = (fc.cam.W + tw - 1) / tw;
-        int px, py;
-        thread_pixel(fc.lanes_y, TileItem{0, (int)(blockIdx.x % ntx), (int)(blockIdx.x / ntx)},
-                     threadIdx.x >> 5, threadIdx.x & 31, px, py);
+        const int tx = (int)(blockIdx.x % ntx), ty = (int)(blockIdx.x / ntx);
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int px = fc.lanes_y ? tx * kMarchWarps + w : tx * kRcLong + lane;
+        const int py = fc.lanes_y ? ty * kRcLong + lane : ty * kMarchWarps + w;
         const bool inframe = px < fc.cam.W && py < fc.cam.H;
-        march_stash(s_lut, fc.nlut)[kWkPix * 256] = inframe ? py * fc.cam.W + px : -1;      // frames hold < 2^31 pixels
+        march_stash(s_lut, fc.nlut)[kWkPix * kMarchThreads] = inframe ? py * fc.cam.W + px : -1;      // frames hold < 2^31 pixels
         if (inframe) {
             ray_eye(fc.cam, px, py, y0, y1, d);
             float o[3];
@@ -1011,23 +1020,23 @@ k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__re
             volatile int *wk = march_stash(s_lut, fc.nlut);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                wk[(kWkX0 + a) * 256] = kx[a];
-                wk[(kWkC0 + a) * 256] = c[a];
+                wk[(kWkX0 + a) * kMarchThreads] = kx[a];
+                wk[(kWkC0 + a) * kMarchThreads] = c[a];
             }
-            wk[kWkK1 * 256] = K1; wk[kWkEnd * 256] = kend; wk[kWkGuard * 256] = guard;
-            wk[kWkSamp * 256] = nsamp;
-            wk[kWkY0 * 256] = __float_as_int(y0); wk[kWkY1 * 256] = __float_as_int(y1);
+            wk[kWkK1 * kMarchThreads] = K1; wk[kWkEnd * kMarchThreads] = kend; wk[kWkGuard * kMarchThreads] = guard;
+            wk[kWkSamp * kMarchThreads] = nsamp;
+            wk[kWkY0 * kMarchThreads] = __float_as_int(y0); wk[kWkY1 * kMarchThreads] = __float_as_int(y1);
             const int j = dvr_segment<S, F, true, MASK>(src, st, atl, mx, my, mz, scale, qx, qy, qz, d, n, fc,
                                                         s_lut, org_z, vcode, c0, c1, c2, T);
             wk = march_stash(s_lut, fc.nlut);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                kx[a] = wk[(kWkX0 + a) * 256];
-                c[a] = wk[(kWkC0 + a) * 256];
+                kx[a] = wk[(kWkX0 + a) * kMarchThreads];
+                c[a] = wk[(kWkC0 + a) * kMarchThreads];
             }
-            K1 = wk[kWkK1 * 256]; kend = wk[kWkEnd * 256]; guard = wk[kWkGuard * 256];
-            nsamp = wk[kWkSamp * 256] + j;
-            y0 = __int_as_float(wk[kWkY0 * 256]); y1 = __int_as_float(wk[kWkY1 * 256]);
+            K1 = wk[kWkK1 * kMarchThreads]; kend = wk[kWkEnd * kMarchThreads]; guard = wk[kWkGuard * kMarchThreads];
+            nsamp = wk[kWkSamp * kMarchThreads] + j;
+            y0 = __int_as_float(wk[kWkY0 * kMarchThreads]); y1 = __int_as_float(wk[kWkY1 * kMarchThreads]);
             DrawBrick &bw = bricks[((long long)c[2] * g.nb[1] + c[1]) * g.nb[0] + c[0]];
             if (j > 0 && bw.sampled == 0 && atomicExch(&bw.sampled, 1) == 0) {
                 atomicAdd(&ctr->bricks_sampled, 1ull);
@@ -1048,7 +1057,7 @@ k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__re
         if (out_of_grid) break;
         k = kend;
     }
-    const int pix = march_stash(s_lut, fc.nlut)[kWkPix * 256];
+    const int pix = march_stash(s_lut, fc.nlut)[kWkPix * kMarchThreads];
     if (pix >= 0) out[pix] = make_float4(c0, c1, c2, 1.0f - T);
     const unsigned int tot = __reduce_add_sync(0xffffffffu, (unsigned int)nsamp);
     if ((threadIdx.x & 31) == 0 && tot > 0) atomicAdd(&ctr->samples, (unsigned long long)tot);
@@ -1404,16 +1413,17 @@ cudaError_t ensure_smem_limit(const void *kernel, int bytes, DeviceAttrs &da) {
 }
 
 // The unified L1 / shared memory of an SM serves the texture gathers as cache: ask for just the
-// shared memory (the table) of the 256-thread CTAs the register file admits, leaving the rest
-// to L1 (measured on HIPASS-scale frames at 5 CTAs: 25 % carveout 3.65 ms, the driver's default
-// 3.75, 50 % 3.98).  Registers are allocated per warp in units of 256, 64 K per SM, at most 64
-// warps.  The kernel's current preference on this device is remembered in `da`.
-cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, DeviceAttrs &da) {
+// shared memory (the table) of the CTAs of `warps` warps the register file admits, leaving the
+// rest to L1 (measured on HIPASS-scale frames at 5 CTAs: 25 % carveout 3.65 ms, the driver's
+// default 3.75, 50 % 3.98).  Registers are allocated per warp in units of 256, 64 K per SM, at
+// most 64 warps and 32 CTAs.  The kernel's current preference on this device is remembered in
+// `da`.
+cudaError_t set_carveout(const void *kernel, size_t smem_per_cta, DeviceAttrs &da, int warps = 8) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
     const int per_warp = (fa.numRegs * 32 + 255) / 256 * 256;
-    const int ctas = std::max(1, std::min(64, 65536 / std::max(per_warp, 256)) / 8);
+    const int ctas = std::max(1, std::min(32, std::min(64, 65536 / std::max(per_warp, 256)) / warps));
     const double need = ctas * (double)(smem_per_cta + 1024) / (228.0 * 1024.0);
     const int pct = std::min(100, std::max(0, (int)std::ceil(100.0 * need)));
     const int dev = current_device();
@@ -1490,11 +1500,11 @@ cudaError_t launch_march(const FrameConsts &fc, const float4 *lut, DrawBrick *br
     const void *kern = reinterpret_cast<const void *>(k_raymarch<S, F, MASK>);
     cudaError_t e = ensure_smem_limit(kern, (int)(2 * sizeof(float4) * kMaxLut + kMarchStashBytes), da);
     const size_t smem = 2 * sizeof(float4) * (size_t)fc.nlut + kMarchStashBytes;
-    if (e == cudaSuccess) e = set_carveout(kern, smem, da);
+    if (e == cudaSuccess) e = set_carveout(kern, smem, da, kMarchWarps);
     if (e != cudaSuccess) return e;
-    const int tw = fc.lanes_y ? kRcShort : kRcLong, th = fc.lanes_y ? kRcLong : kRcShort;
+    const int tw = fc.lanes_y ? kMarchWarps : kRcLong, th = fc.lanes_y ? kRcLong : kMarchWarps;
     const long long ntiles = (long long)((fc.cam.W + tw - 1) / tw) * ((fc.cam.H + th - 1) / th);
-    k_raymarch<S, F, MASK><<<(unsigned)ntiles, 256, smem, s>>>(fc, lut, bricks, g, pool, out, ctr);
+    k_raymarch<S, F, MASK><<<(unsigned)ntiles, kMarchThreads, smem, s>>>(fc, lut, bricks, g, pool, out, ctr);
     return cudaGetLastError();
 }
 
