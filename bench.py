@@ -400,10 +400,11 @@ def traffic_entry(name: str):
     return json.load(open(p)).get(name) if os.path.exists(p) else None
 
 
-def roofline(st, steps, peak, src, name):
-    """The HBM roofline of the ray-cast launch, and beside it the ceiling that binds the texture
-    path: the texels its gathers deliver to registers (32 B per sample: two gathers of four
-    32-bit texels, FP16 texels widened alike) against the L1TEX writeback rate derived from ncu
+def roofline(st, steps, peak, src, name, texel_bytes=32):
+    """The HBM roofline of the ray-cast launch, and beside it the texture unit's texel writeback:
+    the texel bytes its gathers return per second (`texel_bytes` per sample: two gathers of four
+    texels, 32 B for FP32 texels and 16 B for 16-bit ones -- the writeback's busy cycles follow
+    the texel size, not the widened registers) against the L1TEX writeback rate derived from ncu
     (32 B per cycle per SM)."""
     nl = max(st["timed_frames"], 1)
     per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / nl
@@ -415,7 +416,7 @@ def roofline(st, steps, peak, src, name):
           "launch_ms": round(ms, 4)}
     wb = traffic_entry("l1tex_texel_writeback_peak_gbs")
     if wb:
-        tex = 32.0 * st["samples"] / nl / (ms * 1e-3) / 1e9
+        tex = float(texel_bytes) * st["samples"] / nl / (ms * 1e-3) / 1e9
         rl["l1tex"] = {"bound": "l1tex texel writeback", "achieved": round(tex, 1), "peak": wb["value"],
                        "unit": "GB/s", "frac": round(tex / wb["value"], 4),
                        "peak_source": "derived from ncu (profiles/traffic.json)"}
@@ -717,7 +718,8 @@ def run_ours(args, dist):
     t_max = dist.max(ms)
     samples_all = dist.sum(st["samples"])
     value = samples_all / (t_max * 1e-3) / 1e9
-    rl = roofline(st, args.steps, peak, psrc, f"k_raycast<{args.storage},DVR>")
+    rl = roofline(st, args.steps, peak, psrc, f"k_raycast<{args.storage},DVR>",
+                  32 if args.storage == "f32" else 16)
     sortlast = None
     if dist.world > 1:
         try:
@@ -754,7 +756,7 @@ def run_ours(args, dist):
         res["fp16_bricks"] = {
             "value": round(dist.sum(st16["samples"]) / (t16 * 1e-3) / 1e9, 3),
             "unit": "Gsamples/s", "ms_per_frame": round(t16 / args.steps, 4),
-            "roofline": roofline(st16, args.steps, peak, psrc, "k_raycast<f16,DVR>")}
+            "roofline": roofline(st16, args.steps, peak, psrc, "k_raycast<f16,DVR>", 16)}
         ctx.set_bricking(cid, cfg["brick"], 1, "f32")
         res["occlusion"] = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32),
                                          args.warmup)

@@ -436,7 +436,7 @@ FrameConsts make_consts(vr_ctx *c, Cube *cb) {
     // atlases: two gathers per sample.  Linear copies: with a warp's rays along the contiguous
     // axis its loads are nearly coalesced and the stencil cache's bookkeeping costs more than
     // it saves; with a poor alignment it pays
-    fc.fetch = fl.atlas ? 2 : (fl.align < 0.9f ? 1 : 0);
+    fc.fetch = fl.atlas ? (cb->atlas_pair && !cb->streamed ? 5 : 2) : (fl.align < 0.9f ? 1 : 0);
     fc.sub = c->subimage ? 1 : 0;
     // staged slabs: DVR frames of resident FP32 cubes that keep the padded copy of the frame
     // layout; the march axis is the view's dominant axis other than the contiguous one
@@ -640,6 +640,7 @@ void free_atlases(Cube *cb) {
     cb->atlas_tex.clear();
     cb->atlas_arr.clear();
     cb->atlas_bytes = 0;
+    cb->atlas_pair = false;
     for (auto &d : cb->tmpl) { d.atlas = 0; d.alog = 0; }
 }
 
@@ -647,11 +648,15 @@ void free_atlases(Cube *cb) {
 // of a brick of dx x dy x dz stored elements becomes tile (z mod 2^alog, z div 2^alog) of a 2D
 // array of 2^alog dx x ceil(dz / 2^alog) dy texels, with 2^alog the smallest power of two whose
 // square is >= dz.  FP32 bricks keep their values, 16-bit bricks their codes (FP16 as half
-// texels, BF16 as 16-bit unsigned ones).  The array must fit the device's limit for 2D gathers.
+// texels, BF16 as 16-bit unsigned ones).  With layout bit 5, 16-bit bricks get pair atlases
+// instead: dz - 1 tiles of 32-bit texels, tile z holding the codes of slices z and z + 1 (one
+// gather per sample).  The array must fit the device's limit for 2D gathers.
 int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     free_atlases(cb);
     const int nbr = (int)cb->tmpl.size();
-    const size_t esz = cb->storage == VR_F32 ? 4 : 2;
+    const bool pair = (cb->layouts & 32) && cb->storage != VR_F32;
+    const size_t bsz = cb->storage == VR_F32 ? 4 : 2;       // bytes of a stored element
+    const size_t esz = pair ? 4 : bsz;                       // bytes of a texel
     int gw = 0, gh = 0;
     CK(cudaDeviceGetAttribute(&gw, cudaDevAttrMaxTexture2DGatherWidth, c->device));
     CK(cudaDeviceGetAttribute(&gh, cudaDevAttrMaxTexture2DGatherHeight, c->device));
@@ -659,9 +664,10 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     size_t most = 16;
     for (int i = 0; i < nbr; ++i) {
         const int *dm = cb->tmpl[i].dim;
+        const int nt = pair ? dm[2] - 1 : dm[2];            // tiles
         int l = 0;
-        while ((1ll << (2 * l)) < dm[2]) ++l;
-        const long long w = (long long)dm[0] << l, h = (long long)((dm[2] + (1 << l) - 1) >> l) * dm[1];
+        while ((1ll << (2 * l)) < nt) ++l;
+        const long long w = (long long)dm[0] << l, h = (long long)((nt + (1 << l) - 1) >> l) * dm[1];
         if (w > gw || h > gh) return fail(VR_ERR_UNSUPPORTED, "bricks too large for a slice atlas (2D gather limit)");
         lg[i] = l;
         most = std::max(most, (size_t)(w * h) * esz);
@@ -680,14 +686,17 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
     if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
     // FP32 values; FP16 codes as half texels (gathers widen them to float exactly); BF16 codes as
     // 16-bit unsigned texels (widened in the kernel)
-    const cudaChannelFormatDesc cd = esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
+    // (pair atlases: two codes in one 32-bit unsigned texel, widened in the kernel)
+    const cudaChannelFormatDesc cd = pair ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindUnsigned)
+                                   : esz == 4 ? cudaCreateChannelDesc(32, 0, 0, 0, cudaChannelFormatKindFloat)
                                    : cb->storage == VR_F16 ? cudaCreateChannelDescHalf()
                                                            : cudaCreateChannelDesc(16, 0, 0, 0, cudaChannelFormatKindUnsigned);
     cb->atlas_arr.assign(nbr, nullptr);
     cb->atlas_tex.assign(nbr, 0);
     for (int i = 0; i < nbr; ++i) {
         const int *dm = cb->tmpl[i].dim;
-        const size_t w = (size_t)dm[0] << lg[i], h = (size_t)((dm[2] + (1 << lg[i]) - 1) >> lg[i]) * dm[1];
+        const int nt = pair ? dm[2] - 1 : dm[2];
+        const size_t w = (size_t)dm[0] << lg[i], h = (size_t)((nt + (1 << lg[i]) - 1) >> lg[i]) * dm[1];
         cudaArray_t arr = nullptr;
         // written by the pack kernel through a surface where the device allows surface stores on
         // a gather array; else packed into staging and copied (the copy engine's array writes)
@@ -703,16 +712,18 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
         cudaResourceDesc rd{};
         rd.resType = cudaResourceTypeArray;
         rd.res.array.array = arr;
-        const char *src = static_cast<const char *>(cb->d_pool) + (size_t)cb->loff[3 * (size_t)i] * esz;
+        const char *src = static_cast<const char *>(cb->d_pool) + (size_t)cb->loff[3 * (size_t)i] * bsz;
         if (surf_ok) {
             cudaSurfaceObject_t sf = 0;
             if ((e = cudaCreateSurfaceObject(&sf, &rd)) != cudaSuccess) return bail(e, "cudaCreateSurfaceObject");
             surfs.push_back(sf);
-            e = launch_atlas_pack_surf(src, (int)esz, dm[0], dm[1], dm[2], lg[i], (unsigned long long)sf, s);
+            e = pair ? launch_pair_pack(src, dm[0], dm[1], dm[2], lg[i], nullptr, 0, (unsigned long long)sf, s)
+                     : launch_atlas_pack_surf(src, (int)esz, dm[0], dm[1], dm[2], lg[i], (unsigned long long)sf, s);
             if (e != cudaSuccess) return bail(e, "atlas pack launch");
         } else {
-            if ((e = launch_atlas_pack(src, (int)esz, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, s)) != cudaSuccess)
-                return bail(e, "atlas pack launch");
+            e = pair ? launch_pair_pack(src, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, 0ull, s)
+                     : launch_atlas_pack(src, (int)esz, dm[0], dm[1], dm[2], lg[i], tmp, w * esz, s);
+            if (e != cudaSuccess) return bail(e, "atlas pack launch");
             if ((e = cudaMemcpy2DToArrayAsync(arr, 0, 0, tmp, w * esz, w * esz, h, cudaMemcpyDeviceToDevice, s)) !=
                 cudaSuccess)
                 return bail(e, "cudaMemcpy2DToArrayAsync (slice atlas)");
@@ -737,6 +748,7 @@ int build_atlases(vr_ctx *c, Cube *cb, cudaStream_t s) {
         free_atlases(cb);
         return cuda_fail(e, "slice atlas build");
     }
+    cb->atlas_pair = pair;
     return VR_OK;
 }
 
@@ -1431,8 +1443,8 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
-    if (mask < 1 || mask > 31 || !(mask & 1))
-        return arg_fail("layout mask must be 1..31 and keep bit 0 (x contiguous)");
+    if (mask < 1 || mask > 63 || !(mask & 1) || ((mask & 32) && !(mask & 8)))
+        return arg_fail("layout mask must be 1..63, keep bit 0 (x contiguous), and set bit 3 with bit 5");
     if (cb->streamed && mask != 1 && mask != 9)
         return fail(VR_ERR_UNSUPPORTED, "streamed bricks are cached x-contiguous, with or without slot atlases (mask 1 or 9)");
     if (cb->layouts == mask) return VR_OK;

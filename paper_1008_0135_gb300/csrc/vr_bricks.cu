@@ -189,6 +189,59 @@ cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz
     return cudaGetLastError();
 }
 
+// Pair atlas of a 16-bit brick: texel (x, y) of tile z (z < dz - 1), placed at column
+// (z & (2^alog - 1)) dx + x, row (z >> alog) dy + y, holds the code of element (x, y, z) in its
+// low half and that of (x, y, z + 1) in its high half.
+__device__ __forceinline__ void pair_texel(const unsigned short *src, int dx, int dy, int dz, int alog, long long i,
+                                           unsigned int &val, int &col, int &row) {
+    const int x = (int)(i % dx);
+    const long long r = i / dx;
+    const int y = (int)(r % dy), z = (int)(r / dy);
+    const size_t e = ((size_t)z * dy + y) * dx + x;
+    val = (unsigned int)src[e] | ((unsigned int)src[e + (size_t)dx * dy] << 16);
+    col = (z & ((1 << alog) - 1)) * dx + x;
+    row = (z >> alog) * dy + y;
+}
+
+__global__ void k_pair_pack(const unsigned short *__restrict__ src, int dx, int dy, int dz, int alog, char *atlas,
+                            size_t pitch) {
+    const long long n = (long long)dx * dy * (dz - 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned int v;
+        int col, row;
+        pair_texel(src, dx, dy, dz, alog, i, v, col, row);
+        reinterpret_cast<unsigned int *>(atlas + (size_t)row * pitch)[col] = v;
+    }
+}
+
+// The same through a surface (zero boundary mode: a write outside the array is a no-op).
+__global__ void k_pair_pack_surf(const unsigned short *__restrict__ src, int dx, int dy, int dz, int alog,
+                                 cudaSurfaceObject_t surf) {
+    const long long n = (long long)dx * dy * (dz - 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned int v;
+        int col, row;
+        pair_texel(src, dx, dy, dz, alog, i, v, col, row);
+        surf2Dwrite<unsigned int>(v, surf, col * (int)sizeof(unsigned int), row, cudaBoundaryModeZero);
+    }
+}
+
+cudaError_t launch_pair_pack(const void *brick, int dx, int dy, int dz, int alog, void *atlas, size_t pitch,
+                             unsigned long long surf, cudaStream_t s) {
+    const long long n = (long long)dx * dy * (dz - 1);
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    if (surf)
+        k_pair_pack_surf<<<grid, 256, 0, s>>>(static_cast<const unsigned short *>(brick), dx, dy, dz, alog,
+                                              (cudaSurfaceObject_t)surf);
+    else
+        k_pair_pack<<<grid, 256, 0, s>>>(static_cast<const unsigned short *>(brick), dx, dy, dz, alog,
+                                         static_cast<char *>(atlas), pitch);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                int nbricks, const unsigned int *maxbits, int storage, void *pool,
                                int *exps, cudaStream_t s) {

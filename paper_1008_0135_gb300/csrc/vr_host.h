@@ -65,6 +65,7 @@ struct Cube {
     std::vector<cudaArray_t> atlas_arr;          // per brick (layout bit 3)
     std::vector<unsigned long long> atlas_tex;   // texture objects over them
     size_t atlas_bytes = 0;
+    bool atlas_pair = false;           // the atlases are pair atlases (layout bit 5, 16-bit bricks)
     // streamed cubes: bricks are produced on the host and cached in HBM on demand
     bool streamed = false;
     // compressed cubes (also `streamed`): 8x8x8 wavelet blocks in HBM, bricks decoded on demand

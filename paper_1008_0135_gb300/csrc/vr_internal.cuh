@@ -40,7 +40,8 @@ struct FrameConsts {
                                    // keep shared corners; poorly aligned layout), 2 = 2 gathers
                                    // from the brick's slice-atlas texture, 4 = slabs of the
                                    // brick staged in shared memory by bulk copies from the copy
-                                   // with 16-byte rows (DVR, FP32 bricks)
+                                   // with 16-byte rows (DVR, FP32 bricks), 5 = 1 gather from
+                                   // the brick's pair atlas (16-bit bricks)
     const unsigned char *chmask;   // per spectral channel (cube z): 0 = disabled; null = none
     int sub;                       // 1: a part's sub-image -- DVR pixels keep the transmittance T
                                    // (not 1 - T), MIP pixels without samples stay -inf
@@ -110,6 +111,11 @@ cudaError_t launch_atlas_pack(const void *brick, int esz, int dx, int dy, int dz
                               size_t pitch, cudaStream_t s);
 cudaError_t launch_atlas_pack_surf(const void *brick, int esz, int dx, int dy, int dz, int alog,
                                    unsigned long long surf, cudaStream_t s);
+// Packs one x-contiguous 16-bit brick into its pair atlas (dz - 1 tiles of dx x dy 32-bit
+// texels, placed like the slice atlas's tiles): through surface `surf` when non-zero, else into
+// the pitch-linear `atlas` of row pitch `pitch` bytes.
+cudaError_t launch_pair_pack(const void *brick, int dx, int dy, int dz, int alog, void *atlas, size_t pitch,
+                             unsigned long long surf, cudaStream_t s);
 cudaError_t launch_brick_build(const float *cube, int nx, int ny, int nz, const DrawBrick *bricks,
                                int nbricks, const unsigned int *maxbits, int storage, void *pool,
                                int *exps, cudaStream_t s);

@@ -31,6 +31,9 @@
 #ifndef VR_MIP_MIN_BLOCKS
 #define VR_MIP_MIN_BLOCKS 0
 #endif
+#ifndef VR_PAIR_PIPELINE
+#define VR_PAIR_PIPELINE 1
+#endif
 #ifndef VR_RAYMARCH_MIN_BLOCKS
 #define VR_RAYMARCH_MIN_BLOCKS 5
 #endif
@@ -291,6 +294,40 @@ __device__ __forceinline__ void fetch8_atlas(const Atlas &a, int ix, int iy, int
     }
 }
 
+// A 16-bit code of a pair texel widened to binary32 (exact): FP16 through the half conversion,
+// BF16 as the top half of the float.
+template <int S>
+__device__ __forceinline__ float code_value(unsigned int c) {
+    if constexpr (S == 1) return __half2float(__ushort_as_half((unsigned short)c));
+    else return bf16_value(c);
+}
+
+// Pair atlas (16-bit bricks): tile iz holds, in each 32-bit texel (x, y), the codes of voxel
+// (x, y, iz) (low half) and (x, y, iz + 1) (high half), so one gather at slice iz's footprint
+// returns all 8 stencil corners -- 16 bytes of texels per sample instead of 32, one gather
+// instead of two.  Tiles are placed like the slice atlas's, one per slice but the last.
+__device__ __forceinline__ uint4 gather_pair(const Atlas &a, int ix, int iy, int iz) {
+    const int cm = (1 << a.alog) - 1;                   // atlas coordinates < 32768
+    const float x0 = small_int_float((iz & cm) * a.dx + ix + 1), y0 = small_int_float((iz >> a.alog) * a.dy + iy + 1);
+    return tex2Dgather<uint4>(a.tex, x0, y0, 0);
+}
+
+template <int S>
+__device__ __forceinline__ void unpack_pair(const uint4 g, float v[8]) {
+    v[0] = code_value<S>(g.w & 0xffffu); v[4] = code_value<S>(g.w >> 16);
+    v[1] = code_value<S>(g.z & 0xffffu); v[5] = code_value<S>(g.z >> 16);
+    v[2] = code_value<S>(g.x & 0xffffu); v[6] = code_value<S>(g.x >> 16);
+    v[3] = code_value<S>(g.y & 0xffffu); v[7] = code_value<S>(g.y >> 16);
+}
+
+template <int S>
+__device__ __forceinline__ void fetch8_pair(const Atlas &a, int ix, int iy, int iz, float v[8]) {
+    unpack_pair<S>(gather_pair(a, ix, iy, iz), v);
+}
+
+// Whether fetch mode F reads a texture (the slice atlas, 2, or the pair atlas, 5).
+constexpr bool gathers(int F) { return F == 2 || F == 5; }
+
 template <int S>
 __device__ __forceinline__ void fetch8(const void *src, int i0, const Strides &t, float v[8]) {
     v[0] = ldv<S>(src, i0);             v[1] = ldv<S>(src, i0 + t.x);
@@ -391,6 +428,47 @@ __device__ __forceinline__ void over(const DvrSample &s, float &c0, float &c1, f
 // until the segment's transmittance reaches the threshold.  Returns the samples composited.
 // F: how the stencil is read (FrameConsts::fetch).  MASK: a spectral-channel mask is set (its own
 // instantiation, so unmasked frames carry none of its registers or branches).
+// The segment loop over a pair atlas, software-pipelined: a sample is one gather, so the gather
+// of sample j + 1 is issued before sample j is interpolated and composited (its latency overlaps
+// that work at the cost of one more texel quad in registers).  Samples, their order and the
+// arithmetic are those of the plain loop.
+template <int S, bool CLAMP, bool MASK>
+__device__ __forceinline__ int dvr_segment_pair(const Atlas &atl, int mx, int my, int mz, float scale,
+                                                float qx, float qy, float qz, const float d[3], int n,
+                                                const FrameConsts &fc, const float4 *s_lut, int org_z, float vcode,
+                                                float &c0, float &c1, float &c2, float &T) {
+    const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
+    const int lmax = fc.nlut - 2;
+    const float nf = (float)n;            // exact: n <= 2^24 + 1, checked by the host
+    if (n <= 0) return 0;
+    Cell cl;
+    cell_of<CLAMP>(qx, qy, qz, mx, my, mz, cl);
+    uint4 g = gather_pair(atl, cl.ix, cl.iy, cl.iz);
+    float jf = 0.0f;
+    for (;;) {
+        const float jn = __fadd_rn(jf, 1.0f);
+        Cell cn;
+        uint4 gn = make_uint4(0u, 0u, 0u, 0u);
+        if (jn < nf) {                    // the next sample's cell and gather, ahead
+            const float tn = __fmul_rn(jn, fc.step);
+            cell_of<CLAMP>(__fmaf_rn(tn, d[0], qx), __fmaf_rn(tn, d[1], qy), __fmaf_rn(tn, d[2], qz),
+                           mx, my, mz, cn);
+            gn = gather_pair(atl, cn.ix, cn.iy, cn.iz);
+        }
+        float v[8];
+        unpack_pair<S>(g, v);
+        if (MASK) mask_channels(v, cl.iz, org_z, fc.nz, fc.chmask, vcode);
+        DvrSample sm;
+        interp_tf(v, cl, S != 0, scale, vmin, inv_range, lutmax, lmax, s_lut, sm);
+        over(sm, c0, c1, c2, T);
+        if (T <= thr) return (int)jf + 1;
+        if (!(jn < nf)) return (int)jn;
+        jf = jn;
+        cl = cn;
+        g = gn;
+    }
+}
+
 template <int S, int F, bool CLAMP, bool MASK, bool ICOUNT = false>
 __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, const Atlas &atl,
                                            int mx, int my, int mz,
@@ -398,6 +476,9 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
                                            int n, const FrameConsts &fc, const float4 *s_lut,
                                            int org_z, float vcode,
                                            float &c0, float &c1, float &c2, float &T) {
+    if constexpr (F == 5 && VR_PAIR_PIPELINE)
+        return dvr_segment_pair<S, CLAMP, MASK>(atl, mx, my, mz, scale, qx, qy, qz, d, n, fc, s_lut, org_z, vcode,
+                                                c0, c1, c2, T);
     const float vmin = fc.vmin, inv_range = fc.inv_range, lutmax = fc.lutmax, thr = fc.thr;
     const int lmax = fc.nlut - 2;
     int px = -4, py = -4, pz = -4;        // no cell cached yet
@@ -415,6 +496,8 @@ __device__ __forceinline__ int dvr_segment(const void *src, const Strides &st, c
                        mx, my, mz, cl);
         if (F == 2)
             fetch8_atlas<S>(atl, cl.ix, cl.iy, cl.iz, v);
+        else if (F == 5)
+            fetch8_pair<S>(atl, cl.ix, cl.iy, cl.iz, v);
         else if (F == 1)
             fetch8_cached<S>(src, st, cl, px, py, pz, v);
         else
@@ -475,7 +558,7 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
         const Strides st{b.str[0], b.str[1], b.str[2]};
         const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
         const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
-        const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
+        const Atlas atl{gathers(F) ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
         if (MODE == 0) {
             if (hit) {
                 const float qx = anchor(o[0], d[0], b.org_c[0], k0, fc.step);
@@ -520,6 +603,8 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
                     float v[8];
                     if (F == 2)
                         fetch8_atlas<S>(atl, ix, iy, iz, v);
+                    else if (F == 5)
+                        fetch8_pair<S>(atl, ix, iy, iz, v);
                     else
                         fetch8<S>(src, i0, st, v);
                     if (MASK)
@@ -553,7 +638,7 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
 // atlas DVR loop without spills.
 template <int MODE, int F>
 constexpr int rc_min_blocks() {
-    return MODE == 0 ? (F == 2 && VR_DVR_MIN_BLOCKS > 0 ? VR_DVR_MIN_BLOCKS : 1)
+    return MODE == 0 ? (gathers(F) && VR_DVR_MIN_BLOCKS > 0 ? VR_DVR_MIN_BLOCKS : 1)
                      : (VR_MIP_MIN_BLOCKS > 0 ? VR_MIP_MIN_BLOCKS : 1);
 }
 
@@ -1010,7 +1095,7 @@ k_raymarch(const FrameConsts fc, const float4 *__restrict__ lut, DrawBrick *__re
             const Strides st{b.str[0], b.str[1], b.str[2]};
             const int mx = b.dim[0] - 2, my = b.dim[1] - 2, mz = b.dim[2] - 2;
             const float scale = S == 0 ? 1.0f : ldexpf(1.0f, b.exp2);
-            const Atlas atl{F == 2 ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
+            const Atlas atl{gathers(F) ? b.atlas : 0ull, b.alog, b.dim[0], b.dim[1]};
             const float qx = anchor(ray_origin(fc.cam, 0, y0, y1), d[0], b.org_c[0], k, fc.step);
             const float qy = anchor(ray_origin(fc.cam, 1, y0, y1), d[1], b.org_c[1], k, fc.step);
             const float qz = anchor(ray_origin(fc.cam, 2, y0, y1), d[2], b.org_c[2], k, fc.step);
@@ -1470,6 +1555,12 @@ cudaError_t launch_rc_s(const FrameConsts &fc, const float4 *lut, const DrawBric
         return fc.chmask ? launch_staged<true>(fc, lut, db, items, nitems, pool, frags, ctr, s)
                          : launch_staged<false>(fc, lut, db, items, nitems, pool, frags, ctr, s);
 #define VR_RC(MODE, F, MASK) launch_rc<S, MODE, F, MASK>(fc, lut, db, items, nitems, pool, frags, ctr, s)
+    if constexpr (S != 0) {           // pair atlases: 16-bit bricks only
+        if (fc.fetch == 5) {
+            if (fc.chmask) return fc.mode != 0 ? VR_RC(1, 5, true) : VR_RC(0, 5, true);
+            return fc.mode != 0 ? VR_RC(1, 5, false) : VR_RC(0, 5, false);
+        }
+    }
     const bool atlas = fc.fetch == 2;
     if (fc.chmask) {     // masked frames: no stencil cache (same values, fewer instantiations)
         if (fc.mode != 0) return atlas ? VR_RC(1, 2, true) : VR_RC(1, 0, true);
@@ -1511,6 +1602,11 @@ cudaError_t launch_march(const FrameConsts &fc, const float4 *lut, DrawBrick *br
 template <int S>
 cudaError_t launch_march_s(const FrameConsts &fc, const float4 *lut, DrawBrick *bricks, const MarchGrid &g,
                            const void *pool, float4 *out, Counters *ctr, cudaStream_t s) {
+    if constexpr (S != 0) {           // pair atlases: 16-bit bricks only
+        if (fc.fetch == 5)
+            return fc.chmask ? launch_march<S, 5, true>(fc, lut, bricks, g, pool, out, ctr, s)
+                             : launch_march<S, 5, false>(fc, lut, bricks, g, pool, out, ctr, s);
+    }
     const bool atlas = fc.fetch == 2;
     if (fc.chmask)
         return atlas ? launch_march<S, 2, true>(fc, lut, bricks, g, pool, out, ctr, s)

@@ -300,10 +300,12 @@ def test_16bit_bricks(ctx, orc, storage):
 
 # ---------------------------------------------------------------------------------------------
 # brick layouts: the gathered addresses change, the arithmetic does not.  Mask 7 keeps x-, y- and
-# z-contiguous copies; 9 and 15 add slice atlases (texture gathers) that every frame then reads.
+# z-contiguous copies; 9 and 15 add slice atlases (texture gathers) that every frame then reads;
+# 41 and 47 make a 16-bit cube's atlases pair atlases (one gather per sample; FP32 keeps slices).
 # ---------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("storage,layouts", [("f32", 7), ("f16", 7), ("f32", 9), ("f16", 15),
-                                             ("bf16", 9)])
+                                             ("bf16", 9), ("f16", 41), ("bf16", 41), ("f16", 47),
+                                             ("f32", 41)])
 def test_brick_layouts_give_identical_images(ctx, orc, storage, layouts):
     cube = synth.pr1_cube(seed=2)
     lut = synth.ramp_lut(alpha=0.5)
@@ -357,6 +359,53 @@ def test_fp16_atlas_keeps_subnormal_codes(ctx):
         assert np.abs(a).max() > 0 and np.array_equal(a, b)
     ctx.free_cube(one)
     ctx.free_cube(atl)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_pair_atlas_frames_equal_slice_atlas_frames(ctx, storage):
+    """Pair atlases (layout bit 5) hold the codes of slices z and z + 1 in one 32-bit texel: DVR
+    with per-segment and global termination, MIP, a channel mask and a render window give the
+    slice atlases' frames bit for bit, on ragged bricks (the last z layer 5 slices deep) and with
+    FP16 subnormal codes; bit 5 without bit 3 is refused."""
+    import paper_1008_0135_gb300 as P
+    rng = np.random.default_rng(61)
+    cube = synth.pr1_cube(seed=7, n=64)[:45].copy()
+    cube[:, :20, :20] *= 1e-7                       # tiny values: subnormal FP16 codes there
+    cube[3, 3, 3] = 50.0
+    lut = synth.ramp_lut(alpha=0.5)
+    sl = ctx.load_cube(cube)
+    ctx.set_brick_layouts(sl, 9)
+    ctx.set_bricking(sl, (20, 24, 20), 1, storage)
+    pr = ctx.load_cube(cube)
+    with pytest.raises(P.VrError) as e:
+        ctx.set_brick_layouts(pr, 33)
+    assert e.value.status == -1
+    ctx.set_brick_layouts(pr, 41)
+    ctx.set_bricking(pr, (20, 24, 20), 1, storage)
+    mask = (rng.uniform(size=45) > 0.3).astype(np.uint8)
+    cams = [synth.pr1_camera(W=80, H=72), synth.random_camera(rng, (64, 64, 45), 70, 66),
+            dict(view=synth.look_at((32.0, 150.0, 22.0), (32.0, 32.0, 22.0), up=(1.0, 0.0, 0.0)),
+                 proj=1, param=0.9, W=64, H=70)]
+    try:
+        for scope in ("segment", "global"):
+            ctx.set_termination(scope)
+            for cam in cams:
+                for extra in (False, True):
+                    ctx.set_channel_mask(mask if extra else None)
+                    if extra:
+                        ctx.set_window((3, 5, 2), (60, 57, 40))
+                    else:
+                        ctx.set_window()
+                    for mode in ("dvr", "mip"):
+                        a = render(ctx, sl, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.95)
+                        b = render(ctx, pr, lut, (-3, 20), cam, mode=mode, step=0.5, tau=0.95)
+                        assert np.abs(a).max() > 0 and np.array_equal(a, b), (scope, mode, extra)
+    finally:
+        ctx.set_termination("segment")
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+        ctx.free_cube(sl)
+        ctx.free_cube(pr)
 
 
 # ---------------------------------------------------------------------------------------------
