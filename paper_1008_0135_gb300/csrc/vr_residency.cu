@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <atomic>
 #include <cstring>
 #include <deque>
 #include <functional>
@@ -139,18 +140,24 @@ void gen_region(uint64_t seed, const int64_t n[3], const int org[3], const int d
     }
 }
 
-// 16-bit codes of a generated FP32 region: the scale exponent from the region's max |v|
-// (FP16 keeps max|v| 2^-e <= 2^14, BF16 <= 1), round-to-nearest-even codes.
-int encode_region(const float *v, size_t count, int storage, void *codes) {
+// The scale exponent of a 16-bit region whose max |v| is m (FP16 keeps max|v| 2^-e <= 2^14,
+// BF16 <= 1).
+int region_exponent(float m, int storage) {
+    if (!(m > 0.0f)) return 0;
+    int ex;
+    const float f = std::frexp(m, &ex);
+    const int cl = (f == 0.5f) ? ex - 1 : ex;
+    return storage == VR_F16 ? cl - 14 : cl;
+}
+
+float max_abs(const float *v, size_t count) {
     float m = 0.0f;
     for (size_t i = 0; i < count; ++i) m = std::max(m, std::fabs(v[i]));
-    int e = 0;
-    if (m > 0.0f) {
-        int ex;
-        const float f = std::frexp(m, &ex);
-        const int cl = (f == 0.5f) ? ex - 1 : ex;
-        e = storage == VR_F16 ? cl - 14 : cl;
-    }
+    return m;
+}
+
+// Round-to-nearest-even 16-bit codes of v 2^-e.
+void encode_codes(const float *v, size_t count, int storage, int e, void *codes) {
     if (storage == VR_F16) {
         __half *h = static_cast<__half *>(codes);
         for (size_t i = 0; i < count; ++i) h[i] = __float2half_rn(std::ldexp(v[i], -e));
@@ -158,6 +165,13 @@ int encode_region(const float *v, size_t count, int storage, void *codes) {
         __nv_bfloat16 *h = static_cast<__nv_bfloat16 *>(codes);
         for (size_t i = 0; i < count; ++i) h[i] = __float2bfloat16_rn(std::ldexp(v[i], -e));
     }
+}
+
+// 16-bit codes of a generated FP32 region: the scale exponent from the region's max |v|, then
+// the codes.
+int encode_region(const float *v, size_t count, int storage, void *codes) {
+    const int e = region_exponent(max_abs(v, count), storage);
+    encode_codes(v, count, storage, e, codes);
     return e;
 }
 
@@ -442,19 +456,104 @@ static int cache_size(vr_ctx *c, size_t slot_bytes) {
     return VR_OK;
 }
 
-// Generates brick `b` of streamed cube `cb` into pinned memory (FP32 values, or 16-bit codes
-// with the brick's exponent returned in *exp2).
-static void produce_brick(vr_ctx *c, Cube *cb, const DrawBrick &b, void *dst, int *exp2) {
-    const size_t count = (size_t)b.dim[0] * b.dim[1] * b.dim[2];
-    if (cb->storage == VR_F32) {
-        gen_region(cb->proc_seed, cb->n, b.org, b.dim, static_cast<float *>(dst));
-        *exp2 = 0;
+// One brick of a streamed cube produced into pinned memory (FP32 values, or 16-bit codes with
+// the brick's exponent in *exp2) by the whole worker pool: its box is cut into z-slabs generated
+// in parallel -- a voxel depends only on its coordinates, and a slab's source list keeps the
+// cells' order, so the values are those of one pass over the box -- and a 16-bit brick is then
+// encoded slab by slab with the exponent of its max |v| over all slabs.  `done` is set once
+// every slab has finished (or the first error is recorded in *err).
+struct BrickJob {
+    Cube *cb = nullptr;
+    DrawBrick b{};
+    void *dst = nullptr;
+    int *exp2 = nullptr;
+    std::string *err = nullptr;
+    Workers *pool = nullptr;
+    int nslab = 1;
+    std::vector<float> tmp;            // FP32 values of a 16-bit brick
+    std::vector<float> slab_max;
+    std::atomic<int> left{0};
+    std::mutex mu;                     // guards *err
+    std::promise<void> done;
+
+    size_t plane() const { return (size_t)b.dim[0] * b.dim[1]; }
+    int z0(int i) const { return (int)((int64_t)b.dim[2] * i / nslab); }
+    void fail_with(const char *what) {
+        std::lock_guard<std::mutex> l(mu);
+        if (err->empty()) *err = what;
+    }
+};
+
+static void job_encode(const std::shared_ptr<BrickJob> &j, int i);
+
+static void job_generate(const std::shared_ptr<BrickJob> &j, int i) {
+    try {
+        const int z0 = j->z0(i), z1 = j->z0(i + 1);
+        int org[3] = {j->b.org[0], j->b.org[1], j->b.org[2] + z0};
+        int dim[3] = {j->b.dim[0], j->b.dim[1], z1 - z0};
+        float *out = j->cb->storage == VR_F32 ? static_cast<float *>(j->dst) + (size_t)z0 * j->plane()
+                                              : j->tmp.data() + (size_t)z0 * j->plane();
+        if (dim[2] > 0) gen_region(j->cb->proc_seed, j->cb->n, org, dim, out);
+        if (j->cb->storage != VR_F32) j->slab_max[i] = max_abs(out, (size_t)dim[2] * j->plane());
+    } catch (const std::exception &e) {
+        j->fail_with(e.what());
+    }
+    if (j->left.fetch_sub(1) != 1) return;
+    // the last slab: FP32 bricks (or a failed one) are done; 16-bit bricks are encoded next
+    bool failed;
+    {
+        std::lock_guard<std::mutex> l(j->mu);
+        failed = !j->err->empty();
+    }
+    if (j->cb->storage == VR_F32 || failed) {
+        *j->exp2 = 0;
+        j->done.set_value();
         return;
     }
-    std::vector<float> tmp(count);
-    gen_region(cb->proc_seed, cb->n, b.org, b.dim, tmp.data());
-    *exp2 = encode_region(tmp.data(), count, cb->storage, dst);
-    (void)c;
+    float m = 0.0f;
+    for (float v : j->slab_max) m = std::max(m, v);
+    *j->exp2 = region_exponent(m, j->cb->storage);
+    j->left.store(j->nslab);
+    for (int k = 1; k < j->nslab; ++k) j->pool->submit([j, k] { job_encode(j, k); });
+    job_encode(j, 0);
+}
+
+static void job_encode(const std::shared_ptr<BrickJob> &j, int i) {
+    try {
+        const int z0 = j->z0(i), z1 = j->z0(i + 1);
+        const size_t off = (size_t)z0 * j->plane();
+        encode_codes(j->tmp.data() + off, (size_t)(z1 - z0) * j->plane(), j->cb->storage, *j->exp2,
+                     static_cast<char *>(j->dst) + off * 2);
+    } catch (const std::exception &e) {
+        j->fail_with(e.what());
+    }
+    if (j->left.fetch_sub(1) == 1) j->done.set_value();
+}
+
+// Starts the production of brick `b` on the pool; the future completes when it is done.
+static std::future<void> produce_brick(Workers *pool, Cube *cb, const DrawBrick &b, void *dst, int *exp2,
+                                       std::string *err, bool inject) {
+    auto j = std::make_shared<BrickJob>();
+    j->cb = cb;
+    j->b = b;
+    j->dst = dst;
+    j->exp2 = exp2;
+    j->err = err;
+    j->pool = pool;
+    std::future<void> f = j->done.get_future();
+    if (inject) {                      // a failing brick source (host-side fault injection)
+        *err = "brick source failed (injected)";
+        j->done.set_value();
+        return f;
+    }
+    j->nslab = std::max(1, std::min(pool->size(), b.dim[2]));
+    if (cb->storage != VR_F32) {
+        j->tmp.resize(j->plane() * (size_t)b.dim[2]);
+        j->slab_max.assign(j->nslab, 0.0f);
+    }
+    j->left.store(j->nslab);
+    for (int i = 0; i < j->nslab; ++i) pool->submit([j, i] { job_generate(j, i); });
+    return f;
 }
 
 // Slice atlases of cache slots (streamed and compressed cubes whose layout mask has bit 3):
@@ -675,14 +774,11 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         std::string *err = &errors[m];
         const bool inject = c->fault_kind == 1 && k->generated == c->fault_after;
         k->generated++;
-        fut[m] = k->workers->submit([c, cb, brick, dst, ep, err, inject] {
-            try {
-                if (inject) throw std::runtime_error("brick source failed (injected)");
-                produce_brick(c, cb, brick, dst, ep);
-            } catch (const std::exception &e) {
-                *err = e.what();
-            }
-        });
+        try {
+            fut[m] = produce_brick(k->workers, cb, brick, dst, ep, err, inject);
+        } catch (const std::exception &e) {       // the job's buffers could not be had
+            return fail(VR_ERR_OOM, e.what());
+        }
         return VR_OK;
     };
     while (issued < misses.size() && rc == VR_OK) {
