@@ -521,6 +521,7 @@ int backward_view(vr_ctx *c, Cube *cb, const float *grad_out, float *grad_lut, d
                        c->d_frags.p == frags_before;
     const int nitems = (int)wl.items.size();
     if ((rc = ensure(c->d_gpart, (size_t)std::max(nitems, 1) * 4 * fc.nlut, c)) != VR_OK) return rc;
+    if ((rc = ensure(c->d_gchunk, (size_t)kLutGradChunks * 4 * fc.nlut, c)) != VR_OK) return rc;
     char *d = c->d_stage.p;
     const float4 *d_lut = reinterpret_cast<const float4 *>(d + wl.off_lut);
     const DrawBrick *d_db = reinterpret_cast<const DrawBrick *>(d + wl.off_db);
@@ -541,9 +542,9 @@ int backward_view(vr_ctx *c, Cube *cb, const float *grad_out, float *grad_lut, d
                           reinterpret_cast<const float4 *>(c->d_frags.p), c->d_gfrag.p, c->d_gpart.p,
                           grad_voxels, s));
     if (acc) {
-        CK(launch_lut_grad_accumulate(c->d_gpart.p, nitems, fc.nlut, acc, first, s));
+        CK(launch_lut_grad_accumulate(c->d_gpart.p, nitems, fc.nlut, c->d_gchunk.p, acc, first, s));
     } else if (nitems > 0) {
-        CK(launch_lut_grad_reduce(c->d_gpart.p, nitems, fc.nlut, grad_lut, s));
+        CK(launch_lut_grad_reduce(c->d_gpart.p, nitems, fc.nlut, c->d_gchunk.p, grad_lut, s));
     } else {
         CK(cudaMemsetAsync(grad_lut, 0, sizeof(float) * 4 * fc.nlut, s));
     }
@@ -1124,6 +1125,8 @@ void vr_destroy(vr_ctx *c) {
     if (c->d_frags.p) cudaFree(c->d_frags.p);
     if (c->d_gfrag.p) cudaFree(c->d_gfrag.p);
     if (c->d_gpart.p) cudaFree(c->d_gpart.p);
+    if (c->d_gchunk.p) cudaFree(c->d_gchunk.p);
+    if (c->d_gacc.p) cudaFree(c->d_gacc.p);
     if (c->d_out.p) cudaFree(c->d_out.p);
     if (c->d_ctr) cudaFree(c->d_ctr);
     if (c->d_mm) cudaFree(c->d_mm);

@@ -141,6 +141,7 @@ struct vr_ctx {
     vrh::DevBuf<float4> d_gfrag;
     vrh::DevBuf<float> d_gpart;
     vrh::DevBuf<double> d_gacc;         // FP64 table-gradient sum over the views of a batch
+    vrh::DevBuf<double> d_gchunk;       // FP64 chunk sums of a view's table-gradient partials
     vrh::DevBuf<float> d_out;
     cudaEvent_t upload_done = nullptr, frame_done = nullptr;
     bool frame_pending = false;

@@ -152,12 +152,15 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
                            const TileItem *items, int nitems, const float *pool,
                            const float4 *frags, const float4 *gfrag, float *glut_partial,
                            float *gvox, cudaStream_t s);
-cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, float *glut,
-                                   cudaStream_t s);
-// Several views: acc (4 nlut doubles) = (first ? 0 : acc) + the view's partials, in FP64; then
+// The table gradient from the adjoint's per-CTA partials (nparts x 4 nlut floats), summed in
+// FP64 through `chunks` (kLutGradChunks x 4 nlut doubles of scratch): glut = the sum; with
+// several views, acc (4 nlut doubles) = (first ? 0 : acc) + the view's sum, and
 // glut = (float)acc after the last view.
-cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *acc, bool first,
-                                       cudaStream_t s);
+constexpr int kLutGradChunks = 64;
+cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, double *chunks, float *glut,
+                                   cudaStream_t s);
+cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *chunks, double *acc,
+                                       bool first, cudaStream_t s);
 cudaError_t launch_lut_grad_store(const double *acc, int nlut, float *glut, cudaStream_t s);
 
 }  // namespace vr

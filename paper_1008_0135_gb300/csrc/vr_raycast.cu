@@ -1442,24 +1442,35 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
     }
 }
 
-// Final reduction of the per-CTA table-gradient partials, accumulated in FP64.
-__global__ void k_lut_grad_reduce(const float *__restrict__ partial, int nparts, int n,
-                                  float *__restrict__ glut) {
+// Final reduction of the per-CTA table-gradient partials, in FP64 and in two stages so that
+// every entry's sum is spread over many threads yet formed in a fixed order: chunk y sums the
+// partials of parts [y q, (y + 1) q) in part order, then the chunk sums are added in chunk order.
+__global__ void k_lut_grad_chunks(const float *__restrict__ partial, int nparts, int n, double *__restrict__ chunks) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int q = (nparts + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int p0 = (int)blockIdx.y * q, p1 = min(nparts, p0 + q);
+    double a = 0.0;
+    for (int p = p0; p < p1; ++p) a += (double)partial[(long long)p * n + i];
+    chunks[(long long)blockIdx.y * n + i] = a;
+}
+
+__global__ void k_lut_grad_reduce(const double *__restrict__ chunks, int nchunks, int n, float *__restrict__ glut) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double acc = 0.0;
-    for (int p = 0; p < nparts; ++p) acc += (double)partial[(long long)p * n + i];
+    for (int y = 0; y < nchunks; ++y) acc += chunks[(long long)y * n + i];
     glut[i] = (float)acc;
 }
 
-// Several views' table gradients: each view's partials are added to one FP64 accumulator
+// Several views' table gradients: each view's chunk sums are added to one FP64 accumulator
 // (zeroed by the first view), which is rounded to FP32 once, after the last view.
-__global__ void k_lut_grad_accumulate(const float *__restrict__ partial, int nparts, int n,
+__global__ void k_lut_grad_accumulate(const double *__restrict__ chunks, int nchunks, int n,
                                       double *__restrict__ acc, int first) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double a = first ? 0.0 : acc[i];
-    for (int p = 0; p < nparts; ++p) a += (double)partial[(long long)p * n + i];
+    for (int y = 0; y < nchunks; ++y) a += chunks[(long long)y * n + i];
     acc[i] = a;
 }
 
@@ -1673,17 +1684,27 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
     return cudaGetLastError();
 }
 
-cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, float *glut,
-                                   cudaStream_t s) {
-    const int n = 4 * nlut;
-    k_lut_grad_reduce<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, glut);
+static cudaError_t launch_lut_grad_chunks(const float *partial, int nparts, int n, double *chunks, cudaStream_t s) {
+    dim3 grid((n + 255) / 256, kLutGradChunks);
+    k_lut_grad_chunks<<<grid, 256, 0, s>>>(partial, nparts, n, chunks);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *acc, bool first,
-                                       cudaStream_t s) {
+cudaError_t launch_lut_grad_reduce(const float *partial, int nparts, int nlut, double *chunks, float *glut,
+                                   cudaStream_t s) {
     const int n = 4 * nlut;
-    k_lut_grad_accumulate<<<(n + 255) / 256, 256, 0, s>>>(partial, nparts, n, acc, first ? 1 : 0);
+    cudaError_t e = launch_lut_grad_chunks(partial, nparts, n, chunks, s);
+    if (e != cudaSuccess) return e;
+    k_lut_grad_reduce<<<(n + 255) / 256, 256, 0, s>>>(chunks, kLutGradChunks, n, glut);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_grad_accumulate(const float *partial, int nparts, int nlut, double *chunks, double *acc,
+                                       bool first, cudaStream_t s) {
+    const int n = 4 * nlut;
+    cudaError_t e = launch_lut_grad_chunks(partial, nparts, n, chunks, s);
+    if (e != cudaSuccess) return e;
+    k_lut_grad_accumulate<<<(n + 255) / 256, 256, 0, s>>>(chunks, kLutGradChunks, n, acc, first ? 1 : 0);
     return cudaGetLastError();
 }
 
