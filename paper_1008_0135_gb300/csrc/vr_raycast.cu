@@ -37,12 +37,6 @@
 #ifndef VR_RAYMARCH_MIN_BLOCKS
 #define VR_RAYMARCH_MIN_BLOCKS 5
 #endif
-#ifndef VR_ADJ_COPIES
-#define VR_ADJ_COPIES 8
-#endif
-#ifndef VR_ADJ_SMEM_KB
-#define VR_ADJ_SMEM_KB 64
-#endif
 #ifndef VR_ADJ_MIN_BLOCKS
 #define VR_ADJ_MIN_BLOCKS 4
 #endif
@@ -1311,7 +1305,9 @@ __device__ __forceinline__ void flush_voxel_grads(float *__restrict__ gvox, cons
 //   dL/dc_j = gC T_{j-1} a_j
 //   dL/da_j = T_{j-1} [ gC.c_j - (gC.(C_b - C_{<=j}) + gT T_b) / T_j ]   (T_j = T_{j-1}(1-a_j))
 //   last composited sample: dL/da_j = T_{j-1} [ gC.c_j - gT ]
-// Table gradients accumulate per CTA in shared memory and are written as one partial per CTA.
+// Table gradients accumulate per CTA in a partial row in L2 (two float4 atomics per sample; eight
+// float atomics per sample into shared-memory copies were 13 % slower per batch, their retries of
+// contended adds and the copy-out included).
 // Voxel gradients accumulate per ray for the 8 corners of its current cell and are added to the
 // cube's voxels when the ray leaves the cell (ghost copies map back to their source voxel); a
 // step into an adjacent cell keeps the shared face's 4 sums (before: 8 atomics per sample).
@@ -1323,23 +1319,16 @@ __global__ void __launch_bounds__(256, VR_ADJ_MIN_BLOCKS)
 k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick *__restrict__ dbs,
           const TileItem *__restrict__ items, const float *__restrict__ pool,
           const float4 *__restrict__ frags, const float4 *__restrict__ gfrag,
-          float *__restrict__ glut_partial, float *__restrict__ gvox, int ncopies) {
+          float *__restrict__ glut_partial, float *__restrict__ gvox) {
     extern __shared__ float4 s_lut[];
-    // ncopies (1, 2, 4 or 8) table-gradient accumulators, lane l adding into copy l mod ncopies:
-    // neighbouring rays mostly hit the same entries, and same-address shared atomics of one
-    // warp serialise.  A copy holds one row per channel with the entries consecutive, so the
-    // lanes' different entries spread over all 32 banks (entry-major rows put channel c of
-    // every entry in one of 8 banks: the table-gradient pass 1.3 x slower)
-    const int cs = fc.nlut + 2;              // one row per channel: entries along the banks
-    const int gstride = 4 * cs + 8;
-    float *s_g0 = reinterpret_cast<float *>(s_lut + 2 * fc.nlut);
     load_table(lut, fc.nlut, s_lut);
-    for (int i = threadIdx.x; i < ncopies * gstride; i += blockDim.x) s_g0[i] = 0.0f;
     __syncthreads();
     const TileItem it = items[blockIdx.x];
     const DrawBrick &b = dbs[it.db];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *s_g = s_g0 + (lane & (ncopies - 1)) * gstride;
+    // this CTA's table-gradient partial: one float4 (the 4 channels) per entry, zeroed before the
+    // launch; each sample adds its two entries' channels with one vector atomic each (in L2)
+    float4 *g_row = reinterpret_cast<float4 *>(glut_partial) + (long long)blockIdx.x * fc.nlut;
     // a warp's 32 rays are adjacent pixels along the image axis the brick layout follows
     int rx, ry;
     thread_pixel(fc.lanes_y, it, warp, lane, rx, ry);
@@ -1386,11 +1375,9 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                 const float wa = Tb * sm.a;
                 const float gr = gf.x * wa, gg = gf.y * wa, gb = gf.z * wa;
                 const float w1 = sm.lf, w0 = 1.0f - sm.lf;
-                float *g0 = s_g + sm.li;
-                atomicAdd(g0, w0 * gr); atomicAdd(g0 + 1, w1 * gr);
-                atomicAdd(g0 + cs, w0 * gg); atomicAdd(g0 + cs + 1, w1 * gg);
-                atomicAdd(g0 + 2 * cs, w0 * gb); atomicAdd(g0 + 2 * cs + 1, w1 * gb);
-                atomicAdd(g0 + 3 * cs, w0 * ga); atomicAdd(g0 + 3 * cs + 1, w1 * ga);
+                atomicAdd(g_row + sm.li, make_float4(w0 * gr, w0 * gg, w0 * gb, w0 * ga));
+                if (sm.li + 1 < fc.nlut)      // the last entry (u >= 1) has weight 1 and no next entry
+                    atomicAdd(g_row + sm.li + 1, make_float4(w1 * gr, w1 * gg, w1 * gb, w1 * ga));
                 if (gvox != nullptr && sm.u > 0.0f && sm.u < 1.0f) {
                     const float gx = gr * sm.D.x + gg * sm.D.y + gb * sm.D.z + ga * sm.D.w;
                     const float gv = gx * dxdv;
@@ -1421,24 +1408,19 @@ k_adjoint(const FrameConsts fc, const float4 *__restrict__ lut, const DrawBrick 
                         const float vx = 1.0f - ux, vy = 1.0f - uy;
                         const float uz = (fc.chmask && !fc.chmask[gz1]) ? 0.0f : sm.fz;
                         const float vz = (fc.chmask && !fc.chmask[gz0]) ? 0.0f : 1.0f - sm.fz;
-                        acc[0] += gv * vx * vy * vz; acc[1] += gv * ux * vy * vz;
-                        acc[2] += gv * vx * uy * vz; acc[3] += gv * ux * uy * vz;
-                        acc[4] += gv * vx * vy * uz; acc[5] += gv * ux * vy * uz;
-                        acc[6] += gv * vx * uy * uz; acc[7] += gv * ux * uy * uz;
+                        // trilinear weights of the 8 corners, factored by z, then y
+                        const float wz0 = gv * vz, wz1 = gv * uz;
+                        const float g00 = wz0 * vy, g10 = wz0 * uy, g01 = wz1 * vy, g11 = wz1 * uy;
+                        acc[0] = __fmaf_rn(g00, vx, acc[0]); acc[1] = __fmaf_rn(g00, ux, acc[1]);
+                        acc[2] = __fmaf_rn(g10, vx, acc[2]); acc[3] = __fmaf_rn(g10, ux, acc[3]);
+                        acc[4] = __fmaf_rn(g01, vx, acc[4]); acc[5] = __fmaf_rn(g01, ux, acc[5]);
+                        acc[6] = __fmaf_rn(g11, vx, acc[6]); acc[7] = __fmaf_rn(g11, ux, acc[7]);
                     }
                 }
                 if (T <= fc.thr) break;
             }
             if (gvox != nullptr && ccx != -4) flush_voxel_grads(gvox, acc, 0xffu, ccx, ccy, ccz, b, fc);
         }
-    }
-    __syncthreads();
-    float *dst = glut_partial + (long long)blockIdx.x * 4 * fc.nlut;
-    for (int i = threadIdx.x; i < 4 * fc.nlut; i += blockDim.x) {
-        const int at = (i & 3) * cs + (i >> 2);   // entry i / 4, channel i % 4
-        float v = s_g0[at];
-        for (int c = 1; c < ncopies; ++c) v += s_g0[c * gstride + at];
-        dst[i] = v;
     }
 }
 
@@ -1667,20 +1649,17 @@ cudaError_t launch_adjoint(const FrameConsts &fc, const float4 *lut, const DrawB
                            float *gvox, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
     static DeviceAttrs da_lin, da_atl;
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<false>), (int)(48 * kMaxLut + 64), da_lin);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<false>), (int)(32 * kMaxLut), da_lin);
     if (e == cudaSuccess)
-        e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<true>), (int)(48 * kMaxLut + 64), da_atl);
+        e = ensure_smem_limit(reinterpret_cast<const void *>(k_adjoint<true>), (int)(32 * kMaxLut), da_atl);
     if (e != cudaSuccess) return e;
-    // table + differences (32 B per entry) + gradient accumulators (16 B per entry and copy): as
-    // many copies (up to 8) as keep the block within 64 KB
-    int ncopies = VR_ADJ_COPIES;
-    const size_t per_copy = 16 * (size_t)fc.nlut + 64;
-    while (ncopies > 1 && 32 * (size_t)fc.nlut + ncopies * per_copy > ((size_t)VR_ADJ_SMEM_KB << 10)) ncopies >>= 1;
-    const size_t smem = 32 * (size_t)fc.nlut + ncopies * per_copy;
+    const size_t smem = 32 * (size_t)fc.nlut;      // table + differences
+    e = cudaMemsetAsync(glut_partial, 0, sizeof(float) * 4 * (size_t)fc.nlut * nitems, s);
+    if (e != cudaSuccess) return e;
     if (fc.fetch == 2)
-        k_adjoint<true><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
+        k_adjoint<true><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
     else
-        k_adjoint<false><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox, ncopies);
+        k_adjoint<false><<<nitems, 256, smem, s>>>(fc, lut, db, items, pool, frags, gfrag, glut_partial, gvox);
     return cudaGetLastError();
 }
 
