@@ -75,6 +75,26 @@ def test_noalloc_matches_render_frame_on_consecutive_calls(setup):
         assert torch.equal(out, refs[k]), k
 
 
+@pytest.mark.parametrize("storage,layouts", [("f16", 41), ("bf16", 9)])
+def test_noalloc_matches_render_frame_with_16bit_bricks(setup, storage, layouts):
+    """16-bit bricks read through slice atlases or pair atlases (one gather per sample): the same
+    bits as the allocating entry point."""
+    torch, ctx, L, _ = setup
+    cid = ctx.load_cube(synth.pr1_cube(seed=1))
+    ctx.set_brick_layouts(cid, layouts)
+    ctx.set_bricking(cid, (24, 32, 20), 1, storage)
+    try:
+        refs = _references(torch, ctx, cid)
+        for k in range(len(VIEWS)):
+            _set_view(ctx, k)
+            out = torch.full_like(refs[k], float("nan"))
+            _call(torch, ctx, L, cid, out)
+            torch.cuda.synchronize()
+            assert torch.equal(out, refs[k]), (storage, k)
+    finally:
+        ctx.free_cube(cid)
+
+
 def test_noalloc_calls_queued_on_one_stream_allocate_nothing(setup):
     """Calls queued back to back on one stream (each one's upload overwrites the scratch the one
     before it read, in stream order) give every frame its own bits; across them neither the
