@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--frame", type=int, default=0,
                     help="frame edge in pixels of --leg runs (0: the config's); a smaller frame of a "
                          "small cube spaces its rays as far apart as the full cube's (for profiling)")
-    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "compressed", "serving", "sortlast"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "mip", "compressed", "serving", "sortlast"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -179,10 +179,10 @@ def cameras(cfg, n):
 # ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
-def timed_frames(ctx, cid, cams, lut, vr, cfg, steps, warmup, dist, out, clocks=None):
+def timed_frames(ctx, cid, cams, lut, vr, cfg, steps, warmup, dist, out, clocks=None, mode="dvr"):
     import torch
     ctx.set_transfer_function(lut, *vr)
-    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    ctx.set_render_params(mode, cfg["step"], cfg["tau"])
     stream = torch.cuda.current_stream()
     for w in range(warmup):
         ctx.set_camera_dict(cams[w % len(cams)])
@@ -207,6 +207,22 @@ def timed_frames(ctx, cid, cams, lut, vr, cfg, steps, warmup, dist, out, clocks=
     ms = e0.elapsed_time(e1)
     st = ctx.stats()
     return ms, st, clk
+
+
+def mip_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
+    """Maximum-intensity projection (Section 2.4's second mode) of the bench's orbit frames: every
+    lattice sample of every brick segment (no early termination), one FP32 maximum per (brick,
+    pixel) fragment, the fragments' maximum per pixel.  Its roofline counts the sampled bricks'
+    stored bytes and 4 B per fragment."""
+    peak, psrc = peaks()
+    ms, st, _ = timed_frames(ctx, cid, cams, synth.ramp_lut(), cfg["vrange"], cfg, steps, warmup, dist,
+                             out, mode="mip")
+    t = dist.max(ms)
+    ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+    return {"workload": cfg["name"] + f", {cfg['W']}x{cfg['H']} orbit, step {cfg['step']}, MIP",
+            "ms_per_frame": round(t / steps, 4), "samples_per_frame": int(st["samples"] // max(steps, 1)),
+            "Gsamples_per_s": round(dist.sum(st["samples"]) / (t * 1e-3) / 1e9, 3),
+            "roofline": roofline(st, steps, peak, psrc, "k_raycast<f32,MIP>", 32, 4)}
 
 
 def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
@@ -400,14 +416,14 @@ def traffic_entry(name: str):
     return json.load(open(p)).get(name) if os.path.exists(p) else None
 
 
-def roofline(st, steps, peak, src, name, texel_bytes=32):
+def roofline(st, steps, peak, src, name, texel_bytes=32, frag_bytes=16):
     """The HBM roofline of the ray-cast launch, and beside it the texture unit's texel writeback:
     the texel bytes its gathers return per second (`texel_bytes` per sample: two gathers of four
     texels, 32 B for FP32 texels and 16 B for 16-bit ones -- the writeback's busy cycles follow
     the texel size, not the widened registers) against the L1TEX writeback rate derived from ncu
     (32 B per cycle per SM)."""
     nl = max(st["timed_frames"], 1)
-    per_launch = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / nl
+    per_launch = (st["brick_bytes_sampled"] + frag_bytes * st["fragments"]) / nl
     ms = st["ms_raycast"] / nl
     achieved = per_launch / (ms * 1e-3) / 1e9
     rl = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -760,6 +776,7 @@ def run_ours(args, dist):
         ctx.set_bricking(cid, cfg["brick"], 1, "f32")
         res["occlusion"] = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32),
                                          args.warmup)
+        res["mip"] = mip_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
         # end to end through the C ABI with host buffers: table + camera in, frame out.  A
         # viewer's loop: frame k is queued (asynchronous copy into one of two pinned frames)
         # before frame k - 1 is read, so the host's work for a frame overlaps the GPU's
@@ -863,7 +880,7 @@ def main():
         print(json.dumps({"leg": "adjoint", **adjoint_leg(ctx, f"cuda:{dist.local}")}))
         ctx.close()
         return
-    if args.leg in ("occlusion", "compressed", "serving", "sortlast"):
+    if args.leg in ("occlusion", "mip", "compressed", "serving", "sortlast"):
         import torch
         import paper_1008_0135_gb300 as P
         P.build()
@@ -883,6 +900,8 @@ def main():
         cams = cameras(cfg, cfg.get("n_views", 64))
         if args.leg == "occlusion":
             res = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
+        elif args.leg == "mip":
+            res = mip_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
         elif args.leg == "serving":
             res = serving_leg(ctx, cid, device)
         elif args.leg == "sortlast":

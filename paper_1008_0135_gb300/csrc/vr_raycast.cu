@@ -588,11 +588,13 @@ __device__ __forceinline__ void rc_strip(const FrameConsts &fc, const float4 *__
                     const float py = __fadd_rn(o[1], __fmul_rn(t, d[1]));
                     const float pz = __fadd_rn(o[2], __fmul_rn(t, d[2]));
                     const float x = __fsub_rn(px, 0.5f), y = __fsub_rn(py, 0.5f), z = __fsub_rn(pz, 0.5f);
-                    const float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+                    // floors on the FMA and integer pipes (world coordinates are far below 2^22)
+                    float flx, fly, flz;
+                    const int jx = floor_split(x, flx), jy = floor_split(y, fly), jz = floor_split(z, flz);
                     const float fx = __fsub_rn(x, flx), fy = __fsub_rn(y, fly), fz = __fsub_rn(z, flz);
-                    const int ix = clampi((int)flx - b.org[0], 0, mx);
-                    const int iy = clampi((int)fly - b.org[1], 0, my);
-                    const int iz = clampi((int)flz - b.org[2], 0, mz);
+                    const int ix = clampi(jx - b.org[0], 0, mx);
+                    const int iy = clampi(jy - b.org[1], 0, my);
+                    const int iz = clampi(jz - b.org[2], 0, mz);
                     const int i0 = ix * st.x + iy * st.y + iz * st.z;
                     float v[8];
                     if (F == 2)
