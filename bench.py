@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--frame", type=int, default=0,
                     help="frame edge in pixels of --leg runs (0: the config's); a smaller frame of a "
                          "small cube spaces its rays as far apart as the full cube's (for profiling)")
-    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "mip", "compressed", "serving", "sortlast"],
+    ap.add_argument("--leg", default=None, choices=["adjoint", "occlusion", "mip", "subcube", "compressed", "serving",
+                                                         "sortlast"],
                     help="run one extra leg alone and print its JSON (for profiling)")
     return ap.parse_args()
 
@@ -223,6 +224,40 @@ def mip_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
             "ms_per_frame": round(t / steps, 4), "samples_per_frame": int(st["samples"] // max(steps, 1)),
             "Gsamples_per_s": round(dist.sum(st["samples"]) / (t * 1e-3) / 1e9, 3),
             "roofline": roofline(st, steps, peak, psrc, "k_raycast<f32,MIP>", 32, 4)}
+
+
+def subcube_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
+    """Render-time selections (Section 2.3's spectral-channel choice and sub-cube windows): the
+    bench's orbit frames with only a band of channels enabled (the others read as the bottom of
+    the table range), and clipped to a sub-cube window, beside the full frame."""
+    nx, ny, nz = cfg["shape"]
+    lut = synth.ramp_lut()
+    res = {"workload": cfg["name"] + f", {cfg['W']}x{cfg['H']} orbit, step {cfg['step']}, DVR"}
+
+    def run(tag):
+        ms, st, _ = timed_frames(ctx, cid, cams, lut, cfg["vrange"], cfg, steps, warmup, dist, out)
+        t = dist.max(ms)
+        res[tag] = {"ms_per_frame": round(t / steps, 4), "samples_per_frame": int(st["samples"] // max(steps, 1)),
+                    "Gsamples_per_s": round(dist.sum(st["samples"]) / (t * 1e-3) / 1e9, 3)}
+
+    run("full")
+    lo, hi = int(nz * 0.40), int(nz * 0.60)
+    mask = np.zeros(nz, np.uint8)
+    mask[lo:hi] = 1
+    ctx.set_channel_mask(mask)
+    try:
+        run("channel_band")
+    finally:
+        ctx.set_channel_mask(None)
+    res["channel_band"]["channels"] = [lo, hi]
+    wlo, whi = (nx // 4, ny // 4, nz // 4), (3 * nx // 4, 3 * ny // 4, nz // 2)
+    ctx.set_window(wlo, whi)
+    try:
+        run("window")
+    finally:
+        ctx.set_window()
+    res["window"]["box"] = [list(wlo), list(whi)]
+    return res
 
 
 def occlusion_leg(ctx, cid, cfg, cams, dist, out, steps, warmup):
@@ -777,6 +812,7 @@ def run_ours(args, dist):
         res["occlusion"] = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32),
                                          args.warmup)
         res["mip"] = mip_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
+        res["subcube"] = subcube_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 16), args.warmup)
         # end to end through the C ABI with host buffers: table + camera in, frame out.  A
         # viewer's loop: frame k is queued (asynchronous copy into one of two pinned frames)
         # before frame k - 1 is read, so the host's work for a frame overlaps the GPU's
@@ -880,7 +916,7 @@ def main():
         print(json.dumps({"leg": "adjoint", **adjoint_leg(ctx, f"cuda:{dist.local}")}))
         ctx.close()
         return
-    if args.leg in ("occlusion", "mip", "compressed", "serving", "sortlast"):
+    if args.leg in ("occlusion", "mip", "subcube", "compressed", "serving", "sortlast"):
         import torch
         import paper_1008_0135_gb300 as P
         P.build()
@@ -902,6 +938,8 @@ def main():
             res = occlusion_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
         elif args.leg == "mip":
             res = mip_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 32), args.warmup)
+        elif args.leg == "subcube":
+            res = subcube_leg(ctx, cid, cfg, cams, dist, out, min(args.steps, 16), args.warmup)
         elif args.leg == "serving":
             res = serving_leg(ctx, cid, device)
         elif args.leg == "sortlast":
