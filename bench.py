@@ -721,7 +721,7 @@ def empty_space_leg(ctx, device, steps=16):
     return res
 
 
-def cpu_baseline(cube_np, cfg, lut, vr, n_rays):
+def cpu_baseline(cube_np, cfg, lut, vr, n_rays, samples_per_frame=None):
     import oracle
     cam = synth.orbit_camera(cfg, 0)
     pix = synth.sample_pixels(cfg["seed"], cam["W"], cam["H"], n_rays)
@@ -729,9 +729,12 @@ def cpu_baseline(cube_np, cfg, lut, vr, n_rays):
     _, _, ns = oracle.render(cube_np, lut, vr, cam, step=cfg["step"], tau=cfg["tau"],
                              brick=cfg["brick"], pix=pix)
     dt = time.perf_counter() - t0
-    return {"value": round(ns / dt / 1e9, 6), "unit": "Gsamples/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{len(pix)} seeded pixels of orbit view 0 ({ns} samples, {dt:.2f} s wall)"}
+    res = {"value": round(ns / dt / 1e9, 6), "unit": "Gsamples/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": f"{len(pix)} seeded pixels of orbit view 0 ({ns} samples, {dt:.2f} s wall)"}
+    if samples_per_frame:            # a whole frame at the sample's rate
+        res["ms_per_frame_extrapolated"] = round(1e3 * samples_per_frame / (ns / dt), 1)
+    return res
 
 
 def run_ours(args, dist):
@@ -855,7 +858,7 @@ def run_ours(args, dist):
             ctx.free_cube(cid)
             cid = None
             res["empty_space"] = empty_space_leg(ctx, device)
-            res["cpu_baseline"] = cpu_baseline(cube_np, cfg, lut, vr, args.cpu_rays)
+            res["cpu_baseline"] = cpu_baseline(cube_np, cfg, lut, vr, args.cpu_rays, res["samples_per_frame"])
     ctx.close()
     if dist.rank == 0:
         print(json.dumps(res))
