@@ -162,7 +162,7 @@ def _free_port():
     return port
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, backend="gloo"):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -170,7 +170,10 @@ def _rank(rank, world, port, q):
     import torch.distributed as dist
     import paper_1008_0135_gb300 as P
     from paper_1008_0135_gb300.sortlast import SortLast
-    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=120))
+    if backend == "nccl":
+        import torch
+        torch.cuda.set_device(0)
+    dist.init_process_group(backend, rank=rank, world_size=world, timeout=timedelta(seconds=120))
     rng = np.random.default_rng(42)
     nx, ny, nz = SHAPE
     cube = rng.standard_normal((nz, ny, nx)).astype(np.float32)
@@ -181,7 +184,7 @@ def _rank(rank, world, port, q):
         ctx.set_transfer_function(synth.random_lut(3, n=64, alpha_max=0.35), -3.0, 12.0)
         ctx.set_camera_dict(CAMS[2])
         ctx.set_render_params("dvr", 0.5, 0.99)
-        frame = SortLast(ctx, cid, (world,), rank).render().cpu().numpy()
+        frame = SortLast(ctx, cid, (world,), rank, backend=backend).render().cpu().numpy()
     q.put((rank, frame))
     dist.barrier()
     dist.destroy_process_group()
@@ -209,6 +212,29 @@ def test_two_processes_exchange_subimages_over_gloo(setup):
         assert p.exitcode == 0
     for r in range(2):
         assert np.array_equal(got[r], local), r
+
+
+def test_one_rank_over_nccl(setup):
+    """The exchange's NCCL path (groups created with the NCCL backend, the bands gathered with
+    all_gather_into_tensor on CUDA tensors) with one rank on cuda:0 -- one GPU, so no kernel
+    waits on another rank: the frame equals the one-part composite made in this process."""
+    import torch.distributed as dist
+    if not dist.is_nccl_available():
+        pytest.skip("torch built without NCCL")
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx, cube, cid = setup
+    ctx.set_transfer_function(synth.random_lut(3, n=64, alpha_max=0.35), -3.0, 12.0)
+    ctx.set_camera_dict(CAMS[2])
+    ctx.set_render_params("dvr", 0.5, 0.99)
+    local = _sortlast_local(ctx, cid, (1,)).cpu().numpy()
+    mpc = mp.get_context("spawn")
+    q = mpc.Queue()
+    p = mpc.Process(target=_rank, args=(0, 1, _free_port(), q, "nccl"))
+    p.start()
+    rank, got = q.get(timeout=300)
+    p.join(timeout=120)
+    assert p.exitcode == 0 and rank == 0
+    assert np.array_equal(got, local)
 
 
 def test_sortlast_with_16bit_bricks_mask_window_and_streamed_cube(setup, orc):
