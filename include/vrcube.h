@@ -218,9 +218,8 @@ int vr_wavelet_store(vr_ctx *ctx, int cube_id, void *dst, size_t *bytes);
  * and take precedence over atlases for those frames.
  * Bit 5 (with bit 3; resident cubes of FP16 or BF16 bricks) makes the atlases pair atlases:
  * tile z holds, in 32-bit texels, the codes of slices z and z + 1 side by side, so one gather
- * returns a sample's 8 stencil codes (half the texels a frame moves through the texture unit,
- * twice the atlas memory); images are identical to the slice atlases'.  FP32 bricks keep slice
- * atlases.
+ * returns a sample's 8 stencil codes (one texture request per sample instead of two, twice the
+ * atlas memory); images are identical to the slice atlases'.  FP32 bricks keep slice atlases.
  * Mask 1..63 with bit 0 set (and bit 3 with bit 5).  Errors: VR_ERR_ARG (mask), VR_ERR_NOT_FOUND, VR_ERR_UNSUPPORTED
  * (streamed or compressed cube with a mask other than 1 or 9; atlas beyond the gather size,
  * raised by the rebuild, or for streamed cubes by the frame), VR_ERR_OOM, VR_ERR_CUDA. */
