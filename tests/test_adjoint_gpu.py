@@ -37,8 +37,8 @@ def _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau):
     return glut.cpu().numpy().astype(np.float64), gvox.cpu().numpy().astype(np.float64)
 
 
-# the table gradient accumulates in 8 shared-memory copies for small tables, 1 for 2048 entries;
-# an opacity above 1 (transmittance can turn negative) is followed as written
+# small tables and a 2048-entry one (the table gradient's per-CTA partial rows in L2 scale with
+# it); an opacity above 1 (transmittance can turn negative) is followed as written
 @pytest.mark.parametrize("seed,tau,layouts,nlut,over", [(0, 0.95, 1, 32, False), (1, 1.0, 1, 32, False),
                                                         (2, 0.9, 7, 32, False), (3, 0.9, 9, 32, False),
                                                         (4, 0.95, 1, 2048, False), (5, 0.95, 1, 32, True)])
@@ -61,6 +61,37 @@ def test_adjoint_matches_oracle_gradient(ctx, orc, seed, tau, layouts, nlut, ove
     assert np.abs(rl).max() > 0 and np.abs(rv).max() > 0
     assert np.abs(gl - rl).max() <= 2e-4 * np.abs(rl).max(), np.abs(gl - rl).max()
     assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max(), np.abs(gv - rv).max()
+    ctx.free_cube(cid)
+
+
+def test_adjoint_with_channel_mask_and_window_matches_oracle_gradient(ctx, orc):
+    """Disabled channels read as vmin and receive no voxel gradient; a render window clips the
+    rays (voxels outside it still feed the stencils at its faces): the GPU gradients follow the
+    oracle's with both set."""
+    import torch
+    rng, cube, lut, cam, cid = _setup(ctx, 11)
+    vr = (-3.0, 8.0)
+    step, tau = 0.5, 0.95
+    mask = (rng.uniform(size=cube.shape[0]) > 0.3).astype(np.uint8)
+    win = ((2, 3, 1), (21, 20, 22))
+    gout = rng.standard_normal((cam["W"] * cam["H"], 4))
+    try:
+        ctx.set_channel_mask(mask)
+        ctx.set_window(*win)
+        _, flags, _ = orc.render(cube, lut, vr, cam, step=step, tau=tau, brick=(8, 8, 8),
+                                 channels=mask, window=win)
+        gout[(flags & 9).astype(bool)] = 0.0
+        gl, gv = _gpu_grad(ctx, cid, cube, lut, vr, cam, gout, step, tau)
+    finally:
+        ctx.set_channel_mask(None)
+        ctx.set_window()
+    rl, rv = orc.render_grad(cube, lut, vr, cam, gout.astype(np.float32).astype(np.float64),
+                             step=step, tau=tau, brick=(8, 8, 8), channels=mask, window=win)
+    assert np.abs(rl).max() > 0 and np.abs(rv).max() > 0
+    assert np.abs(gl - rl).max() <= 2e-4 * np.abs(rl).max(), np.abs(gl - rl).max()
+    assert np.abs(gv - rv).max() <= 2e-4 * np.abs(rv).max(), np.abs(gv - rv).max()
+    off = mask == 0                       # disabled channels: no voxel gradient at all
+    assert np.all(gv[off] == 0.0)
     ctx.free_cube(cid)
 
 
