@@ -1291,14 +1291,18 @@ __device__ __forceinline__ void shift_face(float acc[8], bool up) {
 __device__ __forceinline__ void flush_voxel_grads(float *__restrict__ gvox, const float acc[8], unsigned mask,
                                                   int cx, int cy, int cz, const DrawBrick &b,
                                                   const FrameConsts &fc) {
-    const int gx[2] = {clampi(b.org[0] + cx, 0, fc.nx - 1), clampi(b.org[0] + cx + 1, 0, fc.nx - 1)};
-    const int gy[2] = {clampi(b.org[1] + cy, 0, fc.ny - 1), clampi(b.org[1] + cy + 1, 0, fc.ny - 1)};
-    const int gz[2] = {clampi(b.org[2] + cz, 0, fc.nz - 1), clampi(b.org[2] + cz + 1, 0, fc.nz - 1)};
-    const long long sy = fc.nx, sz = (long long)fc.nx * fc.ny;
+    const int x0 = clampi(b.org[0] + cx, 0, fc.nx - 1), x1 = clampi(b.org[0] + cx + 1, 0, fc.nx - 1);
+    const int y0 = clampi(b.org[1] + cy, 0, fc.ny - 1), y1 = clampi(b.org[1] + cy + 1, 0, fc.ny - 1);
+    const int z0 = clampi(b.org[2] + cz, 0, fc.nz - 1), z1 = clampi(b.org[2] + cz + 1, 0, fc.nz - 1);
+    // corner (0,0,0)'s address once, the other corners as 32-bit steps from it (a step along an
+    // axis is one voxel's stride, or 0 where the cube's border clamps both corners together)
+    float *p = gvox + ((long long)z0 * fc.ny + y0) * fc.nx + x0;
+    const int dx = x1 - x0, dy = (y1 - y0) * fc.nx;
+    const long long dz = (long long)(z1 - z0) * fc.nx * fc.ny;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
         if (((mask >> c) & 1u) && acc[c] != 0.0f)
-            atomicAdd(gvox + gz[c >> 2] * sz + gy[(c >> 1) & 1] * sy + gx[c & 1], acc[c]);
+            atomicAdd(p + ((c & 1) ? dx : 0) + ((c & 2) ? dy : 0) + ((c & 4) ? dz : 0), acc[c]);
 }
 
 // Adjoint ray cast (FP32 bricks).  Each (brick, pixel) segment is replayed front to back with
