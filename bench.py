@@ -689,10 +689,13 @@ def empty_space_leg(ctx, device, steps=16):
         res[name] = {"ms_per_frame": round(e0.elapsed_time(e1) / steps, 3),
                      "bricks_drawn_per_frame": round(st["bricks_drawn"] / steps, 1),
                      "Gsamples_per_s": round(st["samples"] / (e0.elapsed_time(e1) * 1e-3) / 1e9, 2)}
-    # the GASS-scale configuration itself: the ramp table, FP32 / FP16 / BF16 bricks
+    # the GASS-scale configuration itself: the ramp table, FP32 / FP16 / BF16 bricks through
+    # slice atlases, and the 16-bit bricks again through pair atlases (layout bit 5)
     frames = {}
     ctx.set_transfer_function(synth.ramp_lut(), *cfg["vrange"])
-    for storage in ("f32", "f16", "bf16"):
+    for storage, layouts, tag in (("f32", 9, "f32"), ("f16", 9, "f16"), ("bf16", 9, "bf16"),
+                                  ("f16", 41, "f16_pair_atlas"), ("bf16", 41, "bf16_pair_atlas")):
+        ctx.set_brick_layouts(cid, layouts)
         ctx.set_bricking(cid, cfg["brick"], 1, storage)
         for j in range(3):
             ctx.set_camera_dict(cams[j])
@@ -711,16 +714,16 @@ def empty_space_leg(ctx, device, steps=16):
         ms = e0.elapsed_time(e1) / steps
         alg = (st["brick_bytes_sampled"] + 16 * st["fragments"]) / max(st["timed_frames"], 1)
         rc_ms = st["ms_raycast"] / max(st["timed_frames"], 1)
-        frames[storage] = {"ms_per_frame": round(ms, 3),
+        frames[tag] = {"ms_per_frame": round(ms, 3),
                            "Gsamples_per_s": round(st["samples"] / (ms * steps * 1e-3) / 1e9, 2),
                            "raycast_GB_per_s_upper_bound": round(alg / (rc_ms * 1e-3) / 1e9, 1)}
         g = traffic_entry("k_raycast<f32,DVR>@GASS")
         if storage == "f32" and g:
             dram = g["traffic_over_algorithmic"] * alg / (rc_ms * 1e-3) / 1e9
-            frames[storage]["raycast_dram_GB_per_s"] = round(dram, 1)
-            frames[storage]["hbm_frac_of_measured"] = round(dram / peaks()[0], 4)
+            frames[tag]["raycast_dram_GB_per_s"] = round(dram, 1)
+            frames[tag]["hbm_frac_of_measured"] = round(dram / peaks()[0], 4)
     res["gass_frames"] = dict(frames, table=f"ramp over [{cfg['vrange'][0]}, {cfg['vrange'][1]}], "
-                                            f"step {cfg['step']}, slice atlases",
+                                            f"step {cfg['step']}, slice atlases (pair atlases where named)",
                               bytes="upper bound: stored bytes of every drawn brick / ray-cast time "
                                     "(segments stop early, so a drawn brick is not read whole); "
                                     "dram: that times the DRAM traffic / algorithmic bytes ratio of "
