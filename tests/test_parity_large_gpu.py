@@ -5,7 +5,8 @@ GASS-scale:   2048x2048x1600 (26.8 GB), 256^3 bricks, 1024^2 perspective orbit, 
               FP32 / FP16 / BF16 bricks, error against the FP64 oracle on 4096 sampled rays.
 Both keep the bench's brick layouts (slice atlases + the x-contiguous copy), so every frame
 here gathers from the atlases as the timed frames do; HIPASS also checks global termination
-with the occlusion leg's opaque table.
+with the occlusion leg's opaque table, and GASS's 16-bit frames are rendered again through pair
+atlases (the bench's `*_pair_atlas` frames), which must give the same frame bit for bit.
 The measured maximum errors are written as JSON to the file named by VR_LARGE_ERRORS, if set.
 """
 import json
@@ -36,7 +37,7 @@ def ctx():
     c.close()
 
 
-def _check_config(ctx, orc, cfg, cube_t, storages, views, n_rays, tag):
+def _check_config(ctx, orc, cfg, cube_t, storages, views, n_rays, tag, pair_storages=()):
     import torch
     cube = cube_t.cpu().numpy()
     cid = ctx.load_cube(cube_t)
@@ -80,6 +81,17 @@ def _check_config(ctx, orc, cfg, cube_t, storages, views, n_rays, tag):
                                           brick=cfg["brick"], pix=pix, term="global")
                 errg = compare_dvr(g[pix], refg, flg, cfg["tau"])
                 _record(f"{tag} f32 global-termination view{j}", {"max_abs_err": errg, "rays": int(len(pix))})
+        # 16-bit bricks through pair atlases (layout bit 5), as the bench times GASS-scale frames:
+        # the whole last frame equals the slice atlases' bit for bit
+        if storage in pair_storages:
+            ctx.set_brick_layouts(cid, 41)
+            ctx.set_bricking(cid, cfg["brick"], 1, storage)
+            ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
+            pimg = ctx.render_frame(cid).cpu().numpy().reshape(-1, 4)
+            ctx.set_brick_layouts(cid, 9)
+            same = bool(np.array_equal(pimg, img))
+            _record(f"{tag} {storage} pair-atlas frame view{views[-1]}", {"bit_equal": same})
+            assert same
     ctx.free_cube(cid)
 
 
@@ -92,4 +104,4 @@ def test_hipass_scale(ctx, orc):
 def test_gass_scale(ctx, orc):
     cfg = synth.GASS
     _check_config(ctx, orc, cfg, synth.gass_cube(device="cuda"), ["f32", "f16", "bf16"], [5],
-                  4096, "gass")
+                  4096, "gass", pair_storages=("f16", "bf16"))
