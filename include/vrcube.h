@@ -284,8 +284,10 @@ int vr_set_host_output_async(vr_ctx *ctx, int async);
  * returns after the frame has been copied into `out` (or once that copy is queued, see
  * vr_set_host_output_async).
  * Steps: per-brick rendering rectangles and culling (host), one ray-cast launch over all
- * (brick, 16x16 pixel tile) work items writing one premultiplied fragment per brick and pixel,
- * one compositing launch blending each pixel's fragments front to back (Section 2.5).
+ * (brick, 32x8 or 8x32 pixel tile of its rectangle) work items writing one premultiplied
+ * fragment per brick and pixel, one compositing launch blending each pixel's fragments front to
+ * back in 16x16 screen tiles (Section 2.5).  With VR_TERM_GLOBAL the two launches are one walk
+ * of every pixel's ray through the bricks (see vr_set_termination).
  * Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND, VR_ERR_STATE (no bricking, table or camera),
  * VR_ERR_OOM, VR_ERR_CUDA, VR_ERR_TIMEOUT (streamed bricks did not arrive in time). */
 int vr_render_frame(vr_ctx *ctx, int cube_id, float *out, int out_where, void *cuda_stream);
