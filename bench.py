@@ -311,10 +311,13 @@ def sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, steps, warmup):
                     "exchanged over NCCL, staged depth-ordered compositing, frame gathered on every rank"}
 
 
-def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8, counts_list=((2,), (4,), (8,))):
+def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8,
+                            counts_list=((2,), (4,), (2, 2), (8,), (2, 2, 2))):
     """Sort-last on one GPU, part by part (Sections 2.2, 2.5, 3): for N parts of a longest-axis cut
     (equal layer counts, and cuts balanced by the view's estimated cost) every part's sub-image
     of the same orbit views is rendered and timed alone (CUDA events around each part's frame),
+    for one cut into N slabs (key "N") and for the paper's nested cuts (Fig. 3: nodes, then each
+    node's GPUs, every level along its part's longest axis; key "2x2", "2x2x2"),
     then the staged composite of all parts is timed.  With one part per GPU the frame would take
     the slowest part plus a rank's share of the compositing plus the exchange (each rank sends
     and receives (N - 1)/N of a frame of (C, T) per stage, not timed here): the projection is
@@ -359,11 +362,12 @@ def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8, counts_list=(
                     ctx.set_partition(cid, counts, SL.digits(members[0], counts))
                     return ctx.composite_subimages(cid, level, stack, row0, final)
 
+                SL.composite_parts_local(subs, counts, blend)              # warm (scratch)
                 _, cms = timed(lambda: SL.composite_parts_local(subs, counts, blend))
                 proj.append(max(times) + cms / world)
                 imb.append(max(times) / (sum(times) / world))
                 comp_share.append(cms / world)
-            key = f"{world}_{'balanced' if balanced else 'equal'}"
+            key = f"{'x'.join(map(str, counts))}_{'balanced' if balanced else 'equal'}"
             res[key] = {"projected_ms_per_frame": round(float(np.mean(proj)), 4),
                         "speedup_vs_whole": round(res["whole_ms_per_frame"] / float(np.mean(proj)), 2),
                         "imbalance_slowest_over_mean": round(float(np.mean(imb)), 3),
