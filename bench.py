@@ -312,7 +312,7 @@ def sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, steps, warmup):
 
 
 def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8,
-                            counts_list=((2,), (4,), (2, 2), (8,), (2, 2, 2))):
+                            counts_list=((2,), (4,), (2, 2), (8,), (2, 2, 2)), fine_brick=128):
     """Sort-last on one GPU, part by part (Sections 2.2, 2.5, 3): for N parts of a longest-axis cut
     (equal layer counts, and cuts balanced by the view's estimated cost) every part's sub-image
     of the same orbit views is rendered and timed alone (CUDA events around each part's frame),
@@ -322,7 +322,8 @@ def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8,
     the slowest part plus a rank's share of the compositing plus the exchange (each rank sends
     and receives (N - 1)/N of a frame of (C, T) per stage, not timed here): the projection is
     that sum without the exchange, its speedup over the whole frame, and the parts' imbalance
-    (slowest / mean), the paper's limit on speedup."""
+    (slowest / mean), the paper's limit on speedup.  With fine_brick set, 4 and 8 parts are
+    projected again on bricks of that size (more layers to place the cuts between)."""
     import torch
     from paper_1008_0135_gb300 import sortlast as SL
     ctx.set_transfer_function(lut, *vr)
@@ -337,42 +338,54 @@ def sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr, views=8,
         torch.cuda.synchronize()
         return r, ev[0].elapsed_time(ev[1])
 
-    whole = []
-    for v in range(views):
-        ctx.set_camera_dict(cams[v * len(cams) // views])
-        ctx.render_frame(cid)                              # warm
-        whole.append(timed(lambda: ctx.render_frame(cid))[1])
-    res = {"whole_ms_per_frame": round(float(np.mean(whole)), 4), "views": views}
-    for counts in counts_list:
-        world = int(np.prod(counts))
-        for balanced in (False, True):
-            ctx.set_partition_balance(cid, balanced)
-            proj, imb, comp_share = [], [], []
-            for v in range(views):
-                ctx.set_camera_dict(cams[v * len(cams) // views])
-                subs, times = [], []
-                for r in range(world):
-                    ctx.set_partition(cid, counts, SL.digits(r, counts))
-                    ctx.render_subimage(cid)               # warm (and the cuts for this view)
-                    sub, ms = timed(lambda: ctx.render_subimage(cid))
-                    subs.append(sub)
-                    times.append(ms)
+    def project(counts_list):
+        whole = []
+        for v in range(views):
+            ctx.set_camera_dict(cams[v * len(cams) // views])
+            ctx.render_frame(cid)                              # warm
+            whole.append(timed(lambda: ctx.render_frame(cid))[1])
+        res = {"whole_ms_per_frame": round(float(np.mean(whole)), 4), "views": views}
+        for counts in counts_list:
+            world = int(np.prod(counts))
+            for balanced in (False, True):
+                ctx.set_partition_balance(cid, balanced)
+                proj, imb, comp_share = [], [], []
+                for v in range(views):
+                    ctx.set_camera_dict(cams[v * len(cams) // views])
+                    subs, times = [], []
+                    for r in range(world):
+                        ctx.set_partition(cid, counts, SL.digits(r, counts))
+                        ctx.render_subimage(cid)               # warm (and the cuts for this view)
+                        sub, ms = timed(lambda: ctx.render_subimage(cid))
+                        subs.append(sub)
+                        times.append(ms)
 
-                def blend(level, stack, row0, final, members):
-                    ctx.set_partition(cid, counts, SL.digits(members[0], counts))
-                    return ctx.composite_subimages(cid, level, stack, row0, final)
+                    def blend(level, stack, row0, final, members):
+                        ctx.set_partition(cid, counts, SL.digits(members[0], counts))
+                        return ctx.composite_subimages(cid, level, stack, row0, final)
 
-                SL.composite_parts_local(subs, counts, blend)              # warm (scratch)
-                _, cms = timed(lambda: SL.composite_parts_local(subs, counts, blend))
-                proj.append(max(times) + cms / world)
-                imb.append(max(times) / (sum(times) / world))
-                comp_share.append(cms / world)
-            key = f"{'x'.join(map(str, counts))}_{'balanced' if balanced else 'equal'}"
-            res[key] = {"projected_ms_per_frame": round(float(np.mean(proj)), 4),
-                        "speedup_vs_whole": round(res["whole_ms_per_frame"] / float(np.mean(proj)), 2),
-                        "imbalance_slowest_over_mean": round(float(np.mean(imb)), 3),
-                        "composite_ms_per_rank": round(float(np.mean(comp_share)), 4),
-                        "exchange_bytes_per_rank": int(cfg["W"] * cfg["H"] * 16 * (world - 1) / world)}
+                    SL.composite_parts_local(subs, counts, blend)              # warm (scratch)
+                    _, cms = timed(lambda: SL.composite_parts_local(subs, counts, blend))
+                    proj.append(max(times) + cms / world)
+                    imb.append(max(times) / (sum(times) / world))
+                    comp_share.append(cms / world)
+                key = f"{'x'.join(map(str, counts))}_{'balanced' if balanced else 'equal'}"
+                res[key] = {"projected_ms_per_frame": round(float(np.mean(proj)), 4),
+                            "speedup_vs_whole": round(res["whole_ms_per_frame"] / float(np.mean(proj)), 2),
+                            "imbalance_slowest_over_mean": round(float(np.mean(imb)), 3),
+                            "composite_ms_per_rank": round(float(np.mean(comp_share)), 4),
+                            "exchange_bytes_per_rank": int(cfg["W"] * cfg["H"] * 16 * (world - 1) / world)}
+        ctx.set_partition(cid)
+        ctx.set_partition_balance(cid, False)
+        return res
+
+    res = project(counts_list)
+    if fine_brick:
+        # the same frames with bricks of fine_brick^3: more brick layers per axis, so cuts (equal
+        # or balanced by the view's cost) can even the parts out; the cube is re-bricked after
+        ctx.set_bricking(cid, (fine_brick,) * 3, 1, "f32")
+        res[f"bricks_{fine_brick}"] = project(((4,), (8,)))
+        ctx.set_bricking(cid, cfg["brick"], 1, "f32")
     ctx.set_partition(cid)
     ctx.set_partition_balance(cid, False)
     return res
