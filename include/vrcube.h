@@ -311,7 +311,8 @@ int vr_set_partition(vr_ctx *ctx, int cube_id, int nlevels, const int *counts, c
  * layers crosses k/counts[L] of its total, a brick's cost being the samples a full bundle of
  * the frame's rays takes through it (its window-clipped core volume over a pixel's footprint
  * at its depth times the step; 0 when skipped as empty space or outside the frame; early
- * termination not modelled).  Balanced parts change with the camera, so every rank needs the
+ * termination not modelled; computed once per render state and shared by the part's frame and
+ * compositing calls).  Balanced parts change with the camera, so every rank needs the
  * whole cube (or the bricks any view can give it); the ranks agree on the cuts because they
  * compute them from the same camera, table and bricking.  The no-allocation renderer refuses
  * balanced partitions (VR_ERR_UNSUPPORTED).  Errors: VR_ERR_ARG, VR_ERR_NOT_FOUND. */

@@ -182,14 +182,18 @@ double brick_cost(const vr_ctx *c, const Cube *cb, size_t bi, const int *apre) {
 PartBox partition_box(const vr_ctx *c, const Cube *cb) {
     PartBox p{};
     for (int a = 0; a < 3; ++a) { p.lo[a] = 0; p.hi[a] = (int)cb->nb[a]; }
-    std::vector<double> cost;
     const bool balanced = cb->part_balance && c->cam_set && c->tf_set && cb->part_nlev > 0;
-    if (balanced) {
+    // the bricks' costs depend on the camera, table, parameters, window and bricking, not on the
+    // part: computed once per render state and reused by every rank's part and compositing stage
+    const uint64_t key = c->state_gen - c->part_gen;
+    if (balanced && (cb->cost_key != key || cb->cost_cache.size() != cb->tmpl.size())) {
         std::vector<int> apre;
         alpha_prefix(c, apre);
-        cost.resize(cb->tmpl.size());
-        for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) cost[bi] = brick_cost(c, cb, bi, apre.data());
+        cb->cost_cache.resize(cb->tmpl.size());
+        for (size_t bi = 0; bi < cb->tmpl.size(); ++bi) cb->cost_cache[bi] = brick_cost(c, cb, bi, apre.data());
+        cb->cost_key = key;
     }
+    const std::vector<double> &cost = cb->cost_cache;
     for (int L = 0; L < cb->part_nlev; ++L) {
         int axis = 0;
         int64_t best = -1;
@@ -1730,6 +1734,7 @@ int vr_set_partition(vr_ctx *c, int cube_id, int nlevels, const int *counts, con
         if (counts[L] < 1 || counts[L] > 65536 || index[L] < 0 || index[L] >= counts[L])
             return arg_fail("each level needs 1 <= counts <= 65536 and 0 <= index < counts");
     c->state_gen++;
+    c->part_gen++;                    // a new part: the bricks' estimated costs still hold
     cb->part_nlev = nlevels;
     for (int L = 0; L < nlevels; ++L) { cb->part_counts[L] = counts[L]; cb->part_index[L] = index[L]; }
     return VR_OK;
@@ -1740,7 +1745,7 @@ int vr_set_partition_balance(vr_ctx *c, int cube_id, int balanced) {
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
     if (balanced != 0 && balanced != 1) return arg_fail("balanced must be 0 or 1");
-    if (cb->part_balance != balanced) c->state_gen++;
+    if (cb->part_balance != balanced) { c->state_gen++; c->part_gen++; }
     cb->part_balance = balanced;
     return VR_OK;
 }

@@ -81,6 +81,10 @@ struct Cube {
     int part_counts[kMaxPartLevels] = {0};
     int part_index[kMaxPartLevels] = {0};
     int part_balance = 0;             // 1: cuts balanced by the current camera's estimated cost
+    // balanced cuts: every brick's estimated cost for the render state it was computed in
+    // (cost_key = the context's state_gen - part_gen then; partition calls change neither)
+    mutable std::vector<double> cost_cache;
+    mutable uint64_t cost_key = ~0ull;
 };
 
 // The part of a cube's brick grid that its partition selects: brick index ranges [lo, hi) per
@@ -162,6 +166,7 @@ struct vr_ctx {
     // that can change a frame bumps state_gen; every other write of d_frags clears frag_valid.
     // vr_render_backward reuses them instead of ray-casting the frame again.
     uint64_t state_gen = 0, frag_gen = 0;
+    uint64_t part_gen = 0;            // the state_gen bumps made by partition calls
     int frag_cube = -1;
     bool frag_valid = false;
 };

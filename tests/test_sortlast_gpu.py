@@ -134,6 +134,50 @@ def test_balanced_cuts_even_out_the_parts_work(setup):
     assert worst[True] < worst[False]
 
 
+def test_balanced_cuts_follow_the_render_state(setup):
+    """The bricks' estimated costs behind balanced cuts are kept per render state: after camera,
+    table and window changes, and between the parts' own calls, every part's box equals the one
+    a fresh context computes for the same state."""
+    ctx, cube, cid = setup
+    near = dict(view=synth.look_at((-25.0, 32.0, 20.0), (96.0, 32.0, 20.0)), proj=1,
+                param=math.radians(70.0), W=96, H=96)
+    far = dict(view=synth.look_at((121.0, 32.0, 20.0), (0.0, 32.0, 20.0)), proj=1,
+               param=math.radians(70.0), W=96, H=96)
+    states = [(near, synth.ramp_lut(alpha=0.05), None), (far, synth.ramp_lut(alpha=0.05), None),
+              (far, synth.random_lut(5, n=32, alpha_max=0.3), None),
+              (far, synth.random_lut(5, n=32, alpha_max=0.3), ((40, 0, 0), (96, 64, 40))),
+              (near, synth.ramp_lut(alpha=0.05), None)]
+
+    def boxes(c, k_cube, cam, lut, win):
+        c.set_camera_dict(cam)
+        c.set_transfer_function(lut, -3.0, 12.0)
+        c.set_render_params("dvr", 0.5, 1.0)
+        if win is None:
+            c.set_window()
+        else:
+            c.set_window(*win)
+        c.set_partition_balance(k_cube, True)
+        out = []
+        for k in range(3):
+            c.set_partition(k_cube, (3,), (k,))
+            out.append(c.partition(k_cube, 1)[:2])
+        c.set_partition(k_cube)
+        c.set_partition_balance(k_cube, False)
+        c.set_window()
+        return out
+
+    got = [boxes(ctx, cid, *st) for st in states]
+    assert got[0] != got[1]                               # the view moves the cuts
+    for st, g in zip(states, got):
+        fresh = gpu_ctx()
+        try:
+            fid = fresh.load_cube(cube)
+            fresh.set_bricking(fid, BRICK, 1, "f32")
+            assert boxes(fresh, fid, *st) == g
+        finally:
+            fresh.close()
+
+
 def test_subimage_keeps_transmittance_and_refuses_global_termination(setup):
     import paper_1008_0135_gb300 as P
     ctx, cube, cid = setup
