@@ -81,6 +81,42 @@ def test_mip_axis_aligned_is_column_max(ctx):
     ctx.free_cube(cid)
 
 
+def test_rays_and_samples_on_brick_faces(ctx, orc):
+    """Orthographic rays along z through integer x and y (every ray lies in voxel faces, and in
+    brick faces every 8 voxels) with samples on integer z (brick faces every 8 slices): every
+    lattice sample is owned by exactly one brick (the sample count equals the oracle's), DVR per
+    segment and with global termination matches the oracle, MIP bit for bit."""
+    cube = synth.pr1_cube(seed=6, n=32)[:20].copy()          # nz=20, ny=32, nx=32
+    nx, ny, nz = 32, 32, 20
+    c = np.array([nx / 2.0 - 0.5, ny / 2.0 - 0.5, nz / 2.0])
+    cam = dict(view=synth.look_at(c - np.array([0.0, 0.0, nz + 8.0]), c), proj=0, param=64.0,
+               W=64, H=64)                                       # pixel centres on integer x, y
+    o, _, _ = orc.rays(cam, (nx, ny, nz), step=0.5)
+    assert np.array_equal(o[:, :2], np.round(o[:, :2]))          # exactly, in FP32
+    assert (np.isin(o[:, 0], (8.0, 16.0, 24.0)) | np.isin(o[:, 1], (8.0, 16.0, 24.0))).sum() > 300
+    lut = synth.random_lut(23, n=40, alpha_max=0.4)
+    cid = ctx.load_cube(cube)
+    try:
+        for layouts in (1, 9):
+            ctx.set_brick_layouts(cid, layouts)
+            ctx.set_bricking(cid, (8, 8, 8), 1, "f32")
+            ctx.reset_stats()
+            m = render(ctx, cid, lut, (-3, 20), cam, mode="mip", step=0.5)
+            m32, _, ns = orc.render(cube, lut, (-3, 20), cam, mode="mip32", step=0.5, brick=(8, 8, 8))
+            assert ctx.stats()["samples"] == ns
+            assert np.array_equal(m, m32.astype(np.float32))
+            for scope, tau in (("segment", 1.0), ("segment", 0.9), ("global", 0.9)):
+                ctx.set_termination(scope)
+                g = render(ctx, cid, lut, (-3, 20), cam, step=0.5, tau=tau)
+                ref, flags, _ = orc.render(cube, lut, (-3, 20), cam, step=0.5, tau=tau, brick=(8, 8, 8),
+                                           term=scope)
+                compare_dvr(g, ref, flags, tau)
+            ctx.set_termination("segment")
+    finally:
+        ctx.set_termination("segment")
+        ctx.free_cube(cid)
+
+
 def test_bricked_equals_unbricked(ctx, pr1):
     cube, _ = pr1
     lut = synth.ramp_lut(alpha=0.4)
