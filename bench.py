@@ -66,7 +66,8 @@ class Dist:
         self.pg = None
         if self.world > 1:
             import torch.distributed as dist
-            dist.init_process_group("gloo")
+            import datetime
+            dist.init_process_group("gloo", timeout=datetime.timedelta(seconds=900))
             self.pg = dist
 
     def barrier(self):
@@ -290,7 +291,9 @@ def sortlast_leg(ctx, cid, cfg, cams, lut, vr, dist, steps, warmup):
     from paper_1008_0135_gb300.sortlast import SortLast
     ctx.set_transfer_function(lut, *vr)
     ctx.set_render_params("dvr", cfg["step"], cfg["tau"])
-    sl = SortLast(ctx, cid, (dist.world,), dist.rank, backend="nccl")
+    import datetime
+    # a rank that fails or stalls ends the others' collectives within two minutes
+    sl = SortLast(ctx, cid, (dist.world,), dist.rank, backend="nccl", timeout=datetime.timedelta(seconds=120))
     for w in range(warmup):
         ctx.set_camera_dict(cams[w % len(cams)])
         sl.render()

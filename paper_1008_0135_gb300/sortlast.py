@@ -72,9 +72,11 @@ class TorchExchange:
     """The collectives of a frame over torch.distributed: one process group per sibling set
     (created once, by every rank, in the same order) and the world group for the gather."""
 
-    def __init__(self, counts: Sequence[int], backend: str = None):
+    def __init__(self, counts: Sequence[int], backend: str = None, timeout=None):
         """backend: that of the groups this exchange creates ("nccl": CUDA tensors move
-        GPU to GPU; "gloo": host copies); None: the default group's."""
+        GPU to GPU; "gloo": host copies); None: the default group's.  timeout (a
+        datetime.timedelta, or None for the backend's default): how long a collective of these
+        groups waits for the other ranks before it fails."""
         import torch.distributed as dist
         self.dist = dist
         self.counts = list(counts)
@@ -85,7 +87,8 @@ class TorchExchange:
             raise ValueError(f"the partition has {world} parts for {dist.get_world_size()} ranks")
         backend = backend or dist.get_backend()
         self.host = backend == "gloo"                     # gloo moves host tensors
-        self.world_group = dist.new_group(list(range(world)), backend=backend)
+        kw = {"backend": backend} if timeout is None else {"backend": backend, "timeout": timeout}
+        self.world_group = dist.new_group(list(range(world)), **kw)
         self.groups: Dict[Tuple[int, Tuple[int, ...]], object] = {}
         for level in range(len(counts)):
             seen = set()
@@ -94,7 +97,7 @@ class TorchExchange:
                 if g in seen:
                     continue
                 seen.add(g)
-                self.groups[(level, g)] = dist.new_group(list(g), backend=backend) if len(g) > 1 else None
+                self.groups[(level, g)] = dist.new_group(list(g), **kw) if len(g) > 1 else None
 
     def _to(self, t):
         return t.cpu() if self.host else t
@@ -197,11 +200,11 @@ class SortLast:
     """Sort-last frames of one cube over the ranks of torch.distributed (one GPU each)."""
 
     def __init__(self, ctx, cube_id: int, counts: Sequence[int], rank: int, exchange=None,
-                 backend: str = None, balanced: bool = False):
+                 backend: str = None, balanced: bool = False, timeout=None):
         self.ctx, self.cube_id, self.counts, self.rank = ctx, cube_id, list(counts), rank
         ctx.set_partition(cube_id, self.counts, digits(rank, self.counts))
         ctx.set_partition_balance(cube_id, balanced)
-        self.exchange = exchange if exchange is not None else TorchExchange(self.counts, backend)
+        self.exchange = exchange if exchange is not None else TorchExchange(self.counts, backend, timeout)
 
     def render(self, stream=None):
         """The full frame ((H, W, 4) premultiplied RGBA, or (H, W) MIP) on every rank."""
