@@ -228,7 +228,9 @@ def _rank(rank, world, port, q, backend="gloo"):
         ctx.set_transfer_function(synth.random_lut(3, n=64, alpha_max=0.35), -3.0, 12.0)
         ctx.set_camera_dict(CAMS[2])
         ctx.set_render_params("dvr", 0.5, 0.99)
-        frame = SortLast(ctx, cid, (world,), rank, backend=backend).render().cpu().numpy()
+        # NCCL groups with the bench's bounded wait
+        tmo = timedelta(seconds=120) if backend == "nccl" else None
+        frame = SortLast(ctx, cid, (world,), rank, backend=backend, timeout=tmo).render().cpu().numpy()
     q.put((rank, frame))
     dist.barrier()
     dist.destroy_process_group()
