@@ -461,26 +461,27 @@ static int cache_size(vr_ctx *c, size_t slot_bytes) {
 // in parallel -- a voxel depends only on its coordinates, and a slab's source list keeps the
 // cells' order, so the values are those of one pass over the box -- and a 16-bit brick is then
 // encoded slab by slab with the exponent of its max |v| over all slabs.  `done` is set once
-// every slab has finished (or the first error is recorded in *err).
+// every slab has finished (or the first error is recorded in err).
 struct BrickJob {
     Cube *cb = nullptr;
     DrawBrick b{};
     void *dst = nullptr;
-    int *exp2 = nullptr;
-    std::string *err = nullptr;
+    int exp2 = 0;                      // the brick's scale exponent (16-bit storage)
+    std::string err;                   // the first error of a slab ("" if none)
     Workers *pool = nullptr;
     int nslab = 1;
     std::vector<float> tmp;            // FP32 values of a 16-bit brick
     std::vector<float> slab_max;
     std::atomic<int> left{0};
-    std::mutex mu;                     // guards *err
+    std::mutex mu;                     // guards err
     std::promise<void> done;
+    std::future<void> finished = done.get_future();
 
     size_t plane() const { return (size_t)b.dim[0] * b.dim[1]; }
     int z0(int i) const { return (int)((int64_t)b.dim[2] * i / nslab); }
     void fail_with(const char *what) {
         std::lock_guard<std::mutex> l(mu);
-        if (err->empty()) *err = what;
+        if (err.empty()) err = what;
     }
 };
 
@@ -503,16 +504,16 @@ static void job_generate(const std::shared_ptr<BrickJob> &j, int i) {
     bool failed;
     {
         std::lock_guard<std::mutex> l(j->mu);
-        failed = !j->err->empty();
+        failed = !j->err.empty();
     }
     if (j->cb->storage == VR_F32 || failed) {
-        *j->exp2 = 0;
+        j->exp2 = 0;
         j->done.set_value();
         return;
     }
     float m = 0.0f;
     for (float v : j->slab_max) m = std::max(m, v);
-    *j->exp2 = region_exponent(m, j->cb->storage);
+    j->exp2 = region_exponent(m, j->cb->storage);
     j->left.store(j->nslab);
     for (int k = 1; k < j->nslab; ++k) j->pool->submit([j, k] { job_encode(j, k); });
     job_encode(j, 0);
@@ -522,7 +523,7 @@ static void job_encode(const std::shared_ptr<BrickJob> &j, int i) {
     try {
         const int z0 = j->z0(i), z1 = j->z0(i + 1);
         const size_t off = (size_t)z0 * j->plane();
-        encode_codes(j->tmp.data() + off, (size_t)(z1 - z0) * j->plane(), j->cb->storage, *j->exp2,
+        encode_codes(j->tmp.data() + off, (size_t)(z1 - z0) * j->plane(), j->cb->storage, j->exp2,
                      static_cast<char *>(j->dst) + off * 2);
     } catch (const std::exception &e) {
         j->fail_with(e.what());
@@ -530,21 +531,20 @@ static void job_encode(const std::shared_ptr<BrickJob> &j, int i) {
     if (j->left.fetch_sub(1) == 1) j->done.set_value();
 }
 
-// Starts the production of brick `b` on the pool; the future completes when it is done.
-static std::future<void> produce_brick(Workers *pool, Cube *cb, const DrawBrick &b, void *dst, int *exp2,
-                                       std::string *err, bool inject) {
+// Starts the production of brick `b` on the pool.  The job (shared with the pool's tasks, so a
+// caller that stops waiting leaves nothing they write behind) holds the outcome: `finished`
+// completes once every slab is done, then `exp2` and `err` are final.
+static std::shared_ptr<BrickJob> produce_brick(Workers *pool, Cube *cb, const DrawBrick &b, void *dst,
+                                               bool inject) {
     auto j = std::make_shared<BrickJob>();
     j->cb = cb;
     j->b = b;
     j->dst = dst;
-    j->exp2 = exp2;
-    j->err = err;
     j->pool = pool;
-    std::future<void> f = j->done.get_future();
     if (inject) {                      // a failing brick source (host-side fault injection)
-        *err = "brick source failed (injected)";
+        j->err = "brick source failed (injected)";
         j->done.set_value();
-        return f;
+        return j;
     }
     j->nslab = std::max(1, std::min(pool->size(), b.dim[2]));
     if (cb->storage != VR_F32) {
@@ -553,7 +553,7 @@ static std::future<void> produce_brick(Workers *pool, Cube *cb, const DrawBrick 
     }
     j->left.store(j->nslab);
     for (int i = 0; i < j->nslab; ++i) pool->submit([j, i] { job_generate(j, i); });
-    return f;
+    return j;
 }
 
 // Slice atlases of cache slots (streamed and compressed cubes whose layout mask has bit 3):
@@ -753,10 +753,8 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
     }
     // produce in parallel, at most one staging buffer per brick in flight
     const size_t nstage = k->stage.size();
-    std::vector<std::future<void>> fut(misses.size());
-    std::vector<int> exps(misses.size(), 0);
+    std::vector<std::shared_ptr<BrickJob>> jobs(misses.size());
     std::vector<size_t> st_of(misses.size());
-    std::vector<std::string> errors(misses.size());
     size_t submitted = 0, issued = 0;
     auto submit = [&](size_t m) -> int {
         const size_t si = (k->stage_next++) % nstage;
@@ -770,12 +768,10 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         st_of[m] = si;
         const DrawBrick brick = db[misses[m].first];
         void *dst = sg.host;
-        int *ep = &exps[m];
-        std::string *err = &errors[m];
         const bool inject = c->fault_kind == 1 && k->generated == c->fault_after;
         k->generated++;
         try {
-            fut[m] = produce_brick(k->workers, cb, brick, dst, ep, err, inject);
+            jobs[m] = produce_brick(k->workers, cb, brick, dst, inject);
         } catch (const std::exception &e) {       // the job's buffers could not be had
             return fail(VR_ERR_OOM, e.what());
         }
@@ -785,29 +781,36 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
         while (submitted < misses.size() && submitted < issued + nstage && rc == VR_OK) rc = submit(submitted++);
         if (rc != VR_OK) break;
         const size_t m = issued;
-        if (fut[m].wait_for(std::chrono::duration<double>(kWaitSeconds)) != std::future_status::ready) {
+        BrickJob &job = *jobs[m];
+        if (job.finished.wait_for(std::chrono::duration<double>(kWaitSeconds)) != std::future_status::ready) {
             rc = fail(VR_ERR_TIMEOUT, "brick production did not finish within its time bound");
             break;
         }
-        fut[m].get();
-        if (!errors[m].empty()) {
-            rc = fail(VR_ERR_IO, errors[m]);
+        job.finished.get();
+        if (!job.err.empty()) {
+            rc = fail(VR_ERR_IO, job.err);
             break;
         }
         const int si = misses[m].second;
         Slot &s = k->slots[si];
         const DrawBrick &b = db[misses[m].first];
         Staging &sg = k->stage[st_of[m]];
-        if (s.used) CK(cudaStreamWaitEvent(k->copy, s.last_use, 0));
-        CK(cudaMemcpyAsync(k->d_base + (size_t)si * k->slot_bytes, sg.host, (size_t)b.bytes,
-                           cudaMemcpyHostToDevice, k->copy));
-        CK(cudaEventRecord(sg.done, k->copy));
+        // (errors leave through the loop's end, which lets the producers still running finish)
+        cudaError_t ce = s.used ? cudaStreamWaitEvent(k->copy, s.last_use, 0) : cudaSuccess;
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(k->d_base + (size_t)si * k->slot_bytes, sg.host, (size_t)b.bytes,
+                                 cudaMemcpyHostToDevice, k->copy);
+        if (ce == cudaSuccess) ce = cudaEventRecord(sg.done, k->copy);
+        if (ce != cudaSuccess) {
+            rc = cuda_fail(ce, "brick copy to the cache");
+            break;
+        }
         sg.pending = true;
         s.cube = cb->id;
-        s.exp2 = exps[m];
+        s.exp2 = job.exp2;
         k->where[key_of(cb->id, s.brick)] = si;
         db[misses[m].first].data_off = (long long)((size_t)si * k->slot_bytes / esz);
-        db[misses[m].first].exp2 = exps[m];
+        db[misses[m].first].exp2 = job.exp2;
         db[misses[m].first].atlas = 0ull;
         k->misses++;
         k->bytes += b.bytes;
@@ -827,7 +830,8 @@ static int make_resident(vr_ctx *c, Cube *cb, std::vector<DrawBrick> &db, size_t
     if (rc != VR_OK) {
         // let submitted producers finish (they write into staging we own), drop unfilled slots
         for (size_t m = 0; m < submitted; ++m)
-            if (fut[m].valid()) fut[m].wait_for(std::chrono::duration<double>(kWaitSeconds));
+            if (jobs[m] && jobs[m]->finished.valid())   // (not yet taken by get())
+                jobs[m]->finished.wait_for(std::chrono::duration<double>(kWaitSeconds));
         for (size_t m = issued; m < misses.size(); ++m) {
             Slot &s = k->slots[misses[m].second];
             s.cube = -1;
