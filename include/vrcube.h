@@ -12,7 +12,9 @@
  *
  * Conventions shared by every call
  *   - Return value: VR_OK (0) on success, a negative VR_ERR_* status otherwise.  A failed call
- *     leaves the context usable; vr_error_string() names the status.
+ *     leaves the context usable; vr_error_string() names the status.  No C++ exception leaves
+ *     the library: a host memory allocation that fails inside any call returns VR_ERR_OOM, any
+ *     other host-side exception VR_ERR_STATE (vr_last_error_message() gives its text).
  *   - Ownership: the caller owns every buffer it passes.  The library copies voxels, tables and
  *     camera parameters into its own storage before returning and never keeps caller pointers.
  *   - Geometry: a cube of nx*ny*nz voxels is stored x fastest: index = x + nx*(y + ny*z).

@@ -1092,7 +1092,11 @@ const char *vr_error_string(int status) {
 
 const char *vr_last_error_message(void) { return g_last_error.c_str(); }
 
+static int vr_create_body(vr_ctx **out, int device, size_t cache_bytes);
 int vr_create(vr_ctx **out, int device, size_t cache_bytes) {
+    return abi_guard([&] { return vr_create_body(out, device, cache_bytes); });
+}
+static int vr_create_body(vr_ctx **out, int device, size_t cache_bytes) {
     if (!out) return arg_fail("null out");
     *out = nullptr;
     int ndev = 0;
@@ -1118,7 +1122,14 @@ int vr_create(vr_ctx **out, int device, size_t cache_bytes) {
     return VR_OK;
 }
 
+static void vr_destroy_body(vr_ctx *c);
 void vr_destroy(vr_ctx *c) {
+    try {
+        vr_destroy_body(c);
+    } catch (...) {
+    }
+}
+static void vr_destroy_body(vr_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
@@ -1142,7 +1153,13 @@ void vr_destroy(vr_ctx *c) {
     delete c;
 }
 
+static int vr_load_cube_body(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz, int where,
+                 const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id);
 int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz, int where,
+                 const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id) {
+    return abi_guard([&] { return vr_load_cube_body(c, voxels, dtype, nx, ny, nz, where, sub_origin, sub_extent, cube_id); });
+}
+static int vr_load_cube_body(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t ny, int64_t nz, int where,
                  const int64_t *sub_origin, const int64_t *sub_extent, int *cube_id) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !voxels || !cube_id) return arg_fail("null argument");
@@ -1192,7 +1209,11 @@ int vr_load_cube(vr_ctx *c, const void *voxels, int dtype, int64_t nx, int64_t n
     return VR_OK;
 }
 
+static int vr_load_cube_procedural_body(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int *cube_id);
 int vr_load_cube_procedural(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int *cube_id) {
+    return abi_guard([&] { return vr_load_cube_procedural_body(c, seed, nx, ny, nz, cube_id); });
+}
+static int vr_load_cube_procedural_body(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t nz, int *cube_id) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !cube_id) return arg_fail("null argument");
     if (nx <= 0 || ny <= 0 || nz <= 0) return arg_fail("non-positive size");
@@ -1209,14 +1230,22 @@ int vr_load_cube_procedural(vr_ctx *c, uint64_t seed, int64_t nx, int64_t ny, in
     return VR_OK;
 }
 
+static int vr_set_fault_injection_body(vr_ctx *c, int kind, int64_t after);
 int vr_set_fault_injection(vr_ctx *c, int kind, int64_t after) {
+    return abi_guard([&] { return vr_set_fault_injection_body(c, kind, after); });
+}
+static int vr_set_fault_injection_body(vr_ctx *c, int kind, int64_t after) {
     if (!c || kind < 0 || kind > 3) return arg_fail("bad fault injection");
     c->fault_kind = kind;
     c->fault_after = after;
     return VR_OK;
 }
 
+static int vr_update_cube_body(vr_ctx *c, int cube_id, const void *voxels, int where, void *stream);
 int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *stream) {
+    return abi_guard([&] { return vr_update_cube_body(c, cube_id, voxels, where, stream); });
+}
+static int vr_update_cube_body(vr_ctx *c, int cube_id, const void *voxels, int where, void *stream) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c || !voxels) return arg_fail("null argument");
     if (where != VR_HOST && where != VR_DEVICE) return arg_fail("bad location");
@@ -1234,7 +1263,11 @@ int vr_update_cube(vr_ctx *c, int cube_id, const void *voxels, int where, void *
     return VR_OK;
 }
 
+static int vr_free_cube_body(vr_ctx *c, int cube_id);
 int vr_free_cube(vr_ctx *c, int cube_id) {
+    return abi_guard([&] { return vr_free_cube_body(c, cube_id); });
+}
+static int vr_free_cube_body(vr_ctx *c, int cube_id) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
@@ -1247,7 +1280,11 @@ int vr_free_cube(vr_ctx *c, int cube_id) {
     return VR_OK;
 }
 
+static int vr_compute_minmax_body(vr_ctx *c, int cube_id, float *vmin, float *vmax);
 int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
+    return abi_guard([&] { return vr_compute_minmax_body(c, cube_id, vmin, vmax); });
+}
+static int vr_compute_minmax_body(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
     if (!c || !vmin || !vmax) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1271,7 +1308,11 @@ int vr_compute_minmax(vr_ctx *c, int cube_id, float *vmin, float *vmax) {
     return VR_OK;
 }
 
+static int vr_set_bricking_body(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, int storage);
 int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, int storage) {
+    return abi_guard([&] { return vr_set_bricking_body(c, cube_id, bx, by, bz, ghost, storage); });
+}
+static int vr_set_bricking_body(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, int storage) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
@@ -1368,7 +1409,11 @@ int vr_set_bricking(vr_ctx *c, int cube_id, int bx, int by, int bz, int ghost, i
     return VR_OK;
 }
 
+static int vr_compress_cube_body(vr_ctx *c, int cube_id);
 int vr_compress_cube(vr_ctx *c, int cube_id) {
+    return abi_guard([&] { return vr_compress_cube_body(c, cube_id); });
+}
+static int vr_compress_cube_body(vr_ctx *c, int cube_id) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
@@ -1413,7 +1458,11 @@ int vr_compress_cube(vr_ctx *c, int cube_id) {
     return vr_set_bricking(c, cube_id, cb->B[0], cb->B[1], cb->B[2], cb->ghost, VR_F32);
 }
 
+static int vr_wavelet_store_body(vr_ctx *c, int cube_id, void *dst, size_t *bytes);
 int vr_wavelet_store(vr_ctx *c, int cube_id, void *dst, size_t *bytes) {
+    return abi_guard([&] { return vr_wavelet_store_body(c, cube_id, dst, bytes); });
+}
+static int vr_wavelet_store_body(vr_ctx *c, int cube_id, void *dst, size_t *bytes) {
     if (!c || !bytes) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1430,7 +1479,11 @@ int vr_wavelet_store(vr_ctx *c, int cube_id, void *dst, size_t *bytes) {
     return VR_OK;
 }
 
+static int vr_set_termination_body(vr_ctx *c, int mode);
 int vr_set_termination(vr_ctx *c, int mode) {
+    return abi_guard([&] { return vr_set_termination_body(c, mode); });
+}
+static int vr_set_termination_body(vr_ctx *c, int mode) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (mode != VR_TERM_SEGMENT && mode != VR_TERM_GLOBAL) return arg_fail("termination must be VR_TERM_SEGMENT or VR_TERM_GLOBAL");
@@ -1438,14 +1491,22 @@ int vr_set_termination(vr_ctx *c, int mode) {
     return VR_OK;
 }
 
+static int vr_set_host_output_async_body(vr_ctx *c, int async);
 int vr_set_host_output_async(vr_ctx *c, int async) {
+    return abi_guard([&] { return vr_set_host_output_async_body(c, async); });
+}
+static int vr_set_host_output_async_body(vr_ctx *c, int async) {
     if (!c) return arg_fail("null ctx");
     if (async != 0 && async != 1) return arg_fail("async must be 0 or 1");
     c->async_host_out = async != 0;
     return VR_OK;
 }
 
+static int vr_set_brick_layouts_body(vr_ctx *c, int cube_id, int mask);
 int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
+    return abi_guard([&] { return vr_set_brick_layouts_body(c, cube_id, mask); });
+}
+static int vr_set_brick_layouts_body(vr_ctx *c, int cube_id, int mask) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
@@ -1469,7 +1530,11 @@ int vr_set_brick_layouts(vr_ctx *c, int cube_id, int mask) {
 // The table, camera and parameter setters count a change of the frame (state_gen, which the
 // gradient calls compare before reusing a frame's fragments) only when the value changes:
 // setting the same table, camera or parameters again leaves the last frame's fragments valid.
+static int vr_set_transfer_function_body(vr_ctx *c, const float *rgba, int n, float vmin, float vmax);
 int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
+    return abi_guard([&] { return vr_set_transfer_function_body(c, rgba, n, vmin, vmax); });
+}
+static int vr_set_transfer_function_body(vr_ctx *c, const float *rgba, int n, float vmin, float vmax) {
     if (!c || !rgba) return arg_fail("null argument");
     if (n < 2 || n > kMaxLut) return arg_fail("table size must be 2..4096");
     if (!(vmax > vmin) || !std::isfinite(vmin) || !std::isfinite(vmax)) return arg_fail("need vmax > vmin");
@@ -1487,7 +1552,11 @@ int vr_set_transfer_function(vr_ctx *c, const float *rgba, int n, float vmin, fl
     return VR_OK;
 }
 
+static int vr_set_camera_body(vr_ctx *c, const float view[16], int proj, float param, int width, int height);
 int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int width, int height) {
+    return abi_guard([&] { return vr_set_camera_body(c, view, proj, param, width, height); });
+}
+static int vr_set_camera_body(vr_ctx *c, const float view[16], int proj, float param, int width, int height) {
     if (!c || !view) return arg_fail("null argument");
     Cam cam;
     const int rc = make_cam(view, proj, param, width, height, cam);
@@ -1499,7 +1568,11 @@ int vr_set_camera(vr_ctx *c, const float view[16], int proj, float param, int wi
     return VR_OK;
 }
 
+static int vr_set_render_params_body(vr_ctx *c, int mode, float step, float tau);
 int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
+    return abi_guard([&] { return vr_set_render_params_body(c, mode, step, tau); });
+}
+static int vr_set_render_params_body(vr_ctx *c, int mode, float step, float tau) {
     if (!c) return arg_fail("null ctx");
     if (mode != VR_DVR && mode != VR_MIP) return arg_fail("bad mode");
     if (!(step > 0.0f) || !std::isfinite(step)) return arg_fail("step must be > 0");
@@ -1512,7 +1585,11 @@ int vr_set_render_params(vr_ctx *c, int mode, float step, float tau) {
     return VR_OK;
 }
 
+static int vr_set_channel_mask_body(vr_ctx *c, const unsigned char *mask, int64_t n);
 int vr_set_channel_mask(vr_ctx *c, const unsigned char *mask, int64_t n) {
+    return abi_guard([&] { return vr_set_channel_mask_body(c, mask, n); });
+}
+static int vr_set_channel_mask_body(vr_ctx *c, const unsigned char *mask, int64_t n) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (!mask || n == 0) {
@@ -1525,7 +1602,11 @@ int vr_set_channel_mask(vr_ctx *c, const unsigned char *mask, int64_t n) {
     return VR_OK;
 }
 
+static int vr_set_window_body(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]);
 int vr_set_window(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]) {
+    return abi_guard([&] { return vr_set_window_body(c, lo, hi); });
+}
+static int vr_set_window_body(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     if (!lo || !hi) {
@@ -1539,13 +1620,21 @@ int vr_set_window(vr_ctx *c, const int64_t lo[3], const int64_t hi[3]) {
     return VR_OK;
 }
 
+static int vr_set_timing_body(vr_ctx *c, int enable);
 int vr_set_timing(vr_ctx *c, int enable) {
+    return abi_guard([&] { return vr_set_timing_body(c, enable); });
+}
+static int vr_set_timing_body(vr_ctx *c, int enable) {
     if (!c) return arg_fail("null ctx");
     c->timing = enable != 0;
     return VR_OK;
 }
 
+static int vr_set_full_rect_body(vr_ctx *c, int full);
 int vr_set_full_rect(vr_ctx *c, int full) {
+    return abi_guard([&] { return vr_set_full_rect_body(c, full); });
+}
+static int vr_set_full_rect_body(vr_ctx *c, int full) {
     if (c) c->state_gen++;             // may change what a frame draws
     if (!c) return arg_fail("null ctx");
     c->full_rect = full != 0;
@@ -1713,7 +1802,11 @@ __attribute__((visibility("hidden"))) int render_frame_impl(vr_ctx *c, Cube *cb,
 
 extern "C" {
 
+static int vr_render_frame_body(vr_ctx *c, int cube_id, float *out, int out_where, void *stream);
 int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
+    return abi_guard([&] { return vr_render_frame_body(c, cube_id, out, out_where, stream); });
+}
+static int vr_render_frame_body(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
     if (!c || !out) return arg_fail("null argument");
     if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
     Cube *cb = find_cube(c, cube_id);
@@ -1724,7 +1817,11 @@ int vr_render_frame(vr_ctx *c, int cube_id, float *out, int out_where, void *str
     return render_frame_impl(c, cb, out, out_where, static_cast<cudaStream_t>(stream));
 }
 
+static int vr_set_partition_body(vr_ctx *c, int cube_id, int nlevels, const int *counts, const int *index);
 int vr_set_partition(vr_ctx *c, int cube_id, int nlevels, const int *counts, const int *index) {
+    return abi_guard([&] { return vr_set_partition_body(c, cube_id, nlevels, counts, index); });
+}
+static int vr_set_partition_body(vr_ctx *c, int cube_id, int nlevels, const int *counts, const int *index) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1740,7 +1837,11 @@ int vr_set_partition(vr_ctx *c, int cube_id, int nlevels, const int *counts, con
     return VR_OK;
 }
 
+static int vr_set_partition_balance_body(vr_ctx *c, int cube_id, int balanced);
 int vr_set_partition_balance(vr_ctx *c, int cube_id, int balanced) {
+    return abi_guard([&] { return vr_set_partition_balance_body(c, cube_id, balanced); });
+}
+static int vr_set_partition_balance_body(vr_ctx *c, int cube_id, int balanced) {
     if (!c) return arg_fail("null ctx");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1750,7 +1851,11 @@ int vr_set_partition_balance(vr_ctx *c, int cube_id, int balanced) {
     return VR_OK;
 }
 
+static int vr_get_partition_body(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes);
 int vr_get_partition(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes) {
+    return abi_guard([&] { return vr_get_partition_body(c, cube_id, lo, hi, axes); });
+}
+static int vr_get_partition_body(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes) {
     if (!c || !lo || !hi) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1762,7 +1867,11 @@ int vr_get_partition(vr_ctx *c, int cube_id, int lo[3], int hi[3], int *axes) {
     return VR_OK;
 }
 
+static int vr_render_subimage_body(vr_ctx *c, int cube_id, float *out, int out_where, void *stream);
 int vr_render_subimage(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
+    return abi_guard([&] { return vr_render_subimage_body(c, cube_id, out, out_where, stream); });
+}
+static int vr_render_subimage_body(vr_ctx *c, int cube_id, float *out, int out_where, void *stream) {
     if (!c || !out) return arg_fail("null argument");
     if (out_where != VR_HOST && out_where != VR_DEVICE) return arg_fail("bad output location");
     Cube *cb = find_cube(c, cube_id);
@@ -1778,7 +1887,13 @@ int vr_render_subimage(vr_ctx *c, int cube_id, float *out, int out_where, void *
     return rc;
 }
 
+static int vr_composite_subimages_body(vr_ctx *c, int cube_id, int level, int n, const float *subs, int row0, int rows,
+                           int final_, float *out, void *stream);
 int vr_composite_subimages(vr_ctx *c, int cube_id, int level, int n, const float *subs, int row0, int rows,
+                           int final_, float *out, void *stream) {
+    return abi_guard([&] { return vr_composite_subimages_body(c, cube_id, level, n, subs, row0, rows, final_, out, stream); });
+}
+static int vr_composite_subimages_body(vr_ctx *c, int cube_id, int level, int n, const float *subs, int row0, int rows,
                            int final_, float *out, void *stream) {
     if (!c || !subs || !out) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
@@ -1802,7 +1917,13 @@ int vr_composite_subimages(vr_ctx *c, int cube_id, int level, int n, const float
     return VR_OK;
 }
 
+static int vr_render_backward_body(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,
+                       void *stream);
 int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,
+                       void *stream) {
+    return abi_guard([&] { return vr_render_backward_body(c, cube_id, grad_out, grad_lut, grad_voxels, stream); });
+}
+static int vr_render_backward_body(vr_ctx *c, int cube_id, const float *grad_out, float *grad_lut, float *grad_voxels,
                        void *stream) {
     if (!c || !grad_out || !grad_lut) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
@@ -1814,7 +1935,13 @@ int vr_render_backward(vr_ctx *c, int cube_id, const float *grad_out, float *gra
     return backward_view(c, cb, grad_out, grad_lut, nullptr, false, grad_voxels, static_cast<cudaStream_t>(stream));
 }
 
+static int vr_render_backward_views_body(vr_ctx *c, int cube_id, int n_views, const vr_view *views, const float *grad_out,
+                             float *grad_lut, float *grad_voxels, void *stream);
 int vr_render_backward_views(vr_ctx *c, int cube_id, int n_views, const vr_view *views, const float *grad_out,
+                             float *grad_lut, float *grad_voxels, void *stream) {
+    return abi_guard([&] { return vr_render_backward_views_body(c, cube_id, n_views, views, grad_out, grad_lut, grad_voxels, stream); });
+}
+static int vr_render_backward_views_body(vr_ctx *c, int cube_id, int n_views, const vr_view *views, const float *grad_out,
                              float *grad_lut, float *grad_voxels, void *stream) {
     if (!c || !views || !grad_out || !grad_lut) return arg_fail("null argument");
     if (n_views < 1) return arg_fail("n_views must be >= 1");
@@ -1849,7 +1976,11 @@ int vr_render_backward_views(vr_ctx *c, int cube_id, int n_views, const vr_view 
     return VR_OK;
 }
 
+static int vr_get_stats_body(vr_ctx *c, vr_stats *st);
 int vr_get_stats(vr_ctx *c, vr_stats *st) {
+    return abi_guard([&] { return vr_get_stats_body(c, st); });
+}
+static int vr_get_stats_body(vr_ctx *c, vr_stats *st) {
     if (!c || !st) return arg_fail("null argument");
     int rc = set_dev(c);
     if (rc) return rc;
@@ -1873,7 +2004,11 @@ int vr_get_stats(vr_ctx *c, vr_stats *st) {
     return VR_OK;
 }
 
+static int vr_reset_stats_body(vr_ctx *c);
 int vr_reset_stats(vr_ctx *c) {
+    return abi_guard([&] { return vr_reset_stats_body(c); });
+}
+static int vr_reset_stats_body(vr_ctx *c) {
     if (!c) return arg_fail("null ctx");
     int rc = set_dev(c);
     if (rc) return rc;
@@ -1886,7 +2021,11 @@ int vr_reset_stats(vr_ctx *c) {
     return VR_OK;
 }
 
+static int vr_get_brick_grid_body(vr_ctx *c, int cube_id, int64_t nbricks[3], int *storage);
 int vr_get_brick_grid(vr_ctx *c, int cube_id, int64_t nbricks[3], int *storage) {
+    return abi_guard([&] { return vr_get_brick_grid_body(c, cube_id, nbricks, storage); });
+}
+static int vr_get_brick_grid_body(vr_ctx *c, int cube_id, int64_t nbricks[3], int *storage) {
     if (!c || !nbricks || !storage) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1896,7 +2035,11 @@ int vr_get_brick_grid(vr_ctx *c, int cube_id, int64_t nbricks[3], int *storage) 
     return VR_OK;
 }
 
+static int vr_get_brick_body(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2, void *data);
 int vr_get_brick(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2, void *data) {
+    return abi_guard([&] { return vr_get_brick_body(c, cube_id, brick, dims, org, exp2, data); });
+}
+static int vr_get_brick_body(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3], int *exp2, void *data) {
     if (!c || !dims || !org || !exp2) return arg_fail("null argument");
     Cube *cb = find_cube(c, cube_id);
     if (!cb) return VR_ERR_NOT_FOUND;
@@ -1916,7 +2059,11 @@ int vr_get_brick(vr_ctx *c, int cube_id, int64_t brick, int dims[3], int org[3],
 }
 
 // The no-allocation variant of vr_render_frame (see include/vrcube.h).
+static int vr_render_frame_noalloc_body(vr_ctx *c, int cube_id, float *out, void *stream);
 int vr_render_frame_noalloc(vr_ctx *c, int cube_id, float *out, void *stream) {
+    return abi_guard([&] { return vr_render_frame_noalloc_body(c, cube_id, out, stream); });
+}
+static int vr_render_frame_noalloc_body(vr_ctx *c, int cube_id, float *out, void *stream) {
     if (!c || !out) return arg_fail("null argument");
     if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return arg_fail("out must be 16-byte aligned device memory");
     Cube *cb = find_cube(c, cube_id);

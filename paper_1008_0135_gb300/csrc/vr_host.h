@@ -6,6 +6,8 @@
 
 #include <map>
 #include <string>
+#include <new>
+#include <stdexcept>
 #include <vector>
 
 #include "vr_internal.cuh"
@@ -29,6 +31,31 @@ inline int arg_fail(const char *what) {
 inline int fail(int status, const std::string &what) {
     g_last_error = what;
     return status;
+}
+
+// No C++ exception crosses the C ABI: every entry point runs its body through abi_guard, which
+// turns a host allocation failure into VR_ERR_OOM and any other host-side exception into
+// VR_ERR_STATE (vr_last_error_message gives its text).
+inline int abi_fail(int status, const char *what) noexcept {
+    try {
+        g_last_error = what;
+    } catch (...) {
+    }
+    return status;
+}
+template <class F>
+inline int abi_guard(F &&body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return abi_fail(VR_ERR_OOM, "host memory allocation failed");
+    } catch (const std::length_error &) {
+        return abi_fail(VR_ERR_OOM, "host allocation size out of range");
+    } catch (const std::exception &e) {
+        return abi_fail(VR_ERR_STATE, e.what());
+    } catch (...) {
+        return abi_fail(VR_ERR_STATE, "unexpected host-side exception");
+    }
 }
 
 #define CK(call)                                            \

@@ -339,7 +339,13 @@ struct vr_server {
 };
 
 #pragma GCC visibility push(default)
+static int vr_serve_body(vr_ctx *c, const vr_request *reqs, int n, const vr_serve_config *cfg,
+                        vr_request_result *res, vr_serve_summary *sum);
 extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve_config *cfg,
+                        vr_request_result *res, vr_serve_summary *sum) {
+    return abi_guard([&] { return vr_serve_body(c, reqs, n, cfg, res, sum); });
+}
+static int vr_serve_body(vr_ctx *c, const vr_request *reqs, int n, const vr_serve_config *cfg,
                         vr_request_result *res, vr_serve_summary *sum) {
     if (!c || (!reqs && n > 0) || !cfg || (!res && n > 0)) return arg_fail("null argument");
     if (n < 0 || cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
@@ -379,7 +385,11 @@ extern "C" int vr_serve(vr_ctx *c, const vr_request *reqs, int n, const vr_serve
     return core.failed ? VR_ERR_STATE : VR_OK;
 }
 
+static int vr_serve_open_body(vr_ctx *c, const vr_serve_config *cfg, vr_server **out);
 extern "C" int vr_serve_open(vr_ctx *c, const vr_serve_config *cfg, vr_server **out) {
+    return abi_guard([&] { return vr_serve_open_body(c, cfg, out); });
+}
+static int vr_serve_open_body(vr_ctx *c, const vr_serve_config *cfg, vr_server **out) {
     if (!c || !cfg || !out) return arg_fail("null argument");
     if (cfg->max_inflight < 1 || cfg->max_inflight > 64) return arg_fail("max_inflight must be 1..64");
     *out = nullptr;
@@ -404,7 +414,11 @@ extern "C" int vr_serve_open(vr_ctx *c, const vr_serve_config *cfg, vr_server **
     return VR_OK;
 }
 
+static int vr_serve_submit_body(vr_server *s, const vr_request *req, int64_t *ticket);
 extern "C" int vr_serve_submit(vr_server *s, const vr_request *req, int64_t *ticket) {
+    return abi_guard([&] { return vr_serve_submit_body(s, req, ticket); });
+}
+static int vr_serve_submit_body(vr_server *s, const vr_request *req, int64_t *ticket) {
     if (!s || !req || !ticket) return arg_fail("null argument");
     try {
         std::unique_ptr<Req> r(new Req());
@@ -425,7 +439,13 @@ extern "C" int vr_serve_submit(vr_server *s, const vr_request *req, int64_t *tic
     }
 }
 
+static int vr_serve_poll_body(vr_server *s, int64_t *tickets, vr_request_result *results, int cap, int *n,
+                             int wait_ms);
 extern "C" int vr_serve_poll(vr_server *s, int64_t *tickets, vr_request_result *results, int cap, int *n,
+                             int wait_ms) {
+    return abi_guard([&] { return vr_serve_poll_body(s, tickets, results, cap, n, wait_ms); });
+}
+static int vr_serve_poll_body(vr_server *s, int64_t *tickets, vr_request_result *results, int cap, int *n,
                              int wait_ms) {
     if (!s || !n || (cap > 0 && (!tickets || !results))) return arg_fail("null argument");
     if (cap < 0 || wait_ms < 0 || wait_ms > 60000) return arg_fail("cap >= 0 and 0 <= wait_ms <= 60000");
@@ -445,7 +465,11 @@ extern "C" int vr_serve_poll(vr_server *s, int64_t *tickets, vr_request_result *
     return VR_OK;
 }
 
+static int vr_serve_close_body(vr_server *s, vr_serve_summary *sum);
 extern "C" int vr_serve_close(vr_server *s, vr_serve_summary *sum) {
+    return abi_guard([&] { return vr_serve_close_body(s, sum); });
+}
+static int vr_serve_close_body(vr_server *s, vr_serve_summary *sum) {
     if (!s) return arg_fail("null argument");
     {
         std::lock_guard<std::mutex> l(s->mu);
