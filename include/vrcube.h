@@ -518,7 +518,9 @@ int vr_serve(vr_ctx *ctx, const vr_request *reqs, int n, const vr_serve_config *
  * is ignored); vr_serve_poll returns finished requests; vr_serve_close waits for every submitted
  * request, stops the thread and frees the server.  Admission, concurrency and results are
  * those of vr_serve.  While a server is open its context's cubes must not be loaded, freed,
- * re-bricked or partitioned, and no other call may use the context. */
+ * re-bricked or partitioned, and no other call may use the context.  Should the loop stop on a
+ * host-side exception (e.g. host memory exhausted), it waits for its frames in flight, every
+ * request it holds finishes with VR_ERR_STATE, and later submissions return VR_ERR_STATE. */
 typedef struct vr_server vr_server;
 
 /* cfg->max_inflight frame slots (1..64).  *out: the server (owned by the library until

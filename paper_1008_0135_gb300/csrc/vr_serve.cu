@@ -150,6 +150,26 @@ struct ServeCore {
 
     double now() const { return ms_since(t0); }
 
+    // After a host-side exception in the loop: waits for the frames in flight (their streams and
+    // brick loads), then fails every request the loop still holds, queued or in a slot.
+    void abandon() {
+        for (auto &sl : slots) {
+            if (sl.loading && sl.load.valid()) sl.load.wait();
+            sl.loading = false;
+            if (sl.s) cudaStreamSynchronize(sl.s);
+            if (sl.req) {
+                Req *r = sl.req;
+                sl.req = nullptr;
+                --inflight;
+                finish(r, VR_ERR_STATE);
+            }
+        }
+        while (!queue.empty()) {
+            finish(queue.front(), VR_ERR_STATE);
+            queue.pop_front();
+        }
+    }
+
     void finish(Req *r, int status) {
         r->res.done_ms = now();
         r->res.latency_ms = r->res.done_ms - r->arrival_ms;
@@ -309,9 +329,44 @@ struct vr_server {
     int64_t next_ticket = 0;
     int64_t outstanding = 0;             // submitted, not yet finished
     bool closing = false;
+    bool broken = false;                 // the loop stopped on a host-side exception
+    std::string broken_what;
 
     void run() {
         cudaSetDevice(c->device);
+        try {
+            loop();
+        } catch (const std::exception &e) {
+            stop_after_error(e.what());
+        } catch (...) {
+            stop_after_error("unexpected host-side exception");
+        }
+    }
+
+    // The loop cannot go on: every request it holds or has not yet taken fails, waiters wake,
+    // and later submissions are refused.
+    void stop_after_error(const char *what) {
+        try {
+            core.abandon();
+        } catch (...) {
+        }
+        std::lock_guard<std::mutex> l(mu);
+        broken = true;
+        try {
+            broken_what = what;
+            while (!submitted.empty()) {
+                core.finish(submitted.front(), VR_ERR_STATE);
+                submitted.pop_front();
+            }
+            for (Req *r : core.finished) completed.push_back(r);
+        } catch (...) {
+        }
+        core.finished.clear();
+        outstanding = 0;
+        cv.notify_all();
+    }
+
+    void loop() {
         for (;;) {
             {
                 std::lock_guard<std::mutex> l(mu);
@@ -371,17 +426,25 @@ static int vr_serve_body(vr_ctx *c, const vr_request *reqs, int n, const vr_serv
         return rc;
     }
     int next = 0;
-    while (core.done < n) {
-        const double now = core.now();
-        while (next < n && rq[next].arrival_ms <= now) core.queue.push_back(&rq[next++]);
-        const bool progress = core.step();
-        core.finished.clear();
-        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    try {
+        while (core.done < n) {
+            const double now = core.now();
+            while (next < n && rq[next].arrival_ms <= now) core.queue.push_back(&rq[next++]);
+            const bool progress = core.step();
+            core.finished.clear();
+            if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    } catch (const std::exception &e) {
+        // no frame of this call may still write into the callers' outputs after it returns
+        rc = fail(VR_ERR_STATE, e.what());
+        core.abandon();
+        for (int i = next; i < n; ++i) core.finish(&rq[i], VR_ERR_STATE);
     }
     const double wall = core.now();
     core.close();
     for (int i = 0; i < n; ++i) res[i] = rq[i].res;
     core.summary(sum, wall);
+    if (rc != VR_OK) return rc;
     return core.failed ? VR_ERR_STATE : VR_OK;
 }
 
@@ -427,6 +490,7 @@ static int vr_serve_submit_body(vr_server *s, const vr_request *req, int64_t *ti
         Req *p = r.get();
         std::lock_guard<std::mutex> l(s->mu);
         if (s->closing) return fail(VR_ERR_STATE, "the server is closing");
+        if (s->broken) return fail(VR_ERR_STATE, "the server's loop stopped: " + s->broken_what);
         p->arrival_ms = s->core.now();
         p->ticket = s->next_ticket++;
         *ticket = p->ticket;
