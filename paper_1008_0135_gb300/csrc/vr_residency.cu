@@ -515,7 +515,12 @@ static void job_generate(const std::shared_ptr<BrickJob> &j, int i) {
     for (float v : j->slab_max) m = std::max(m, v);
     j->exp2 = region_exponent(m, j->cb->storage);
     j->left.store(j->nslab);
-    for (int k = 1; k < j->nslab; ++k) j->pool->submit([j, k] { job_encode(j, k); });
+    int k = 1;
+    try {
+        for (; k < j->nslab; ++k) j->pool->submit([j, k] { job_encode(j, k); });
+    } catch (...) {                    // no room to queue a task: encode the rest here
+        for (; k < j->nslab; ++k) job_encode(j, k);
+    }
     job_encode(j, 0);
 }
 
@@ -552,7 +557,12 @@ static std::shared_ptr<BrickJob> produce_brick(Workers *pool, Cube *cb, const Dr
         j->slab_max.assign(j->nslab, 0.0f);
     }
     j->left.store(j->nslab);
-    for (int i = 0; i < j->nslab; ++i) pool->submit([j, i] { job_generate(j, i); });
+    int i = 0;
+    try {
+        for (; i < j->nslab; ++i) pool->submit([j, i] { job_generate(j, i); });
+    } catch (...) {                    // no room to queue a task: generate the rest here
+        for (; i < j->nslab; ++i) job_generate(j, i);
+    }
     return j;
 }
 
