@@ -117,3 +117,51 @@ def test_gloo_ranks_composite_the_frame(counts, H, W):
     assert np.array_equal(local, ref)
     for r in range(world):
         assert np.array_equal(got[r], ref), r
+
+
+def _rank_stalls(rank, port, q):
+    """Rank 1 creates the exchange's groups, then never takes part in a frame; rank 0's
+    composite, with the groups' bounded wait, must fail instead of waiting for it."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import time
+    import torch.distributed as dist
+    from datetime import timedelta
+    from paper_1008_0135_gb300 import sortlast as S
+    dist.init_process_group("gloo", rank=rank, world_size=2, timeout=timedelta(seconds=60))
+    ex = S.TorchExchange((2,), None, timedelta(seconds=3))
+    if rank == 1:
+        time.sleep(12.0)                      # alive, but not in the exchange
+        q.put((1, "stalled", 0.0))
+        return
+    t0 = time.perf_counter()
+    try:
+        S.composite_frame(_subimage(0, 8, 4), (2,), 0, ex,
+                          lambda level, stack, row0, final, members: _over(stack))
+        q.put((0, "completed", time.perf_counter() - t0))
+    except Exception as e:                    # the collective's timeout
+        q.put((0, type(e).__name__, time.perf_counter() - t0))
+
+
+def test_stalled_rank_ends_the_others_exchange_within_its_timeout():
+    """Failure detection on the host: a rank that stops taking part (alive, holding no GPU work)
+    makes the other rank's collective fail after the exchange's timeout, not hang."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_stalls, args=(r, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = {}
+    for _ in procs:
+        r, what, t = q.get(timeout=120)
+        got[r] = (what, t)
+    for p in procs:
+        p.join(timeout=60)
+        if p.is_alive():
+            p.kill()
+    what, t = got[0]
+    assert what != "completed", "the exchange completed without its peer"
+    assert t < 11.0, f"the failure took {t:.1f} s (timeout 3 s)"
+    assert got[1][0] == "stalled"
