@@ -790,7 +790,7 @@ def run_ours(args, dist):
     cid = ctx.load_cube(cube)
     load_s = time.perf_counter() - t_setup
     cube_np = None
-    if dist.rank == 0 and not args.no_extras:
+    if dist.world == 1 and not args.no_extras:
         cube_np = cube.cpu().numpy()
     del cube
     torch.cuda.empty_cache()
@@ -884,7 +884,9 @@ def run_ours(args, dist):
                       "ms_per_frame": round(1e3 * e2e_s / args.steps, 4),
                       "loop": "table + camera set, frame queued with an asynchronous copy into "
                               "one of two pinned host frames, previous frame read"}
-        if dist.rank == 0:
+        if dist.world == 1:
+            # the one-GPU legs (and the CPU baseline) run in the N = 1 line only: a scaling run's
+            # other GPUs are not held while they run
             res["sortlast_projection"] = sortlast_projection_leg(ctx, cid, cfg, cams, lut, vr)
             res["adjoint"] = adjoint_leg(ctx, device)
             res["serving"] = serving_leg(ctx, cid, device)
