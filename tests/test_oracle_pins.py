@@ -276,6 +276,55 @@ def _brute(cube, lut, vrange, o, d, k0, k1, step, tau, seg_of=None):
     return np.array([*C, 1 - T])
 
 
+@pytest.mark.parametrize("step,brick", [(2.3, (2, 3, 2)), (5.0, (1, 2, 3)), (3.7, (3, 3, 3))])
+def test_long_steps_closed_form_and_bricking(orc, step, brick):
+    """Steps longer than a brick (most bricks take no sample of a ray, some take one): the
+    constant cube still gives 1 - (1 - a)^n with n the lattice points in [t0, t1), unbricked and
+    bricked alike (no early termination); the brute-force sum over owned segments agrees on a
+    random cube with early termination."""
+    rng = np.random.default_rng(int(step * 10))
+    shape = (9, 7, 11)
+    cube = synth.constant_cube(shape, 0.7)
+    lut = synth.constant_lut([0.3, 0.6, 0.9, 0.13])
+    rgba = lut[0].astype(np.float64)
+    cam = synth.random_camera(rng, shape, 20, 18)
+    out, _, _ = orc.render(cube, lut, (0, 1), cam, step=step, tau=1.0)
+    outb, _, _ = orc.render(cube, lut, (0, 1), cam, step=step, tau=1.0, brick=brick)
+    assert np.allclose(outb, out, atol=1e-12)
+    o, d, _ = orc.rays(cam, shape, step=step)
+    st = float(np.float32(step))                  # the lattice spacing the library is given
+    checked = 0
+    for p in range(20 * 18):
+        tt = _slab64(o[p].astype(np.float64), d[p].astype(np.float64), shape)
+        if tt is None:
+            n = 0
+        else:
+            t0, t1 = tt
+            if min(abs(t0 / st - round(t0 / st)), abs(t1 / st - round(t1 / st))) < 1e-3:
+                continue
+            n = max(0, math.ceil(t1 / st) - math.ceil(t0 / st))
+        A = 1 - (1 - rgba[3]) ** n
+        assert abs(out[p, 3] - A) < 1e-12
+        checked += 1
+    assert checked > 250
+    # random values, bricked with early termination, against the brute-force sum
+    nx, ny, nz = shape
+    cube = rng.uniform(-1, 3, (nz, ny, nx)).astype(np.float32)
+    lut = synth.random_lut(7, n=24, alpha_max=0.8)
+    out, flags, _ = orc.render(cube, lut, (-1, 3), cam, step=step, tau=0.7, brick=brick)
+    o, d, k = orc.rays(cam, shape, step=step)
+    for p in range(0, 20 * 18, 3):
+        seg = None
+        if k[p, 1] > k[p, 0]:
+            seg = [tuple(r) for r in orc.sample_owners(shape, cam, p, step, brick)]
+        # the library's step is a binary32 parameter: 2.3 and 3.7 are not exact
+        ref = _brute(cube, lut, (-1, 3), o[p], d[p], k[p, 0], k[p, 1], float(np.float32(step)), 0.7, seg)
+        if flags[p] & 1:
+            assert np.all(np.abs(out[p] - ref) <= 0.3 + 1e-9)
+        else:
+            assert np.allclose(out[p], ref, atol=1e-12), (p, out[p], ref)
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_bruteforce_tiny_cubes(orc, seed):
     rng = np.random.default_rng(100 + seed)
