@@ -344,7 +344,7 @@ def test_bruteforce_tiny_cubes(orc, seed):
             if b is not None and k[p, 1] > k[p, 0]:
                 own = orc.sample_owners(shape, cam, p, step, b)
                 seg = [tuple(r) for r in own]
-            ref = _brute(cube, lut, (-1, 3), o[p], d[p], k[p, 0], k[p, 1], step, tau, seg)
+            ref = _brute(cube, lut, (-1, 3), o[p], d[p], k[p, 0], k[p, 1], float(np.float32(step)), tau, seg)
             if flags[p] & 1:
                 assert np.all(np.abs(out[p] - ref) <= (1 - tau) + 1e-9)
             else:
